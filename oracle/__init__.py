@@ -1,0 +1,182 @@
+"""CPU oracle for the order-statistics cone-hash search (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path never does: it shares
+no code with the C source here (``osann_oracle.c``), which is compiled with
+gcc into ``oracle/_build/libosann_oracle.so`` by :func:`build`.
+
+The wrappers below only marshal numpy arrays; every step of the method is in
+the C file, which cites the paper section each function follows.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "osann_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libosann_oracle.so")
+_lib = None
+
+_f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+_u32p = np.ctypeslib.ndpointer(np.uint32, flags="C_CONTIGUOUS")
+_i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags: it runs on x86 and Arm)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
+                           "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        c = ctypes
+        L.oracle_binom.restype = c.c_uint64
+        L.oracle_binom.argtypes = [c.c_int64, c.c_int64]
+        L.oracle_num_cones.restype = c.c_int64
+        L.oracle_num_cones.argtypes = [c.c_int, c.c_int]
+        L.oracle_magnitude_order.restype = None
+        L.oracle_magnitude_order.argtypes = [_f32p, c.c_int, _i32p]
+        L.oracle_key.restype = c.c_uint32
+        L.oracle_key.argtypes = [_f32p, c.c_int, c.c_int]
+        L.oracle_keys.restype = None
+        L.oracle_keys.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _u32p]
+        L.oracle_buckets.restype = None
+        L.oracle_buckets.argtypes = [_u32p, c.c_int64, c.c_int64, _u32p, _u32p]
+        L.oracle_probes.restype = c.c_int64
+        L.oracle_probes.argtypes = [_f32p, c.c_int, c.c_int, c.c_int64, _u32p]
+        L.oracle_search.restype = None
+        L.oracle_search.argtypes = [
+            _f32p, c.c_int64, c.c_int, c.c_int, _u32p, _u32p, _f32p, c.c_int64,
+            c.c_int64, c.c_int, c.c_void_p, c.c_int64, c.c_int64, _i64p, _f64p,
+            c.c_void_p]
+        L.oracle_bruteforce.restype = None
+        L.oracle_bruteforce.argtypes = [
+            _f32p, c.c_int64, c.c_int, _f32p, c.c_int64, c.c_int, c.c_void_p,
+            c.c_int64, c.c_int64, _i64p, _f64p]
+        L.oracle_pair_dists.restype = None
+        L.oracle_pair_dists.argtypes = [_f32p, c.c_int, _f32p, c.c_int64,
+                                        c.c_int, _i64p, _f64p]
+        _lib = L
+    return _lib
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def binom(n: int, k: int) -> int:
+    return int(lib().oracle_binom(n, k))
+
+
+def num_cones(d: int, L: int) -> int:
+    return int(lib().oracle_num_cones(d, L))
+
+
+def magnitude_order(y) -> np.ndarray:
+    y = _f32(y)
+    out = np.empty(y.shape[-1], np.int32)
+    lib().oracle_magnitude_order(y, y.shape[-1], out)
+    return out
+
+
+def key(x, L: int) -> int:
+    x = _f32(x)
+    return int(lib().oracle_key(x, x.shape[-1], L))
+
+
+def keys(X, L: int) -> np.ndarray:
+    X = _f32(X)
+    N, d = X.shape
+    out = np.empty(N, np.uint32)
+    lib().oracle_keys(X, N, d, L, out)
+    return out
+
+
+def buckets(k: np.ndarray, NC: int):
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    offsets = np.empty(NC + 1, np.uint32)
+    perm = np.empty(k.shape[0], np.uint32)
+    lib().oracle_buckets(k, k.shape[0], NC, offsets, perm)
+    return offsets, perm
+
+
+def probes(y, L: int, P: int) -> np.ndarray:
+    y = _f32(y)
+    out = np.empty(max(P, 1), np.uint32)
+    n = lib().oracle_probes(y, y.shape[-1], L, P, out)
+    return out[:n].copy()
+
+
+def _src_ptr(query_src):
+    if query_src is None:
+        return None, None
+    arr = np.ascontiguousarray(query_src, dtype=np.int64)
+    return arr, arr.ctypes.data_as(ctypes.c_void_p)
+
+
+class Index:
+    """Oracle index: keys, stable counting sort into cone buckets."""
+
+    def __init__(self, X, L: int):
+        self.X = _f32(X)
+        self.N, self.d = self.X.shape
+        self.L = L
+        self.NC = num_cones(self.d, L)
+        if self.NC < 0:
+            raise ValueError("N_C does not fit")
+        self.keys = keys(self.X, L)
+        self.offsets, self.perm = buckets(self.keys, self.NC)
+
+    def search(self, Y, P: int, k: int, query_src=None, grid_w: int = 0,
+               radius: int = 0, want_counts: bool = False):
+        Y = _f32(Y)
+        Q = Y.shape[0]
+        ids = np.empty(Q * k, np.int64)
+        dists = np.empty(Q * k, np.float64)
+        counts = np.empty(Q, np.int64) if want_counts else None
+        keep, src = _src_ptr(query_src)
+        lib().oracle_search(
+            self.X, self.N, self.d, self.L, self.offsets, self.perm, Y, Q, P, k,
+            src, grid_w, radius, ids, dists,
+            counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+        del keep
+        ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
+        return (ids, dists, counts) if want_counts else (ids, dists)
+
+
+def bruteforce(X, Y, k: int, query_src=None, grid_w: int = 0, radius: int = 0):
+    X, Y = _f32(X), _f32(Y)
+    N, d = X.shape
+    Q = Y.shape[0]
+    ids = np.empty(Q * k, np.int64)
+    dists = np.empty(Q * k, np.float64)
+    keep, src = _src_ptr(query_src)
+    lib().oracle_bruteforce(X, N, d, Y, Q, k, src, grid_w, radius, ids, dists)
+    del keep
+    return ids.reshape(Q, k), dists.reshape(Q, k)
+
+
+def pair_dists(X, Y, ids) -> np.ndarray:
+    X, Y = _f32(X), _f32(Y)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    Q, k = ids.shape
+    out = np.empty(Q * k, np.float64)
+    lib().oracle_pair_dists(X, X.shape[1], Y, Q, k, ids.reshape(-1), out)
+    return out.reshape(Q, k)

@@ -1,0 +1,360 @@
+/*
+ * osann_oracle.c -- plain, slow, single-threaded CPU oracle for the
+ * order-statistics cone-hash ANN search of Verdoliva, Cozzolino and Poggi,
+ * "A reliable order-statistics-based approximate nearest neighbor search
+ * algorithm" (ROSANNA), restricted to one basis (R = 1).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load this library.  The product path
+ * (the CUDA library under paper_1509_03453_gb300/csrc) shares no code,
+ * header, table or helper with this file, and never calls it.
+ *
+ * Every function follows the paper's steps in the paper's order and notation
+ * (K = vector length, called d here; G = components used, called L here;
+ * C = cones visited, called P here).  Distances are accumulated in double
+ * precision.  No blocking, fusion or reordering is done beyond what the
+ * definitions state.
+ *
+ * Readings of the paper that this file fixes (the paper is silent on them):
+ *   - ties between equal magnitudes go to the lower component index;
+ *   - profiles (unordered G-subsets) are numbered in colexicographic order,
+ *     rank(S) = sum_j C(s_j, j+1) with s_0 < s_1 < ...;
+ *   - the sign code of a cone puts the lowest component index in the most
+ *     significant bit and counts zero (and -0.0) as positive (Fig. 2);
+ *   - cone id = rank(S) * 2^G + sign code;
+ *   - within one profile distance class the probe order is the lexicographic
+ *     order of the substituted rank tuple; each probed profile contributes the
+ *     cone carrying the query's own signs; after all C(K,G) profiles the
+ *     sign-flipped cones follow (h flips ascending, profile order, flip
+ *     subsets lexicographic over the members sorted by |y| ascending).
+ * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
+ * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
+ * The intra-class probe order and the sign-flip extension are this
+ * project's specification: parity unpinned by the paper for those two parts.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORACLE_MAX_D 1024
+#define ORACLE_MAX_L 32
+
+/* Binomial coefficient C(n, k), exact, saturating at UINT64_MAX.  Plain
+ * multiplicative formula; every intermediate quotient is an integer. */
+uint64_t oracle_binom(int64_t n, int64_t k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    unsigned __int128 r = 1;
+    for (int64_t i = 1; i <= k; ++i) {
+        r = r * (unsigned __int128)(n - k + i) / (unsigned __int128)i;
+        if (r > (unsigned __int128)UINT64_MAX) return UINT64_MAX;
+    }
+    return (uint64_t)r;
+}
+
+/* Number of cones N_C = C(K, G) * 2^G (Sec. 2, Table I).  -1 if it does not
+ * fit in 63 bits. */
+int64_t oracle_num_cones(int d, int L)
+{
+    if (d < 1 || L < 1 || L > d || L > 62) return -1;
+    uint64_t c = oracle_binom(d, L);
+    if (c == UINT64_MAX || c > ((uint64_t)INT64_MAX >> L)) return -1;
+    return (int64_t)(c << L);
+}
+
+/* Indices of the components of y sorted by decreasing magnitude,
+ * i_1, i_2, ..., i_K of Sec. 3-B.  Selection sort: at each position take the
+ * not-yet-used index with the largest |y|, the lowest index on ties. */
+void oracle_magnitude_order(const float *y, int d, int32_t *order)
+{
+    unsigned char used[ORACLE_MAX_D];
+    memset(used, 0, (size_t)d);
+    for (int pos = 0; pos < d; ++pos) {
+        int best = -1;
+        for (int j = 0; j < d; ++j) {
+            if (used[j]) continue;
+            if (best < 0 || fabsf(y[j]) > fabsf(y[best])) best = j;
+        }
+        used[best] = 1;
+        order[pos] = best;
+    }
+}
+
+/* Cone id of the profile S (G distinct component indices, any order) with the
+ * signs of y on its members, optionally with the members listed in
+ * flip_mask (bit m set = flip the sign of the member whose position in the
+ * ascending-|y| ordering of S is m) sign-inverted. */
+static uint32_t cone_of_profile(const int32_t *S_in, int L, const float *y,
+                                const int32_t *rank_of, uint32_t flip_mask)
+{
+    int32_t s[ORACLE_MAX_L];
+    memcpy(s, S_in, sizeof(int32_t) * (size_t)L);
+    /* sort S by component index, ascending (insertion sort) */
+    for (int a = 1; a < L; ++a) {
+        int32_t v = s[a];
+        int b = a - 1;
+        while (b >= 0 && s[b] > v) { s[b + 1] = s[b]; --b; }
+        s[b + 1] = v;
+    }
+    uint64_t rank = 0;
+    for (int j = 0; j < L; ++j) rank += oracle_binom(s[j], j + 1);
+    uint32_t code = 0;
+    for (int j = 0; j < L; ++j) {
+        uint32_t bit = (y[s[j]] >= 0.0f) ? 1u : 0u;
+        if (flip_mask) {
+            /* position of s[j] in S sorted by |y| ascending = number of members
+             * with a larger rank (smaller magnitude) than s[j] */
+            int pos = 0;
+            for (int t = 0; t < L; ++t)
+                if (rank_of[s[t]] > rank_of[s[j]]) ++pos;
+            if ((flip_mask >> pos) & 1u) bit ^= 1u;
+        }
+        code |= bit << (L - 1 - j);
+    }
+    return (uint32_t)((rank << L) | code);
+}
+
+/* Cone id of one vector (Sec. 2): profile = the G largest-magnitude
+ * components (as an unordered set), cone = profile plus their signs. */
+uint32_t oracle_key(const float *x, int d, int L)
+{
+    int32_t order[ORACLE_MAX_D];
+    oracle_magnitude_order(x, d, order);
+    return cone_of_profile(order, L, x, NULL, 0);
+}
+
+void oracle_keys(const float *X, int64_t N, int d, int L, uint32_t *keys)
+{
+    for (int64_t n = 0; n < N; ++n) keys[n] = oracle_key(X + n * d, d, L);
+}
+
+/* Bucket index: offsets[N_C + 1] (exclusive prefix sum of the cone counts)
+ * and perm[N] (point ids, ascending inside each cone: a stable counting
+ * sort).  The paper only says that one hash table per basis maps cones to
+ * points (Sec. 4, preparation phase). */
+void oracle_buckets(const uint32_t *keys, int64_t N, int64_t NC,
+                    uint32_t *offsets, uint32_t *perm)
+{
+    for (int64_t c = 0; c <= NC; ++c) offsets[c] = 0;
+    for (int64_t n = 0; n < N; ++n) offsets[keys[n] + 1] += 1;
+    for (int64_t c = 0; c < NC; ++c) offsets[c + 1] += offsets[c];
+    uint32_t *cursor = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(NC + 1));
+    memcpy(cursor, offsets, sizeof(uint32_t) * (size_t)(NC + 1));
+    for (int64_t n = 0; n < N; ++n) perm[cursor[keys[n]]++] = (uint32_t)n;
+    free(cursor);
+}
+
+/* Advance comb[0..m-1] (strictly increasing values in [lo, hi]) to the next
+ * combination in lexicographic order.  Returns 0 when exhausted. */
+static int next_combination(int32_t *comb, int m, int lo, int hi)
+{
+    (void)lo;
+    int i = m - 1;
+    while (i >= 0 && comb[i] == hi - (m - 1 - i)) --i;
+    if (i < 0) return 0;
+    comb[i] += 1;
+    for (int j = i + 1; j < m; ++j) comb[j] = comb[j - 1] + 1;
+    return 1;
+}
+
+/* Enumerate the level-G profiles in the paper's neighbouring-cone order
+ * (Sec. 3-B): distance delta = G - (level of the closest common ancestor
+ * with the query's profile) ascending; the profiles at distance delta keep
+ * the query's top G-delta components and take the other delta members from
+ * the ranks G-delta+2 .. K (rank G-delta+1 excluded, otherwise the common
+ * ancestor would be deeper); inside a class, lexicographic in those ranks.
+ * Calls emit(S) for each profile until it returns nonzero.  Ranks are
+ * 1-based in the paper; positions into order[] here are 0-based. */
+typedef int (*profile_cb)(const int32_t *S, void *ctx);
+
+static void enumerate_profiles(const int32_t *order, int d, int L,
+                               profile_cb emit, void *ctx)
+{
+    int32_t S[ORACLE_MAX_L];
+    int32_t T[ORACLE_MAX_L];
+    for (int delta = 0; delta <= L; ++delta) {
+        int keep = L - delta;
+        for (int j = 0; j < keep; ++j) S[j] = order[j];
+        if (delta == 0) {
+            if (emit(S, ctx)) return;
+            continue;
+        }
+        /* 0-based positions keep+1 .. d-1 (rank keep+1 is position keep) */
+        int lo = keep + 1, hi = d - 1;
+        if (hi - lo + 1 < delta) continue;
+        for (int j = 0; j < delta; ++j) T[j] = lo + j;
+        do {
+            for (int j = 0; j < delta; ++j) S[keep + j] = order[T[j]];
+            if (emit(S, ctx)) return;
+        } while (next_combination(T, delta, lo, hi));
+    }
+}
+
+struct probe_ctx {
+    const float *y;
+    const int32_t *rank_of;
+    int L;
+    int64_t P, count;
+    uint32_t *out;
+    uint32_t flip_mask; /* 0 in the first sweep */
+    int h;              /* flips per cone in the current sweep */
+    int32_t F[ORACLE_MAX_L];
+};
+
+static int emit_unflipped(const int32_t *S, void *vctx)
+{
+    struct probe_ctx *c = (struct probe_ctx *)vctx;
+    if (c->count >= c->P) return 1;
+    c->out[c->count++] = cone_of_profile(S, c->L, c->y, c->rank_of, 0);
+    return c->count >= c->P;
+}
+
+static int emit_flipped(const int32_t *S, void *vctx)
+{
+    struct probe_ctx *c = (struct probe_ctx *)vctx;
+    int32_t F[ORACLE_MAX_L];
+    for (int j = 0; j < c->h; ++j) F[j] = j;
+    do {
+        if (c->count >= c->P) return 1;
+        uint32_t mask = 0;
+        for (int j = 0; j < c->h; ++j) mask |= 1u << F[j];
+        c->out[c->count++] = cone_of_profile(S, c->L, c->y, c->rank_of, mask);
+    } while (next_combination(F, c->h, 0, c->L - 1));
+    return c->count >= c->P;
+}
+
+/* Ordered list of cones to visit for query y (Algorithm 1, "find ordered
+ * list of cones"), truncated at P entries.  Returns the number written,
+ * min(P, N_C). */
+int64_t oracle_probes(const float *y, int d, int L, int64_t P, uint32_t *out)
+{
+    int32_t order[ORACLE_MAX_D], rank_of[ORACLE_MAX_D];
+    oracle_magnitude_order(y, d, order);
+    for (int r = 0; r < d; ++r) rank_of[order[r]] = r;
+    struct probe_ctx c;
+    c.y = y; c.rank_of = rank_of; c.L = L; c.P = P; c.count = 0; c.out = out;
+    c.flip_mask = 0; c.h = 0;
+    enumerate_profiles(order, d, L, emit_unflipped, &c);
+    for (int h = 1; h <= L && c.count < P; ++h) {
+        c.h = h;
+        enumerate_profiles(order, d, L, emit_flipped, &c);
+    }
+    return c.count;
+}
+
+/* Candidate exclusion used by the patch workload: data id n sits at grid
+ * position (n / grid_w, n % grid_w); it is skipped for a query taken from
+ * grid id src when the Chebyshev distance is <= radius. */
+static int excluded(int64_t n, int64_t src, int64_t grid_w, int64_t radius)
+{
+    if (src < 0 || grid_w <= 0) return 0;
+    int64_t dr = n / grid_w - src / grid_w;
+    int64_t dc = n % grid_w - src % grid_w;
+    if (dr < 0) dr = -dr;
+    if (dc < 0) dc = -dc;
+    return (dr > dc ? dr : dc) <= radius;
+}
+
+/* Squared Euclidean distance in double precision (Eq. 1). */
+static double sqdist(const float *x, const float *y, int d)
+{
+    double s = 0.0;
+    for (int i = 0; i < d; ++i) {
+        double t = (double)x[i] - (double)y[i];
+        s += t * t;
+    }
+    return s;
+}
+
+/* Keep the k best (distance, id) pairs, ascending by distance then id. */
+static void topk_insert(double *bd, int64_t *bi, int k, double dist, int64_t id)
+{
+    if (dist > bd[k - 1] || (dist == bd[k - 1] && id >= bi[k - 1])) return;
+    int j = k - 1;
+    while (j > 0 && (bd[j - 1] > dist || (bd[j - 1] == dist && bi[j - 1] > id))) {
+        bd[j] = bd[j - 1];
+        bi[j] = bi[j - 1];
+        --j;
+    }
+    bd[j] = dist;
+    bi[j] = id;
+}
+
+static void topk_init(double *bd, int64_t *bi, int k)
+{
+    for (int j = 0; j < k; ++j) { bd[j] = INFINITY; bi[j] = -1; }
+}
+
+/* ROSANNA search with one basis (Algorithm 1 with R = 1): hash the query,
+ * build its ordered cone list, and scan the cones' points in that order with
+ * exact distances, keeping the k nearest.  With R = 1 the visited cones are
+ * disjoint, so the "analyzed" flag of Algorithm 1 never fires and partial
+ * distance elimination only skips work, never changes the result; both are
+ * left out.  query_src may be NULL (no exclusion).  Outputs ids[Q*k] (-1 pad)
+ * and dists[Q*k] (+inf pad), squared distances.  probe_buf must hold P
+ * entries.  cand_count (may be NULL) receives the number of candidates
+ * scanned per query. */
+void oracle_search(const float *X, int64_t N, int d, int L,
+                   const uint32_t *offsets, const uint32_t *perm,
+                   const float *Y, int64_t Q, int64_t P, int k,
+                   const int64_t *query_src, int64_t grid_w, int64_t radius,
+                   int64_t *ids, double *dists, int64_t *cand_count)
+{
+    (void)N;
+    int64_t NC = oracle_num_cones(d, L);
+    if (P > NC) P = NC;
+    uint32_t *probes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(P > 0 ? P : 1));
+    for (int64_t q = 0; q < Q; ++q) {
+        const float *y = Y + q * d;
+        double *bd = dists + q * k;
+        int64_t *bi = ids + q * k;
+        topk_init(bd, bi, k);
+        int64_t np = oracle_probes(y, d, L, P, probes);
+        int64_t cands = 0;
+        int64_t src = query_src ? query_src[q] : -1;
+        for (int64_t l = 0; l < np; ++l) {
+            uint32_t c = probes[l];
+            for (uint32_t r = offsets[c]; r < offsets[c + 1]; ++r) {
+                int64_t n = perm[r];
+                if (excluded(n, src, grid_w, radius)) continue;
+                ++cands;
+                topk_insert(bd, bi, k, sqdist(X + n * d, y, d), n);
+            }
+        }
+        if (cand_count) cand_count[q] = cands;
+    }
+    free(probes);
+}
+
+/* Exact linear search (Eq. 1): the k nearest of all N points. */
+void oracle_bruteforce(const float *X, int64_t N, int d, const float *Y,
+                       int64_t Q, int k, const int64_t *query_src,
+                       int64_t grid_w, int64_t radius, int64_t *ids,
+                       double *dists)
+{
+    for (int64_t q = 0; q < Q; ++q) {
+        const float *y = Y + q * d;
+        double *bd = dists + q * k;
+        int64_t *bi = ids + q * k;
+        topk_init(bd, bi, k);
+        int64_t src = query_src ? query_src[q] : -1;
+        for (int64_t n = 0; n < N; ++n) {
+            if (excluded(n, src, grid_w, radius)) continue;
+            topk_insert(bd, bi, k, sqdist(X + n * d, y, d), n);
+        }
+    }
+}
+
+/* Exact squared distance of given (query, id) pairs, for checking returned
+ * distances element by element.  ids < 0 give +inf. */
+void oracle_pair_dists(const float *X, int d, const float *Y, int64_t Q,
+                       int k, const int64_t *ids, double *out)
+{
+    for (int64_t q = 0; q < Q; ++q)
+        for (int j = 0; j < k; ++j) {
+            int64_t n = ids[q * k + j];
+            out[q * k + j] = n < 0 ? INFINITY : sqdist(X + n * d, Y + q * d, d);
+        }
+}
