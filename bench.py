@@ -1,0 +1,412 @@
+"""Benchmark: queries/s at recall@1 >= 0.9 of the cone-hash search on GB300.
+
+Workload (the scale-up Gaussian case): N = 1,000,000 data and Q = 10,000
+query vectors, d = 32, iid N(0,1) (seeds 1002 / 2002, +rank under torchrun),
+key depth L = 2, k = 1.  The probe budget P is the smallest of a fixed
+ladder whose recall@1 against exact linear search reaches 0.9.
+
+One step = the whole path over one batch: build the index of the N points
+(cone keys, histogram + scan, stable sort, permuted copy) and search the Q
+queries (query order, probe lists, cone-major work list, tile scan, merge).
+`value` = Q / device time of a step (CUDA events on the stream, inputs
+resident in HBM, L2 flushed by a 256 MiB write before every step);
+`e2e` = the same through host buffers (pinned H2D of X and Y, D2H of the
+results inside the timed region).
+
+--impl reference times the CPU oracle (the single-threaded plain program)
+on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_FULL, Q_FULL, D, L, K = 1_000_000, 10_000, 32, 2, 1
+P_LADDER = [64, 96, 128, 160, 192, 224, 256, 320, 384, 512]
+WORKLOAD = "gauss32: N=1,000,000 x d=32 data, Q=10,000 queries, iid N(0,1), L=2 (N_C=1984), k=1"
+METRIC = "queries/s at recall@1>=0.9"
+FP32_LANES_PER_SM = 128
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def gen(rank, n=N_FULL, q=Q_FULL):
+    from paper_1509_03453_gb300 import datagen
+    X = datagen.gaussian(n, D, 1002 + rank)
+    Y = datagen.gaussian(q, D, 2002 + rank)
+    return X, Y
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() in ("active", "1", "0x1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def recall1(ids, d2, gt_ids, gt_d2):
+    hit = ids[:, 0] == gt_ids[:, 0]
+    near = np.abs(d2[:, 0].astype(np.float64) - gt_d2[:, 0]) <= 1e-6 * gt_d2[:, 0]
+    return float(np.mean(hit | near))
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1509_03453_gb300 as osann
+    from paper_1509_03453_gb300 import build as libbuild
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if not libbuild.up_to_date() and rank == 0:
+        libbuild.build()
+    if ws > 1:
+        dist.barrier()
+    osann.load()
+
+    X, Y = gen(rank)
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    # ground truth (exact linear search on the GPU) and the probe budget
+    idx = osann.Index(Xd, L)
+    gt_ids, gt_d2 = (t.cpu().numpy() for t in idx.bruteforce(Yd, K))
+    P, rec = None, None
+    if args.P:
+        P = args.P
+        ids, d2 = idx.search(Yd, P, K)
+        rec = recall1(ids.cpu().numpy(), d2.cpu().numpy(), gt_ids, gt_d2)
+    else:
+        for cand in P_LADDER:
+            ids, d2 = idx.search(Yd, cand, K)
+            rec = recall1(ids.cpu().numpy(), d2.cpu().numpy(), gt_ids, gt_d2)
+            P = cand
+            if rec >= 0.9:
+                break
+    if ws > 1:
+        t = torch.tensor([P], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        P = int(t.item())
+    ws_bytes = idx.workspace_size(Q_FULL, P, K)
+    idx.close()
+    work = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    out_ids = torch.empty((Q_FULL, K), dtype=torch.int64, device=dev)
+    out_d2 = torch.empty((Q_FULL, K), dtype=torch.float32, device=dev)
+
+    def step(path="auto"):
+        ix = osann.Index(Xd, L)
+        ix.search(Yd, P, K, path=path, out=(out_ids, out_d2), workspace=work)
+        return ix
+
+    def timed(path, steps, warmup, with_stats=False):
+        times = []
+        for i in range(warmup + steps):
+            flush.zero_()
+            if with_stats and i == warmup:
+                osann.stats(enable=True, reset=True)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ix = step(path)
+            b.record(stream)
+            b.synchronize()
+            ix.close()
+            if i >= warmup:
+                times.append(a.elapsed_time(b))
+        st = osann.stats(enable=False) if with_stats else None
+        return times, st
+
+    # warm-up, then exactly `steps` timed steps bracketed by barrier + sync
+    for _ in range(args.warmup):
+        flush.zero_()
+        step().close()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = osann.launch_count()
+    t_wall0 = time.perf_counter()
+    times, stats = timed("auto", args.steps, 0, with_stats=True)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = osann.launch_count() - launches0
+    clocks = sampler.stop()
+    if ws > 1:
+        dist.barrier()
+    ms = sum(times) / len(times)
+    ms_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(ms_max, op=dist.ReduceOp.MAX)
+    ms_step = float(ms_max.item())
+    value = ws * Q_FULL / (ms_step / 1e3)
+
+    # plain per-query fp32 scan and exact linear search, same P, same clocking
+    plain_times, _ = timed("plain", max(3, args.steps // 2), 1)
+    bf_times = []
+    for i in range(3):
+        ix = osann.Index(Xd, L)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ix.bruteforce(Yd, K)
+        b.record(stream)
+        b.synchronize()
+        ix.close()
+        if i:
+            bf_times.append(a.elapsed_time(b))
+
+    # end to end through host buffers (pinned), copies inside the timed region
+    Xh = torch.from_numpy(X).pin_memory()
+    Yh = torch.from_numpy(Y).pin_memory()
+    ids_h = torch.empty((Q_FULL, K), dtype=torch.int64).pin_memory()
+    d2_h = torch.empty((Q_FULL, K), dtype=torch.float32).pin_memory()
+    e2e_times = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        xd = Xh.to(dev, non_blocking=True)
+        yd = Yh.to(dev, non_blocking=True)
+        ix = osann.Index(xd, L)
+        ix.search(yd, P, K, out=(out_ids, out_d2), workspace=work)
+        ids_h.copy_(out_ids, non_blocking=True)
+        d2_h.copy_(out_d2, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        ix.close()
+        if i >= args.warmup:
+            e2e_times.append(a.elapsed_time(b))
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(e2e_t.item())
+
+    # roofline of the dominant stage
+    peaks, peak_src = load_peaks()
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in stats.items() if v[1]}
+    stage_n = {k: v[1] / args.steps for k, v in stats.items() if v[1]}
+    dom = max(stats, key=lambda s: stats[s][0])
+    pairs = None
+    roof = None
+    # candidate pairs of the timed search (exact count from the probe lists)
+    ix = osann.Index(Xd, L)
+    off = ix.export()[1]
+    pr = ix.probes(Yd, P)
+    sizes = (off[1:] - off[:-1])
+    pairs = int(sizes[pr].sum().item())
+    ix.close()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    dom_ms = stage_ms[dom]
+    if dom in ("tile_scan", "plain_scan", "bruteforce"):
+        flops = 3.0 * D * pairs  # d subtractions, d squares, d additions per pair
+        peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} fp32 lanes x 2 (FMA) x "
+                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
+                "algorithmic": f"{pairs} (query, candidate) pairs x 3d flops per launch",
+                "avg_launch_ms": round(dom_ms, 4)}
+    else:
+        byts = 4.0 * N_FULL * D * 3
+        achieved = byts / (dom_ms / 1e3) / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} copy bandwidth",
+                "avg_launch_ms": round(dom_ms, 4)}
+
+    line = {
+        "metric": METRIC,
+        "value": round(value, 1),
+        "unit": "queries/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic (seeded iid N(0,1), generated on the host)",
+        "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P,
+                   "path": "auto (batched: cone-major work list + persistent tile scan)",
+                   "step": "index build + search of the Q queries",
+                   "l2": "flushed before every step by a 256 MiB device write (untimed)",
+                   "parallelism": f"replicas x{ws} (independent data per rank)"},
+        "recall_at_1": round(rec, 4),
+        "latency_ms": {"p50": round(float(np.percentile(times, 50)), 4),
+                       "p99": round(float(np.percentile(times, 99)), 4),
+                       "note": "per batch step of Q queries"},
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "stage_launches_per_step": stage_n,
+        "plain_fp32": {"value": round(Q_FULL / (np.mean(plain_times) / 1e3), 1), "unit": "queries/s",
+                       "ms_per_step": round(float(np.mean(plain_times)), 4)},
+        "bruteforce_fp32": {"value": round(Q_FULL / (np.mean(bf_times) / 1e3), 1), "unit": "queries/s",
+                            "ms_per_search": round(float(np.mean(bf_times)), 4), "recall_at_1": 1.0},
+        "e2e": {"value": round(ws * Q_FULL / (e2e_ms / 1e3), 1), "unit": "queries/s",
+                "ms_per_step": round(e2e_ms, 4),
+                "h2d_bytes_per_step": int(X.nbytes + Y.nbytes),
+                "d2h_bytes_per_step": int(out_ids.numel() * 8 + out_d2.numel() * 4)},
+        "roofline": roof,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+        "wall_s_timed": round(t_wall, 3),
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(P, budget_s=args.cpu_budget)
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(P, budget_s=15.0, rank=0):
+    """The oracle as it stands, single-threaded, on a bounded sample: the full
+    build of the N points plus a sample of the queries, scaled to a step of
+    the whole workload (build + Q queries)."""
+    import oracle
+    oracle.build()
+    X, Y = gen(rank)
+    t0 = time.perf_counter()
+    ref = oracle.Index(X, L)
+    t_build = time.perf_counter() - t0
+    n, t_search = 0, 0.0
+    chunk = 25
+    while t_search < max(1.0, budget_s - t_build) and n < Q_FULL:
+        t1 = time.perf_counter()
+        ref.search(Y[n:n + chunk], P, K)
+        t_search += time.perf_counter() - t1
+        n += chunk
+    t_step = t_build + t_search * Q_FULL / n
+    return {"value": round(Q_FULL / t_step, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle build of all {N_FULL} points ({t_build:.2f} s) + search of {n} of {Q_FULL} "
+                      f"queries at P={P} ({t_search:.2f} s), scaled to build + {Q_FULL} queries",
+            "P": P}
+
+
+def run_reference(args):
+    """CPU oracle arm: each step = oracle build + a bounded query sample."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    P = args.P or 256
+    X, Y = gen(0)
+    sample = 40
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        ref = oracle.Index(X, L)
+        tb = time.perf_counter() - t0
+        t1 = time.perf_counter()
+        s = (i * sample) % (Q_FULL - sample)
+        ref.search(Y[s:s + sample], P, K)
+        tq = time.perf_counter() - t1
+        if i >= args.warmup:
+            times.append(tb + tq * Q_FULL / sample)
+    t_step = float(np.mean(times))
+    value = Q_FULL / t_step
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded iid N(0,1))",
+            "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P},
+            "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
+                             "sample": f"per step: oracle build of all {N_FULL} points + {sample} queries at "
+                                       f"P={P}, scaled to {Q_FULL} queries"},
+            "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="osann", choices=["osann", "reference"])
+    ap.add_argument("--P", type=int, default=0, help="fixed probe budget (default: recall ladder)")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

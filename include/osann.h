@@ -1,0 +1,185 @@
+/*
+ * osann.h -- C ABI of libosann: order-statistics cone-hash approximate
+ * nearest-neighbour search (Verdoliva, Cozzolino, Poggi, "A reliable
+ * order-statistics-based approximate nearest neighbor search algorithm",
+ * ROSANNA) on one GB300 GPU (sm_103a), one basis (R = 1).
+ *
+ * Notation: the paper's K (vector length) is d, G (components used for the
+ * hash) is L, C (cones visited per basis) is P, N_C = C(d, L) * 2^L.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE pointers on the current CUDA device,
+ *     caller-owned, contiguous, row-major.  Float inputs must be 16-byte
+ *     aligned when d % 4 == 0 (vector loads), otherwise 4-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  All work is enqueued on it; only osann_build and
+ *     osann_status synchronise it.
+ *   - Return value: OSANN_OK (0) or a negative OSANN_ERR_* code;
+ *     osann_last_error() then gives a message (thread-local).  On error no
+ *     output is guaranteed to be written and no memory is leaked.
+ *   - Distances are squared Euclidean distances (Eq. 1) in fp32.  Results
+ *     per query are ordered by (distance, id) ascending; missing entries
+ *     (fewer than k candidates) are id -1, distance +inf.
+ */
+#ifndef OSANN_H
+#define OSANN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OSANN_OK 0
+#define OSANN_ERR_INVALID (-1)     /* bad argument (sizes, null pointers, ranges) */
+#define OSANN_ERR_UNSUPPORTED (-2) /* N_C or N beyond the 31-bit index space */
+#define OSANN_ERR_OOM (-3)         /* device allocation failed */
+#define OSANN_ERR_NONFINITE (-4)   /* NaN or Inf in the data */
+#define OSANN_ERR_CUDA (-5)        /* a CUDA call failed */
+#define OSANN_ERR_TIMEOUT (-6)     /* a bounded device wait gave up */
+
+/* Search paths (same results, different schedules). */
+#define OSANN_PATH_AUTO 0    /* batched when enough queries share a cone */
+#define OSANN_PATH_PLAIN 1   /* one CTA per query scanning its cones */
+#define OSANN_PATH_BATCHED 2 /* cone-major work list, persistent tile scan */
+
+/* Status flags returned by osann_status. */
+#define OSANN_STATUS_NONFINITE_DATA 1u
+#define OSANN_STATUS_NONFINITE_QUERY 2u
+#define OSANN_STATUS_TIMEOUT 4u
+
+typedef struct osann_index osann_index; /* opaque; owns its device buffers */
+
+/* Optional device allocator used for index buffers and for search
+ * workspaces that the caller does not provide.  alloc returns a device
+ * pointer (NULL on failure) usable in stream order on `stream`; free
+ * releases it in stream order.  Passing NULL functions restores the default
+ * (cudaMallocAsync / cudaFreeAsync).  Not thread-safe with concurrent
+ * builds. */
+typedef void *(*osann_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*osann_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int osann_set_allocator(osann_alloc_fn alloc, osann_free_fn free_fn, void *ctx);
+
+/* Number of cones N_C = C(d, L) * 2^L (Sec. 2, Table I).  Errors:
+ * INVALID for d < 1, L < 1, L > d; UNSUPPORTED if N_C >= 2^31. */
+int osann_num_cones(int32_t d, int32_t L, int64_t *nc);
+
+/* Cone id of each of n vectors (Sec. 2: profile = unordered set of the L
+ * largest-magnitude components, ties to the lower index; cone = profile
+ * plus their signs, zero counted positive).  key = rank(S) * 2^L + code with
+ * rank(S) = sum_j C(s_j, j+1) over the members in ascending order and
+ * code = sum_j [x_{s_j} >= 0] 2^(L-1-j).
+ * d_vectors: n x d fp32.  d_keys: n uint32 (written).  1 <= d <= 256,
+ * 1 <= L <= min(d, 16).  Non-finite inputs are not reported here. */
+int osann_keys(const float *d_vectors, int64_t n, int32_t d, int32_t L, uint32_t *d_keys, void *stream);
+
+/* Magnitude order i_1..i_d of each query (Sec. 3-B): d_order[q*d + r] is the
+ * component with the (r+1)-th largest |y| (ties to the lower index), uint8.
+ * d_signs[q*8 + w] bit b is set when y[32w + b] >= 0 (8 words per query).
+ * 1 <= d <= 256. */
+int osann_query_order(const float *d_queries, int64_t Q, int32_t d, uint8_t *d_order, uint32_t *d_signs,
+                      void *stream);
+
+/* Build the index of one basis (Sec. 4, preparation phase; Table II):
+ * cone keys of all points, cone histogram and exclusive scan (CSR offsets),
+ * stable counting sort of point ids by cone, and the permuted fp32 copy of
+ * the vectors (zero padded to d_pad in {16, 32, 64, 128, 256}).
+ * d_data: N x d fp32, read only (the index keeps its own copy).
+ * Synchronises `stream` once.  Errors: INVALID (N < 1, d outside [1,256],
+ * L outside [1, min(d,16)], out == NULL), UNSUPPORTED (N >= 2^31 or
+ * N_C >= 2^31), NONFINITE (NaN/Inf in d_data), OOM, CUDA. */
+int osann_build(const float *d_data, int64_t N, int32_t d, int32_t L, void *stream, osann_index **out);
+
+/* Release an index.  NULL is accepted.  The caller must ensure that no
+ * work using the index is still pending on any stream. */
+int osann_free(osann_index *index);
+
+/* Sizes of an index.  Any output pointer may be NULL.  max_bucket is the
+ * largest cone population. */
+int osann_info(const osann_index *index, int64_t *N, int32_t *d, int32_t *L, int64_t *NC, int64_t *max_bucket);
+
+/* Copy the index's bucket structure out (for verification): d_keys[N]
+ * (cone of each point, original order), d_offsets[N_C + 1], d_perm[N]
+ * (point ids, ascending inside each cone).  Any pointer may be NULL. */
+int osann_export(const osann_index *index, uint32_t *d_keys, uint32_t *d_offsets, uint32_t *d_perm, void *stream);
+
+/* Ordered list of cones to visit (Algorithm 1, "find ordered list of
+ * cones"; Sec. 3-B): d_probes[q * P_eff + p], P_eff = min(P, N_C).  Order:
+ * profile distance delta = L - (level of the closest common ancestor with
+ * the query's profile {i_1..i_L}) ascending; inside a class the substituted
+ * ranks in lexicographic order; each profile with the query's signs; then
+ * the sign-flipped cones (h flips ascending, profile order, flipped members
+ * as h-subsets of the members sorted by |y| ascending).  Needs a workspace of
+ * osann_search_workspace_size(index, Q, P, 1, OSANN_PATH_PLAIN) bytes
+ * (d_ws may be NULL: then it is allocated and released in stream order). */
+int osann_probes(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, uint32_t *d_probes,
+                 void *d_ws, size_t ws_bytes, void *stream);
+
+/* Workspace bytes that osann_search / osann_search_excl need for (Q, P, k)
+ * on `path`. */
+size_t osann_search_workspace_size(const osann_index *index, int64_t Q, int32_t P, int32_t k, int32_t path);
+
+/* ROSANNA search with one basis (Algorithm 1, R = 1): hash each query,
+ * visit its first P_eff = min(P, N_C) cones in the order of osann_probes and
+ * return the k nearest candidates by exact squared Euclidean distance
+ * (Eq. 1, fp32 direct differences), ordered by (distance, id).
+ * d_queries: Q x d fp32.  d_ids: Q x k int64 (point ids, -1 pad).
+ * d_sqdists: Q x k fp32 (+inf pad).  d_ws/ws_bytes: workspace of at least
+ * osann_search_workspace_size(...) bytes, 256-byte aligned (NULL: allocated
+ * and released in stream order).  1 <= k <= 32, P >= 1, Q >= 0.
+ * Asynchronous.  Non-finite queries set OSANN_STATUS_NONFINITE_QUERY (see
+ * osann_status); their results are unspecified but in range. */
+int osann_search(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k, int32_t path,
+                 void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists, void *stream);
+
+/* As osann_search, skipping for query q every point n whose grid position
+ * (n / grid_w, n % grid_w) is within Chebyshev distance `radius` of
+ * d_query_src[q]'s position (self and near-duplicates of an image patch).
+ * grid_w >= 1, radius >= 0; a negative source disables the filter for
+ * that query. */
+int osann_search_excl(const osann_index *index, const float *d_queries, const int64_t *d_query_src, int64_t Q,
+                      int32_t P, int32_t k, int64_t grid_w, int32_t radius, int32_t path, void *d_ws,
+                      size_t ws_bytes, int64_t *d_ids, float *d_sqdists, void *stream);
+
+/* Exact linear search (Eq. 1 over all N points of the index), fp32 direct
+ * differences, cuBLAS-free: the ground truth for recall.  d_query_src may
+ * be NULL (no exclusion).  Workspace: osann_bruteforce_workspace_size. */
+size_t osann_bruteforce_workspace_size(const osann_index *index, int64_t Q, int32_t k);
+int osann_bruteforce(const osann_index *index, const float *d_queries, const int64_t *d_query_src, int64_t Q,
+                     int32_t k, int64_t grid_w, int32_t radius, void *d_ws, size_t ws_bytes, int64_t *d_ids,
+                     float *d_sqdists, void *stream);
+
+/* Synchronise `stream`, return the index's device status flags
+ * (OSANN_STATUS_*) accumulated since the last call, and clear them. */
+int osann_status(const osann_index *index, void *stream, uint32_t *flags);
+
+/* Message of the last error on this thread ("" if none). */
+const char *osann_last_error(void);
+
+/* Instrumentation.  With stats enabled, every stage records CUDA events on
+ * its stream; osann_stats_get synchronises those events and returns the
+ * accumulated milliseconds and launch count of `stage` (OSANN_STAGE_*).
+ * osann_launch_count returns the number of kernels this library has
+ * launched in this process. */
+#define OSANN_STAGE_DATA_KEYS 0
+#define OSANN_STAGE_BUCKETS 1
+#define OSANN_STAGE_GATHER 2
+#define OSANN_STAGE_QUERY_ORDER 3
+#define OSANN_STAGE_PROBES 4
+#define OSANN_STAGE_WORKLIST 5
+#define OSANN_STAGE_TILE_SCAN 6
+#define OSANN_STAGE_MERGE 7
+#define OSANN_STAGE_PLAIN_SCAN 8
+#define OSANN_STAGE_BRUTEFORCE 9
+#define OSANN_NUM_STAGES 10
+int osann_stats_enable(int on);
+int osann_stats_reset(void);
+int osann_stats_get(int32_t stage, double *total_ms, int64_t *count);
+int64_t osann_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OSANN_H */

@@ -1,0 +1,196 @@
+"""osann: order-statistics cone-hash approximate nearest-neighbour search
+(ROSANNA, one basis) on GB300.
+
+Python face of libosann (include/osann.h).  torch supplies device memory and
+streams; every step of the search runs in the library's CUDA kernels.
+
+    idx = Index(data_cuda_f32, L)            # cone keys, buckets, permuted copy
+    ids, d2 = idx.search(queries, P, k)      # ordered probing, exact top-k
+    gt_ids, gt_d2 = idx.bruteforce(queries, k)
+"""
+from __future__ import annotations
+
+import ctypes
+
+from . import _lib
+from ._lib import OsannError, PATHS, STAGES, load
+
+__all__ = ["Index", "OsannError", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(t, name):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32 or t.dim() != 2:
+        raise TypeError(f"{name} must be a 2-D float32 tensor")
+    return t.contiguous()
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def num_cones(d: int, L: int) -> int:
+    out = ctypes.c_int64()
+    _lib.check(load().osann_num_cones(d, L, ctypes.byref(out)))
+    return out.value
+
+
+def keys(vectors, L: int, stream=None):
+    """Cone id (uint32 as int64 tensor) of every row."""
+    torch = _torch()
+    v = _dev_f32(vectors, "vectors")
+    out = torch.empty(v.shape[0], dtype=torch.int32, device=v.device)
+    _lib.check(load().osann_keys(_ptr(v), v.shape[0], v.shape[1], L, _ptr(out), _stream_ptr(stream)))
+    return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def query_order(queries, stream=None):
+    """(order uint8 [Q, d], sign words int64 [Q, 8])."""
+    torch = _torch()
+    q = _dev_f32(queries, "queries")
+    Q, d = q.shape
+    order = torch.empty((Q, d), dtype=torch.uint8, device=q.device)
+    signs = torch.empty((Q, 8), dtype=torch.int32, device=q.device)
+    _lib.check(load().osann_query_order(_ptr(q), Q, d, _ptr(order), _ptr(signs), _stream_ptr(stream)))
+    return order, signs.to(torch.int64) & 0xFFFFFFFF
+
+
+def stats(enable: bool | None = None, reset: bool = False) -> dict:
+    L = load()
+    if enable is not None:
+        L.osann_stats_enable(1 if enable else 0)
+    out = {}
+    for i, name in enumerate(STAGES):
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        L.osann_stats_get(i, ctypes.byref(ms), ctypes.byref(n))
+        out[name] = (ms.value, n.value)
+    if reset:
+        L.osann_stats_reset()
+    return out
+
+
+def launch_count() -> int:
+    return int(load().osann_launch_count())
+
+
+class Index:
+    """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
+
+    def __init__(self, data, L: int, stream=None):
+        torch = _torch()
+        x = _dev_f32(data, "data")
+        self.N, self.d = x.shape
+        self.L = L
+        self.device = x.device
+        h = ctypes.c_void_p()
+        with torch.cuda.device(x.device):
+            _lib.check(load().osann_build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
+        self._h = h
+        NC, mb = ctypes.c_int64(), ctypes.c_int64()
+        _lib.check(load().osann_info(h, None, None, None, ctypes.byref(NC), ctypes.byref(mb)))
+        self.NC, self.max_bucket = NC.value, mb.value
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_h", None):
+            load().osann_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- queries
+    def workspace_size(self, Q: int, P: int, k: int, path: str = "auto") -> int:
+        return int(load().osann_search_workspace_size(self._h, Q, P, k, PATHS[path]))
+
+    def search(self, queries, P: int, k: int, path: str = "auto", query_src=None, grid_w: int = 0,
+               radius: int = 0, stream=None, out=None, workspace=None):
+        """Top-k by exact squared distance over the first min(P, N_C)
+        probed cones.  Returns (ids int64 [Q,k], sqdists float32 [Q,k])."""
+        torch = _torch()
+        q = _dev_f32(queries, "queries")
+        Q = q.shape[0]
+        if q.shape[1] != self.d:
+            raise ValueError("query dimension differs from the index's")
+        if out is None:
+            ids = torch.empty((Q, k), dtype=torch.int64, device=q.device)
+            d2 = torch.empty((Q, k), dtype=torch.float32, device=q.device)
+        else:
+            ids, d2 = out
+        ws_bytes = self.workspace_size(Q, P, k, path)
+        ws = workspace if workspace is not None else torch.empty(ws_bytes, dtype=torch.uint8, device=q.device)
+        L = load()
+        if query_src is None:
+            rc = L.osann_search(self._h, _ptr(q), Q, P, k, PATHS[path], _ptr(ws), ws.numel(), _ptr(ids),
+                                _ptr(d2), _stream_ptr(stream))
+        else:
+            src = query_src.contiguous()
+            rc = L.osann_search_excl(self._h, _ptr(q), _ptr(src), Q, P, k, grid_w, radius, PATHS[path],
+                                     _ptr(ws), ws.numel(), _ptr(ids), _ptr(d2), _stream_ptr(stream))
+        _lib.check(rc)
+        return ids, d2
+
+    def bruteforce(self, queries, k: int, query_src=None, grid_w: int = 0, radius: int = 0, stream=None):
+        """Exact linear search over all N points (Eq. 1)."""
+        torch = _torch()
+        q = _dev_f32(queries, "queries")
+        Q = q.shape[0]
+        ids = torch.empty((Q, k), dtype=torch.int64, device=q.device)
+        d2 = torch.empty((Q, k), dtype=torch.float32, device=q.device)
+        L = load()
+        ws = torch.empty(int(L.osann_bruteforce_workspace_size(self._h, Q, k)), dtype=torch.uint8,
+                         device=q.device)
+        src = query_src.contiguous() if query_src is not None else None
+        _lib.check(L.osann_bruteforce(self._h, _ptr(q), _ptr(src), Q, k, grid_w, radius, _ptr(ws), ws.numel(),
+                                      _ptr(ids), _ptr(d2), _stream_ptr(stream)))
+        return ids, d2
+
+    def probes(self, queries, P: int, stream=None):
+        """Ordered cone ids visited per query: int64 [Q, min(P, N_C)]."""
+        torch = _torch()
+        q = _dev_f32(queries, "queries")
+        Q = q.shape[0]
+        P_eff = min(P, self.NC)
+        out = torch.empty((Q, P_eff), dtype=torch.int32, device=q.device)
+        ws = torch.empty(self.workspace_size(Q, P, 1, "plain"), dtype=torch.uint8, device=q.device)
+        _lib.check(load().osann_probes(self._h, _ptr(q), Q, P, _ptr(out), _ptr(ws), ws.numel(),
+                                       _stream_ptr(stream)))
+        return out.to(torch.int64) & 0xFFFFFFFF
+
+    def export(self, stream=None):
+        """(keys [N], offsets [N_C+1], perm [N]) as int64 tensors."""
+        torch = _torch()
+        k = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        o = torch.empty(self.NC + 1, dtype=torch.int32, device=self.device)
+        p = torch.empty(self.N, dtype=torch.int32, device=self.device)
+        _lib.check(load().osann_export(self._h, _ptr(k), _ptr(o), _ptr(p), _stream_ptr(stream)))
+        m = 0xFFFFFFFF
+        return k.to(torch.int64) & m, o.to(torch.int64) & m, p.to(torch.int64) & m
+
+    def status(self, stream=None) -> int:
+        """Synchronise and return (and clear) the device status flags."""
+        f = ctypes.c_uint32()
+        _lib.check(load().osann_status(self._h, _stream_ptr(stream), ctypes.byref(f)))
+        return f.value

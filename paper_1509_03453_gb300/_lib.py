@@ -1,0 +1,95 @@
+"""ctypes view of libosann.so (the C ABI in include/osann.h).
+
+Argument marshalling only.  Loading fails loudly when the CUDA library has
+not been built: there is no CPU fallback anywhere in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c = ctypes
+_lib = None
+
+OK = 0
+ERRORS = {
+    -1: "invalid argument",
+    -2: "unsupported size",
+    -3: "out of device memory",
+    -4: "non-finite data",
+    -5: "CUDA error",
+    -6: "device wait timed out",
+}
+PATHS = {"auto": 0, "plain": 1, "batched": 2}
+STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
+          "plain_scan", "bruteforce"]
+STATUS_NONFINITE_DATA = 1
+STATUS_NONFINITE_QUERY = 2
+STATUS_TIMEOUT = 4
+
+# exported symbols and their signatures: (restype, argtypes)
+SIGNATURES = {
+    "osann_set_allocator": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_num_cones": (c.c_int, [c.c_int32, c.c_int32, c.POINTER(c.c_int64)]),
+    "osann_keys": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p]),
+    "osann_query_order": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_build": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p,
+                              c.POINTER(c.c_void_p)]),
+    "osann_free": (c.c_int, [c.c_void_p]),
+    "osann_info": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
+                             c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),
+    "osann_export": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_probes": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_void_p, c.c_void_p,
+                               c.c_size_t, c.c_void_p]),
+    "osann_search_workspace_size": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32]),
+    "osann_search": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_void_p,
+                               c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_search_excl": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32,
+                                    c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p,
+                                    c.c_void_p, c.c_void_p]),
+    "osann_bruteforce_workspace_size": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32]),
+    "osann_bruteforce": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int64,
+                                   c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_status": (c.c_int, [c.c_void_p, c.c_void_p, c.POINTER(c.c_uint32)]),
+    "osann_last_error": (c.c_char_p, []),
+    "osann_stats_enable": (c.c_int, [c.c_int]),
+    "osann_stats_reset": (c.c_int, []),
+    "osann_stats_get": (c.c_int, [c.c_int32, c.POINTER(c.c_double), c.POINTER(c.c_int64)]),
+    "osann_launch_count": (c.c_int64, []),
+}
+
+
+class OsannError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib_path() -> str:
+    return _build.LIB_PATH
+
+
+def load():
+    """Load libosann.so; raise if it has not been built."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"libosann.so not found at {path}: build it first "
+                "(python -c 'import __graft_entry__ as g; g.build()')")
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def check(rc: int):
+    if rc != OK:
+        msg = load().osann_last_error().decode(errors="replace")
+        raise OsannError(rc, msg)

@@ -1,0 +1,410 @@
+// Bucket index build: cone histogram, exclusive scan (CSR offsets), stable
+// counting sort of point ids by cone, and the gather of the permuted vectors.
+//
+// The paper keeps one hash table per basis mapping each cone to its points
+// (Sec. 4, preparation phase).  Here the table is a CSR layout:
+//   offsets[N_C + 1]  exclusive prefix sum of the cone counts,
+//   perm[N]           point ids, ascending inside every cone (stable order),
+//   xs[N x d_pad]     the vectors in perm order, fp32, zero padded,
+//   xb[N x d_pad]     the same in bf16 (tensor-core screening path),
+//   norm2[N]          fp32 squared norms of the xs rows.
+// Nothing here spins on another block: the scan is reduce-then-scan, the sort
+// is a least-significant-digit radix sort whose passes are stable by lane
+// rank inside each warp chunk and by chunk order across chunks.
+#include "osann_device.cuh"
+#include "osann_launch.h"
+
+namespace osann {
+
+constexpr int SCAN_THREADS = 256;
+constexpr int SCAN_ITEMS = 8;
+constexpr int SCAN_TILE = SCAN_THREADS * SCAN_ITEMS;
+
+// ---------------------------------------------------------------- scan
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_sums, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < SCAN_THREADS / 32 ? warp_sums[lane] : 0;
+        uint32_t s = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        if (lane < SCAN_THREADS / 32) warp_sums[lane] = s - w;
+        if (lane == SCAN_THREADS / 32 - 1) *total = s;
+    }
+    __syncthreads();
+    return x - v + warp_sums[warp];
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) scan_reduce_kernel(const uint32_t* __restrict__ in, int64_t n,
+                                                                   uint32_t* __restrict__ sums)
+{
+    __shared__ uint32_t ws[32];
+    const int64_t base = int64_t(blockIdx.x) * SCAN_TILE;
+    uint32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        int64_t j = base + i * SCAN_THREADS + threadIdx.x;
+        if (j < n) s += in[j];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < SCAN_THREADS / 32; ++w) t += ws[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of one tile per block, plus the block's offset (if any).
+// Safe in place: the whole tile is read before any of it is written.
+__global__ void __launch_bounds__(SCAN_THREADS) scan_tile_kernel(const uint32_t* in, uint32_t* out, int64_t n,
+                                                                 const uint32_t* __restrict__ block_off)
+{
+    __shared__ uint32_t tile[SCAN_TILE];
+    __shared__ uint32_t ws[32];
+    __shared__ uint32_t total;
+    const int64_t base = int64_t(blockIdx.x) * SCAN_TILE;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        int64_t j = base + i * SCAN_THREADS + threadIdx.x;
+        tile[i * SCAN_THREADS + threadIdx.x] = j < n ? in[j] : 0u;
+    }
+    __syncthreads();
+    uint32_t v[SCAN_ITEMS], s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        v[i] = tile[threadIdx.x * SCAN_ITEMS + i];
+        s += v[i];
+    }
+    uint32_t pre = block_exclusive_scan(s, ws, &total);
+    if (block_off) pre += block_off[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        tile[threadIdx.x * SCAN_ITEMS + i] = pre;
+        pre += v[i];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        int64_t j = base + i * SCAN_THREADS + threadIdx.x;
+        if (j < n) out[j] = tile[i * SCAN_THREADS + threadIdx.x];
+    }
+}
+
+size_t scan_temp_bytes(int64_t n)
+{
+    size_t b = 0;
+    while (n > SCAN_TILE) {
+        n = (n + SCAN_TILE - 1) / SCAN_TILE;
+        b += size_t((n + 63) / 64 * 64) * sizeof(uint32_t);
+    }
+    return b + 256;
+}
+
+int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t st)
+{
+    if (n <= 0) return 0;
+    if (n <= SCAN_TILE) {
+        scan_tile_kernel<<<1, SCAN_THREADS, 0, st>>>(in, out, n, nullptr);
+        return count_launch();
+    }
+    const int64_t nb = (n + SCAN_TILE - 1) / SCAN_TILE;
+    uint32_t* sums = static_cast<uint32_t*>(temp);
+    void* rest = sums + (nb + 63) / 64 * 64;
+    scan_reduce_kernel<<<unsigned(nb), SCAN_THREADS, 0, st>>>(in, n, sums);
+    int rc = count_launch();
+    if (rc) return rc;
+    rc = launch_exclusive_scan(sums, sums, nb, rest, st);
+    if (rc) return rc;
+    scan_tile_kernel<<<unsigned(nb), SCAN_THREADS, 0, st>>>(in, out, n, sums);
+    return count_launch();
+}
+
+// ---------------------------------------------------------------- histogram
+
+__global__ void __launch_bounds__(512) hist_smem_kernel(const uint32_t* __restrict__ keys, int64_t N, int NC,
+                                                        uint32_t* __restrict__ counts)
+{
+    extern __shared__ uint32_t h[];
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x)
+    {
+        const uint32_t key = keys[i];
+        if (key < uint32_t(NC)) atomicAdd(&h[key], 1u);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NC; c += blockDim.x)
+        if (h[c]) atomicAdd(&counts[c], h[c]);
+}
+
+__global__ void hist_global_kernel(const uint32_t* __restrict__ keys, int64_t N, int64_t NC,
+                                   uint32_t* __restrict__ counts)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < N; i += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t key = keys[i];
+        if (key < NC) atomicAdd(&counts[key], 1u);
+    }
+}
+
+int launch_key_histogram(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* counts, cudaStream_t st,
+                         int num_sms)
+{
+    if (N == 0) return 0;
+    int64_t blocks = (N + 4095) / 4096;
+    if (NC <= 12288) {
+        if (blocks > 2 * num_sms) blocks = 2 * num_sms;
+        hist_smem_kernel<<<unsigned(blocks), 512, size_t(NC) * 4, st>>>(keys, N, int(NC), counts);
+    } else {
+        if (blocks > 8 * num_sms) blocks = 8 * num_sms;
+        hist_global_kernel<<<unsigned(blocks), 256, 0, st>>>(keys, N, NC, counts);
+    }
+    return count_launch();
+}
+
+// ---------------------------------------------------------------- radix sort
+
+constexpr int RADIX_CHUNK = 2048;  // elements per warp chunk
+constexpr int RADIX_WARPS = 4;     // warps per block
+
+struct RadixPlan {
+    int passes, bits_per_pass, B;
+    int64_t nchunks;
+};
+
+static RadixPlan radix_plan(int64_t N, int64_t NC)
+{
+    int bits = 1;
+    while ((int64_t(1) << bits) < NC) ++bits;
+    RadixPlan p;
+    p.passes = (bits + 10) / 11;
+    p.bits_per_pass = (bits + p.passes - 1) / p.passes;
+    p.B = 1 << p.bits_per_pass;
+    p.nchunks = (N + RADIX_CHUNK - 1) / RADIX_CHUNK;
+    return p;
+}
+
+__global__ void __launch_bounds__(RADIX_WARPS * 32) radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t N,
+                                                                      int shift, int B, int64_t nchunks,
+                                                                      uint32_t* __restrict__ H)
+{
+    extern __shared__ uint32_t sh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = int64_t(blockIdx.x) * RADIX_WARPS + warp;
+    if (chunk >= nchunks) return;
+    uint32_t* h = sh + warp * B;
+    for (int i = lane; i < B; i += 32) h[i] = 0;
+    __syncwarp();
+    const int64_t begin = chunk * RADIX_CHUNK;
+    const int64_t end = begin + RADIX_CHUNK < N ? begin + RADIX_CHUNK : N;
+    const uint32_t mask = uint32_t(B - 1);
+    for (int64_t i = begin + lane; i < end; i += 32) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
+    __syncwarp();
+    for (int dg = lane; dg < B; dg += 32) H[int64_t(dg) * nchunks + chunk] = h[dg];
+}
+
+__global__ void __launch_bounds__(RADIX_WARPS * 32) radix_scatter_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ ids_in, int64_t N, int shift, int B,
+    int64_t nchunks, const uint32_t* __restrict__ Hs, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ ids_out)
+{
+    extern __shared__ uint32_t sh[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t chunk = int64_t(blockIdx.x) * RADIX_WARPS + warp;
+    if (chunk >= nchunks) return;
+    uint32_t* run = sh + warp * B;
+    for (int dg = lane; dg < B; dg += 32) run[dg] = Hs[int64_t(dg) * nchunks + chunk];
+    __syncwarp();
+    const int64_t begin = chunk * RADIX_CHUNK;
+    const int64_t end = begin + RADIX_CHUNK < N ? begin + RADIX_CHUNK : N;
+    const uint32_t mask = uint32_t(B - 1);
+    const unsigned lt = (1u << lane) - 1u;
+    for (int64_t base = begin; base < end; base += 32) {
+        const int64_t i = base + lane;
+        const bool live = i < end;
+        uint32_t key = live ? keys_in[i] : 0u;
+        uint32_t id = live ? (ids_in ? ids_in[i] : uint32_t(i)) : 0u;
+        uint32_t digit = live ? ((key >> shift) & mask) : 0xFFFFFFFFu;
+        unsigned peers = __match_any_sync(0xffffffffu, digit);
+        if (live) {
+            uint32_t pos = run[digit] + __popc(peers & lt);
+            ids_out[pos] = id;
+            if (keys_out) keys_out[pos] = key;
+        }
+        __syncwarp();
+        if (live && lane == __ffs(peers) - 1) run[digit] += __popc(peers);
+        __syncwarp();
+    }
+}
+
+size_t radix_temp_bytes(int64_t N, int64_t NC)
+{
+    RadixPlan p = radix_plan(N, NC);
+    const int64_t hn = int64_t(p.B) * p.nchunks;
+    size_t b = size_t((hn + 63) / 64 * 64) * 4;
+    b += scan_temp_bytes(hn);
+    b += size_t((N + 63) / 64 * 64) * 4 * 4;  // two (keys, ids) ping-pong pairs
+    return b + 1024;
+}
+
+int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
+                           cudaStream_t st)
+{
+    if (N == 0) return 0;
+    RadixPlan p = radix_plan(N, NC);
+    const int64_t hn = int64_t(p.B) * p.nchunks;
+    char* t = static_cast<char*>(temp);
+    uint32_t* H = reinterpret_cast<uint32_t*>(t);
+    t += size_t((hn + 63) / 64 * 64) * 4;
+    void* stemp = t;
+    t += (scan_temp_bytes(hn) + 255) / 256 * 256;
+    const size_t nb = size_t((N + 63) / 64 * 64) * 4;
+    uint32_t* ka = reinterpret_cast<uint32_t*>(t);
+    uint32_t* ia = reinterpret_cast<uint32_t*>(t + nb);
+    uint32_t* kb = reinterpret_cast<uint32_t*>(t + 2 * nb);
+    uint32_t* ib = reinterpret_cast<uint32_t*>(t + 3 * nb);
+    const unsigned blocks = unsigned((p.nchunks + RADIX_WARPS - 1) / RADIX_WARPS);
+    const size_t smem = size_t(RADIX_WARPS) * p.B * 4;
+    const uint32_t* kin = keys;
+    const uint32_t* iin = nullptr;
+    for (int pass = 0; pass < p.passes; ++pass) {
+        const int shift = pass * p.bits_per_pass;
+        const bool last = pass == p.passes - 1;
+        uint32_t* kout = last ? nullptr : (pass % 2 == 0 ? ka : kb);
+        uint32_t* iout = last ? perm : (pass % 2 == 0 ? ia : ib);
+        radix_hist_kernel<<<blocks, RADIX_WARPS * 32, smem, st>>>(kin, N, shift, p.B, p.nchunks, H);
+        int rc = count_launch();
+        if (rc) return rc;
+        rc = launch_exclusive_scan(H, H, hn, stemp, st);
+        if (rc) return rc;
+        radix_scatter_kernel<<<blocks, RADIX_WARPS * 32, smem, st>>>(kin, iin, N, shift, p.B, p.nchunks, H, kout,
+                                                                     iout);
+        rc = count_launch();
+        if (rc) return rc;
+        kin = kout;
+        iin = iout;
+    }
+    return 0;
+}
+
+// ---------------------------------------------------------------- gather
+
+// One group of LPV lanes per output row; lane l owns float4 slots l, l+LPV
+// of the padded row.  VEC: source rows are 16-byte aligned (d % 4 == 0).
+template <int LPV, bool VEC>
+__global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restrict__ X, int64_t N, int d, int d_pad,
+                                                         const uint32_t* __restrict__ perm, float* __restrict__ xs,
+                                                         __nv_bfloat16* __restrict__ xb, float* __restrict__ norm2)
+{
+    const int lane = threadIdx.x & 31;
+    const int glane = lane & (LPV - 1);
+    const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / LPV;
+    const int64_t ngroups = int64_t(gridDim.x) * blockDim.x / LPV;
+    const int64_t iters = (N + ngroups - 1) / ngroups;
+    const int n4p = d_pad >> 2;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t r = gid + it * ngroups;
+        const bool live = r < N;
+        const int64_t src = live ? int64_t(__ldg(perm + r)) : 0;
+        const float* xr = X + src * int64_t(d);
+        float s = 0.0f;
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+            const int i4 = glane + f * LPV;
+            if (live && i4 < n4p) {
+                float4 v;
+                if (VEC) {
+                    v = (4 * i4 < d) ? __ldg(reinterpret_cast<const float4*>(xr) + i4) : make_float4(0, 0, 0, 0);
+                } else {
+                    const int c = 4 * i4;
+                    v.x = c + 0 < d ? __ldg(xr + c + 0) : 0.0f;
+                    v.y = c + 1 < d ? __ldg(xr + c + 1) : 0.0f;
+                    v.z = c + 2 < d ? __ldg(xr + c + 2) : 0.0f;
+                    v.w = c + 3 < d ? __ldg(xr + c + 3) : 0.0f;
+                }
+                reinterpret_cast<float4*>(xs + r * int64_t(d_pad))[i4] = v;
+                if (xb) {
+                    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
+                    __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
+                    uint2 packed;
+                    packed.x = *reinterpret_cast<uint32_t*>(&lo);
+                    packed.y = *reinterpret_cast<uint32_t*>(&hi);
+                    reinterpret_cast<uint2*>(xb + r * int64_t(d_pad))[i4] = packed;
+                }
+                s = fmaf(v.x, v.x, s);
+                s = fmaf(v.y, v.y, s);
+                s = fmaf(v.z, v.z, s);
+                s = fmaf(v.w, v.w, s);
+            }
+        }
+#pragma unroll
+        for (int m = LPV / 2; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+        if (live && glane == 0) norm2[r] = s;
+    }
+}
+
+int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
+                       __nv_bfloat16* xb, float* norm2, cudaStream_t st, int num_sms)
+{
+    if (N == 0) return 0;
+    const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    const int n4p = d_pad / 4;
+    int lpv = 4;
+    while (lpv < n4p && lpv < 32) lpv <<= 1;
+    int64_t blocks = (N * lpv + 255) / 256;
+    if (blocks > int64_t(num_sms) * 16) blocks = int64_t(num_sms) * 16;
+    const dim3 g(static_cast<unsigned>(blocks)), b(256u);
+#define OSANN_GATHER(LP)                                                                                 \
+    if (vec)                                                                                             \
+        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2);              \
+    else                                                                                                 \
+        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2);
+    switch (lpv) {
+    case 4: OSANN_GATHER(4); break;
+    case 8: OSANN_GATHER(8); break;
+    case 16: OSANN_GATHER(16); break;
+    default: OSANN_GATHER(32); break;
+    }
+#undef OSANN_GATHER
+    return count_launch();
+}
+
+__global__ void max_bucket_kernel(const uint32_t* __restrict__ offsets, int64_t NC, uint32_t* __restrict__ out)
+{
+    uint32_t m = 0;
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < NC; c += int64_t(gridDim.x) * blockDim.x) {
+        uint32_t s = offsets[c + 1] - offsets[c];
+        m = s > m ? s : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
+        m = y > m ? y : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+}
+
+int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st)
+{
+    int64_t blocks = (NC + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    max_bucket_kernel<<<unsigned(blocks), 256, 0, st>>>(offsets, NC, out_max);
+    return count_launch();
+}
+
+}  // namespace osann

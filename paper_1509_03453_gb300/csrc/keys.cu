@@ -1,0 +1,196 @@
+// Cone keys of data vectors and magnitude orders of query vectors.
+//
+// Sec. 2 of the paper: a vector's profile is the unordered set of its G
+// largest-magnitude components, its cone the profile plus the signs of those
+// components.  Here G is called L and the key is
+//     key = rank(S) * 2^L + signcode,
+//     rank(S)  = sum_j C(s_j, j+1) over the members sorted ascending (s_0 < s_1 ...),
+//     signcode = sum_j [x_{s_j} >= 0] * 2^(L-1-j),
+// ties between equal magnitudes going to the lower component index.
+// Queries additionally need the full order i_1..i_K of Sec. 3-B (indices by
+// decreasing magnitude), from which the probe kernel derives the
+// neighbouring cones, and their sign bits.
+#include "osann_device.cuh"
+#include "osann_launch.h"
+
+namespace osann {
+
+// Selection key of one component: |x| bits in the high word, then the
+// complement of the component index (so that equal magnitudes prefer the
+// lower index under max), then the sign bit.
+__device__ __forceinline__ uint64_t sel_key(float x, int comp)
+{
+    uint32_t a = __float_as_uint(x) & 0x7FFFFFFFu;
+    uint32_t lo = (uint32_t(MAX_D - 1 - comp) << 1) | (x >= 0.0f ? 1u : 0u);
+    return (uint64_t(a) << 32) | lo;
+}
+__device__ __forceinline__ int sel_comp(uint64_t k) { return MAX_D - 1 - int((uint32_t(k) >> 1) & 0x3FFu); }
+__device__ __forceinline__ uint32_t sel_sign(uint64_t k) { return uint32_t(k) & 1u; }
+
+__device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7F800000u) != 0x7F800000u; }
+
+// Cone id from the L selected (component, sign) pairs, in any order.
+__device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L], int L,
+                                                      const uint64_t* __restrict__ binom)
+{
+    uint64_t rank = 0;
+    uint32_t code = 0;
+#pragma unroll
+    for (int j = 0; j < MAX_L; ++j) {
+        if (j < L) {
+            int pos = 0;  // position of member j in ascending component order
+#pragma unroll
+            for (int t = 0; t < MAX_L; ++t)
+                if (t < L && comp[t] < comp[j]) ++pos;
+            rank += __ldg(binom + comp[j] * (MAX_L + 1) + pos + 1);
+            code |= sgn[j] << (L - 1 - pos);
+        }
+    }
+    return uint32_t((rank << L) | code);
+}
+
+// One group of LPV lanes per row.  VEC: d % 4 == 0 and 16-byte aligned rows,
+// lane l holds float4 number l, l+LPV (128-bit loads); else lane l holds the
+// scalars l, l+32, ... (LPV = 32).  At most 8 values per lane (d <= 256).
+template <int LPV, bool VEC>
+__global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict__ X, int64_t N, int d, int L,
+                                                       const uint64_t* __restrict__ binom,
+                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ status)
+{
+    const int lane = threadIdx.x & 31;
+    const int glane = lane & (LPV - 1);
+    const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / LPV;
+    const int64_t ngroups = int64_t(gridDim.x) * blockDim.x / LPV;
+    bool bad = false;
+    // every group of the warp runs the same trip count so shuffles stay converged
+    const int64_t iters = (N + ngroups - 1) / ngroups;
+    for (int64_t it = 0; it < iters; ++it) {
+        const int64_t row = gid + it * ngroups;
+        const bool live = row < N;
+        uint64_t v[8];
+#pragma unroll
+        for (int f = 0; f < 8; ++f) v[f] = 0;  // 0 = empty slot (real keys are > 0)
+        if (VEC) {
+            const float4* xr = reinterpret_cast<const float4*>(X + (live ? row : 0) * int64_t(d));
+            const int n4 = d >> 2;
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                int i4 = glane + f * LPV;
+                if (live && i4 < n4) {
+                    float4 t = __ldg(xr + i4);
+                    bad |= !(finite_f(t.x) && finite_f(t.y) && finite_f(t.z) && finite_f(t.w));
+                    v[4 * f + 0] = sel_key(t.x, 4 * i4 + 0);
+                    v[4 * f + 1] = sel_key(t.y, 4 * i4 + 1);
+                    v[4 * f + 2] = sel_key(t.z, 4 * i4 + 2);
+                    v[4 * f + 3] = sel_key(t.w, 4 * i4 + 3);
+                }
+            }
+        } else {
+            const float* xr = X + (live ? row : 0) * int64_t(d);
+#pragma unroll
+            for (int f = 0; f < 8; ++f) {
+                int c = glane + f * 32;
+                if (live && c < d) {
+                    float t = __ldg(xr + c);
+                    bad |= !finite_f(t);
+                    v[f] = sel_key(t, c);
+                }
+            }
+        }
+        int comp[MAX_L];
+        uint32_t sgn[MAX_L];
+#pragma unroll
+        for (int r = 0; r < MAX_L; ++r) {
+            comp[r] = 0;
+            sgn[r] = 0;
+            if (r < L) {
+                uint64_t best = 0;
+#pragma unroll
+                for (int f = 0; f < 8; ++f) best = v[f] > best ? v[f] : best;
+#pragma unroll
+                for (int m = LPV / 2; m > 0; m >>= 1) {
+                    uint64_t o = shfl_xor_u64(best, m);
+                    best = o > best ? o : best;
+                }
+#pragma unroll
+                for (int f = 0; f < 8; ++f)
+                    if (v[f] == best) v[f] = 0;  // taken (keys are unique per row)
+                comp[r] = sel_comp(best);
+                sgn[r] = sel_sign(best);
+            }
+        }
+        if (live && glane == 0) keys[row] = cone_from_members(comp, sgn, L, binom);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_DATA);
+}
+
+// One warp per query: full magnitude order (rank -> component, u8) and sign
+// bits (bit c of word c/32 set when y_c >= 0).
+__global__ void __launch_bounds__(128) query_order_kernel(const float* __restrict__ Y, int64_t Q, int d,
+                                                          uint8_t* __restrict__ qorder,
+                                                          uint32_t* __restrict__ qsign,
+                                                          uint32_t* __restrict__ status)
+{
+    __shared__ uint64_t sk[4][MAX_D];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t q = int64_t(blockIdx.x) * 4 + warp;
+    if (q >= Q) return;  // whole warp leaves together
+    const float* y = Y + q * int64_t(d);
+    bool bad = false;
+    for (int c = lane; c < d; c += 32) {
+        float t = y[c];
+        bad |= !finite_f(t);
+        sk[warp][c] = sel_key(t, c) | 1u;  // sign bit neutralised: order uses |y| and index only
+    }
+    for (int w = 0; w < (d + 31) / 32; ++w) {
+        int c = w * 32 + lane;
+        bool pos = c < d ? (y[c] >= 0.0f) : false;
+        unsigned b = __ballot_sync(0xffffffffu, pos);
+        if (lane == 0) qsign[q * (MAX_D / 32) + w] = b;
+    }
+    __syncwarp();
+    for (int c = lane; c < d; c += 32) {
+        uint64_t me = sk[warp][c];
+        int rank = 0;
+        for (int j = 0; j < d; ++j) rank += sk[warp][j] > me ? 1 : 0;
+        qorder[q * int64_t(d) + rank] = uint8_t(c);
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_QUERY);
+}
+
+int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
+                     uint32_t* status, cudaStream_t st, int num_sms)
+{
+    if (N == 0) return 0;
+    const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
+    int n4 = d / 4, lpv = 4;
+    while (lpv < n4 && lpv < 32) lpv <<= 1;
+    if (!vec) lpv = 32;
+    const int threads = 256;
+    const int64_t groups_needed = N;
+    int64_t blocks = (groups_needed * lpv + threads - 1) / threads;
+    const int64_t cap = int64_t(num_sms) * 16;
+    if (blocks > cap) blocks = cap;
+    const dim3 g(static_cast<unsigned>(blocks)), b(static_cast<unsigned>(threads));
+    if (vec) {
+        switch (lpv) {
+        case 4: data_keys_kernel<4, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        case 8: data_keys_kernel<8, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        case 16: data_keys_kernel<16, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        default: data_keys_kernel<32, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        }
+    } else {
+        data_keys_kernel<32, false><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status);
+    }
+    return count_launch();
+}
+
+int launch_query_order(const float* Y, int64_t Q, int d, uint8_t* qorder, uint32_t* qsign, uint32_t* status,
+                       cudaStream_t st)
+{
+    if (Q == 0) return 0;
+    query_order_kernel<<<unsigned((Q + 3) / 4), 128, 0, st>>>(Y, Q, d, qorder, qsign, status);
+    return count_launch();
+}
+
+}  // namespace osann

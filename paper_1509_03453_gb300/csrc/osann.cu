@@ -1,0 +1,730 @@
+// libosann host library: the C ABI declared in include/osann.h.
+//
+// Validation, device allocation (stream-ordered, through an optional
+// caller-installed allocator), per-device constant tables, workspace layout,
+// the index build and the two search schedules, and stage timing.  Every
+// step of the method runs in the kernels of keys.cu, buckets.cu, probes.cu,
+// scan_plain.cu and scan_batched.cu; this file only sequences them.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "osann.h"
+#include "osann_device.cuh"
+#include "osann_launch.h"
+
+// Binomial coefficients C(n, k), n <= MAX_D, k <= MAX_L, saturated at
+// UINT64_MAX; used by the key (profile rank) and probe (unranking) kernels.
+__device__ uint64_t g_binom_table[(osann::MAX_D + 1) * (osann::MAX_L + 1)];
+// Status word for the stateless entry points (osann_keys, osann_query_order).
+__device__ uint32_t g_scratch_status[4];
+
+namespace osann {
+
+static thread_local char g_err[1024];
+static std::atomic<int64_t> g_launches{0};
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int count_launch()
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("kernel launch failed: %s", cudaGetErrorString(e));
+        return OSANN_ERR_CUDA;
+    }
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return 0;
+}
+
+static int cuda_fail(cudaError_t e, const char* what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return OSANN_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- allocator
+
+static osann_alloc_fn g_alloc = nullptr;
+static osann_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+static void* dev_alloc(size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) bytes = 256;
+    if (g_alloc) return g_alloc(bytes, st, g_alloc_ctx);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+static void dev_free(void* p, size_t bytes, cudaStream_t st)
+{
+    if (!p) return;
+    if (g_free) g_free(p, bytes, st, g_alloc_ctx);
+    else cudaFreeAsync(p, st);
+}
+
+// ---------------------------------------------------------------- per device
+
+struct DeviceState {
+    bool ready = false;
+    int num_sms = 0;
+    uint64_t* binom = nullptr;
+    uint32_t* scratch_status = nullptr;
+};
+static DeviceState g_dev[64];
+static std::mutex g_dev_mu;
+
+static int device_state(DeviceState** out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) {
+        set_error("device ordinal %d out of range", dev);
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceState& s = g_dev[dev];
+    if (!s.ready) {
+        std::vector<uint64_t> t((MAX_D + 1) * (MAX_L + 1), 0);
+        for (int n = 0; n <= MAX_D; ++n)
+            for (int k = 0; k <= MAX_L; ++k) {
+                uint64_t v;
+                if (k == 0) v = 1;
+                else if (n == 0) v = 0;
+                else {
+                    uint64_t a = t[(n - 1) * (MAX_L + 1) + k - 1], b = t[(n - 1) * (MAX_L + 1) + k];
+                    v = (a > UINT64_MAX - b) ? UINT64_MAX : a + b;
+                }
+                t[n * (MAX_L + 1) + k] = v;
+            }
+        if ((e = cudaMemcpyToSymbol(g_binom_table, t.data(), t.size() * sizeof(uint64_t))) != cudaSuccess)
+            return cuda_fail(e, "binomial table upload");
+        if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.binom), g_binom_table)) != cudaSuccess)
+            return cuda_fail(e, "binomial table address");
+        if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.scratch_status), g_scratch_status)) != cudaSuccess)
+            return cuda_fail(e, "status word address");
+        if ((e = cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return cuda_fail(e, "SM count");
+        // keep stream-ordered allocations cached in this process's pool
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+        s.ready = true;
+    }
+    *out = &s;
+    return 0;
+}
+
+// ---------------------------------------------------------------- stats
+
+struct StageRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+static std::mutex g_stats_mu;
+static bool g_stats_on = false;
+static std::vector<StageRec> g_pending;
+static std::vector<cudaEvent_t> g_event_pool;
+static double g_stage_ms[OSANN_NUM_STAGES];
+static int64_t g_stage_n[OSANN_NUM_STAGES];
+
+static cudaEvent_t take_event()
+{
+    if (!g_event_pool.empty()) {
+        cudaEvent_t e = g_event_pool.back();
+        g_event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct StageScope {
+    int stage;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    StageScope(int s, cudaStream_t stream) : stage(s), st(stream)
+    {
+        if (!g_stats_on) return;
+        std::lock_guard<std::mutex> lk(g_stats_mu);
+        a = take_event();
+        cudaEventRecord(a, st);
+    }
+    ~StageScope()
+    {
+        if (!a) return;
+        std::lock_guard<std::mutex> lk(g_stats_mu);
+        cudaEvent_t b = take_event();
+        cudaEventRecord(b, st);
+        g_pending.push_back({stage, a, b});
+    }
+};
+
+static void stats_collect()
+{
+    for (auto& r : g_pending) {
+        float ms = 0.0f;
+        cudaEventSynchronize(r.b);
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        g_stage_ms[r.stage] += ms;
+        g_stage_n[r.stage] += 1;
+        g_event_pool.push_back(r.a);
+        g_event_pool.push_back(r.b);
+    }
+    g_pending.clear();
+}
+
+}  // namespace osann
+
+using namespace osann;
+
+struct osann_index {
+    int64_t N = 0, NC = 0, max_bucket = 0;
+    int d = 0, d_pad = 0, L = 0, device = 0, num_sms = 0;
+    cudaStream_t stream = nullptr;
+    uint32_t* keys = nullptr;
+    uint32_t* offsets = nullptr;
+    uint32_t* perm = nullptr;
+    float* xs = nullptr;
+    float* norm2 = nullptr;
+    uint32_t* status = nullptr;  // [0] flags, [1] largest cone
+    uint64_t* binom = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;
+};
+
+static void index_release(osann_index* ix)
+{
+    for (auto& a : ix->allocs) dev_free(a.first, a.second, ix->stream);
+    ix->allocs.clear();
+    delete ix;
+}
+
+template <class T>
+static T* index_alloc(osann_index* ix, size_t count)
+{
+    const size_t bytes = count * sizeof(T);
+    void* p = dev_alloc(bytes, ix->stream);
+    if (p) ix->allocs.push_back({p, bytes});
+    return static_cast<T*>(p);
+}
+
+static int64_t cones_or_error(int d, int L)
+{
+    if (d < 1 || L < 1 || L > d) return OSANN_ERR_INVALID;
+    if (L > MAX_L || d > MAX_D) return OSANN_ERR_INVALID;
+    // C(d, L) by the multiplicative formula; every prefix quotient is exact
+    unsigned __int128 c = 1;
+    for (int i = 1; i <= L; ++i) {
+        c = c * (unsigned __int128)(d - L + i) / (unsigned __int128)i;
+        if (c > ((unsigned __int128)1 << 40)) return OSANN_ERR_UNSUPPORTED;
+    }
+    const unsigned __int128 nc = c << L;
+    if (nc >= ((unsigned __int128)1 << 31)) return OSANN_ERR_UNSUPPORTED;
+    return int64_t(nc);
+}
+
+static int pad_dim(int d)
+{
+    if (d <= 16) return 16;
+    int p = 32;
+    while (p < d) p <<= 1;
+    return p;
+}
+
+static inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+// ---------------------------------------------------------------- workspace
+
+struct WsLayout {
+    size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
+    size_t total;
+    int64_t max_items;
+};
+
+static int group_size(int d_pad) { return 128 / (d_pad == 16 ? 1 : d_pad / 32); }
+
+static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, bool batched)
+{
+    WsLayout w{};
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = al256(off + bytes);
+        return o;
+    };
+    w.qorder = take(size_t(Q) * ix->d);
+    w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
+    w.probes = take(size_t(Q) * P_eff * 4);
+    if (batched) {
+        const int G = group_size(ix->d_pad);
+        const int64_t n = Q * P_eff;
+        int64_t mi = n / G + ix->NC + 1;
+        if (mi > n) mi = n;
+        w.max_items = mi;
+        w.partial = take(size_t(n) * k * 8);
+        w.qcount = take(size_t(ix->NC + 1) * 4);
+        w.qoff = take(size_t(ix->NC + 1) * 4);
+        w.fill = take(size_t(ix->NC + 1) * 4);
+        w.nitems = take(size_t(ix->NC + 1) * 4);
+        w.item_off = take(size_t(ix->NC + 1) * 4);
+        w.qlist = take(size_t(n) * 4);
+        w.items = take(size_t(mi > 0 ? mi : 1) * 8);
+        w.counters = take(256);
+        w.scan_temp = take(batched_scan_temp_bytes(ix->NC));
+    }
+    w.total = off + 256;
+    return w;
+}
+
+static bool choose_batched(const osann_index* ix, int64_t Q, int64_t P_eff, int path)
+{
+    if (path == OSANN_PATH_PLAIN) return false;
+    if (path == OSANN_PATH_BATCHED) return true;
+    return double(Q) * double(P_eff) >= 16.0 * double(ix->NC);
+}
+
+// ---------------------------------------------------------------- C ABI
+
+extern "C" {
+
+int osann_set_allocator(osann_alloc_fn alloc, osann_free_fn free_fn, void* ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("allocator and free function must be set together");
+        return OSANN_ERR_INVALID;
+    }
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = ctx;
+    return OSANN_OK;
+}
+
+int osann_num_cones(int32_t d, int32_t L, int64_t* nc)
+{
+    int64_t r = cones_or_error(d, L);
+    if (r < 0) {
+        set_error("no cone count for d=%d L=%d", d, L);
+        return int(r);
+    }
+    if (nc) *nc = r;
+    return OSANN_OK;
+}
+
+const char* osann_last_error(void) { return g_err; }
+
+int64_t osann_launch_count(void) { return g_launches.load(); }
+
+int osann_stats_enable(int on)
+{
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    g_stats_on = on != 0;
+    return OSANN_OK;
+}
+
+int osann_stats_reset(void)
+{
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    stats_collect();
+    for (int i = 0; i < OSANN_NUM_STAGES; ++i) {
+        g_stage_ms[i] = 0;
+        g_stage_n[i] = 0;
+    }
+    return OSANN_OK;
+}
+
+int osann_stats_get(int32_t stage, double* total_ms, int64_t* count)
+{
+    if (stage < 0 || stage >= OSANN_NUM_STAGES) return OSANN_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(g_stats_mu);
+    stats_collect();
+    if (total_ms) *total_ms = g_stage_ms[stage];
+    if (count) *count = g_stage_n[stage];
+    return OSANN_OK;
+}
+
+int osann_keys(const float* d_vectors, int64_t n, int32_t d, int32_t L, uint32_t* d_keys, void* stream)
+{
+    int64_t nc = cones_or_error(d, L);
+    if (nc < 0 || n < 0 || (n > 0 && (!d_vectors || !d_keys))) {
+        set_error("osann_keys: invalid arguments");
+        return nc < 0 ? int(nc) : OSANN_ERR_INVALID;
+    }
+    DeviceState* ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    return launch_data_keys(d_vectors, n, d, L, ds->binom, d_keys, ds->scratch_status,
+                            static_cast<cudaStream_t>(stream), ds->num_sms);
+}
+
+int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_order, uint32_t* d_signs, void* stream)
+{
+    if (d < 1 || d > MAX_D || Q < 0 || (Q > 0 && (!d_queries || !d_order || !d_signs))) {
+        set_error("osann_query_order: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    DeviceState* ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    return launch_query_order(d_queries, Q, d, d_order, d_signs, ds->scratch_status,
+                              static_cast<cudaStream_t>(stream));
+}
+
+int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
+{
+    if (!out || !d_data || N < 1) {
+        set_error("osann_build: invalid arguments (data=%p N=%lld out=%p)", (const void*)d_data, (long long)N,
+                  (void*)out);
+        return OSANN_ERR_INVALID;
+    }
+    *out = nullptr;
+    const int64_t NC = cones_or_error(d, L);
+    if (NC < 0) {
+        set_error("osann_build: unsupported (d=%d, L=%d): need 1<=d<=%d, 1<=L<=min(d,%d), N_C < 2^31", d, L, MAX_D,
+                  MAX_L);
+        return int(NC);
+    }
+    if (N >= (int64_t(1) << 31)) {
+        set_error("osann_build: N=%lld exceeds 2^31-1", (long long)N);
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    DeviceState* ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    osann_index* ix = new osann_index();
+    ix->N = N;
+    ix->NC = NC;
+    ix->d = d;
+    ix->d_pad = pad_dim(d);
+    ix->L = L;
+    ix->stream = st;
+    ix->num_sms = ds->num_sms;
+    ix->binom = ds->binom;
+    cudaGetDevice(&ix->device);
+
+    ix->keys = index_alloc<uint32_t>(ix, size_t(N));
+    ix->offsets = index_alloc<uint32_t>(ix, size_t(NC + 1));
+    ix->perm = index_alloc<uint32_t>(ix, size_t(N));
+    ix->xs = index_alloc<float>(ix, size_t(N) * ix->d_pad);
+    ix->norm2 = index_alloc<float>(ix, size_t(N));
+    ix->status = index_alloc<uint32_t>(ix, 64);
+    const size_t counts_bytes = al256(size_t(NC + 1) * 4);
+    const size_t scan_bytes = al256(scan_temp_bytes(NC + 1));
+    const size_t radix_bytes = al256(radix_temp_bytes(N, NC));
+    const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes;
+    char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
+    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->norm2 || !ix->status || !temp) {
+        if (temp) dev_free(temp, temp_bytes, st);
+        index_release(ix);
+        set_error("osann_build: device allocation failed");
+        return OSANN_ERR_OOM;
+    }
+    uint32_t* counts = reinterpret_cast<uint32_t*>(temp);
+    void* scan_temp = temp + counts_bytes;
+    void* radix_temp = temp + counts_bytes + scan_bytes;
+
+    cudaMemsetAsync(ix->status, 0, 64 * 4, st);
+    cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
+    {
+        StageScope s(OSANN_STAGE_DATA_KEYS, st);
+        rc = launch_data_keys(d_data, N, d, L, ix->binom, ix->keys, ix->status, st, ix->num_sms);
+    }
+    if (!rc) {
+        StageScope s(OSANN_STAGE_BUCKETS, st);
+        rc = launch_key_histogram(ix->keys, N, NC, counts, st, ix->num_sms);
+        if (!rc) rc = launch_exclusive_scan(counts, ix->offsets, NC + 1, scan_temp, st);
+        if (!rc) rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, radix_temp, st);
+    }
+    if (!rc) {
+        StageScope s(OSANN_STAGE_GATHER, st);
+        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, nullptr, ix->norm2, st, ix->num_sms);
+    }
+    if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st);
+    dev_free(temp, temp_bytes, st);
+    uint32_t host_status[2] = {0, 0};
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(host_status, ix->status, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "osann_build");
+    }
+    if (!rc && (host_status[0] & ST_TIMEOUT)) {
+        set_error("osann_build: a device wait timed out");
+        rc = OSANN_ERR_TIMEOUT;
+    }
+    if (!rc && (host_status[0] & ST_NONFINITE_DATA)) {
+        set_error("osann_build: data contains NaN or Inf");
+        rc = OSANN_ERR_NONFINITE;
+    }
+    if (rc) {
+        index_release(ix);
+        return rc;
+    }
+    cudaMemsetAsync(ix->status, 0, 4, st);
+    ix->max_bucket = host_status[1];
+    *out = ix;
+    return OSANN_OK;
+}
+
+int osann_free(osann_index* index)
+{
+    if (!index) return OSANN_OK;
+    index_release(index);
+    return OSANN_OK;
+}
+
+int osann_info(const osann_index* ix, int64_t* N, int32_t* d, int32_t* L, int64_t* NC, int64_t* max_bucket)
+{
+    if (!ix) {
+        set_error("osann_info: null index");
+        return OSANN_ERR_INVALID;
+    }
+    if (N) *N = ix->N;
+    if (d) *d = ix->d;
+    if (L) *L = ix->L;
+    if (NC) *NC = ix->NC;
+    if (max_bucket) *max_bucket = ix->max_bucket;
+    return OSANN_OK;
+}
+
+int osann_export(const osann_index* ix, uint32_t* d_keys, uint32_t* d_offsets, uint32_t* d_perm, void* stream)
+{
+    if (!ix) {
+        set_error("osann_export: null index");
+        return OSANN_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (d_keys && e == cudaSuccess)
+        e = cudaMemcpyAsync(d_keys, ix->keys, size_t(ix->N) * 4, cudaMemcpyDeviceToDevice, st);
+    if (d_offsets && e == cudaSuccess)
+        e = cudaMemcpyAsync(d_offsets, ix->offsets, size_t(ix->NC + 1) * 4, cudaMemcpyDeviceToDevice, st);
+    if (d_perm && e == cudaSuccess)
+        e = cudaMemcpyAsync(d_perm, ix->perm, size_t(ix->N) * 4, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? OSANN_OK : cuda_fail(e, "osann_export");
+}
+
+int osann_status(const osann_index* ix, void* stream, uint32_t* flags)
+{
+    if (!ix || !flags) {
+        set_error("osann_status: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, ix->status, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ix->status, 0, 4, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "osann_status");
+    *flags = h;
+    return OSANN_OK;
+}
+
+size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path)
+{
+    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K) return 0;
+    const int64_t P_eff = P < ix->NC ? P : ix->NC;
+    return ws_layout(ix, Q, P_eff, k, choose_batched(ix, Q, P_eff, path)).total;
+}
+
+static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_eff, const WsLayout& L, char* w,
+                       bool init_partial, int k, cudaStream_t st)
+{
+    int rc;
+    {
+        StageScope s(OSANN_STAGE_QUERY_ORDER, st);
+        rc = launch_query_order(Y, Q, ix->d, reinterpret_cast<uint8_t*>(w + L.qorder),
+                                reinterpret_cast<uint32_t*>(w + L.qsign), ix->status, st);
+    }
+    if (rc) return rc;
+    StageScope s(OSANN_STAGE_PROBES, st);
+    return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Q, ix->d,
+                         ix->L, P_eff, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
+                         init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st);
+}
+
+int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32_t P, uint32_t* d_probes, void* d_ws,
+                 size_t ws_bytes, void* stream)
+{
+    if (!ix || Q < 0 || P < 1 || (Q > 0 && (!d_queries || !d_probes))) {
+        set_error("osann_probes: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    if (Q == 0) return OSANN_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int64_t P_eff = P < ix->NC ? P : ix->NC;
+    const WsLayout L = ws_layout(ix, Q, P_eff, 1, false);
+    void* owned = nullptr;
+    if (!d_ws) {
+        owned = d_ws = dev_alloc(L.total, st);
+        if (!d_ws) {
+            set_error("osann_probes: workspace allocation failed");
+            return OSANN_ERR_OOM;
+        }
+    } else if (ws_bytes < L.total) {
+        set_error("osann_probes: workspace too small (%zu < %zu)", ws_bytes, L.total);
+        return OSANN_ERR_INVALID;
+    }
+    char* w = static_cast<char*>(d_ws);
+    int rc = query_front(ix, d_queries, Q, P_eff, L, w, false, 1, st);
+    if (!rc) {
+        cudaError_t e = cudaMemcpyAsync(d_probes, w + L.probes, size_t(Q) * P_eff * 4, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "osann_probes");
+    }
+    if (owned) dev_free(owned, L.total, st);
+    return rc;
+}
+
+static int search_impl(const osann_index* ix, const float* Y, const int64_t* src, int64_t Q, int32_t P, int32_t k,
+                       int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
+                       float* dists, void* stream)
+{
+    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > 2 ||
+        (Q > 0 && (!Y || !ids || !dists))) {
+        set_error("osann_search: invalid arguments (Q=%lld P=%d k=%d path=%d)", (long long)Q, P, k, path);
+        return OSANN_ERR_INVALID;
+    }
+    if (src && (grid_w < 1 || radius < 0)) {
+        set_error("osann_search_excl: grid_w must be >= 1 and radius >= 0");
+        return OSANN_ERR_INVALID;
+    }
+    if (Q == 0) return OSANN_OK;
+    const int64_t P_eff = P < ix->NC ? P : ix->NC;
+    if (Q * P_eff >= (int64_t(1) << 32)) {
+        set_error("osann_search: Q * min(P, N_C) must stay below 2^32");
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool batched = choose_batched(ix, Q, P_eff, path);
+    const WsLayout L = ws_layout(ix, Q, P_eff, k, batched);
+    void* owned = nullptr;
+    if (!d_ws) {
+        owned = d_ws = dev_alloc(L.total, st);
+        if (!d_ws) {
+            set_error("osann_search: workspace allocation failed (%zu bytes)", L.total);
+            return OSANN_ERR_OOM;
+        }
+    } else if (ws_bytes < L.total) {
+        set_error("osann_search: workspace too small (%zu < %zu)", ws_bytes, L.total);
+        return OSANN_ERR_INVALID;
+    }
+    char* w = static_cast<char*>(d_ws);
+    int rc = query_front(ix, Y, Q, P_eff, L, w, batched, k, st);
+    if (!rc && batched) {
+        BatchedBuffers b{};
+        b.qcount = reinterpret_cast<uint32_t*>(w + L.qcount);
+        b.qoff = reinterpret_cast<uint32_t*>(w + L.qoff);
+        b.fill = reinterpret_cast<uint32_t*>(w + L.fill);
+        b.nitems = reinterpret_cast<uint32_t*>(w + L.nitems);
+        b.item_off = reinterpret_cast<uint32_t*>(w + L.item_off);
+        b.qlist = reinterpret_cast<uint32_t*>(w + L.qlist);
+        b.items = reinterpret_cast<uint2*>(w + L.items);
+        b.counters = reinterpret_cast<uint32_t*>(w + L.counters);
+        b.n_items_dev = b.item_off + ix->NC;
+        b.scan_temp = w + L.scan_temp;
+        b.max_items = L.max_items;
+        const int G = group_size(ix->d_pad);
+        uint64_t* partial = reinterpret_cast<uint64_t*>(w + L.partial);
+        {
+            StageScope s(OSANN_STAGE_WORKLIST, st);
+            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probes), Q, P_eff, ix->offsets, ix->NC, G, b, st,
+                                 ix->num_sms);
+        }
+        if (!rc) {
+            StageScope s(OSANN_STAGE_TILE_SCAN, st);
+            rc = launch_tile_scan(ix->xs, ix->offsets, ix->perm, ix->d_pad, Y, ix->d, P_eff, k, src, grid_w, radius, b,
+                                  G, partial, ix->status, st, ix->num_sms);
+        }
+        if (!rc) {
+            StageScope s(OSANN_STAGE_MERGE, st);
+            rc = launch_merge(partial, Q, P_eff, k, nullptr, ids, dists, st);
+        }
+    } else if (!rc) {
+        StageScope s(OSANN_STAGE_PLAIN_SCAN, st);
+        rc = launch_plain_scan(ix->xs, ix->offsets, ix->perm, ix->d_pad, Y, ix->d, Q,
+                               reinterpret_cast<uint32_t*>(w + L.probes), P_eff, uint32_t(ix->NC), k, src, grid_w,
+                               radius, ids, dists,
+                               ix->status, st);
+    }
+    if (owned) dev_free(owned, L.total, st);
+    return rc;
+}
+
+int osann_search(const osann_index* index, const float* d_queries, int64_t Q, int32_t P, int32_t k, int32_t path,
+                 void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists, void* stream)
+{
+    return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream);
+}
+
+int osann_search_excl(const osann_index* index, const float* d_queries, const int64_t* d_query_src, int64_t Q,
+                      int32_t P, int32_t k, int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes,
+                      int64_t* d_ids, float* d_sqdists, void* stream)
+{
+    if (!d_query_src && Q > 0) {
+        set_error("osann_search_excl: null query source array");
+        return OSANN_ERR_INVALID;
+    }
+    return search_impl(index, d_queries, d_query_src, Q, P, k, grid_w, radius, path, d_ws, ws_bytes, d_ids, d_sqdists,
+                       stream);
+}
+
+size_t osann_bruteforce_workspace_size(const osann_index* ix, int64_t Q, int32_t k)
+{
+    if (!ix || Q < 0 || k < 1 || k > MAX_K) return 0;
+    return al256(bruteforce_ws_bytes(ix->N, ix->d_pad, Q, k)) + 256;
+}
+
+int osann_bruteforce(const osann_index* ix, const float* d_queries, const int64_t* d_query_src, int64_t Q, int32_t k,
+                     int64_t grid_w, int32_t radius, void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists,
+                     void* stream)
+{
+    if (!ix || Q < 0 || k < 1 || k > MAX_K || (Q > 0 && (!d_queries || !d_ids || !d_sqdists)) ||
+        (d_query_src && (grid_w < 1 || radius < 0))) {
+        set_error("osann_bruteforce: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    if (Q == 0) return OSANN_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t need = osann_bruteforce_workspace_size(ix, Q, k);
+    void* owned = nullptr;
+    if (!d_ws) {
+        owned = d_ws = dev_alloc(need, st);
+        if (!d_ws) {
+            set_error("osann_bruteforce: workspace allocation failed");
+            return OSANN_ERR_OOM;
+        }
+    } else if (ws_bytes < need) {
+        set_error("osann_bruteforce: workspace too small (%zu < %zu)", ws_bytes, need);
+        return OSANN_ERR_INVALID;
+    }
+    char* w = static_cast<char*>(d_ws);
+    uint32_t* counter = reinterpret_cast<uint32_t*>(w + need - 256);
+    int rc;
+    {
+        StageScope s(OSANN_STAGE_BRUTEFORCE, st);
+        rc = launch_bruteforce_rows(ix->xs, ix->perm, ix->N, ix->d_pad, d_queries, ix->d, Q, k, d_query_src, grid_w,
+                                    radius, w, counter, d_ids, d_sqdists, ix->status, st, ix->num_sms);
+    }
+    if (owned) dev_free(owned, need, st);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Host-side declarations of the kernel launchers (internal to libosann).
+// Every launcher returns 0 or a negative OSANN_ERR_* code, and counts the
+// kernels it launched.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace osann {
+
+// Launch bookkeeping: checks cudaGetLastError, bumps the launch counter.
+int count_launch();
+void set_error(const char* fmt, ...);
+
+// keys.cu
+int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
+                     uint32_t* status, cudaStream_t st, int num_sms);
+int launch_query_order(const float* Y, int64_t Q, int d, uint8_t* qorder, uint32_t* qsign, uint32_t* status,
+                       cudaStream_t st);
+
+// buckets.cu
+size_t scan_temp_bytes(int64_t n);
+int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, void* temp, cudaStream_t st);
+int launch_key_histogram(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* counts, cudaStream_t st,
+                         int num_sms);
+size_t radix_temp_bytes(int64_t N, int64_t NC);
+int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
+                           cudaStream_t st);
+int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
+                       __nv_bfloat16* xb, float* norm2, cudaStream_t st, int num_sms);  // xb may be null
+int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st);
+
+// probes.cu
+int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
+                  const uint64_t* binom, uint32_t* probes, uint64_t* partial, int k, cudaStream_t st);
+
+// scan_plain.cu
+int launch_plain_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad,
+                      const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, uint32_t NC, int k,
+                      const int64_t* query_src, int64_t grid_w, int radius, int64_t* out_ids, float* out_d,
+                      uint32_t* status, cudaStream_t st);
+
+// scan_batched.cu
+struct BatchedBuffers {
+    uint32_t* qcount;     // NC + 1
+    uint32_t* qoff;       // NC + 1
+    uint32_t* fill;       // NC
+    uint32_t* nitems;     // NC + 1
+    uint32_t* item_off;   // NC + 1
+    uint32_t* qlist;      // Q * P_eff
+    uint2* items;         // max_items
+    uint32_t* counters;   // word 0: work counter of the tile scan
+    const uint32_t* n_items_dev;  // device word holding the item count (item_off + NC)
+    void* scan_temp;
+    int64_t max_items;
+};
+size_t batched_scan_temp_bytes(int64_t NC);
+int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
+                    int group, BatchedBuffers& b, cudaStream_t st, int num_sms);
+int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y,
+                     int d, int64_t slots_per_query, int k, const int64_t* query_src, int64_t grid_w, int radius,
+                     const BatchedBuffers& b, int group, uint64_t* partial, uint32_t* status, cudaStream_t st,
+                     int num_sms);
+int launch_merge(const uint64_t* partial, int64_t Q, int64_t slots, int k, const uint32_t* perm_or_null,
+                 int64_t* out_ids, float* out_d, cudaStream_t st);
+
+// linear search (scan_batched.cu): dense tile scan over all rows of xs
+size_t bruteforce_ws_bytes(int64_t N, int d_pad, int64_t Q, int k);
+int launch_bruteforce_rows(const float* xs, const uint32_t* perm, int64_t N, int d_pad, const float* Y, int d,
+                           int64_t Q, int k, const int64_t* query_src, int64_t grid_w, int radius, void* ws,
+                           uint32_t* counter, int64_t* out_ids, float* out_d, uint32_t* status, cudaStream_t st,
+                           int num_sms);
+
+}  // namespace osann

@@ -1,0 +1,506 @@
+// Batched candidate scan: the (query, probed cone) pairs of a whole query
+// batch are inverted into cone-major work, so that each cone's points are
+// streamed once per group of queries that visit it instead of once per query.
+// The arithmetic per (query, point) pair is exactly the plain scan's (fp32
+// direct differences, Eq. 1), so results are identical to the plain path.
+//
+//   work list  (all on device, no host round trip, graph-capturable):
+//     qcount[c]  = number of queries that probe non-empty cone c
+//     qoff       = exclusive scan of qcount
+//     qlist      = the (query, probe position) slots grouped by cone
+//     items      = (cone, group) pairs, group = up to G consecutive slots of
+//                  the cone's list; G = 128 / TPR queries per CTA
+//   tile scan  (persistent CTAs, atomic work counter):
+//     thread 0 streams the rows of successive items into a ring of shared
+//     memory stages with 1-D bulk copies (TMA engine) and mbarriers, across
+//     item boundaries; every thread owns one query slice (DPT dims of one
+//     query, TPR threads per query) and compares it with every row of the
+//     stage (broadcast reads); a register top-k per query is flushed to the
+//     query's slot when the item ends.
+//   merge      (one warp per query): top-k over the query's slots.
+//
+// Linear search (Eq. 1 over all N) reuses the tile scan in a dense mode:
+// items are (row chunk, consecutive query group) pairs.
+#include "osann_device.cuh"
+#include "osann_launch.h"
+
+namespace osann {
+
+constexpr int TILE_THREADS = 128;
+constexpr int TILE_STAGES = 4;
+constexpr int TILE_STAGE_FLOATS = 4096;  // 16 KB per stage
+constexpr int BF_CHUNK_ROWS = 4096;      // rows per linear-search chunk
+
+// ---------------------------------------------------------------- work list
+
+// probe values are < N_C by construction; the bound check guards the reads
+__device__ __forceinline__ bool cone_nonempty(const uint32_t* __restrict__ offsets, uint32_t b, uint32_t NC)
+{
+    return b < NC && __ldg(offsets + b + 1) > __ldg(offsets + b);
+}
+
+__global__ void __launch_bounds__(512) wl_count_smem_kernel(const uint32_t* __restrict__ probes, int64_t n,
+                                                            const uint32_t* __restrict__ offsets, int NC,
+                                                            uint32_t* __restrict__ qcount)
+{
+    extern __shared__ uint32_t h[];
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t b = probes[t];
+        if (cone_nonempty(offsets, b, uint32_t(NC))) atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NC; c += blockDim.x)
+        if (h[c]) atomicAdd(&qcount[c], h[c]);
+}
+
+__global__ void wl_count_global_kernel(const uint32_t* __restrict__ probes, int64_t n,
+                                       const uint32_t* __restrict__ offsets, uint32_t NC,
+                                       uint32_t* __restrict__ qcount)
+{
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t b = probes[t];
+        if (cone_nonempty(offsets, b, NC)) atomicAdd(&qcount[b], 1u);
+    }
+}
+
+__global__ void wl_fill_kernel(const uint32_t* __restrict__ probes, int64_t n, const uint32_t* __restrict__ offsets,
+                               uint32_t NC, const uint32_t* __restrict__ qoff, uint32_t* __restrict__ fill,
+                               uint32_t* __restrict__ qlist)
+{
+    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t b = probes[t];
+        if (cone_nonempty(offsets, b, NC)) qlist[qoff[b] + atomicAdd(&fill[b], 1u)] = uint32_t(t);
+    }
+}
+
+__global__ void wl_nitems_kernel(const uint32_t* __restrict__ qcount, int64_t NC, int G, uint32_t* __restrict__ nitems)
+{
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c <= NC; c += int64_t(gridDim.x) * blockDim.x)
+        nitems[c] = c < NC ? (qcount[c] + G - 1) / G : 0u;
+}
+
+__global__ void wl_items_kernel(const uint32_t* __restrict__ nitems, const uint32_t* __restrict__ item_off,
+                                int64_t NC, uint2* __restrict__ items, uint32_t* __restrict__ counters)
+{
+    const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (gtid == 0) counters[0] = 0;  // work counter of the tile scan that follows
+    for (int64_t c = gtid; c < NC; c += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t n = nitems[c], o = item_off[c];
+        for (uint32_t g = 0; g < n; ++g) items[o + g] = make_uint2(uint32_t(c), g);
+    }
+}
+
+size_t batched_scan_temp_bytes(int64_t NC) { return scan_temp_bytes(NC + 1); }
+
+int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC, int group,
+                    BatchedBuffers& b, cudaStream_t st, int num_sms)
+{
+    const int64_t n = Q * P_eff;
+    cudaMemsetAsync(b.qcount, 0, size_t(NC + 1) * 4, st);
+    cudaMemsetAsync(b.fill, 0, size_t(NC) * 4, st);
+    int64_t blocks = (n + 4095) / 4096;
+    if (blocks < 1) blocks = 1;
+    int rc;
+    if (NC <= 12288) {
+        int64_t bl = blocks > 2 * num_sms ? 2 * num_sms : blocks;
+        wl_count_smem_kernel<<<unsigned(bl), 512, size_t(NC) * 4, st>>>(probes, n, offsets, int(NC), b.qcount);
+    } else {
+        int64_t bl = blocks > 8 * num_sms ? 8 * num_sms : blocks;
+        wl_count_global_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qcount);
+    }
+    if ((rc = count_launch())) return rc;
+    if ((rc = launch_exclusive_scan(b.qcount, b.qoff, NC + 1, b.scan_temp, st))) return rc;
+    {
+        int64_t bl = blocks > 8 * num_sms ? 8 * num_sms : blocks;
+        wl_fill_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qoff, b.fill, b.qlist);
+        if ((rc = count_launch())) return rc;
+    }
+    int64_t cb = (NC + 256) / 256;
+    if (cb > 4 * num_sms) cb = 4 * num_sms;
+    wl_nitems_kernel<<<unsigned(cb), 256, 0, st>>>(b.qcount, NC, group, b.nitems);
+    if ((rc = count_launch())) return rc;
+    if ((rc = launch_exclusive_scan(b.nitems, b.item_off, NC + 1, b.scan_temp, st))) return rc;
+    wl_items_kernel<<<unsigned(cb), 256, 0, st>>>(b.nitems, b.item_off, NC, b.items, b.counters);
+    return count_launch();
+}
+
+// ---------------------------------------------------------------- tile scan
+
+struct TileArgs {
+    const float* xs;           // rows, stride d_pad
+    const uint32_t* offsets;   // cone offsets (sparse mode)
+    const uint32_t* perm;      // row -> point id
+    const float* Y;            // queries, stride d
+    const int64_t* query_src;  // exclusion sources (nullable)
+    const uint2* items;        // sparse mode: (cone, group)
+    const uint32_t* n_items_dev;
+    const uint32_t* qcount;
+    const uint32_t* qoff;
+    const uint32_t* qlist;     // slot ids = q * S + s
+    uint32_t* counter;
+    uint64_t* partial;         // [Q * S * k]
+    uint32_t* status;
+    int64_t S;                 // slots per query
+    int64_t grid_w;
+    int64_t N, Q;              // dense mode sizes
+    int64_t n_groups, n_items_dense;
+    int d_pad, d, k, radius;
+    int dense;                 // 1: linear search items
+};
+
+struct ItemDesc {
+    uint32_t row0, row1;  // rows of the item
+    uint32_t qbeg, qn;    // slot list range (sparse) or first query and count (dense)
+    uint32_t chunk;       // dense: chunk index = slot offset
+};
+
+__device__ __forceinline__ ItemDesc load_item(const TileArgs& a, uint32_t item, int G)
+{
+    ItemDesc it;
+    if (a.dense) {
+        const uint32_t c = item / uint32_t(a.n_groups), g = item % uint32_t(a.n_groups);
+        it.row0 = c * BF_CHUNK_ROWS;
+        const int64_t e = int64_t(it.row0) + BF_CHUNK_ROWS;
+        it.row1 = uint32_t(e < a.N ? e : a.N);
+        it.qbeg = g * uint32_t(G);
+        const int64_t qe = int64_t(it.qbeg) + G;
+        it.qn = uint32_t((qe < a.Q ? qe : a.Q) - it.qbeg);
+        it.chunk = c;
+    } else {
+        const uint2 bg = a.items[item];
+        it.row0 = __ldg(a.offsets + bg.x);
+        it.row1 = __ldg(a.offsets + bg.x + 1);
+        const uint32_t cnt = a.qcount[bg.x];
+        it.qbeg = a.qoff[bg.x] + bg.y * uint32_t(G);
+        const uint32_t rest = cnt - bg.y * uint32_t(G);
+        it.qn = rest < uint32_t(G) ? rest : uint32_t(G);
+        it.chunk = 0;
+    }
+    return it;
+}
+
+template <int DPT, int KMAX, bool EXCL>
+__global__ void __launch_bounds__(TILE_THREADS) tile_scan_kernel(const TileArgs a)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* stage_buf = reinterpret_cast<float*>(smem_raw);
+    __shared__ __align__(8) uint64_t bars[TILE_STAGES];
+    __shared__ int4 meta[TILE_STAGES];  // (first row, rows or -1, item, last chunk of item)
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    const int TPR = a.d_pad / DPT;
+    const int G = TILE_THREADS / TPR;
+    const int RPC = TILE_STAGE_FLOATS / a.d_pad;
+    const int qs = tid / TPR, sub = tid % TPR;
+    const uint32_t n_items = a.dense ? uint32_t(a.n_items_dense) : *a.n_items_dev;
+
+    // producer state (thread 0 only)
+    bool done = false;
+    int cur_item = -1;
+    uint32_t cur = 0, cur_end = 0;
+    auto issue = [&](int s) {
+        while (!done && cur >= cur_end) {
+            const uint32_t it = atomicAdd(a.counter, 1u);
+            if (it >= n_items) {
+                done = true;
+                break;
+            }
+            const ItemDesc d = load_item(a, it, G);
+            cur_item = int(it);
+            cur = d.row0;
+            cur_end = d.row1;
+        }
+        if (done) {
+            meta[s] = make_int4(0, -1, -1, 0);
+            return;
+        }
+        const uint32_t n = cur_end - cur < uint32_t(RPC) ? cur_end - cur : uint32_t(RPC);
+        meta[s] = make_int4(int(cur), int(n), cur_item, cur + n == cur_end ? 1 : 0);
+        const uint32_t bytes = n * uint32_t(a.d_pad) * 4u;
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(&bars[s], bytes);
+        bulk_g2s(stage_buf + size_t(s) * TILE_STAGE_FLOATS, a.xs + size_t(cur) * a.d_pad, bytes, &bars[s]);
+        cur += n;
+    };
+
+    if (tid == 0) {
+        for (int s = 0; s < TILE_STAGES; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < TILE_STAGES; ++s) issue(s);
+    __syncthreads();
+
+    float4 qv[DPT / 4];
+    uint64_t list[KMAX];
+    int item = -1;
+    bool active = false;
+    int64_t slot = 0, src = -1;
+
+    int c = 0;
+    for (;; ++c) {
+        const int s = c % TILE_STAGES;
+        const int4 m = meta[s];
+        if (m.y < 0) break;
+        if (m.z != item) {
+            // first chunk of a new item: load this thread's query slice
+            item = m.z;
+            const ItemDesc d = load_item(a, uint32_t(item), G);
+            active = uint32_t(qs) < d.qn;
+            int64_t q = 0;
+            if (active) {
+                if (a.dense) {
+                    q = int64_t(d.qbeg) + qs;
+                    slot = q * a.S + d.chunk;
+                } else {
+                    slot = int64_t(a.qlist[d.qbeg + qs]);
+                    q = slot / a.S;
+                }
+            }
+            const float* y = a.Y + q * int64_t(a.d);
+#pragma unroll
+            for (int jj = 0; jj < DPT / 4; ++jj) {
+                const int cc = sub * DPT + jj * 4;
+                qv[jj].x = active && cc + 0 < a.d ? y[cc + 0] : 0.0f;
+                qv[jj].y = active && cc + 1 < a.d ? y[cc + 1] : 0.0f;
+                qv[jj].z = active && cc + 2 < a.d ? y[cc + 2] : 0.0f;
+                qv[jj].w = active && cc + 3 < a.d ? y[cc + 3] : 0.0f;
+            }
+            if (EXCL) src = active ? a.query_src[q] : -1;
+            topk_init<KMAX>(list, a.k);
+        }
+        const bool ok = mbar_wait_bounded(&bars[s], uint32_t((c / TILE_STAGES) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicOr(a.status, ST_TIMEOUT);
+                abort_flag = 1;
+            }
+            break;
+        }
+        const float* base = stage_buf + size_t(s) * TILE_STAGE_FLOATS + sub * DPT;
+        const int n = m.y;
+        for (int r = 0; r < n; r += 4) {
+            // canonical piece tree (osann_device.cuh), four rows at a time;
+            // rows past the chunk read stale stage memory and are discarded
+            float acc[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float4* row = reinterpret_cast<const float4*>(base + (r + u) * a.d_pad);
+                float cpart[DPT / 4];
+#pragma unroll
+                for (int jj = 0; jj < DPT / 4; ++jj) cpart[jj] = sq4(row[jj], qv[jj]);
+                acc[u] = pair_tree<DPT / 4>(cpart);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = lane_tree(acc[u], TPR);
+            if (active && sub == 0) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (r + u < n) {
+                        const uint32_t row = uint32_t(m.x + r + u);
+                        if (EXCL) {
+                            const uint32_t id = a.perm ? __ldg(a.perm + row) : row;
+                            const int64_t dr = int64_t(id) / a.grid_w - src / a.grid_w;
+                            const int64_t dc = int64_t(id) % a.grid_w - src % a.grid_w;
+                            const int64_t ch = (dr < 0 ? -dr : dr) > (dc < 0 ? -dc : dc) ? (dr < 0 ? -dr : dr)
+                                                                                          : (dc < 0 ? -dc : dc);
+                            if (src < 0 || ch > a.radius) {
+                                const uint64_t v = pack_di(acc[u], id);
+                                if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
+                            }
+                        } else if (acc[u] <= di_dist(list[KMAX - 1])) {
+                            const uint32_t id = a.perm ? __ldg(a.perm + row) : row;
+                            const uint64_t v = pack_di(acc[u], id);
+                            if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
+                        }
+                    }
+                }
+            }
+        }
+        if (m.w && active && sub == 0) {
+            uint64_t* out = a.partial + slot * a.k;
+#pragma unroll
+            for (int j = 0; j < KMAX; ++j)
+                if (j >= KMAX - a.k) out[j - (KMAX - a.k)] = list[j];
+        }
+        __syncthreads();
+        if (tid == 0) issue(s);
+    }
+    if (abort_flag) {
+        if (tid == 0)
+            for (int i = 0; i < TILE_STAGES; ++i) {
+                const int cc = c + i, ss = cc % TILE_STAGES;
+                if (meta[ss].y >= 0) mbar_wait_bounded(&bars[ss], uint32_t((cc / TILE_STAGES) & 1));
+            }
+        __syncthreads();
+    }
+}
+
+template <int DPT, int KMAX, bool EXCL>
+static int launch_tile_t(const TileArgs& a, cudaStream_t st, int num_sms)
+{
+    const int smem = TILE_STAGES * TILE_STAGE_FLOATS * 4;
+    auto kern = tile_scan_kernel<DPT, KMAX, EXCL>;
+    static int blocks_per_sm = 0;
+    if (blocks_per_sm == 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TILE_THREADS, smem);
+        if (blocks_per_sm < 1) blocks_per_sm = 1;
+    }
+    kern<<<unsigned(num_sms * blocks_per_sm), TILE_THREADS, smem, st>>>(a);
+    return count_launch();
+}
+
+template <int DPT, bool EXCL>
+static int launch_tile_k(const TileArgs& a, cudaStream_t st, int num_sms)
+{
+    if (a.k <= 1) return launch_tile_t<DPT, 1, EXCL>(a, st, num_sms);
+    if (a.k <= 4) return launch_tile_t<DPT, 4, EXCL>(a, st, num_sms);
+    if (a.k <= 16) return launch_tile_t<DPT, 16, EXCL>(a, st, num_sms);
+    return launch_tile_t<DPT, 32, EXCL>(a, st, num_sms);
+}
+
+static int launch_tile_any(const TileArgs& a, cudaStream_t st, int num_sms)
+{
+    const bool excl = a.query_src != nullptr;
+    if (a.d_pad == 16) return excl ? launch_tile_k<16, true>(a, st, num_sms) : launch_tile_k<16, false>(a, st, num_sms);
+    return excl ? launch_tile_k<32, true>(a, st, num_sms) : launch_tile_k<32, false>(a, st, num_sms);
+}
+
+int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y, int d,
+                     int64_t slots_per_query, int k, const int64_t* query_src, int64_t grid_w, int radius,
+                     const BatchedBuffers& b, int group, uint64_t* partial, uint32_t* status, cudaStream_t st,
+                     int num_sms)
+{
+    (void)group;
+    TileArgs a{};
+    a.xs = xs;
+    a.offsets = offsets;
+    a.perm = perm;
+    a.Y = Y;
+    a.query_src = query_src;
+    a.items = b.items;
+    a.n_items_dev = b.n_items_dev;
+    a.qcount = b.qcount;
+    a.qoff = b.qoff;
+    a.qlist = b.qlist;
+    a.counter = b.counters;
+    a.partial = partial;
+    a.status = status;
+    a.S = slots_per_query;
+    a.grid_w = grid_w;
+    a.d_pad = d_pad;
+    a.d = d;
+    a.k = k;
+    a.radius = radius;
+    a.dense = 0;
+    return launch_tile_any(a, st, num_sms);
+}
+
+// ---------------------------------------------------------------- merge
+
+template <int KMAX>
+__global__ void __launch_bounds__(128) merge_kernel(const uint64_t* __restrict__ partial, int64_t Q, int64_t S, int k,
+                                                    int64_t* __restrict__ out_ids, float* __restrict__ out_d)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    if (q >= Q) return;
+    const uint64_t* p = partial + q * S * k;
+    const int64_t n = S * k;
+    // each lane keeps the k best of its share, then k rounds of warp minimum
+    uint64_t list[KMAX];
+    topk_init<KMAX>(list, k);
+    for (int64_t i = lane; i < n; i += 32) {
+        const uint64_t v = p[i];
+        if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
+    }
+    for (int j = 0; j < k; ++j) {
+        const uint64_t head = topk_head<KMAX>(list, k);
+        const uint64_t best = warp_min_u64(head);
+        if (head == best && best != EMPTY_DI) topk_remove<KMAX>(list, k, best);
+        if (lane == 0) {
+            const uint32_t id = di_id(best);
+            out_ids[q * k + j] = id == 0xFFFFFFFFu ? int64_t(-1) : int64_t(id);
+            out_d[q * k + j] = di_dist(best);
+        }
+    }
+}
+
+int launch_merge(const uint64_t* partial, int64_t Q, int64_t S, int k, const uint32_t* perm_or_null, int64_t* out_ids,
+                 float* out_d, cudaStream_t st)
+{
+    (void)perm_or_null;
+    if (Q == 0) return 0;
+    const unsigned blocks = unsigned((Q * 32 + 127) / 128);
+    if (k <= 1) merge_kernel<1><<<blocks, 128, 0, st>>>(partial, Q, S, k, out_ids, out_d);
+    else if (k <= 4) merge_kernel<4><<<blocks, 128, 0, st>>>(partial, Q, S, k, out_ids, out_d);
+    else if (k <= 16) merge_kernel<16><<<blocks, 128, 0, st>>>(partial, Q, S, k, out_ids, out_d);
+    else merge_kernel<32><<<blocks, 128, 0, st>>>(partial, Q, S, k, out_ids, out_d);
+    return count_launch();
+}
+
+// ---------------------------------------------------------------- linear search
+
+size_t bruteforce_ws_bytes(int64_t N, int d_pad, int64_t Q, int k)
+{
+    const int64_t S = (N + BF_CHUNK_ROWS - 1) / BF_CHUNK_ROWS;
+    (void)d_pad;
+    return size_t(Q) * size_t(S) * size_t(k) * 8 + 256;
+}
+
+__global__ void fill_u64_kernel(uint64_t* __restrict__ p, int64_t n, uint64_t v)
+{
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+        p[i] = v;
+}
+
+int launch_bruteforce_rows(const float* xs, const uint32_t* perm, int64_t N, int d_pad, const float* Y, int d,
+                           int64_t Q, int k, const int64_t* query_src, int64_t grid_w, int radius, void* ws,
+                           uint32_t* counter, int64_t* out_ids, float* out_d, uint32_t* status, cudaStream_t st,
+                           int num_sms)
+{
+    if (Q == 0) return 0;
+    const int64_t S = (N + BF_CHUNK_ROWS - 1) / BF_CHUNK_ROWS;
+    uint64_t* partial = static_cast<uint64_t*>(ws);
+    const int64_t np = Q * S * k;
+    int64_t fb = (np + 255) / 256;
+    if (fb > 8 * num_sms) fb = 8 * num_sms;
+    if (fb < 1) fb = 1;
+    fill_u64_kernel<<<unsigned(fb), 256, 0, st>>>(partial, np, EMPTY_DI);
+    int rc = count_launch();
+    if (rc) return rc;
+    if (N > 0) {
+        const int DPT = d_pad == 16 ? 16 : 32;
+        const int G = TILE_THREADS / (d_pad / DPT);
+        cudaMemsetAsync(counter, 0, 4, st);
+        TileArgs a{};
+        a.xs = xs;
+        a.perm = perm;
+        a.Y = Y;
+        a.query_src = query_src;
+        a.counter = counter;
+        a.partial = partial;
+        a.status = status;
+        a.S = S;
+        a.grid_w = grid_w;
+        a.N = N;
+        a.Q = Q;
+        a.n_groups = (Q + G - 1) / G;
+        a.n_items_dense = S * a.n_groups;
+        a.d_pad = d_pad;
+        a.d = d;
+        a.k = k;
+        a.radius = radius;
+        a.dense = 1;
+        if ((rc = launch_tile_any(a, st, num_sms))) return rc;
+    }
+    return launch_merge(partial, Q, S, k, nullptr, out_ids, out_d, st);
+}
+
+}  // namespace osann

@@ -1,0 +1,70 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports
+every entry point include/osann.h declares.  Only host-side calls are made
+here (no kernel runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1509_03453_gb300 import _lib, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "osann.h")
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set()
+    for line in text.splitlines():
+        if line.lstrip().startswith("#"):
+            continue
+        names.update(re.findall(r"\b(osann_\w+)\s*\(", line))
+    names.discard("osann_alloc_fn")
+    names.discard("osann_free_fn")
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return _lib.load()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("osann_build", "osann_search", "osann_free", "osann_search_excl", "osann_bruteforce",
+                 "osann_probes", "osann_keys", "osann_export"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = _declared()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+    # the binding covers exactly the declared entry points
+    assert set(_lib.SIGNATURES) == names
+
+
+def test_host_only_entry_points(L):
+    out = ctypes.c_int64()
+    assert L.osann_num_cones(3, 2, ctypes.byref(out)) == 0 and out.value == 12
+    assert L.osann_num_cones(16, 4, ctypes.byref(out)) == 0 and out.value == 29120
+    assert L.osann_num_cones(128, 3, ctypes.byref(out)) == 0 and out.value == 2731008
+    assert L.osann_num_cones(3, 4, ctypes.byref(out)) == -1          # L > d
+    assert L.osann_num_cones(64, 16, ctypes.byref(out)) == -2        # N_C >= 2^31
+    h = ctypes.c_void_p()
+    assert L.osann_build(None, 10, 4, 2, None, ctypes.byref(h)) == -1
+    assert b"invalid" in L.osann_last_error()
+    assert L.osann_search(None, None, 1, 1, 1, 0, None, 0, None, None, None) == -1
+    assert L.osann_free(None) == 0
+    assert L.osann_search_workspace_size(None, 1, 1, 1, 0) == 0
+    assert L.osann_stats_get(99, None, None) == -1
+    assert L.osann_launch_count() >= 0
+
+
+def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "_lib", None)
+    monkeypatch.setattr(build, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError, match="not found"):
+        _lib.load()

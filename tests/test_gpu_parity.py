@@ -1,0 +1,148 @@
+"""GPU parity against the CPU oracle at sizes the oracle finishes in seconds.
+
+Every call goes through the C ABI (the ctypes binding).  Cases span several
+tiles and ragged tails: N is never a multiple of the stage, chunk or group
+sizes, and every workload family of the benchmark appears at reduced size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import assert_knn_match, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osann():
+    import paper_1509_03453_gb300 as m
+    from paper_1509_03453_gb300 import build
+    build.build()
+    m.load()
+    return m
+
+
+def _gauss(n, d, seed):
+    return np.random.default_rng(seed).standard_normal((n, d), dtype=np.float32)
+
+
+def _workloads():
+    from paper_1509_03453_gb300 import datagen
+    out = {}
+    w = datagen.workload("gauss16")
+    out["gauss16"] = (w["X"], w["Y"], 2, [1, 4, 16, 64], 1, None)
+    out["gauss32"] = (_gauss(100_003, 32, 1002), _gauss(300, 32, 2002), 2, [1, 16, 64, 256], 1, None)
+    out["gauss32_L3"] = (_gauss(100_003, 32, 1002), _gauss(300, 32, 2002), 3, [4, 64], 1, None)
+    img = datagen.patch_image(1003, 192)
+    X = datagen.patches(img)
+    rng = np.random.default_rng(7)
+    src = np.sort(rng.choice(X.shape[0], 250, replace=False)).astype(np.int64)
+    out["patch64"] = (X, X[src].copy(), 3, [4, 16, 64], 4, (src, 192 - 8 + 1, 8))
+    out["desc128"] = (datagen.descriptors(60_001, 1004), datagen.descriptor_queries(200, 2004), 3,
+                      [8, 32, 128], 10, None)
+    return out
+
+
+WL = None
+
+
+def wl(name):
+    global WL
+    if WL is None:
+        WL = _workloads()
+    return WL[name]
+
+
+NAMES = ["gauss16", "gauss32", "gauss32_L3", "patch64", "desc128"]
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_keys_and_buckets_bit_exact(osann, name):
+    X, Y, L, Ps, k, ex = wl(name)
+    ref = oracle.Index(X, L)
+    idx = osann.Index(to_dev(X), L)
+    assert idx.NC == ref.NC
+    keys, offsets, perm = (to_np(t) for t in idx.export())
+    assert np.array_equal(keys, ref.keys.astype(np.int64))
+    assert np.array_equal(offsets, ref.offsets.astype(np.int64))
+    assert np.array_equal(perm, ref.perm.astype(np.int64))
+    assert idx.max_bucket == int(np.diff(ref.offsets.astype(np.int64)).max())
+    # the stateless key entry point agrees too, on queries
+    assert np.array_equal(to_np(osann.keys(to_dev(Y), L)), oracle.keys(Y, L).astype(np.int64))
+    assert idx.status() == 0
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_query_order_and_probes_bit_exact(osann, name):
+    X, Y, L, Ps, k, ex = wl(name)
+    idx = osann.Index(to_dev(X), L)
+    order, signs = (to_np(t) for t in osann.query_order(to_dev(Y)))
+    d = Y.shape[1]
+    for q in range(Y.shape[0]):
+        assert order[q].tolist() == oracle.magnitude_order(Y[q]).tolist()
+        bits = [(int(signs[q, c // 32]) >> (c % 32)) & 1 for c in range(d)]
+        assert bits == (Y[q] >= 0).astype(int).tolist()
+    for P in sorted(set(Ps + [oracle.binom(d, L) + 37])):
+        pr = to_np(idx.probes(to_dev(Y), P))
+        for q in range(Y.shape[0]):
+            assert np.array_equal(pr[q], oracle.probes(Y[q], L, P).astype(np.int64)), (name, P, q)
+
+
+@pytest.mark.parametrize("name", NAMES)
+@pytest.mark.parametrize("path", ["plain", "batched"])
+def test_search_matches_oracle(osann, name, path):
+    X, Y, L, Ps, k, ex = wl(name)
+    ref = oracle.Index(X, L)
+    idx = osann.Index(to_dev(X), L)
+    Yd = to_dev(Y)
+    for P in Ps:
+        if ex is None:
+            oids, od = ref.search(Y, P, k)
+            gids, gd = idx.search(Yd, P, k, path=path)
+        else:
+            src, gw, rad = ex
+            oids, od = ref.search(Y, P, k, query_src=src, grid_w=gw, radius=rad)
+            gids, gd = idx.search(Yd, P, k, path=path, query_src=to_dev(src), grid_w=gw, radius=rad)
+        assert_knn_match(X, Y, to_np(gids), to_np(gd), oids, od)
+    assert idx.status() == 0
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_paths_bit_identical_and_deterministic(osann, name):
+    """Plain, batched and linear search evaluate the same fp32 expression."""
+    X, Y, L, Ps, k, ex = wl(name)
+    idx = osann.Index(to_dev(X), L)
+    Yd = to_dev(Y)
+    kw = {}
+    if ex is not None:
+        kw = dict(query_src=to_dev(ex[0]), grid_w=ex[1], radius=ex[2])
+    P = Ps[-1]
+    a = idx.search(Yd, P, k, path="plain", **kw)
+    b = idx.search(Yd, P, k, path="batched", **kw)
+    c = idx.search(Yd, P, k, path="batched", **kw)
+    for u, v in ((a, b), (b, c)):
+        assert np.array_equal(to_np(u[0]), to_np(v[0]))
+        assert np.array_equal(to_np(u[1]).view(np.uint32), to_np(v[1]).view(np.uint32))
+    # visiting every cone is linear search, bit for bit
+    full = idx.search(Yd, idx.NC, k, path="batched", **kw)
+    bf = idx.bruteforce(Yd, k, **kw)
+    assert np.array_equal(to_np(full[0]), to_np(bf[0]))
+    assert np.array_equal(to_np(full[1]).view(np.uint32), to_np(bf[1]).view(np.uint32))
+
+
+@pytest.mark.parametrize("name", NAMES)
+def test_bruteforce_matches_oracle(osann, name):
+    X, Y, L, Ps, k, ex = wl(name)
+    idx = osann.Index(to_dev(X), L)
+    kw, okw = {}, {}
+    if ex is not None:
+        kw = dict(query_src=to_dev(ex[0]), grid_w=ex[1], radius=ex[2])
+        okw = dict(query_src=ex[0], grid_w=ex[1], radius=ex[2])
+    sub = slice(0, min(120, Y.shape[0]))
+    Ys = np.ascontiguousarray(Y[sub])
+    if ex is not None:
+        kw["query_src"] = to_dev(ex[0][sub])
+        okw["query_src"] = ex[0][sub]
+    gids, gd = idx.bruteforce(to_dev(Ys), k, **kw)
+    oids, od = oracle.bruteforce(X, Ys, k, **okw)
+    assert_knn_match(X, Ys, to_np(gids), to_np(gd), oids, od)
