@@ -45,7 +45,7 @@ def assert_knn_match(X, Y, gids, gd, oids, od, rel_d=REL_D, rel_gap=REL_GAP):
     qn2 = (np.asarray(Y, np.float64) ** 2).sum(1)[:, None] * np.ones_like(d64)
     valid = gids >= 0
     floor = 1e-7 * qn2
-    err = np.abs(gd - d64)
+    err = np.where(valid, np.abs(np.where(valid, gd, 0.0) - np.where(valid, d64, 0.0)), 0.0)
     bad = valid & (err > rel_d * d64 + floor)
     assert not bad.any(), f"distance error: {np.argwhere(bad)[:5]} gpu={gd[bad][:5]} fp64={d64[bad][:5]}"
     mism = valid & (gids != oids)
