@@ -142,6 +142,26 @@ int osann_search_excl(const osann_index *index, const float *d_queries, const in
                       int32_t P, int32_t k, int64_t grid_w, int32_t radius, int32_t path, void *d_ws,
                       size_t ws_bytes, int64_t *d_ids, float *d_sqdists, void *stream);
 
+/* Search without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * at query time -- a plugin inside a host process that owns the device
+ * allocator, a latency-critical thread that must not take allocator locks
+ * or synchronise, or a program that reserved all device memory up front.
+ * It runs the plain path of osann_search (same results, bit for bit) with
+ * its scratch in a fixed 32 MiB device array compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ * Inputs and outputs are as for osann_search; nothing is allocated, freed
+ * or returned to an allocator.  The scratch needed is
+ * osann_search_workspace_size(index, Q, P, k, OSANN_PATH_PLAIN); calls that
+ * need more than 32 MiB fail with OSANN_ERR_INVALID (split the batch).
+ * The first call on a device looks up the array's device address and the
+ * library's per-device tables; make it before any stream capture.  All
+ * calls share the one array, which keeps the last call's contents (every
+ * byte a call reads it has written first): calls that overlap on the GPU,
+ * on any streams, race and must be serialised by the caller. */
+int osann_search_noalloc(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k,
+                         int64_t *d_ids, float *d_sqdists, void *stream);
+
 /* Exact linear search (Eq. 1 over all N points of the index), fp32 direct
  * differences, cuBLAS-free: the ground truth for recall.  d_query_src may
  * be NULL (no exclusion).  Workspace: osann_bruteforce_workspace_size. */

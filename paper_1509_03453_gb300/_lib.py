@@ -49,6 +49,8 @@ SIGNATURES = {
     "osann_search_excl": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32,
                                     c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p,
                                     c.c_void_p, c.c_void_p]),
+    "osann_search_noalloc": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p,
+                                       c.c_void_p, c.c_void_p]),
     "osann_bruteforce_workspace_size": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32]),
     "osann_bruteforce": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int64,
                                    c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),

@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libosann.so")
-SOURCES = ["osann.cu", "keys.cu", "buckets.cu", "probes.cu", "scan_plain.cu", "scan_batched.cu"]
+SOURCES = ["osann.cu", "keys.cu", "buckets.cu", "probes.cu", "scan_plain.cu", "scan_batched.cu",
+           "static_search.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
