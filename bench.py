@@ -113,6 +113,34 @@ def recall1(ids, d2, gt_ids, gt_d2):
     return float(np.mean(hit | near))
 
 
+def run_profile(args):
+    """Only the warm-up and timed steps (fixed P, chosen path): the command
+    the ncu captures under profiles/ run, so that the launch list holds
+    exactly the kernels of the step."""
+    import torch
+
+    import paper_1509_03453_gb300 as osann
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    osann.load()
+    X, Y = gen(0)
+    Xd = torch.from_numpy(X).to(dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    P = args.P or 224
+    times = []
+    for i in range(args.warmup + args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ix = osann.Index(Xd, L)
+        ix.search(Yd, P, K, path=args.path)
+        b.record()
+        b.synchronize()
+        ix.close()
+        if i >= args.warmup:
+            times.append(a.elapsed_time(b))
+    print(json.dumps({"profile_run": True, "P": P, "path": args.path, "ms_per_step": float(np.mean(times))}))
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -399,11 +427,15 @@ def main():
     ap.add_argument("--P", type=int, default=0, help="fixed probe budget (default: recall ladder)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.profile:
+        run_profile(args)
     else:
         run_gpu(args)
 
