@@ -428,7 +428,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -42,12 +42,16 @@ extern "C" {
 /* Search paths (same results, different schedules). */
 #define OSANN_PATH_AUTO 0    /* batched when enough queries share a cone */
 #define OSANN_PATH_PLAIN 1   /* one CTA per query scanning its cones */
-#define OSANN_PATH_BATCHED 2 /* cone-major work list, persistent tile scan */
+#define OSANN_PATH_BATCHED 2 /* cone-major work list, persistent fp32 tile scan */
+#define OSANN_PATH_BF16 3    /* cone-major work list, bf16 tensor-core screening with a
+                                certified error bound, exact fp32 rerank (d <= 128) */
 
 /* Status flags returned by osann_status. */
 #define OSANN_STATUS_NONFINITE_DATA 1u
 #define OSANN_STATUS_NONFINITE_QUERY 2u
 #define OSANN_STATUS_TIMEOUT 4u
+#define OSANN_STATUS_BOUND 16u /* a debug check of the screening error bound failed
+                                  (only with OSANN_DEBUG_CHECKS=1 in the environment) */
 
 typedef struct osann_index osann_index; /* opaque; owns its device buffers */
 
@@ -123,7 +127,9 @@ size_t osann_search_workspace_size(const osann_index *index, int64_t Q, int32_t 
 /* ROSANNA search with one basis (Algorithm 1, R = 1): hash each query,
  * visit its first P_eff = min(P, N_C) cones in the order of osann_probes and
  * return the k nearest candidates by exact squared Euclidean distance
- * (Eq. 1, fp32 direct differences), ordered by (distance, id).
+ * (Eq. 1, fp32 direct differences), ordered by (distance, id).  All paths
+ * return the same bits: OSANN_PATH_BF16 only screens candidates with a
+ * proven error bound before the same fp32 evaluation.
  * d_queries: Q x d fp32.  d_ids: Q x k int64 (point ids, -1 pad).
  * d_sqdists: Q x k fp32 (+inf pad).  d_ws/ws_bytes: workspace of at least
  * osann_search_workspace_size(...) bytes, 256-byte aligned (NULL: allocated
@@ -169,6 +175,12 @@ size_t osann_bruteforce_workspace_size(const osann_index *index, int64_t Q, int3
 int osann_bruteforce(const osann_index *index, const float *d_queries, const int64_t *d_query_src, int64_t Q,
                      int32_t k, int64_t grid_w, int32_t radius, void *d_ws, size_t ws_bytes, int64_t *d_ids,
                      float *d_sqdists, void *stream);
+
+/* Counters of the tensor-core screening path since the last call (then
+ * cleared), after synchronising `stream`: out4[0] survivors reranked,
+ * out4[1] queries whose survivor list overflowed and were rescanned in full,
+ * out4[2] / out4[3] error-bound checks made / failed (debug checks only). */
+int osann_screen_stats(const osann_index *index, void *stream, int64_t *out4);
 
 /* Synchronise `stream`, return the index's device status flags
  * (OSANN_STATUS_*) accumulated since the last call, and clear them. */

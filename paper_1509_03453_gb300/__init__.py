@@ -189,6 +189,12 @@ class Index:
         m = 0xFFFFFFFF
         return k.to(torch.int64) & m, o.to(torch.int64) & m, p.to(torch.int64) & m
 
+    def screen_stats(self, stream=None) -> dict:
+        """Counters of the tensor-core screening path since the last call."""
+        out = (ctypes.c_int64 * 4)()
+        _lib.check(load().osann_screen_stats(self._h, _stream_ptr(stream), out))
+        return {"survivors": out[0], "fallbacks": out[1], "bound_checks": out[2], "bound_violations": out[3]}
+
     def status(self, stream=None) -> int:
         """Synchronise and return (and clear) the device status flags."""
         f = ctypes.c_uint32()

@@ -22,12 +22,13 @@ ERRORS = {
     -5: "CUDA error",
     -6: "device wait timed out",
 }
-PATHS = {"auto": 0, "plain": 1, "batched": 2}
+PATHS = {"auto": 0, "plain": 1, "batched": 2, "bf16": 3}
 STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
           "plain_scan", "bruteforce"]
 STATUS_NONFINITE_DATA = 1
 STATUS_NONFINITE_QUERY = 2
 STATUS_TIMEOUT = 4
+STATUS_BOUND = 16
 
 # exported symbols and their signatures: (restype, argtypes)
 SIGNATURES = {
@@ -55,6 +56,7 @@ SIGNATURES = {
     "osann_bruteforce": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int64,
                                    c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
     "osann_status": (c.c_int, [c.c_void_p, c.c_void_p, c.POINTER(c.c_uint32)]),
+    "osann_screen_stats": (c.c_int, [c.c_void_p, c.c_void_p, c.POINTER(c.c_int64)]),
     "osann_last_error": (c.c_char_p, []),
     "osann_stats_enable": (c.c_int, [c.c_int]),
     "osann_stats_reset": (c.c_int, []),

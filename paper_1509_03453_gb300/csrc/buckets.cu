@@ -308,7 +308,8 @@ int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t
 template <int LPV, bool VEC>
 __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restrict__ X, int64_t N, int d, int d_pad,
                                                          const uint32_t* __restrict__ perm, float* __restrict__ xs,
-                                                         __nv_bfloat16* __restrict__ xb, float* __restrict__ norm2)
+                                                         __nv_bfloat16* __restrict__ xb, float* __restrict__ norm2,
+                                                         float4* __restrict__ rowstat, float Bn)
 {
     const int lane = threadIdx.x & 31;
     const int glane = lane & (LPV - 1);
@@ -353,12 +354,15 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restric
         }
 #pragma unroll
         for (int m = LPV / 2; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
-        if (live && glane == 0) norm2[r] = s;
+        if (live && glane == 0) {
+            norm2[r] = s;
+            if (rowstat) rowstat[r] = make_float4(s * (1.0f - Bn), sqrtf(s), s, 0.0f);
+        }
     }
 }
 
 int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
-                       __nv_bfloat16* xb, float* norm2, cudaStream_t st, int num_sms)
+                       __nv_bfloat16* xb, float* norm2, float4* rowstat, float Bn, cudaStream_t st, int num_sms)
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -370,9 +374,9 @@ int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32
     const dim3 g(static_cast<unsigned>(blocks)), b(256u);
 #define OSANN_GATHER(LP)                                                                                 \
     if (vec)                                                                                             \
-        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2);              \
+        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, Bn); \
     else                                                                                                 \
-        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2);
+        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, Bn);
     switch (lpv) {
     case 4: OSANN_GATHER(4); break;
     case 8: OSANN_GATHER(8); break;

@@ -6,7 +6,9 @@
 // step of the method runs in the kernels of keys.cu, buckets.cu, probes.cu,
 // scan_plain.cu and scan_batched.cu; this file only sequences them.
 #include <atomic>
+#include <cmath>
 #include <cstdarg>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -206,10 +208,37 @@ struct osann_index {
     uint32_t* perm = nullptr;
     float* xs = nullptr;
     float* norm2 = nullptr;
-    uint32_t* status = nullptr;  // [0] flags, [1] largest cone
+    __nv_bfloat16* xb = nullptr;  // bf16 copy of xs (tensor-core screening)
+    float4* rowstat = nullptr;    // per row (1-B)|x|^2, |x|, |x|^2; N + TC_N rows
+    uint32_t* status = nullptr;   // [0] flags, [1] largest cone
+    unsigned long long* diag = nullptr;  // screening counters (survivors, fallbacks, checks, violations)
     uint64_t* binom = nullptr;
+    float cdot2 = 0.f, Bn = 0.f;  // screening error-bound coefficients
+    bool tc_ok = false;           // tensor map encoded
+    alignas(64) unsigned char tmap[128];
     std::vector<std::pair<void*, size_t>> allocs;
 };
+
+// Coefficients of the screening bound E = cdot2 |q||x| + Bn (|q|^2 + |x|^2):
+// bf16 rounding of both operands (unit roundoff u = 2^-8) and the fp32
+// accumulation of d_pad products (taken as d_pad 2^-20, sixteen times the
+// round-to-nearest bound), the fp32 norms (d_pad 2^-23) and a cushion of
+// 4e-6 for the fp32 rounding of the exact distances compared at the end.
+static void screen_coefficients(int d_pad, float* cdot2, float* Bn)
+{
+    const double u = std::ldexp(1.0, -8);
+    const double c = 2 * u + u * u + d_pad * std::ldexp(1.0, -20) * (1 + u) * (1 + u);
+    *cdot2 = float(2 * c);
+    *Bn = float(d_pad * std::ldexp(1.0, -23) + 4e-6);
+}
+
+// OSANN_DEBUG_CHECKS=1 makes the screening kernel verify its error bound
+// against an fp32 dot product for one column per thread and tile.
+static int debug_checks()
+{
+    const char* e = std::getenv("OSANN_DEBUG_CHECKS");
+    return (e && e[0] && e[0] != '0') ? 1 : 0;
+}
 
 static void index_release(osann_index* ix)
 {
@@ -252,17 +281,22 @@ static int pad_dim(int d)
 
 static inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
+constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat)
+
 // ---------------------------------------------------------------- workspace
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
+    size_t yb, qstat, ubits, scnt, surv;
     size_t total;
     int64_t max_items;
 };
 
+enum SearchMode { MODE_PLAIN = 0, MODE_BATCHED = 1, MODE_BF16 = 2 };
+
 static int group_size(int d_pad) { return 128 / (d_pad == 16 ? 1 : d_pad / 32); }
 
-static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, bool batched)
+static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, int mode)
 {
     WsLayout w{};
     size_t off = 0;
@@ -274,13 +308,13 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
     w.qorder = take(size_t(Q) * ix->d);
     w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
-    if (batched) {
-        const int G = group_size(ix->d_pad);
+    if (mode != MODE_PLAIN) {
+        const int G = mode == MODE_BF16 ? TC_GROUP : group_size(ix->d_pad);
         const int64_t n = Q * P_eff;
         int64_t mi = n / G + ix->NC + 1;
         if (mi > n) mi = n;
         w.max_items = mi;
-        w.partial = take(size_t(n) * k * 8);
+        if (mode == MODE_BATCHED) w.partial = take(size_t(n) * k * 8);
         w.qcount = take(size_t(ix->NC + 1) * 4);
         w.qoff = take(size_t(ix->NC + 1) * 4);
         w.fill = take(size_t(ix->NC + 1) * 4);
@@ -291,15 +325,25 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         w.counters = take(256);
         w.scan_temp = take(batched_scan_temp_bytes(ix->NC));
     }
+    if (mode == MODE_BF16) {
+        w.yb = take(size_t(Q) * ix->d_pad * 2);
+        w.qstat = take(size_t(Q) * 16);
+        w.ubits = take(size_t(Q) * 4);
+        w.scnt = take(size_t(Q) * 4);
+        w.surv = take(size_t(Q) * TC_SURV_CAP * 4);
+    }
     w.total = off + 256;
     return w;
 }
 
-static bool choose_batched(const osann_index* ix, int64_t Q, int64_t P_eff, int path)
+static int choose_mode(const osann_index* ix, int64_t Q, int64_t P_eff, int path)
 {
-    if (path == OSANN_PATH_PLAIN) return false;
-    if (path == OSANN_PATH_BATCHED) return true;
-    return double(Q) * double(P_eff) >= 16.0 * double(ix->NC);
+    if (path == OSANN_PATH_PLAIN) return MODE_PLAIN;
+    if (path == OSANN_PATH_BATCHED) return MODE_BATCHED;
+    if (path == OSANN_PATH_BF16) return MODE_BF16;
+    const double per_cone = double(Q) * double(P_eff) / double(ix->NC);
+    if (ix->tc_ok && per_cone >= 64.0) return MODE_BF16;
+    return per_cone >= 16.0 ? MODE_BATCHED : MODE_PLAIN;
 }
 
 // ---------------------------------------------------------------- C ABI
@@ -426,13 +470,18 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     ix->perm = index_alloc<uint32_t>(ix, size_t(N));
     ix->xs = index_alloc<float>(ix, size_t(N) * ix->d_pad);
     ix->norm2 = index_alloc<float>(ix, size_t(N));
+    ix->xb = index_alloc<__nv_bfloat16>(ix, size_t(N) * ix->d_pad);
+    ix->rowstat = index_alloc<float4>(ix, size_t(N) + TC_N_ROWS);
     ix->status = index_alloc<uint32_t>(ix, 64);
+    ix->diag = index_alloc<unsigned long long>(ix, 8);
+    screen_coefficients(ix->d_pad, &ix->cdot2, &ix->Bn);
     const size_t counts_bytes = al256(size_t(NC + 1) * 4);
     const size_t scan_bytes = al256(scan_temp_bytes(NC + 1));
     const size_t radix_bytes = al256(radix_temp_bytes(N, NC));
     const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes;
     char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
-    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->norm2 || !ix->status || !temp) {
+    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->norm2 || !ix->xb || !ix->rowstat ||
+        !ix->status || !ix->diag || !temp) {
         if (temp) dev_free(temp, temp_bytes, st);
         index_release(ix);
         set_error("osann_build: device allocation failed");
@@ -443,6 +492,8 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     void* radix_temp = temp + counts_bytes + scan_bytes;
 
     cudaMemsetAsync(ix->status, 0, 64 * 4, st);
+    cudaMemsetAsync(ix->diag, 0, 8 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(ix->rowstat + N, 0, TC_N_ROWS * sizeof(float4), st);
     cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
     {
         StageScope s(OSANN_STAGE_DATA_KEYS, st);
@@ -456,7 +507,8 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_GATHER, st);
-        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, nullptr, ix->norm2, st, ix->num_sms);
+        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->xb, ix->norm2, ix->rowstat, ix->Bn, st,
+                                ix->num_sms);
     }
     if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st);
     dev_free(temp, temp_bytes, st);
@@ -480,6 +532,9 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     cudaMemsetAsync(ix->status, 0, 4, st);
     ix->max_bucket = host_status[1];
+    static_assert(sizeof(ix->tmap) >= 128, "tensor map storage");
+    ix->tc_ok = tc_map_bytes() <= sizeof(ix->tmap) && ix->d_pad <= 128 &&
+                tc_encode_rows_map(ix->tmap, ix->xb, N, ix->d_pad) == 0;
     *out = ix;
     return OSANN_OK;
 }
@@ -541,8 +596,9 @@ int osann_status(const osann_index* ix, void* stream, uint32_t* flags)
 size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path)
 {
     if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K) return 0;
+    if (path < 0 || path > OSANN_PATH_BF16) return 0;
     const int64_t P_eff = P < ix->NC ? P : ix->NC;
-    return ws_layout(ix, Q, P_eff, k, choose_batched(ix, Q, P_eff, path)).total;
+    return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path)).total;
 }
 
 static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_eff, const WsLayout& L, char* w,
@@ -571,7 +627,7 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
     if (Q == 0) return OSANN_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int64_t P_eff = P < ix->NC ? P : ix->NC;
-    const WsLayout L = ws_layout(ix, Q, P_eff, 1, false);
+    const WsLayout L = ws_layout(ix, Q, P_eff, 1, MODE_PLAIN);
     void* owned = nullptr;
     if (!d_ws) {
         owned = d_ws = dev_alloc(L.total, st);
@@ -597,7 +653,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
                        int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
                        float* dists, void* stream)
 {
-    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > 2 ||
+    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_BF16 ||
         (Q > 0 && (!Y || !ids || !dists))) {
         set_error("osann_search: invalid arguments (Q=%lld P=%d k=%d path=%d)", (long long)Q, P, k, path);
         return OSANN_ERR_INVALID;
@@ -613,8 +669,13 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_UNSUPPORTED;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool batched = choose_batched(ix, Q, P_eff, path);
-    const WsLayout L = ws_layout(ix, Q, P_eff, k, batched);
+    const int mode = choose_mode(ix, Q, P_eff, path);
+    if (mode == MODE_BF16 && !ix->tc_ok) {
+        set_error("osann_search: the tensor-core path needs d <= 128 and a TMA tensor map (unavailable)");
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    const bool batched = mode != MODE_PLAIN;
+    const WsLayout L = ws_layout(ix, Q, P_eff, k, mode);
     void* owned = nullptr;
     if (!d_ws) {
         owned = d_ws = dev_alloc(L.total, st);
@@ -627,7 +688,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, Y, Q, P_eff, L, w, batched, k, st);
+    int rc = query_front(ix, Y, Q, P_eff, L, w, mode == MODE_BATCHED, k, st);
     if (!rc && batched) {
         BatchedBuffers b{};
         b.qcount = reinterpret_cast<uint32_t*>(w + L.qcount);
@@ -641,21 +702,48 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         b.n_items_dev = b.item_off + ix->NC;
         b.scan_temp = w + L.scan_temp;
         b.max_items = L.max_items;
-        const int G = group_size(ix->d_pad);
+        const int G = mode == MODE_BF16 ? TC_GROUP : group_size(ix->d_pad);
         uint64_t* partial = reinterpret_cast<uint64_t*>(w + L.partial);
-        {
+        const uint32_t* probes = reinterpret_cast<uint32_t*>(w + L.probes);
+        if (mode == MODE_BF16) {
+            StageScope s(OSANN_STAGE_QUERY_ORDER, st);
+            rc = launch_tc_query_prep(Y, Q, ix->d, ix->d_pad, probes, P_eff, ix->offsets, uint32_t(ix->NC), ix->xs, k,
+                                      src == nullptr, reinterpret_cast<__nv_bfloat16*>(w + L.yb),
+                                      reinterpret_cast<float4*>(w + L.qstat), reinterpret_cast<uint32_t*>(w + L.ubits),
+                                      reinterpret_cast<uint32_t*>(w + L.scnt), st);
+        }
+        if (!rc) {
             StageScope s(OSANN_STAGE_WORKLIST, st);
-            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probes), Q, P_eff, ix->offsets, ix->NC, G, b, st,
-                                 ix->num_sms);
+            rc = launch_worklist(probes, Q, P_eff, ix->offsets, ix->NC, G, b, st, ix->num_sms);
         }
-        if (!rc) {
-            StageScope s(OSANN_STAGE_TILE_SCAN, st);
-            rc = launch_tile_scan(ix->xs, ix->offsets, ix->perm, ix->d_pad, Y, ix->d, P_eff, k, src, grid_w, radius, b,
-                                  G, partial, ix->status, st, ix->num_sms);
-        }
-        if (!rc) {
-            StageScope s(OSANN_STAGE_MERGE, st);
-            rc = launch_merge(partial, Q, P_eff, k, nullptr, ids, dists, st);
+        if (!rc && mode == MODE_BF16) {
+            {
+                StageScope s(OSANN_STAGE_TILE_SCAN, st);
+                rc = launch_tc_scan(ix->tmap, ix->offsets, ix->perm, ix->rowstat,
+                                    reinterpret_cast<const __nv_bfloat16*>(w + L.yb),
+                                    reinterpret_cast<const float4*>(w + L.qstat), src, grid_w, radius, b,
+                                    reinterpret_cast<uint32_t*>(w + L.ubits), reinterpret_cast<uint32_t*>(w + L.scnt),
+                                    reinterpret_cast<uint32_t*>(w + L.surv), TC_SURV_CAP, ix->status, ix->diag, ix->xs,
+                                    Y, P_eff, ix->d, ix->d_pad, k, ix->cdot2, ix->Bn, debug_checks(), st,
+                                    ix->num_sms);
+            }
+            if (!rc) {
+                StageScope s(OSANN_STAGE_MERGE, st);
+                rc = launch_tc_rerank(ix->xs, ix->d_pad, ix->perm, ix->offsets, uint32_t(ix->NC), Y, ix->d, Q, probes,
+                                      P_eff, reinterpret_cast<uint32_t*>(w + L.scnt),
+                                      reinterpret_cast<uint32_t*>(w + L.surv), TC_SURV_CAP, k, src, grid_w, radius,
+                                      ix->diag, ids, dists, st);
+            }
+        } else if (!rc) {
+            {
+                StageScope s(OSANN_STAGE_TILE_SCAN, st);
+                rc = launch_tile_scan(ix->xs, ix->offsets, ix->perm, ix->d_pad, Y, ix->d, P_eff, k, src, grid_w,
+                                      radius, b, G, partial, ix->status, st, ix->num_sms);
+            }
+            if (!rc) {
+                StageScope s(OSANN_STAGE_MERGE, st);
+                rc = launch_merge(partial, Q, P_eff, k, nullptr, ids, dists, st);
+            }
         }
     } else if (!rc) {
         StageScope s(OSANN_STAGE_PLAIN_SCAN, st);
@@ -684,6 +772,22 @@ int osann_search_excl(const osann_index* index, const float* d_queries, const in
     }
     return search_impl(index, d_queries, d_query_src, Q, P, k, grid_w, radius, path, d_ws, ws_bytes, d_ids, d_sqdists,
                        stream);
+}
+
+int osann_screen_stats(const osann_index* ix, void* stream, int64_t* out4)
+{
+    if (!ix || !out4) {
+        set_error("osann_screen_stats: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, ix->diag, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ix->diag, 0, sizeof(h), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "osann_screen_stats");
+    for (int i = 0; i < 4; ++i) out4[i] = int64_t(h[i]);
+    return OSANN_OK;
 }
 
 size_t osann_bruteforce_workspace_size(const osann_index* ix, int64_t Q, int32_t k)

@@ -18,6 +18,7 @@ enum : uint32_t {
     ST_NONFINITE_QUERY = 2u,
     ST_TIMEOUT = 4u,
     ST_OVERFLOW = 8u,
+    ST_BOUND = 16u,  // a debug check of the screening error bound failed
 };
 
 constexpr int MAX_D = 256;

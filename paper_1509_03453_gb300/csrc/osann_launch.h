@@ -29,7 +29,8 @@ size_t radix_temp_bytes(int64_t N, int64_t NC);
 int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
                            cudaStream_t st);
 int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
-                       __nv_bfloat16* xb, float* norm2, cudaStream_t st, int num_sms);  // xb may be null
+                       __nv_bfloat16* xb, float* norm2, float4* rowstat, float Bn, cudaStream_t st,
+                       int num_sms);  // xb, rowstat may be null
 int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st);
 
 // probes.cu
@@ -72,5 +73,23 @@ int launch_bruteforce_rows(const float* xs, const uint32_t* perm, int64_t N, int
                            int64_t Q, int k, const int64_t* query_src, int64_t grid_w, int radius, void* ws,
                            uint32_t* counter, int64_t* out_ids, float* out_d, uint32_t* status, cudaStream_t st,
                            int num_sms);
+
+// tc_scan.cu: bf16 tensor-core screening + fp32 rerank
+constexpr int TC_GROUP = 128;
+constexpr int TC_SURV_CAP = 256;
+size_t tc_map_bytes();
+int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_pad);
+int launch_tc_query_prep(const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes, int64_t P_eff,
+                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, __nv_bfloat16* Yb,
+                         float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st);
+int launch_tc_scan(const void* map, const uint32_t* offsets, const uint32_t* perm, const float4* rowstat,
+                   const __nv_bfloat16* Yb, const float4* qstat, const int64_t* query_src, int64_t grid_w, int radius,
+                   const BatchedBuffers& b, uint32_t* Ubits, uint32_t* surv_cnt, uint32_t* surv, int cap,
+                   uint32_t* status, unsigned long long* diag, const float* xs, const float* Y, int64_t S, int d,
+                   int d_pad, int k, float cdot2, float Bn, int debug, cudaStream_t st, int num_sms);
+int launch_tc_rerank(const float* xs, int d_pad, const uint32_t* perm, const uint32_t* offsets, uint32_t NC,
+                     const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, const uint32_t* surv_cnt,
+                     const uint32_t* surv, int cap, int k, const int64_t* query_src, int64_t grid_w, int radius,
+                     unsigned long long* diag, int64_t* out_ids, float* out_d, cudaStream_t st);
 
 }  // namespace osann

@@ -1,0 +1,92 @@
+"""Tensor-core screening path (bf16 tcgen05 tiles + certified bound + fp32
+rerank): same bits as the fp32 paths, parity with the oracle, and the
+on-device check of the error bound (OSANN_DEBUG_CHECKS=1) never fails."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import assert_knn_match, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def osann():
+    import paper_1509_03453_gb300 as m
+    from paper_1509_03453_gb300 import build
+    build.build()
+    m.load()
+    os.environ["OSANN_DEBUG_CHECKS"] = "1"
+    yield m
+    os.environ.pop("OSANN_DEBUG_CHECKS", None)
+
+
+def _cases():
+    from paper_1509_03453_gb300 import datagen
+    rng = np.random.default_rng(11)
+    out = []
+    w = datagen.workload("gauss16")
+    out.append(("gauss16", w["X"], w["Y"], 2, [4, 64], 1, None))
+    out.append(("gauss32", rng.standard_normal((120_011, 32), dtype=np.float32),
+                rng.standard_normal((2_000, 32), dtype=np.float32), 2, [16, 128], 1, None))
+    out.append(("gauss32_k5", rng.standard_normal((60_013, 32), dtype=np.float32),
+                rng.standard_normal((1_500, 32), dtype=np.float32), 2, [64], 5, None))
+    img = datagen.patch_image(1003, 192)
+    X = datagen.patches(img)
+    src = np.sort(rng.choice(X.shape[0], 600, replace=False)).astype(np.int64)
+    out.append(("patch64", X, X[src].copy(), 3, [16, 64], 4, (src, 185, 8)))
+    out.append(("desc128", datagen.descriptors(40_009, 1004), datagen.descriptor_queries(400, 2004), 3,
+                [32], 10, None))
+    out.append(("d20", rng.standard_normal((30_007, 20), dtype=np.float32),
+                rng.standard_normal((700, 20), dtype=np.float32), 2, [40], 3, None))
+    out.append(("d100", rng.standard_normal((20_011, 100), dtype=np.float32),
+                rng.standard_normal((300, 100), dtype=np.float32), 1, [30], 2, None))
+    return out
+
+
+CASES = None
+
+
+def case(i):
+    global CASES
+    if CASES is None:
+        CASES = _cases()
+    return CASES[i]
+
+
+@pytest.mark.parametrize("i", range(7))
+def test_bf16_screen_is_exact(osann, i):
+    name, X, Y, L, Ps, k, ex = case(i)
+    idx = osann.Index(to_dev(X), L)
+    Yd = to_dev(Y)
+    kw, okw = {}, {}
+    if ex is not None:
+        kw = dict(query_src=to_dev(ex[0]), grid_w=ex[1], radius=ex[2])
+        okw = dict(query_src=ex[0], grid_w=ex[1], radius=ex[2])
+    ref = oracle.Index(X, L)
+    idx.screen_stats()
+    for P in Ps:
+        a = idx.search(Yd, P, k, path="bf16", **kw)
+        b = idx.search(Yd, P, k, path="batched", **kw)
+        assert np.array_equal(to_np(a[0]), to_np(b[0])), name
+        assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(b[1]).view(np.uint32)), name
+        oids, od = ref.search(Y, P, k, **okw)
+        assert_knn_match(X, Y, to_np(a[0]), to_np(a[1]), oids, od)
+    st = idx.screen_stats()
+    assert st["bound_checks"] > 0
+    assert st["bound_violations"] == 0, st
+    assert idx.status() == 0
+    print(name, st)
+
+
+def test_bf16_full_budget_is_linear_search(osann):
+    name, X, Y, L, Ps, k, ex = case(0)
+    idx = osann.Index(to_dev(X), L)
+    Yd = to_dev(Y)
+    a = idx.search(Yd, idx.NC, k, path="bf16")
+    bf = idx.bruteforce(Yd, k)
+    assert np.array_equal(to_np(a[0]), to_np(bf[0]))
+    assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(bf[1]).view(np.uint32))
+    assert idx.screen_stats()["bound_violations"] == 0
