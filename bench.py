@@ -284,6 +284,8 @@ def run_gpu(args):
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stats.items() if v[1]}
     stage_n = {k: v[1] / args.steps for k, v in stats.items() if v[1]}
     dom = max(stats, key=lambda s: stats[s][0])
+    path_used = "bf16" if stats.get("tc_scan", (0, 0))[1] else ("batched" if stats.get("tile_scan", (0, 0))[1]
+                                                              else "plain")
     pairs = None
     roof = None
     # candidate pairs of the timed search (exact count from the probe lists)
@@ -295,7 +297,18 @@ def run_gpu(args):
     ix.close()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     dom_ms = stage_ms[dom]
-    if dom in ("tile_scan", "plain_scan", "bruteforce"):
+    if dom == "tc_scan":
+        # the contraction: 2d flops per (query, candidate) pair on bf16 tensor cores
+        flops = 2.0 * D * pairs
+        peak = peaks.get("bf16_tflops", 1900.0)
+        achieved = flops / (dom_ms / 1e3) / 1e12
+        roof = {"kernel": dom, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": f"{peak_src} bf16 dense (burst)",
+                "algorithmic": f"{pairs} (query, candidate) pairs x 2d flops per launch "
+                               f"(issued MMA work is larger: padded tiles and one extra K block of 16)",
+                "avg_launch_ms": round(dom_ms, 4)}
+    elif dom in ("tile_scan", "plain_scan", "bruteforce"):
         flops = 3.0 * D * pairs  # d subtractions, d squares, d additions per pair
         peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = flops / (dom_ms / 1e3) / 1e12
@@ -327,7 +340,7 @@ def run_gpu(args):
         "dtype": "f32",
         "data": "synthetic (seeded iid N(0,1), generated on the host)",
         "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P,
-                   "path": "auto (batched: cone-major work list + persistent tile scan)",
+                   "path": f"auto -> {path_used}",
                    "step": "index build + search of the Q queries",
                    "l2": "flushed before every step by a 256 MiB device write (untimed)",
                    "parallelism": f"replicas x{ws} (independent data per rank)"},

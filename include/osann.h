@@ -204,7 +204,10 @@ const char *osann_last_error(void);
 #define OSANN_STAGE_MERGE 7
 #define OSANN_STAGE_PLAIN_SCAN 8
 #define OSANN_STAGE_BRUTEFORCE 9
-#define OSANN_NUM_STAGES 10
+#define OSANN_STAGE_TC_PREP 10   /* bf16 queries, norms, seed bounds */
+#define OSANN_STAGE_TC_SCAN 11   /* tensor-core screening */
+#define OSANN_STAGE_TC_RERANK 12 /* exact fp32 rerank of the survivors */
+#define OSANN_NUM_STAGES 13
 int osann_stats_enable(int on);
 int osann_stats_reset(void);
 int osann_stats_get(int32_t stage, double *total_ms, int64_t *count);

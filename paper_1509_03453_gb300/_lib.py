@@ -24,7 +24,7 @@ ERRORS = {
 }
 PATHS = {"auto": 0, "plain": 1, "batched": 2, "bf16": 3}
 STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
-          "plain_scan", "bruteforce"]
+          "plain_scan", "bruteforce", "tc_prep", "tc_scan", "tc_rerank"]
 STATUS_NONFINITE_DATA = 1
 STATUS_NONFINITE_QUERY = 2
 STATUS_TIMEOUT = 4

@@ -309,7 +309,8 @@ template <int LPV, bool VEC>
 __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restrict__ X, int64_t N, int d, int d_pad,
                                                          const uint32_t* __restrict__ perm, float* __restrict__ xs,
                                                          __nv_bfloat16* __restrict__ xb, float* __restrict__ norm2,
-                                                         float4* __restrict__ rowstat, float Bn)
+                                                         float4* __restrict__ rowstat, __nv_bfloat16* __restrict__ xe,
+                                                         float Bn)
 {
     const int lane = threadIdx.x & 31;
     const int glane = lane & (LPV - 1);
@@ -356,13 +357,32 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restric
         for (int m = LPV / 2; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
         if (live && glane == 0) {
             norm2[r] = s;
-            if (rowstat) rowstat[r] = make_float4(s * (1.0f - Bn), sqrtf(s), s, 0.0f);
+            const float xn1 = s * (1.0f - Bn), nrm = sqrtf(s);
+            if (rowstat) rowstat[r] = make_float4(xn1, nrm, s, 0.0f);
+            if (xe) {
+                // extra K block of the tensor-core screen: bf16 hi/lo splits of
+                // (1-B)|x|^2 and |x|, then zeros
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(xn1);
+                const __nv_bfloat16 l0 = __float2bfloat16_rn(xn1 - __bfloat162float(h0));
+                const __nv_bfloat16 h1 = __float2bfloat16_rn(nrm);
+                const __nv_bfloat16 l1 = __float2bfloat16_rn(nrm - __bfloat162float(h1));
+                const __nv_bfloat162 p0 = __halves2bfloat162(h0, l0), p1 = __halves2bfloat162(h1, l1);
+                uint4 e0;
+                e0.x = *reinterpret_cast<const uint32_t*>(&p0);
+                e0.y = *reinterpret_cast<const uint32_t*>(&p1);
+                e0.z = 0;
+                e0.w = 0;
+                uint4* dst = reinterpret_cast<uint4*>(xe + r * 16);
+                dst[0] = e0;
+                dst[1] = make_uint4(0, 0, 0, 0);
+            }
         }
     }
 }
 
 int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
-                       __nv_bfloat16* xb, float* norm2, float4* rowstat, float Bn, cudaStream_t st, int num_sms)
+                       __nv_bfloat16* xb, float* norm2, float4* rowstat, __nv_bfloat16* xe, float Bn, cudaStream_t st,
+                       int num_sms)
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -374,9 +394,9 @@ int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32
     const dim3 g(static_cast<unsigned>(blocks)), b(256u);
 #define OSANN_GATHER(LP)                                                                                 \
     if (vec)                                                                                             \
-        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, Bn); \
+        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, xe, Bn); \
     else                                                                                                 \
-        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, Bn);
+        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, xe, Bn);
     switch (lpv) {
     case 4: OSANN_GATHER(4); break;
     case 8: OSANN_GATHER(8); break;

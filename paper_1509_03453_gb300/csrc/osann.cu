@@ -210,26 +210,29 @@ struct osann_index {
     float* norm2 = nullptr;
     __nv_bfloat16* xb = nullptr;  // bf16 copy of xs (tensor-core screening)
     float4* rowstat = nullptr;    // per row (1-B)|x|^2, |x|, |x|^2; N + TC_N rows
+    __nv_bfloat16* xe = nullptr;  // per row extra K block of the screen (16 bf16)
     uint32_t* status = nullptr;   // [0] flags, [1] largest cone
     unsigned long long* diag = nullptr;  // screening counters (survivors, fallbacks, checks, violations)
     uint64_t* binom = nullptr;
     float cdot2 = 0.f, Bn = 0.f;  // screening error-bound coefficients
     bool tc_ok = false;           // tensor map encoded
-    alignas(64) unsigned char tmap[128];
+    alignas(64) unsigned char tmap[256];  // tensor maps over xb and xe
     std::vector<std::pair<void*, size_t>> allocs;
 };
 
 // Coefficients of the screening bound E = cdot2 |q||x| + Bn (|q|^2 + |x|^2):
 // bf16 rounding of both operands (unit roundoff u = 2^-8) and the fp32
 // accumulation of d_pad products (taken as d_pad 2^-20, sixteen times the
-// round-to-nearest bound), the fp32 norms (d_pad 2^-23) and a cushion of
-// 4e-6 for the fp32 rounding of the exact distances compared at the end.
+// round-to-nearest bound); for Bn the fp32 norms, the accumulation of the
+// folded norm terms over d_pad + 16 columns, their bf16 hi/lo split (2^-15)
+// and a cushion of 4e-6 for the fp32 rounding of the exact distances
+// compared at the end.
 static void screen_coefficients(int d_pad, float* cdot2, float* Bn)
 {
     const double u = std::ldexp(1.0, -8);
     const double c = 2 * u + u * u + d_pad * std::ldexp(1.0, -20) * (1 + u) * (1 + u);
     *cdot2 = float(2 * c);
-    *Bn = float(d_pad * std::ldexp(1.0, -23) + 4e-6);
+    *Bn = float(d_pad * std::ldexp(1.0, -23) + (d_pad + 16) * std::ldexp(1.0, -20) + std::ldexp(1.0, -15) + 4e-6);
 }
 
 // OSANN_DEBUG_CHECKS=1 makes the screening kernel verify its error bound
@@ -472,6 +475,7 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     ix->norm2 = index_alloc<float>(ix, size_t(N));
     ix->xb = index_alloc<__nv_bfloat16>(ix, size_t(N) * ix->d_pad);
     ix->rowstat = index_alloc<float4>(ix, size_t(N) + TC_N_ROWS);
+    ix->xe = index_alloc<__nv_bfloat16>(ix, size_t(N) * 16);
     ix->status = index_alloc<uint32_t>(ix, 64);
     ix->diag = index_alloc<unsigned long long>(ix, 8);
     screen_coefficients(ix->d_pad, &ix->cdot2, &ix->Bn);
@@ -480,7 +484,7 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     const size_t radix_bytes = al256(radix_temp_bytes(N, NC));
     const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes;
     char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
-    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->norm2 || !ix->xb || !ix->rowstat ||
+    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->norm2 || !ix->xb || !ix->rowstat || !ix->xe ||
         !ix->status || !ix->diag || !temp) {
         if (temp) dev_free(temp, temp_bytes, st);
         index_release(ix);
@@ -507,8 +511,8 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_GATHER, st);
-        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->xb, ix->norm2, ix->rowstat, ix->Bn, st,
-                                ix->num_sms);
+        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->xb, ix->norm2, ix->rowstat, ix->xe,
+                                ix->Bn, st, ix->num_sms);
     }
     if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st);
     dev_free(temp, temp_bytes, st);
@@ -534,7 +538,8 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     ix->max_bucket = host_status[1];
     static_assert(sizeof(ix->tmap) >= 128, "tensor map storage");
     ix->tc_ok = tc_map_bytes() <= sizeof(ix->tmap) && ix->d_pad <= 128 &&
-                tc_encode_rows_map(ix->tmap, ix->xb, N, ix->d_pad) == 0;
+                tc_encode_rows_map(ix->tmap, ix->xb, N, ix->d_pad) == 0 &&
+                tc_encode_rows_map(ix->tmap + tc_map_bytes() / 2, ix->xe, N, 0) == 0;
     *out = ix;
     return OSANN_OK;
 }
@@ -706,9 +711,10 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         uint64_t* partial = reinterpret_cast<uint64_t*>(w + L.partial);
         const uint32_t* probes = reinterpret_cast<uint32_t*>(w + L.probes);
         if (mode == MODE_BF16) {
-            StageScope s(OSANN_STAGE_QUERY_ORDER, st);
+            StageScope s(OSANN_STAGE_TC_PREP, st);
             rc = launch_tc_query_prep(Y, Q, ix->d, ix->d_pad, probes, P_eff, ix->offsets, uint32_t(ix->NC), ix->xs, k,
-                                      src == nullptr, reinterpret_cast<__nv_bfloat16*>(w + L.yb),
+                                      true, ix->cdot2, ix->perm, src, grid_w, radius,
+                                      reinterpret_cast<__nv_bfloat16*>(w + L.yb),
                                       reinterpret_cast<float4*>(w + L.qstat), reinterpret_cast<uint32_t*>(w + L.ubits),
                                       reinterpret_cast<uint32_t*>(w + L.scnt), st);
         }
@@ -718,7 +724,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         }
         if (!rc && mode == MODE_BF16) {
             {
-                StageScope s(OSANN_STAGE_TILE_SCAN, st);
+                StageScope s(OSANN_STAGE_TC_SCAN, st);
                 rc = launch_tc_scan(ix->tmap, ix->offsets, ix->perm, ix->rowstat,
                                     reinterpret_cast<const __nv_bfloat16*>(w + L.yb),
                                     reinterpret_cast<const float4*>(w + L.qstat), src, grid_w, radius, b,
@@ -728,7 +734,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
                                     ix->num_sms);
             }
             if (!rc) {
-                StageScope s(OSANN_STAGE_MERGE, st);
+                StageScope s(OSANN_STAGE_TC_RERANK, st);
                 rc = launch_tc_rerank(ix->xs, ix->d_pad, ix->perm, ix->offsets, uint32_t(ix->NC), Y, ix->d, Q, probes,
                                       P_eff, reinterpret_cast<uint32_t*>(w + L.scnt),
                                       reinterpret_cast<uint32_t*>(w + L.surv), TC_SURV_CAP, k, src, grid_w, radius,

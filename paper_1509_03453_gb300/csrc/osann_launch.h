@@ -29,8 +29,8 @@ size_t radix_temp_bytes(int64_t N, int64_t NC);
 int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
                            cudaStream_t st);
 int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
-                       __nv_bfloat16* xb, float* norm2, float4* rowstat, float Bn, cudaStream_t st,
-                       int num_sms);  // xb, rowstat may be null
+                       __nv_bfloat16* xb, float* norm2, float4* rowstat, __nv_bfloat16* xe, float Bn, cudaStream_t st,
+                       int num_sms);  // xb, rowstat, xe may be null
 int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st);
 
 // probes.cu
@@ -78,10 +78,11 @@ int launch_bruteforce_rows(const float* xs, const uint32_t* perm, int64_t N, int
 constexpr int TC_GROUP = 128;
 constexpr int TC_SURV_CAP = 256;
 size_t tc_map_bytes();
-int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_pad);
+int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_pad);  // d_pad 0: extra block
 int launch_tc_query_prep(const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes, int64_t P_eff,
-                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, __nv_bfloat16* Yb,
-                         float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st);
+                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, float cdot2,
+                         const uint32_t* perm, const int64_t* query_src, int64_t grid_w, int radius,
+                         __nv_bfloat16* Yb, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st);
 int launch_tc_scan(const void* map, const uint32_t* offsets, const uint32_t* perm, const float4* rowstat,
                    const __nv_bfloat16* Yb, const float4* qstat, const int64_t* query_src, int64_t grid_w, int radius,
                    const BatchedBuffers& b, uint32_t* Ubits, uint32_t* surv_cnt, uint32_t* surv, int cap,

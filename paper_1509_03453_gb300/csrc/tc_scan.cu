@@ -10,8 +10,14 @@
 // bound U on its k-th best exact distance; a row survives the screen when
 //     d~ - E(q, x) <= U,   E = 2 c |q| |x| + B (|q|^2 + |x|^2),
 // where c bounds the bf16 rounding of both operands plus the fp32
-// accumulation (c = 2u + u^2 + K 2^-22, u = 2^-8) and B the fp32 error of
-// the norms plus a cushion for the fp32 rounding of the exact distance.  A
+// accumulation (c = 2u + u^2 + K 2^-20, u = 2^-8) and B the fp32 error of
+// the norms, of their bf16 hi/lo split and a cushion for the fp32 rounding of
+// the exact distance.  The per-row terms are folded into the product by one
+// extra K block of 16 columns: the query side holds (1, 1, -A', -A') with
+// A' >= 2c|q| rounded up to bf16, the row side (|x|^2 hi, lo, |x| hi, lo)
+// with |x|^2 scaled by (1-B), so the accumulator is directly
+//     D = (1-B)|x|^2 - A'|x| - 2 q.x     and a row survives iff
+//     D <= U - (1-B)|q|^2.  A
 // discarded row is therefore provably farther than some candidate already
 // seen, so the survivors contain the exact top-k.  Survivors are appended to
 // a per-query list; the rerank computes their canonical fp32 distance (the
@@ -26,7 +32,6 @@
 
 namespace osann {
 
-constexpr int TC_THREADS = 128;
 constexpr int TC_M = 128;  // queries per item = MMA M
 constexpr int TC_N = 128;  // cone rows per tile = MMA N = TMEM columns
 
@@ -38,8 +43,8 @@ struct TcArgs {
     const uint32_t* offsets;
     const uint32_t* perm;
     const float4* rowstat;    // per row: ((1-B)|x|^2, |x|, |x|^2, 0); N + TC_N rows
-    const __nv_bfloat16* Yb;  // Q x d_pad
-    const float4* qstat;      // per query: (|q|^2, |q|, 0, 0)
+    const __nv_bfloat16* Yb;  // Q x d_pad, holds bf16(-2 y)
+    const float4* qstat;      // per query: (|q|^2, |q|, -A' (bf16 value, A' >= A = 2c|q|), 0)
     const int64_t* query_src;
     const uint2* items;
     const uint32_t* n_items_dev;
@@ -61,241 +66,402 @@ struct TcArgs {
     float Bn;     // B
 };
 
+// Item descriptor passed from the producer warp to the MMA and epilogue warps.
+struct TcItem {
+    uint32_t r0, r1;    // cone rows; r0 == 0xFFFFFFFF marks the end of the work
+    uint32_t qbeg, qn;  // slot-list range of the query group
+};
+
+// Warp roles (256 threads): warp 0 lane 0 fetches items and streams the cone
+// tiles with TMA; warp 1 lane 0 issues the MMAs (warp 1 owns the TMEM
+// allocation); warps 2-3 ("loaders", 64 threads) write the query tile of each
+// item and the per-query constants into one of two shared buffers, up to two
+// items ahead; warps 4-7 (128 threads, one per query row and TMEM lane)
+// screen the accumulators.  Hand-offs are mbarriers: item queue (4 slots, the
+// producer one item ahead of its tiles), tile stages (full/empty), query
+// buffers (full/empty), accumulators (2 TMEM buffers of 128 columns,
+// full/empty), so the MMA of one tile overlaps the screening of the previous
+// one and the query loads overlap both.  Every wait is bounded; a timeout
+// sets ST_TIMEOUT and makes all roles drop out.
+constexpr int TC_ROLE_THREADS = 256;
+constexpr int TC_IQ = 4;
+constexpr int TC_SBUF = 16;  // survivors buffered per thread before a flush
+
+// per-query constants of a query tile, written by the loaders
+struct TcQConst {
+    float qn2;   // |q|^2
+    float Uthr;  // U - (1-B)|q|^2
+    float Aq1;   // A'
+    float U;     // upper bound on the k-th best exact distance
+};
+
+__device__ __forceinline__ float min32_tree(const float (&v)[32])
+{
+    float a[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) a[j] = fminf(v[2 * j], v[2 * j + 1]);
+#pragma unroll
+    for (int w = 8; w > 0; w >>= 1)
+#pragma unroll
+        for (int j = 0; j < w; ++j) a[j] = fminf(a[j], a[j + w]);
+    return a[0];
+}
+
 template <int KMAX, bool EXCL>
-__global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                                 const TcArgs a)
+__global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
+    tc_scan_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_x,
+                   const TcArgs a)
 {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t bfull[4];
-    __shared__ __align__(8) uint64_t mma_bar;
+    __shared__ __align__(8) uint64_t iq_full[TC_IQ], iq_empty[TC_IQ];
+    __shared__ __align__(8) uint64_t bfull[4], bempty[4];
+    __shared__ __align__(8) uint64_t afull[2], aempty[2], accfull[2], accempty[2];
+    __shared__ TcItem iq[TC_IQ];
+    __shared__ TcQConst qc[2][TC_M];
+    __shared__ uint32_t qidx[2][TC_M];  // query index, 0xFFFFFFFF for an unused row
     __shared__ uint32_t tmem_base_sh;
-    __shared__ uint32_t item_sh;
-    __shared__ int fail_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ uint32_t sbuf_row[TC_SBUF * 128];  // survivors buffered per screening thread
+    __shared__ float sbuf_val[TC_SBUF * 128];
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int row_bytes = tc_row_bytes(a.d_pad);
     const int kblocks = tc_kblocks(a.d_pad);
-    const int epb = row_bytes / 2;                 // bf16 elements per row block
-    const int ksteps_pb = epb / 16;                // MMA K-steps per row block
-    const int tileA = TC_M * a.d_pad * 2, tileB = TC_N * a.d_pad * 2;
+    const int epb = row_bytes / 2;
+    const int ksteps_pb = epb / 16;
+    const int mainA = TC_M * a.d_pad * 2, mainB = TC_N * a.d_pad * 2;
+    const int extA = TC_M * 32, extB = TC_N * 32;  // extra K block: 16 bf16 per row
     const int S = a.stages;
-    unsigned char* sA = base;
-    unsigned char* sB = base + tileA;
-    float4* sR = reinterpret_cast<float4*>(sB + size_t(S) * tileB);
-    const uint32_t n_items = *a.n_items_dev;
+    unsigned char* sA = base;                             // 2 x (mainA + extA)
+    unsigned char* sB = base + 2 * size_t(mainA + extA);  // S x (mainB + extB)
     const uint32_t idesc = idesc_bf16_f32(TC_M, TC_N);
-    const uint32_t tx_bytes = uint32_t(tileB + TC_N * 16);
+    const uint32_t tx_bytes = uint32_t(mainB + extB);
 
-    if (warp == 0) {
-        tmem_alloc(&tmem_base_sh, TC_N);
+    if (warp == 1) {
+        tmem_alloc(&tmem_base_sh, 2 * TC_N);
         tmem_relinquish();
     }
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bfull[s], 1);
-        mbar_init(&mma_bar, 1);
+        for (int i = 0; i < TC_IQ; ++i) {
+            mbar_init(&iq_full[i], 1);
+            mbar_init(&iq_empty[i], 1 + 64 + 128);
+        }
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&bfull[s], 1);
+            mbar_init(&bempty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&afull[b], 64);
+            mbar_init(&aempty[b], 128);
+            mbar_init(&accfull[b], 1);
+            mbar_init(&accempty[b], 128);
+        }
         fence_mbar_init();
-        fail_sh = 0;
+        abort_sh = 0;
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_base_sh;
 
-    auto issue_tile = [&](uint32_t g, int y0) {
-        const int s = int(g % uint32_t(S));
-        fence_proxy_async_smem();
-        mbar_arrive_expect_tx(&bfull[s], tx_bytes);
-        for (int kb = 0; kb < kblocks; ++kb)
-            tma_load_2d(sB + size_t(s) * tileB + size_t(kb) * TC_N * row_bytes, &tmap, kb * epb, y0, &bfull[s]);
-        bulk_g2s(sR + size_t(s) * TC_N, a.rowstat + y0, TC_N * 16, &bfull[s]);
+    auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        if (abort_sh) return false;
+        if (mbar_wait_bounded(bar, parity)) return true;
+        if (!abort_sh) atomicOr(a.status, ST_TIMEOUT);
+        abort_sh = 1;
+        return false;
     };
 
-    uint32_t gt = 0;      // tiles consumed by this CTA (stage ring position)
-    uint32_t mphase = 0;  // parity of the next MMA completion
-    bool failed = false;
-    int pending_from = 0, pending_to = 0;  // issued-not-consumed tiles [from, to) of the current item
-
-    for (;;) {
-        if (tid == 0) item_sh = atomicAdd(a.counter, 1u);
-        __syncthreads();
-        const uint32_t item = item_sh;
-        __syncthreads();
-        if (item >= n_items) break;
-
-        const uint2 bg = a.items[item];
-        const uint32_t r0 = __ldg(a.offsets + bg.x), r1 = __ldg(a.offsets + bg.x + 1);
-        const uint32_t cnt = a.qcount[bg.x];
-        const uint32_t qbeg = a.qoff[bg.x] + bg.y * TC_M;
-        const uint32_t qn = min(cnt - bg.y * TC_M, uint32_t(TC_M));
-        const bool active = uint32_t(tid) < qn;
-        int64_t slot = 0, q = 0;
-        if (active) {
-            slot = int64_t(a.qlist[qbeg + tid]);
-            q = slot / a.S;
-        }
-        // this thread's query row of A, written in the swizzled K-major layout
-        {
-            const uint4* src = reinterpret_cast<const uint4*>(a.Yb + q * int64_t(a.d_pad));
-            const int chunks = row_bytes / 16;
-            for (int kb = 0; kb < kblocks; ++kb)
-                for (int c = 0; c < chunks; ++c) {
-                    uint4 v = active ? src[kb * chunks + c] : make_uint4(0, 0, 0, 0);
-                    *reinterpret_cast<uint4*>(sA + size_t(kb) * TC_M * row_bytes + swz_offset(tid, c, row_bytes)) = v;
+    if (warp == 0) {
+        // ------------------------------------------------ producer
+        if (lane == 0) {
+            const uint32_t n_items = *a.n_items_dev;
+            uint32_t it = 0, tc = 0;
+            bool done = false;
+            auto publish = [&](TcItem& out) -> bool {
+                const int slot = int(it % TC_IQ);
+                if (it >= TC_IQ && !wait(&iq_empty[slot], ((it / TC_IQ) - 1) & 1u)) return false;
+                TcItem d;
+                const uint32_t item = done ? n_items : atomicAdd(a.counter, 1u);
+                if (item >= n_items) {
+                    d.r0 = 0xFFFFFFFFu;
+                    d.r1 = d.qbeg = d.qn = 0;
+                    done = true;
+                } else {
+                    const uint2 bg = a.items[item];
+                    d.r0 = __ldg(a.offsets + bg.x);
+                    d.r1 = __ldg(a.offsets + bg.x + 1);
+                    const uint32_t cnt = a.qcount[bg.x];
+                    d.qbeg = a.qoff[bg.x] + bg.y * TC_M;
+                    d.qn = min(cnt - bg.y * TC_M, uint32_t(TC_M));
                 }
+                iq[slot] = d;
+                mbar_arrive(&iq_full[slot]);
+                ++it;
+                out = d;
+                return d.r0 != 0xFFFFFFFFu;
+            };
+            TcItem cur, nxt;
+            bool have = publish(cur);
+            while (have && !abort_sh) {
+                const bool have_next = publish(nxt);  // one item ahead of its tiles
+                const int ntiles = int((cur.r1 - cur.r0 + TC_N - 1) / TC_N);
+                for (int t = 0; t < ntiles; ++t, ++tc) {
+                    const int s = int(tc % uint32_t(S));
+                    if (tc >= uint32_t(S) && !wait(&bempty[s], ((tc / uint32_t(S)) - 1) & 1u)) break;
+                    const int y0 = int(cur.r0) + t * TC_N;
+                    unsigned char* dst = sB + size_t(s) * (mainB + extB);
+                    mbar_arrive_expect_tx(&bfull[s], tx_bytes);
+                    for (int kb = 0; kb < kblocks; ++kb)
+                        tma_load_2d(dst + size_t(kb) * TC_N * row_bytes, &tmap, kb * epb, y0, &bfull[s]);
+                    tma_load_2d(dst + mainB, &tmap_x, 0, y0, &bfull[s]);
+                }
+                if (abort_sh) break;
+                cur = nxt;
+                have = have_next;
+            }
+            if (abort_sh) {
+                // let the last tile issued into each stage land before shared memory goes away
+                for (uint32_t g = tc > uint32_t(S) ? tc - uint32_t(S) : 0u; g < tc; ++g)
+                    mbar_wait_bounded(&bfull[g % uint32_t(S)], (g / uint32_t(S)) & 1u);
+            }
         }
-        float qn2 = 0.f, qnorm = 0.f, U = INFINITY;
-        if (active) {
-            const float4 st = a.qstat[q];
-            qn2 = st.x;
-            qnorm = st.y;
-            U = __uint_as_float(a.Ubits[q]);
-        }
-        const float Aq = a.cdot2 * qnorm;
-        const float omb = 1.0f - a.Bn;
-        float ubl[KMAX];  // k smallest upper bounds seen by this thread in this item (ascending)
-#pragma unroll
-        for (int j = 0; j < KMAX; ++j) ubl[j] = INFINITY;
-        float Uthr = U - omb * qn2;  // survive iff (1-B)|x|^2 - A|x| - 2 acc <= Uthr
-        int64_t src = EXCL && active ? a.query_src[q] : -1;
-
-        fence_proxy_async_smem();
-        __syncthreads();
-
-        const int ntiles = int((r1 - r0 + TC_N - 1) / TC_N);
-        if (tid == 0)
-            for (int t = 0; t < ntiles && t < S; ++t) issue_tile(gt + uint32_t(t), int(r0) + t * TC_N);
-        pending_from = 0;
-        pending_to = ntiles < S ? ntiles : S;
-
-        for (int t = 0; t < ntiles; ++t) {
-            const uint32_t g = gt;
-            const int s = int(g % uint32_t(S));
-            if (tid == 0) {
-                bool ok = mbar_wait_bounded(&bfull[s], (g / uint32_t(S)) & 1u);
-                if (ok) {
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t it = 0, tc = 0;
+            const int ksteps = kblocks * ksteps_pb;
+            for (;;) {
+                const int slot = int(it % TC_IQ);
+                if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
+                const TcItem d = iq[slot];
+                if (d.r0 == 0xFFFFFFFFu) break;
+                const int ab = int(it & 1u);
+                if (!wait(&afull[ab], (it >> 1) & 1u)) break;
+                const int ntiles = int((d.r1 - d.r0 + TC_N - 1) / TC_N);
+                const uint32_t a_main = smem_u32(sA + size_t(ab) * (mainA + extA));
+                bool ok = true;
+                for (int t = 0; t < ntiles; ++t, ++tc) {
+                    const int s = int(tc % uint32_t(S));
+                    const int acc = int(tc & 1u);
+                    if (!wait(&bfull[s], (tc / uint32_t(S)) & 1u)) { ok = false; break; }
+                    if (tc >= 2 && !wait(&accempty[acc], ((tc >> 1) - 1) & 1u)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t aaddr = smem_u32(sA), baddr = smem_u32(sB + size_t(s) * tileB);
-                    const int ksteps = kblocks * ksteps_pb;
+                    const uint32_t b_main = smem_u32(sB + size_t(s) * (mainB + extB));
+                    const uint32_t dt = tmem + uint32_t(acc * TC_N);
                     for (int kk = 0; kk < ksteps; ++kk) {
                         const int kb = kk / ksteps_pb, w = kk % ksteps_pb;
-                        const uint32_t off_a = uint32_t(kb * TC_M * row_bytes + w * 32);
-                        const uint32_t off_b = uint32_t(kb * TC_N * row_bytes + w * 32);
-                        mma_bf16_ss(tmem, smem_desc_kmajor(aaddr + off_a, row_bytes),
-                                    smem_desc_kmajor(baddr + off_b, row_bytes), idesc, kk > 0 ? 1u : 0u);
+                        mma_bf16_ss(dt, smem_desc_kmajor(a_main + uint32_t(kb * TC_M * row_bytes + w * 32), row_bytes),
+                                    smem_desc_kmajor(b_main + uint32_t(kb * TC_N * row_bytes + w * 32), row_bytes), idesc,
+                                    kk > 0 ? 1u : 0u);
                     }
-                    mma_commit(&mma_bar);
-                } else {
-                    fail_sh = 1;
+                    // extra K block: |x|^2 and |x| terms folded into the product
+                    mma_bf16_ss(dt, smem_desc_kmajor(a_main + uint32_t(mainA), 32),
+                                smem_desc_kmajor(b_main + uint32_t(mainB), 32), idesc, 1u);
+                    mma_commit(&bempty[s]);
+                    mma_commit(&accfull[acc]);
                 }
+                if (!ok) break;
+                mbar_arrive(&iq_empty[slot]);
+                ++it;
             }
-            if (__syncthreads_or(tid == 0 && fail_sh)) {
-                failed = true;
-                pending_from = t;
-                break;
-            }
-            const bool mok = mbar_wait_bounded(&mma_bar, mphase);
-            mphase ^= 1u;
-            if (__syncthreads_or(!mok)) {
-                failed = true;
-                pending_from = t + 1;
-                break;
-            }
-            tc_fence_after();
-
-            // ---- epilogue: screen the tile's columns for this thread's query
-            const int y0 = int(r0) + t * TC_N;
-            const int nvalid = min(TC_N, int(r1) - y0);
-            const float4* srow = sR + size_t(s) * TC_N;
-            const uint32_t taddr = tmem + (uint32_t(warp * 32) << 16);
-            for (int c0 = 0; c0 < nvalid; c0 += 32) {
-                float acc[32];
-                tmem_ld32(taddr + uint32_t(c0), acc);
+            if (abort_sh && tc > 0) mbar_wait_bounded(&accfull[(tc - 1) & 1u], ((tc - 1) >> 1) & 1u);
+        }
+    } else if (warp < 4) {
+        // ------------------------------------------------ query tile loaders
+        const int lt = tid - 64;  // 0..63, rows lt and lt + 64
+        const int chunks = row_bytes / 16;
+        for (uint32_t it = 0;; ++it) {
+            const int slot = int(it % TC_IQ);
+            if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
+            const TcItem d = iq[slot];
+            if (d.r0 == 0xFFFFFFFFu) break;
+            const int ab = int(it & 1u);
+            if (it >= 2 && !wait(&aempty[ab], ((it >> 1) - 1) & 1u)) break;
+            unsigned char* dstA = sA + size_t(ab) * (mainA + extA);
+            for (int h = 0; h < 2; ++h) {
+                const int r = lt + 64 * h;
+                const bool active = uint32_t(r) < d.qn;
+                uint32_t q = 0;
+                float4 qs = make_float4(0.f, 0.f, 0.f, 0.f);
+                float U = INFINITY;
                 if (active) {
+                    q = uint32_t(int64_t(a.qlist[d.qbeg + r]) / a.S);
+                    qs = a.qstat[q];
+                    U = __uint_as_float(a.Ubits[q]);
+                }
+                const uint4* src = reinterpret_cast<const uint4*>(a.Yb + int64_t(q) * a.d_pad);
+                for (int kb = 0; kb < kblocks; ++kb)
+                    for (int c = 0; c < chunks; ++c) {
+                        const uint4 v = active ? src[kb * chunks + c] : make_uint4(0, 0, 0, 0);
+                        *reinterpret_cast<uint4*>(dstA + size_t(kb) * TC_M * row_bytes + swz_offset(r, c, row_bytes)) = v;
+                    }
+                // extra block: (1, 1, -A', -A', 0, ...) against (|x|^2 hi, lo, |x| hi, lo, 0, ...)
+                uint4 e0 = make_uint4(0, 0, 0, 0);
+                if (active) {
+                    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), na = __float2bfloat16_rn(qs.z);
+                    const __nv_bfloat162 p0 = __halves2bfloat162(one, one), p1 = __halves2bfloat162(na, na);
+                    e0.x = *reinterpret_cast<const uint32_t*>(&p0);
+                    e0.y = *reinterpret_cast<const uint32_t*>(&p1);
+                }
+                *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 0, 32)) = e0;
+                *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 1, 32)) = make_uint4(0, 0, 0, 0);
+                TcQConst c;
+                c.qn2 = qs.x;
+                c.U = U;
+                c.Uthr = U - (1.0f - a.Bn) * qs.x;
+                c.Aq1 = -qs.z;
+                qc[ab][r] = c;
+                qidx[ab][r] = active ? q : 0xFFFFFFFFu;
+            }
+            fence_proxy_async_smem();
+            mbar_arrive(&afull[ab]);
+            mbar_arrive(&iq_empty[slot]);
+        }
+    } else {
+        // ------------------------------------------------ screening
+        const int er = 32 * (warp & 3) + lane;  // query row of the group = TMEM lane
+        const uint32_t tl = tmem + (uint32_t(32 * (warp & 3)) << 16);
+        for (uint32_t it = 0, tc = 0;; ++it) {
+            const int slot = int(it % TC_IQ);
+            if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
+            const TcItem dc = iq[slot];
+            if (dc.r0 == 0xFFFFFFFFu) break;
+            const int ab = int(it & 1u);
+            if (!wait(&afull[ab], (it >> 1) & 1u)) break;
+            TcQConst cur = qc[ab][er];
+            const uint32_t qi = qidx[ab][er];
+            const bool active = qi != 0xFFFFFFFFu;
+            const int64_t q = active ? int64_t(qi) : 0;
+            const int64_t src = EXCL && active ? a.query_src[q] : -1;
+            const int ntiles = int((dc.r1 - dc.r0 + TC_N - 1) / TC_N);
+            float ubl[KMAX];  // k smallest upper bounds seen for this query in this item
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float4 rs = srow[c0 + j];
-                        float v = fmaf(-Aq, rs.y, rs.x);
-                        v = fmaf(-2.0f, acc[j], v);
-                        if (v <= Uthr && c0 + j < nvalid) {
-                            const uint32_t row = uint32_t(y0 + c0 + j);
-                            if (EXCL) {
-                                const uint32_t id = __ldg(a.perm + row);
-                                const int64_t dr = int64_t(id) / a.grid_w - src / a.grid_w;
-                                const int64_t dc = int64_t(id) % a.grid_w - src % a.grid_w;
-                                const int64_t adr = dr < 0 ? -dr : dr, adc = dc < 0 ? -dc : dc;
-                                if (src >= 0 && (adr > adc ? adr : adc) <= a.radius) continue;
-                            }
-                            const uint32_t pos = atomicAdd(a.surv_cnt + q, 1u);
-                            if (pos < uint32_t(a.cap)) a.surv[q * a.cap + pos] = row;
-                            // upper bound on this row's exact distance
-                            const float dt = fmaf(-2.0f, acc[j], qn2 + rs.z);
-                            const float ub = fmaxf(dt + fmaf(Aq, rs.y, a.Bn * (qn2 + rs.z)), 0.0f);
-                            if (ub < ubl[KMAX - 1]) {
+            for (int u = 0; u < KMAX; ++u) ubl[u] = INFINITY;
+            int nb = 0;  // survivors buffered in shared memory by this thread
+            // append the buffered survivors (minus excluded rows) to the query's
+            // list, then tighten U with their upper bounds (deferred: a stale U
+            // only admits more rows)
+            auto flush = [&]() {
+                int keep = 0;
+                for (int i = 0; i < nb; ++i) {
+                    const uint32_t row = sbuf_row[i * 128 + er];
+                    if (EXCL && src >= 0) {
+                        const int64_t id = int64_t(__ldg(a.perm + row));
+                        int64_t dr = id / a.grid_w - src / a.grid_w, dcc = id % a.grid_w - src % a.grid_w;
+                        dr = dr < 0 ? -dr : dr;
+                        dcc = dcc < 0 ? -dcc : dcc;
+                        if ((dr > dcc ? dr : dcc) <= a.radius) continue;
+                    }
+                    sbuf_row[keep * 128 + er] = row;
+                    sbuf_val[keep * 128 + er] = sbuf_val[i * 128 + er];
+                    ++keep;
+                }
+                if (keep > 0) {
+                    const uint32_t pos = atomicAdd(a.surv_cnt + q, uint32_t(keep));
+                    for (int i = 0; i < keep; ++i) {
+                        const uint32_t row = sbuf_row[i * 128 + er];
+                        const float D = sbuf_val[i * 128 + er];
+                        if (pos + uint32_t(i) < uint32_t(a.cap)) a.surv[q * a.cap + pos + i] = row;
+                        // d~ + E <= D + (1+B)|q|^2 + 2B|x|^2 + 2A'|x|
+                        const float4 rs = __ldg(a.rowstat + row);
+                        const float ub = fmaxf((D + (1.0f + a.Bn) * cur.qn2 + 2.0f * a.Bn * rs.z +
+                                                2.0f * cur.Aq1 * rs.y) * (1.0f + 1e-6f),
+                                               0.0f);
+                        if (ub < ubl[KMAX - 1]) {
 #pragma unroll
-                                for (int u = KMAX - 1; u > 0; --u) {
-                                    const float pu = ubl[u - 1];
-                                    if (pu > ub) ubl[u] = pu;
-                                    else if (ubl[u] > ub) ubl[u] = ub;
-                                }
-                                if (ubl[0] > ub) ubl[0] = ub;
+                            for (int u = KMAX - 1; u > 0; --u) {
+                                const float pu = ubl[u - 1];
+                                if (pu > ub) ubl[u] = pu;
+                                else if (ubl[u] > ub) ubl[u] = ub;
                             }
-                            // the k-th smallest bound of k distinct candidates bounds the k-th best
-                            float kth = INFINITY;
-#pragma unroll
-                            for (int u = 0; u < KMAX; ++u)
-                                if (u == a.k - 1) kth = ubl[u];
-                            if (kth < U) {
-                                U = kth;
-                                Uthr = U - omb * qn2;
-                            }
+                            if (ubl[0] > ub) ubl[0] = ub;
                         }
                     }
-                    if (a.debug && lane < nvalid - c0) {
-                        // tensor-core dot product against an fp32 one for one column per thread
-                        const float* xr = a.xs + size_t(y0 + c0 + lane) * a.d_pad;
+                    // the k-th smallest bound of k distinct candidates bounds the k-th best
+                    float kth = INFINITY;
+#pragma unroll
+                    for (int u = 0; u < KMAX; ++u)
+                        if (u == a.k - 1) kth = ubl[u];
+                    if (kth < cur.U) {
+                        cur.U = kth;
+                        cur.Uthr = cur.U - (1.0f - a.Bn) * cur.qn2;
+                    }
+                }
+                nb = 0;
+            };
+            bool ok = true;
+            for (int t = 0; t < ntiles; ++t, ++tc) {
+                const int acc = int(tc & 1u);
+                if (!wait(&accfull[acc], (tc >> 1) & 1u)) { ok = false; break; }
+                tc_fence_after();
+                const int y0 = int(dc.r0) + t * TC_N;
+                const int nvalid = min(TC_N, int(dc.r1) - y0);
+                for (int c0 = 0; c0 < nvalid; c0 += 32) {
+                    float v[32];
+                    tmem_ld32(tl + uint32_t(acc * TC_N + c0), v);
+                    const int lim = nvalid - c0;
+                    if (lim < 32) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            if (j >= lim) v[j] = INFINITY;  // rows of the next cone
+                    }
+                    if (active && min32_tree(v) <= cur.Uthr) {
+                        uint32_t mask = 0;
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) mask |= (v[j] <= cur.Uthr ? 1u : 0u) << j;
+                        // a masked column is +inf, which an unbounded U would admit
+                        if (lim < 32) mask &= (1u << lim) - 1u;
+                        while (mask) {
+                            const int j = __ffs(int(mask)) - 1;
+                            mask &= mask - 1u;
+                            float val = v[0];
+#pragma unroll
+                            for (int u = 1; u < 32; ++u) val = u == j ? v[u] : val;
+                            if (nb == TC_SBUF) flush();
+                            sbuf_row[nb * 128 + er] = uint32_t(y0 + c0 + j);
+                            sbuf_val[nb * 128 + er] = val;
+                            ++nb;
+                        }
+                    }
+                    if (a.debug && active && lane < lim) {
+                        // folded product against an fp32 evaluation, one column per thread
+                        const int row = y0 + c0 + lane;
+                        const float* xr = a.xs + size_t(row) * a.d_pad;
                         const float* yr = a.Y + q * int64_t(a.d);
                         float dot = 0.f;
                         for (int i = 0; i < a.d; ++i) dot = fmaf(xr[i], yr[i], dot);
-                        float accl = 0.f;
+                        const float4 rs = __ldg(a.rowstat + row);
+                        float mine = v[0];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j == lane) accl = acc[j];
-                        const float lim = 0.5f * a.cdot2 * qnorm * srow[c0 + lane].y * 1.0001f +
-                                          1e-6f * (qn2 + srow[c0 + lane].z) + 1e-30f;
+                        for (int u = 1; u < 32; ++u) mine = u == lane ? v[u] : mine;
+                        const float ref = -2.0f * dot + rs.x - cur.Aq1 * rs.y;
+                        const float qnorm = sqrtf(cur.qn2);
+                        const float lim2 = a.cdot2 * qnorm * rs.y * 1.001f + 4.0f * a.Bn * (cur.qn2 + rs.z) + 1e-30f;
                         atomicAdd(a.diag + 2, 1ull);
-                        if (fabsf(accl - dot) > lim) {
+                        if (fabsf(mine - ref) > lim2) {
                             atomicAdd(a.diag + 3, 1ull);
                             atomicOr(a.status, ST_BOUND);
                         }
                     }
                 }
+                tc_fence_before();
+                mbar_arrive(&accempty[acc]);
             }
-            tc_fence_before();
-            __syncthreads();
-            ++gt;
-            if (tid == 0 && t + S < ntiles) issue_tile(gt + uint32_t(S - 1), int(r0) + (t + S) * TC_N);
-            pending_from = t + 1;
-            pending_to = ntiles < t + 1 + S ? ntiles : t + 1 + S;
-        }
-        if (failed) break;
-        if (active) atomicMin(a.Ubits + q, __float_as_uint(fmaxf(U, 0.0f)));
-    }
-    if (failed) {
-        if (tid == 0) {
-            atomicOr(a.status, ST_TIMEOUT);
-            // let tiles still in flight land before shared memory goes away
-            for (int t = pending_from; t < pending_to; ++t) {
-                const uint32_t g = gt + uint32_t(t - pending_from);
-                mbar_wait_bounded(&bfull[g % uint32_t(S)], (g / uint32_t(S)) & 1u);
+            if (!ok) break;
+            if (active) {
+                flush();
+                atomicMin(a.Ubits + q, __float_as_uint(fmaxf(cur.U, 0.0f)));
             }
-            mbar_wait_bounded(&mma_bar, mphase);
+            mbar_arrive(&aempty[ab]);
+            mbar_arrive(&iq_empty[slot]);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TC_N);
+    if (warp == 1) tmem_dealloc(tmem, 2 * TC_N);
 }
 
 // ---------------------------------------------------------------- query prep
@@ -306,7 +472,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) tc_scan_kernel(const __grid_con
 __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restrict__ Y, int64_t Q, int d, int d_pad,
                                                             const uint32_t* __restrict__ probes, int64_t P_eff,
                                                             const uint32_t* __restrict__ offsets, uint32_t NC,
-                                                            const float* __restrict__ xs, int k, int seed,
+                                                            const float* __restrict__ xs, int k, int seed, float cdot2,
+                                                            const uint32_t* __restrict__ perm,
+                                                            const int64_t* __restrict__ query_src, int64_t grid_w,
+                                                            int radius,
                                                             __nv_bfloat16* __restrict__ Yb, float4* __restrict__ qstat,
                                                             uint32_t* __restrict__ Ubits,
                                                             uint32_t* __restrict__ surv_cnt)
@@ -322,7 +491,9 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
         v.y = c + 1 < d ? y[c + 1] : 0.f;
         v.z = c + 2 < d ? y[c + 2] : 0.f;
         v.w = c + 3 < d ? y[c + 3] : 0.f;
-        __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y), hi = __floats2bfloat162_rn(v.z, v.w);
+        // bf16(-2 y) = -2 bf16(y) exactly: the scale is a power of two
+        __nv_bfloat162 lo = __floats2bfloat162_rn(-2.f * v.x, -2.f * v.y),
+                       hi = __floats2bfloat162_rn(-2.f * v.z, -2.f * v.w);
         uint2 pk;
         pk.x = *reinterpret_cast<uint32_t*>(&lo);
         pk.y = *reinterpret_cast<uint32_t*>(&hi);
@@ -334,32 +505,76 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    // initial U: the k-th smallest distance among up to 128 rows of the first
+    // probed cones (in probe order), inflated by the fp32 error bound
     float U = INFINITY;
     if (seed) {
-        for (int64_t p = 0; p < P_eff; ++p) {
+        constexpr int SEED = 128;
+        float best[SEED / 32];
+        int have = 0;
+        for (int j = 0; j < SEED / 32; ++j) best[j] = INFINITY;
+        for (int64_t p = 0; p < P_eff && have < SEED; ++p) {
             const uint32_t b = probes[q * P_eff + p];
             if (b >= NC) continue;
             const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
-            if (o1 - o0 < uint32_t(k)) continue;
-            float worst = 0.f;
-            for (int j = 0; j < k; ++j) {
-                const float* xr = xs + size_t(o0 + j) * d_pad;
-                float t = 0.f;
-                for (int c = lane; c < d; c += 32) {
-                    const float df = xr[c] - y[c];
-                    t = fmaf(df, df, t);
+            for (uint32_t r0 = o0; r0 < o1 && have < SEED; r0 += 32) {
+                const uint32_t r = r0 + lane;
+                float t = INFINITY;
+                bool usable = r < o1;
+                if (usable && query_src && query_src[q] >= 0) {
+                    // an excluded row is not a candidate and cannot seed the bound
+                    const int64_t src = query_src[q];
+                    const int64_t id = int64_t(perm[r]);
+                    int64_t dr = id / grid_w - src / grid_w, dc = id % grid_w - src % grid_w;
+                    dr = dr < 0 ? -dr : dr;
+                    dc = dc < 0 ? -dc : dc;
+                    usable = (dr > dc ? dr : dc) > radius;
                 }
+                if (usable) {
+                    const float* xr = xs + size_t(r) * d_pad;
+                    t = 0.f;
+                    for (int c = 0; c < d; ++c) {
+                        const float df = xr[c] - y[c];
+                        t = fmaf(df, df, t);
+                    }
+                }
+                const int slot = have / 32;
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-                worst = fmaxf(worst, t);
+                for (int j = 0; j < SEED / 32; ++j)
+                    if (j == slot) best[j] = t;
+                have += 32;
             }
-            // any summation order is within (d + 6) 2^-24 relative of the exact value
-            U = worst * (1.0f + float(d + 8) * 5.9604645e-8f) + 1e-30f;
-            break;
         }
+        // k rounds of warp minimum over the (at most 128) seed distances
+        float kth = INFINITY;
+        int found = 0;
+        for (int j = 0; j < k; ++j) {
+            float m = best[0];
+            int mi = 0;
+#pragma unroll
+            for (int u = 1; u < SEED / 32; ++u)
+                if (best[u] < m) { m = best[u]; mi = u; }
+            float w = m;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
+            if (w == INFINITY) break;
+            const unsigned owner = __ballot_sync(0xffffffffu, m == w);
+            if (lane == __ffs(owner) - 1) {
+#pragma unroll
+                for (int u = 0; u < SEED / 32; ++u)
+                    if (u == mi) best[u] = INFINITY;
+            }
+            kth = w;
+            ++found;
+        }
+        // any summation order is within (d + 6) 2^-24 relative of the exact value
+        if (found == k) U = kth * (1.0f + float(d + 8) * 5.9604645e-8f) + 1e-30f;
     }
     if (lane == 0) {
-        qstat[q] = make_float4(s, sqrtf(s), 0.f, 0.f);
+        // A' = 2c|q| inflated by 2^-14 (bf16 hi/lo split of |x|) and rounded up to bf16
+        const float A = cdot2 * sqrtf(s) * (1.0f + 6.1035156e-5f);
+        const float Ap = __bfloat162float(__float2bfloat16_ru(A));
+        qstat[q] = make_float4(s, sqrtf(s), -Ap, 0.f);
         Ubits[q] = __float_as_uint(U);
         surv_cnt[q] = 0;
     }
@@ -474,9 +689,11 @@ int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_
         }
         fn = reinterpret_cast<EncodeTiledFn>(p);
     }
-    const int row_bytes = tc_row_bytes(d_pad);
-    const cuuint64_t dims[2] = {cuuint64_t(d_pad), cuuint64_t(N)};
-    const cuuint64_t strides[1] = {cuuint64_t(d_pad) * 2};
+    // d_pad == 0 encodes the 16-column extra block array instead
+    const int width = d_pad > 0 ? d_pad : 16;
+    const int row_bytes = d_pad > 0 ? tc_row_bytes(d_pad) : 32;
+    const cuuint64_t dims[2] = {cuuint64_t(width), cuuint64_t(N)};
+    const cuuint64_t strides[1] = {cuuint64_t(width) * 2};
     const cuuint32_t box[2] = {cuuint32_t(row_bytes / 2), cuuint32_t(TC_N)};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapSwizzle sw = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
@@ -492,37 +709,47 @@ int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_
     return 0;
 }
 
-size_t tc_map_bytes() { return sizeof(CUtensorMap); }
+size_t tc_map_bytes() { return 2 * sizeof(CUtensorMap); }
 
 int launch_tc_query_prep(const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes, int64_t P_eff,
-                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, __nv_bfloat16* Yb,
-                         float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st)
+                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, float cdot2,
+                         const uint32_t* perm, const int64_t* query_src, int64_t grid_w, int radius,
+                         __nv_bfloat16* Yb, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st)
 {
     if (Q == 0) return 0;
     tc_query_prep_kernel<<<unsigned((Q * 32 + 127) / 128), 128, 0, st>>>(Y, Q, d, d_pad, probes, P_eff, offsets, NC,
-                                                                         xs, k, seed ? 1 : 0, Yb, qstat, Ubits,
-                                                                         surv_cnt);
+                                                                         xs, k, seed ? 1 : 0, cdot2, perm, query_src,
+                                                                         grid_w, radius, Yb, qstat, Ubits, surv_cnt);
     return count_launch();
 }
 
 size_t tc_smem_bytes(int d_pad)
 {
-    const size_t need = 1024 + size_t(TC_M) * d_pad * 2 + size_t(tc_stages(d_pad)) * (size_t(TC_N) * d_pad * 2 + TC_N * 16);
-    // at least 47 KB so that at most four CTAs (4 x 128 TMEM columns) share an SM
-    return need < 47u * 1024u ? 47u * 1024u : need;
+    const size_t tileA = size_t(TC_M) * d_pad * 2 + TC_M * 32, tileB = size_t(TC_N) * d_pad * 2 + TC_N * 32;
+    const size_t need = 1024 + 2 * tileA + size_t(tc_stages(d_pad)) * tileB;
+    // at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
+    return need < 80u * 1024u ? 80u * 1024u : need;
 }
 
 template <int KMAX, bool EXCL>
-static int launch_tc_t(const void* map, const TcArgs& a, cudaStream_t st, int num_sms)
+static int launch_tc_t(const void* maps, const TcArgs& a, cudaStream_t st, int num_sms)
 {
     const size_t smem = tc_smem_bytes(a.d_pad);
     auto kern = tc_scan_kernel<KMAX, EXCL>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    int occ = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TC_THREADS, smem);
+    // resident CTAs per SM: registers, shared memory (228 KB per SM, 1 KB
+    // reserved per CTA) and TMEM (512 columns, 256 per CTA)
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, kern);
+    const int regs = fa.numRegs > 0 ? fa.numRegs : 255;
+    const int by_regs = 65536 / (regs * TC_ROLE_THREADS);
+    const int by_smem = int((228u * 1024u) / (smem + 1024u + size_t(fa.sharedSizeBytes)));
+    int occ = by_regs < by_smem ? by_regs : by_smem;
+    if (occ > 2) occ = 2;
     if (occ < 1) occ = 1;
-    if (occ > 4) occ = 4;
-    kern<<<unsigned(num_sms * occ), TC_THREADS, smem, st>>>(*static_cast<const CUtensorMap*>(map), a);
+    cudaGetLastError();
+    const CUtensorMap* m = static_cast<const CUtensorMap*>(maps);
+    kern<<<unsigned(num_sms * occ), TC_ROLE_THREADS, smem, st>>>(m[0], m[1], a);
     return count_launch();
 }
 
