@@ -29,19 +29,23 @@ __device__ __forceinline__ uint32_t sel_sign(uint64_t k) { return uint32_t(k) & 
 
 __device__ __forceinline__ bool finite_f(float x) { return (__float_as_uint(x) & 0x7F800000u) != 0x7F800000u; }
 
-// Cone id from the L selected (component, sign) pairs, in any order.
+// Cone id from the L selected (component, sign) pairs, in any order.  LC is
+// L when it is a compile-time constant (the loops then unroll to exactly L),
+// or 0 for a runtime L up to MAX_L.
+template <int LC>
 __device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L], int L,
                                                       const uint64_t* __restrict__ binom)
 {
+    constexpr int LM = LC > 0 ? LC : MAX_L;
     uint64_t rank = 0;
     uint32_t code = 0;
 #pragma unroll
-    for (int j = 0; j < MAX_L; ++j) {
-        if (j < L) {
+    for (int j = 0; j < LM; ++j) {
+        if (LC > 0 || j < L) {
             int pos = 0;  // position of member j in ascending component order
 #pragma unroll
-            for (int t = 0; t < MAX_L; ++t)
-                if (t < L && comp[t] < comp[j]) ++pos;
+            for (int t = 0; t < LM; ++t)
+                if ((LC > 0 || t < L) && comp[t] < comp[j]) ++pos;
             rank += __ldg(binom + comp[j] * (MAX_L + 1) + pos + 1);
             code |= sgn[j] << (L - 1 - pos);
         }
@@ -52,11 +56,12 @@ __device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], 
 // One group of LPV lanes per row.  VEC: d % 4 == 0 and 16-byte aligned rows,
 // lane l holds float4 number l, l+LPV (128-bit loads); else lane l holds the
 // scalars l, l+32, ... (LPV = 32).  At most 8 values per lane (d <= 256).
-template <int LPV, bool VEC>
+template <int LPV, bool VEC, int LC>
 __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                        const uint64_t* __restrict__ binom,
                                                        uint32_t* __restrict__ keys, uint32_t* __restrict__ status)
 {
+    constexpr int LM = LC > 0 ? LC : MAX_L;
     const int lane = threadIdx.x & 31;
     const int glane = lane & (LPV - 1);
     const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / LPV;
@@ -103,7 +108,10 @@ __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict_
         for (int r = 0; r < MAX_L; ++r) {
             comp[r] = 0;
             sgn[r] = 0;
-            if (r < L) {
+        }
+#pragma unroll
+        for (int r = 0; r < LM; ++r) {
+            if (LC > 0 || r < L) {
                 uint64_t best = 0;
 #pragma unroll
                 for (int f = 0; f < 8; ++f) best = v[f] > best ? v[f] : best;
@@ -119,7 +127,7 @@ __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict_
                 sgn[r] = sel_sign(best);
             }
         }
-        if (live && glane == 0) keys[row] = cone_from_members(comp, sgn, L, binom);
+        if (live && glane == 0) keys[row] = cone_from_members<LC>(comp, sgn, L, binom);
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_DATA);
 }
@@ -158,6 +166,22 @@ __global__ void __launch_bounds__(128) query_order_kernel(const float* __restric
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_QUERY);
 }
 
+template <int LC>
+static void launch_keys_lc(bool vec, int lpv, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d,
+                           int L, const uint64_t* binom, uint32_t* keys, uint32_t* status)
+{
+    if (vec) {
+        switch (lpv) {
+        case 4: data_keys_kernel<4, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        case 8: data_keys_kernel<8, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        case 16: data_keys_kernel<16, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        default: data_keys_kernel<32, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        }
+    } else {
+        data_keys_kernel<32, false, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status);
+    }
+}
+
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
                      uint32_t* status, cudaStream_t st, int num_sms)
 {
@@ -167,20 +191,16 @@ int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* bi
     while (lpv < n4 && lpv < 32) lpv <<= 1;
     if (!vec) lpv = 32;
     const int threads = 256;
-    const int64_t groups_needed = N;
-    int64_t blocks = (groups_needed * lpv + threads - 1) / threads;
+    int64_t blocks = (N * lpv + threads - 1) / threads;
     const int64_t cap = int64_t(num_sms) * 16;
     if (blocks > cap) blocks = cap;
     const dim3 g(static_cast<unsigned>(blocks)), b(static_cast<unsigned>(threads));
-    if (vec) {
-        switch (lpv) {
-        case 4: data_keys_kernel<4, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        case 8: data_keys_kernel<8, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        case 16: data_keys_kernel<16, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        default: data_keys_kernel<32, true><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        }
-    } else {
-        data_keys_kernel<32, false><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status);
+    switch (L) {
+    case 1: launch_keys_lc<1>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
+    case 2: launch_keys_lc<2>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
+    case 3: launch_keys_lc<3>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
+    case 4: launch_keys_lc<4>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
+    default: launch_keys_lc<0>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
     }
     return count_launch();
 }

@@ -290,7 +290,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv;
+    size_t yb, qstat, ubits, scnt, surv, hbuf;
     size_t total;
     int64_t max_items;
 };
@@ -324,9 +324,10 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         w.nitems = take(size_t(ix->NC + 1) * 4);
         w.item_off = take(size_t(ix->NC + 1) * 4);
         w.qlist = take(size_t(n) * 4);
-        w.items = take(size_t(mi > 0 ? mi : 1) * 8);
+        w.items = take(size_t(mi > 0 ? mi : 1) * 16);
         w.counters = take(256);
-        w.scan_temp = take(batched_scan_temp_bytes(ix->NC));
+        w.hbuf = take(size_t(wl_hist_entries(ix->NC, n, ix->num_sms)) * 4 + 4);
+        w.scan_temp = take(batched_scan_temp_bytes(ix->NC, n, ix->num_sms));
     }
     if (mode == MODE_BF16) {
         w.yb = take(size_t(Q) * ix->d_pad * 2);
@@ -702,7 +703,8 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         b.nitems = reinterpret_cast<uint32_t*>(w + L.nitems);
         b.item_off = reinterpret_cast<uint32_t*>(w + L.item_off);
         b.qlist = reinterpret_cast<uint32_t*>(w + L.qlist);
-        b.items = reinterpret_cast<uint2*>(w + L.items);
+        b.items = reinterpret_cast<uint4*>(w + L.items);
+        b.hbuf = reinterpret_cast<uint32_t*>(w + L.hbuf);
         b.counters = reinterpret_cast<uint32_t*>(w + L.counters);
         b.n_items_dev = b.item_off + ix->NC;
         b.scan_temp = w + L.scan_temp;

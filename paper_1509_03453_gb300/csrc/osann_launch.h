@@ -51,13 +51,15 @@ struct BatchedBuffers {
     uint32_t* nitems;     // NC + 1
     uint32_t* item_off;   // NC + 1
     uint32_t* qlist;      // Q * P_eff
-    uint2* items;         // max_items
+    uint4* items;         // max_items descriptors (first row, end row, first slot, slot count)
+    uint32_t* hbuf;       // per-block cone histograms (N_C <= 12288)
     uint32_t* counters;   // word 0: work counter of the tile scan
     const uint32_t* n_items_dev;  // device word holding the item count (item_off + NC)
     void* scan_temp;
     int64_t max_items;
 };
-size_t batched_scan_temp_bytes(int64_t NC);
+size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms);
+int wl_hist_entries(int64_t NC, int64_t n, int num_sms);
 int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
                     int group, BatchedBuffers& b, cudaStream_t st, int num_sms);
 int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y,

@@ -39,22 +39,6 @@ __device__ __forceinline__ bool cone_nonempty(const uint32_t* __restrict__ offse
     return b < NC && __ldg(offsets + b + 1) > __ldg(offsets + b);
 }
 
-__global__ void __launch_bounds__(512) wl_count_smem_kernel(const uint32_t* __restrict__ probes, int64_t n,
-                                                            const uint32_t* __restrict__ offsets, int NC,
-                                                            uint32_t* __restrict__ qcount)
-{
-    extern __shared__ uint32_t h[];
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) h[c] = 0;
-    __syncthreads();
-    for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, uint32_t(NC))) atomicAdd(&h[b], 1u);
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < NC; c += blockDim.x)
-        if (h[c]) atomicAdd(&qcount[c], h[c]);
-}
-
 __global__ void wl_count_global_kernel(const uint32_t* __restrict__ probes, int64_t n,
                                        const uint32_t* __restrict__ offsets, uint32_t NC,
                                        uint32_t* __restrict__ qcount)
@@ -75,54 +59,135 @@ __global__ void wl_fill_kernel(const uint32_t* __restrict__ probes, int64_t n, c
     }
 }
 
+// Cone-major per-block histograms: H[c * nb + b] = probes of block b's chunk
+// that hit non-empty cone c.  One exclusive scan of H (plus a trailing zero)
+// then gives every (cone, block) its first slot in the cone-major list.
+__global__ void __launch_bounds__(512) wl_block_hist_kernel(const uint32_t* __restrict__ probes, int64_t n,
+                                                            int64_t chunk, const uint32_t* __restrict__ offsets,
+                                                            int NC, uint32_t* __restrict__ H)
+{
+    extern __shared__ uint32_t h[];
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) h[c] = 0;
+    __syncthreads();
+    const int64_t t0 = int64_t(blockIdx.x) * chunk, t1 = t0 + chunk < n ? t0 + chunk : n;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const uint32_t b = probes[t];
+        if (cone_nonempty(offsets, b, uint32_t(NC))) atomicAdd(&h[b], 1u);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) H[int64_t(c) * gridDim.x + blockIdx.x] = h[c];
+}
+
+__global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __restrict__ probes, int64_t n,
+                                                            int64_t chunk, const uint32_t* __restrict__ offsets,
+                                                            int NC, const uint32_t* __restrict__ Hs,
+                                                            uint32_t* __restrict__ qlist)
+{
+    extern __shared__ uint32_t cur[];
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) cur[c] = Hs[int64_t(c) * gridDim.x + blockIdx.x];
+    __syncthreads();
+    const int64_t t0 = int64_t(blockIdx.x) * chunk, t1 = t0 + chunk < n ? t0 + chunk : n;
+    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const uint32_t b = probes[t];
+        if (cone_nonempty(offsets, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = uint32_t(t);
+    }
+}
+
+__global__ void wl_counts_from_H_kernel(const uint32_t* __restrict__ Hs, int64_t NC, int64_t nb,
+                                        uint32_t* __restrict__ qcount, uint32_t* __restrict__ qoff)
+{
+    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < NC; c += int64_t(gridDim.x) * blockDim.x) {
+        const uint32_t o = Hs[c * nb], e = Hs[(c + 1) * nb];  // Hs[NC * nb] is the total
+        qoff[c] = o;
+        qcount[c] = e - o;
+    }
+}
+
 __global__ void wl_nitems_kernel(const uint32_t* __restrict__ qcount, int64_t NC, int G, uint32_t* __restrict__ nitems)
 {
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c <= NC; c += int64_t(gridDim.x) * blockDim.x)
         nitems[c] = c < NC ? (qcount[c] + G - 1) / G : 0u;
 }
 
+// Item descriptors (first row, end row, first slot, slot count) of every
+// (cone, query group) pair.
 __global__ void wl_items_kernel(const uint32_t* __restrict__ nitems, const uint32_t* __restrict__ item_off,
-                                int64_t NC, uint2* __restrict__ items, uint32_t* __restrict__ counters)
+                                const uint32_t* __restrict__ offsets, const uint32_t* __restrict__ qcount,
+                                const uint32_t* __restrict__ qoff, int64_t NC, int G, uint4* __restrict__ items,
+                                uint32_t* __restrict__ counters)
 {
     const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (gtid == 0) counters[0] = 0;  // work counter of the tile scan that follows
     for (int64_t c = gtid; c < NC; c += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t n = nitems[c], o = item_off[c];
-        for (uint32_t g = 0; g < n; ++g) items[o + g] = make_uint2(uint32_t(c), g);
+        if (n == 0) continue;
+        const uint32_t r0 = offsets[c], r1 = offsets[c + 1], cnt = qcount[c], q0 = qoff[c];
+        for (uint32_t g = 0; g < n; ++g) {
+            const uint32_t rest = cnt - g * uint32_t(G);
+            items[o + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
+        }
     }
 }
 
-size_t batched_scan_temp_bytes(int64_t NC) { return scan_temp_bytes(NC + 1); }
+static int wl_blocks_impl(int64_t n, int num_sms)
+{
+    int64_t nb = (n + 4095) / 4096;
+    if (nb > 2 * num_sms) nb = 2 * num_sms;
+    return int(nb < 1 ? 1 : nb);
+}
+
+int wl_hist_entries(int64_t NC, int64_t n, int num_sms)
+{
+    return NC <= 12288 ? int(NC * wl_blocks_impl(n, num_sms) + 1) : 0;
+}
+
+size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms)
+{
+    const int64_t hn = NC <= 12288 ? NC * wl_blocks_impl(n, num_sms) + 1 : 0;
+    const int64_t m = hn > NC + 1 ? hn : NC + 1;
+    return scan_temp_bytes(m);
+}
+
 
 int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC, int group,
                     BatchedBuffers& b, cudaStream_t st, int num_sms)
 {
     const int64_t n = Q * P_eff;
-    cudaMemsetAsync(b.qcount, 0, size_t(NC + 1) * 4, st);
-    cudaMemsetAsync(b.fill, 0, size_t(NC) * 4, st);
-    int64_t blocks = (n + 4095) / 4096;
-    if (blocks < 1) blocks = 1;
     int rc;
+    int64_t cb = (NC + 256) / 256;
+    if (cb > 4 * num_sms) cb = 4 * num_sms;
     if (NC <= 12288) {
-        int64_t bl = blocks > 2 * num_sms ? 2 * num_sms : blocks;
-        wl_count_smem_kernel<<<unsigned(bl), 512, size_t(NC) * 4, st>>>(probes, n, offsets, int(NC), b.qcount);
+        // per-block cone histograms, one scan, shared-memory cursors: no
+        // contended global atomics
+        const int nb = wl_blocks_impl(n, num_sms);
+        const int64_t chunk = (n + nb - 1) / nb;
+        const int64_t hn = NC * nb + 1;
+        cudaMemsetAsync(b.hbuf + NC * nb, 0, 4, st);
+        wl_block_hist_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf);
+        if ((rc = count_launch())) return rc;
+        if ((rc = launch_exclusive_scan(b.hbuf, b.hbuf, hn, b.scan_temp, st))) return rc;
+        wl_counts_from_H_kernel<<<unsigned(cb), 256, 0, st>>>(b.hbuf, NC, nb, b.qcount, b.qoff);
+        if ((rc = count_launch())) return rc;
+        wl_block_fill_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf,
+                                                                         b.qlist);
+        if ((rc = count_launch())) return rc;
     } else {
+        cudaMemsetAsync(b.qcount, 0, size_t(NC + 1) * 4, st);
+        cudaMemsetAsync(b.fill, 0, size_t(NC) * 4, st);
+        int64_t blocks = (n + 4095) / 4096;
+        if (blocks < 1) blocks = 1;
         int64_t bl = blocks > 8 * num_sms ? 8 * num_sms : blocks;
         wl_count_global_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qcount);
-    }
-    if ((rc = count_launch())) return rc;
-    if ((rc = launch_exclusive_scan(b.qcount, b.qoff, NC + 1, b.scan_temp, st))) return rc;
-    {
-        int64_t bl = blocks > 8 * num_sms ? 8 * num_sms : blocks;
+        if ((rc = count_launch())) return rc;
+        if ((rc = launch_exclusive_scan(b.qcount, b.qoff, NC + 1, b.scan_temp, st))) return rc;
         wl_fill_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qoff, b.fill, b.qlist);
         if ((rc = count_launch())) return rc;
     }
-    int64_t cb = (NC + 256) / 256;
-    if (cb > 4 * num_sms) cb = 4 * num_sms;
     wl_nitems_kernel<<<unsigned(cb), 256, 0, st>>>(b.qcount, NC, group, b.nitems);
     if ((rc = count_launch())) return rc;
     if ((rc = launch_exclusive_scan(b.nitems, b.item_off, NC + 1, b.scan_temp, st))) return rc;
-    wl_items_kernel<<<unsigned(cb), 256, 0, st>>>(b.nitems, b.item_off, NC, b.items, b.counters);
+    wl_items_kernel<<<unsigned(cb), 256, 0, st>>>(b.nitems, b.item_off, offsets, b.qcount, b.qoff, NC, group,
+                                                   b.items, b.counters);
     return count_launch();
 }
 
@@ -134,7 +199,7 @@ struct TileArgs {
     const uint32_t* perm;      // row -> point id
     const float* Y;            // queries, stride d
     const int64_t* query_src;  // exclusion sources (nullable)
-    const uint2* items;        // sparse mode: (cone, group)
+    const uint4* items;        // sparse mode: (first row, end row, first slot, slot count)
     const uint32_t* n_items_dev;
     const uint32_t* qcount;
     const uint32_t* qoff;
@@ -169,13 +234,11 @@ __device__ __forceinline__ ItemDesc load_item(const TileArgs& a, uint32_t item, 
         it.qn = uint32_t((qe < a.Q ? qe : a.Q) - it.qbeg);
         it.chunk = c;
     } else {
-        const uint2 bg = a.items[item];
-        it.row0 = __ldg(a.offsets + bg.x);
-        it.row1 = __ldg(a.offsets + bg.x + 1);
-        const uint32_t cnt = a.qcount[bg.x];
-        it.qbeg = a.qoff[bg.x] + bg.y * uint32_t(G);
-        const uint32_t rest = cnt - bg.y * uint32_t(G);
-        it.qn = rest < uint32_t(G) ? rest : uint32_t(G);
+        const uint4 d = a.items[item];
+        it.row0 = d.x;
+        it.row1 = d.y;
+        it.qbeg = d.z;
+        it.qn = d.w;
         it.chunk = 0;
     }
     return it;

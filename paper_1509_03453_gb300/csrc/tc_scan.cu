@@ -46,7 +46,7 @@ struct TcArgs {
     const __nv_bfloat16* Yb;  // Q x d_pad, holds bf16(-2 y)
     const float4* qstat;      // per query: (|q|^2, |q|, -A' (bf16 value, A' >= A = 2c|q|), 0)
     const int64_t* query_src;
-    const uint2* items;
+    const uint4* items;  // (first row, end row, first slot, slot count)
     const uint32_t* n_items_dev;
     const uint32_t* qcount;
     const uint32_t* qoff;
@@ -179,23 +179,21 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         if (lane == 0) {
             const uint32_t n_items = *a.n_items_dev;
             uint32_t it = 0, tc = 0;
-            bool done = false;
+            // the next item's index and descriptor are fetched one publish
+            // ahead, so their latency overlaps the current item's tiles
+            uint32_t pf_item = atomicAdd(a.counter, 1u);
+            uint4 pf = pf_item < n_items ? a.items[pf_item] : make_uint4(0xFFFFFFFFu, 0, 0, 0);
             auto publish = [&](TcItem& out) -> bool {
                 const int slot = int(it % TC_IQ);
                 if (it >= TC_IQ && !wait(&iq_empty[slot], ((it / TC_IQ) - 1) & 1u)) return false;
                 TcItem d;
-                const uint32_t item = done ? n_items : atomicAdd(a.counter, 1u);
-                if (item >= n_items) {
-                    d.r0 = 0xFFFFFFFFu;
-                    d.r1 = d.qbeg = d.qn = 0;
-                    done = true;
-                } else {
-                    const uint2 bg = a.items[item];
-                    d.r0 = __ldg(a.offsets + bg.x);
-                    d.r1 = __ldg(a.offsets + bg.x + 1);
-                    const uint32_t cnt = a.qcount[bg.x];
-                    d.qbeg = a.qoff[bg.x] + bg.y * TC_M;
-                    d.qn = min(cnt - bg.y * TC_M, uint32_t(TC_M));
+                d.r0 = pf.x;
+                d.r1 = pf.y;
+                d.qbeg = pf.z;
+                d.qn = pf.w;
+                if (d.r0 != 0xFFFFFFFFu) {
+                    pf_item = atomicAdd(a.counter, 1u);
+                    pf = pf_item < n_items ? a.items[pf_item] : make_uint4(0xFFFFFFFFu, 0, 0, 0);
                 }
                 iq[slot] = d;
                 mbar_arrive(&iq_full[slot]);
@@ -466,23 +464,27 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
 
 // ---------------------------------------------------------------- query prep
 
-// One warp per query: bf16 copy, norms, survivor counter reset, and the
-// initial upper bound U: k rows of the first probed cone holding at least k
-// rows (their fp32 distances, inflated by the fp32 error bound), or +inf.
+// One warp per query: bf16 copy of -2y, norms and A', survivor counter reset,
+// and the initial upper bound U: the k-th smallest canonical fp32 distance
+// among up to TC_SEED rows of the first probed cones (in probe order, excluded
+// rows skipped), inflated by the fp32 error bound; +inf if fewer than k rows.
+constexpr int TC_SEED = 128;
+
+template <int F>
 __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restrict__ Y, int64_t Q, int d, int d_pad,
                                                             const uint32_t* __restrict__ probes, int64_t P_eff,
                                                             const uint32_t* __restrict__ offsets, uint32_t NC,
-                                                            const float* __restrict__ xs, int k, int seed, float cdot2,
+                                                            const float* __restrict__ xs, int k, float cdot2,
                                                             const uint32_t* __restrict__ perm,
                                                             const int64_t* __restrict__ query_src, int64_t grid_w,
-                                                            int radius,
-                                                            __nv_bfloat16* __restrict__ Yb, float4* __restrict__ qstat,
-                                                            uint32_t* __restrict__ Ubits,
+                                                            int radius, __nv_bfloat16* __restrict__ Yb,
+                                                            float4* __restrict__ qstat, uint32_t* __restrict__ Ubits,
                                                             uint32_t* __restrict__ surv_cnt)
 {
-    const int lane = threadIdx.x & 31;
+    __shared__ float seed[4][TC_SEED];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    if (q >= Q) return;
+    if (q >= Q) return;  // whole warp
     const float* y = Y + q * int64_t(d);
     float s = 0.f;
     for (int c = lane * 4; c < d_pad; c += 128) {
@@ -505,70 +507,82 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    // initial U: the k-th smallest distance among up to 128 rows of the first
-    // probed cones (in probe order), inflated by the fp32 error bound
-    float U = INFINITY;
-    if (seed) {
-        constexpr int SEED = 128;
-        float best[SEED / 32];
-        int have = 0;
-        for (int j = 0; j < SEED / 32; ++j) best[j] = INFINITY;
-        for (int64_t p = 0; p < P_eff && have < SEED; ++p) {
-            const uint32_t b = probes[q * P_eff + p];
-            if (b >= NC) continue;
-            const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
-            for (uint32_t r0 = o0; r0 < o1 && have < SEED; r0 += 32) {
-                const uint32_t r = r0 + lane;
-                float t = INFINITY;
-                bool usable = r < o1;
-                if (usable && query_src && query_src[q] >= 0) {
-                    // an excluded row is not a candidate and cannot seed the bound
-                    const int64_t src = query_src[q];
-                    const int64_t id = int64_t(perm[r]);
-                    int64_t dr = id / grid_w - src / grid_w, dc = id % grid_w - src % grid_w;
-                    dr = dr < 0 ? -dr : dr;
-                    dc = dc < 0 ? -dc : dc;
-                    usable = (dr > dc ? dr : dc) > radius;
-                }
-                if (usable) {
-                    const float* xr = xs + size_t(r) * d_pad;
-                    t = 0.f;
-                    for (int c = 0; c < d; ++c) {
-                        const float df = xr[c] - y[c];
-                        t = fmaf(df, df, t);
-                    }
-                }
-                const int slot = have / 32;
+
+    // seed rows: TPR lanes per row (canonical distance, as in the rerank)
+    const int n4 = d_pad >> 2;
+    const int TPR = n4 / F, CPP = 32 / TPR;
+    const int g = lane / TPR, sub = lane % TPR;
+    float4 qv[F];
 #pragma unroll
-                for (int j = 0; j < SEED / 32; ++j)
-                    if (j == slot) best[j] = t;
-                have += 32;
+    for (int f = 0; f < F; ++f) {
+        const int c = 4 * (sub * F + f);
+        qv[f].x = c + 0 < d ? y[c + 0] : 0.f;
+        qv[f].y = c + 1 < d ? y[c + 1] : 0.f;
+        qv[f].z = c + 2 < d ? y[c + 2] : 0.f;
+        qv[f].w = c + 3 < d ? y[c + 3] : 0.f;
+    }
+    const int64_t src = query_src ? query_src[q] : -1;
+    int n = 0;  // seed slots used (multiple of CPP)
+    for (int64_t p = 0; p < P_eff && n < TC_SEED; ++p) {
+        const uint32_t b = probes[q * P_eff + p];
+        if (b >= NC) continue;
+        const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
+        for (uint32_t r0 = o0; r0 < o1 && n < TC_SEED; r0 += CPP) {
+            const uint32_t r = r0 + g;
+            bool usable = r < o1;
+            const float4* xr = reinterpret_cast<const float4*>(xs + size_t(usable ? r : o0) * d_pad) + sub * F;
+            float cpart[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) cpart[f] = sq4(xr[f], qv[f]);
+            const float dist = lane_tree(pair_tree<F>(cpart), TPR);
+            if (usable && src >= 0) {
+                // an excluded row is not a candidate and cannot seed the bound
+                const int64_t id = int64_t(perm[r]);
+                int64_t dr = id / grid_w - src / grid_w, dc = id % grid_w - src % grid_w;
+                dr = dr < 0 ? -dr : dr;
+                dc = dc < 0 ? -dc : dc;
+                usable = (dr > dc ? dr : dc) > radius;
             }
+            if (sub == 0) seed[w][n + g] = usable ? dist : INFINITY;
+            n += CPP;
         }
-        // k rounds of warp minimum over the (at most 128) seed distances
+    }
+    __syncwarp();
+    // k rounds of warp minimum over the seed distances
+    float U = INFINITY;
+    {
+        float mine[TC_SEED / 32];
+#pragma unroll
+        for (int i = 0; i < TC_SEED / 32; ++i) {
+            const int slot = lane + 32 * i;
+            mine[i] = slot < n ? seed[w][slot] : INFINITY;
+        }
         float kth = INFINITY;
         int found = 0;
         for (int j = 0; j < k; ++j) {
-            float m = best[0];
+            float m = mine[0];
             int mi = 0;
 #pragma unroll
-            for (int u = 1; u < SEED / 32; ++u)
-                if (best[u] < m) { m = best[u]; mi = u; }
-            float w = m;
+            for (int i = 1; i < TC_SEED / 32; ++i)
+                if (mine[i] < m) {
+                    m = mine[i];
+                    mi = i;
+                }
+            float wm = m;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) w = fminf(w, __shfl_xor_sync(0xffffffffu, w, o));
-            if (w == INFINITY) break;
-            const unsigned owner = __ballot_sync(0xffffffffu, m == w);
+            for (int o = 16; o > 0; o >>= 1) wm = fminf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
+            if (wm == INFINITY) break;
+            const unsigned owner = __ballot_sync(0xffffffffu, m == wm);
             if (lane == __ffs(owner) - 1) {
 #pragma unroll
-                for (int u = 0; u < SEED / 32; ++u)
-                    if (u == mi) best[u] = INFINITY;
+                for (int i = 0; i < TC_SEED / 32; ++i)
+                    if (i == mi) mine[i] = INFINITY;
             }
-            kth = w;
+            kth = wm;
             ++found;
         }
-        // any summation order is within (d + 6) 2^-24 relative of the exact value
-        if (found == k) U = kth * (1.0f + float(d + 8) * 5.9604645e-8f) + 1e-30f;
+        // the canonical fp32 distance is within 6.6e-7 relative of the exact one
+        if (found == k) U = kth * (1.0f + 2e-6f) + 1e-30f;
     }
     if (lane == 0) {
         // A' = 2c|q| inflated by 2^-14 (bf16 hi/lo split of |x|) and rounded up to bf16
@@ -717,9 +731,14 @@ int launch_tc_query_prep(const float* Y, int64_t Q, int d, int d_pad, const uint
                          __nv_bfloat16* Yb, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st)
 {
     if (Q == 0) return 0;
-    tc_query_prep_kernel<<<unsigned((Q * 32 + 127) / 128), 128, 0, st>>>(Y, Q, d, d_pad, probes, P_eff, offsets, NC,
-                                                                         xs, k, seed ? 1 : 0, cdot2, perm, query_src,
-                                                                         grid_w, radius, Yb, qstat, Ubits, surv_cnt);
+    const unsigned blocks = unsigned((Q * 32 + 127) / 128);
+    const int64_t pe = seed ? P_eff : 0;
+    if (d_pad <= 128)
+        tc_query_prep_kernel<1><<<blocks, 128, 0, st>>>(Y, Q, d, d_pad, probes, pe, offsets, NC, xs, k, cdot2, perm,
+                                                        query_src, grid_w, radius, Yb, qstat, Ubits, surv_cnt);
+    else
+        tc_query_prep_kernel<2><<<blocks, 128, 0, st>>>(Y, Q, d, d_pad, probes, pe, offsets, NC, xs, k, cdot2, perm,
+                                                        query_src, grid_w, radius, Yb, qstat, Ubits, surv_cnt);
     return count_launch();
 }
 
