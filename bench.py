@@ -284,8 +284,8 @@ def run_gpu(args):
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stats.items() if v[1]}
     stage_n = {k: v[1] / args.steps for k, v in stats.items() if v[1]}
     dom = max(stats, key=lambda s: stats[s][0])
-    path_used = "bf16" if stats.get("tc_scan", (0, 0))[1] else ("batched" if stats.get("tile_scan", (0, 0))[1]
-                                                              else "plain")
+    path_used = "tensor-core screen (fp16 operands)" if stats.get("tc_scan", (0, 0))[1] else (
+        "batched fp32" if stats.get("tile_scan", (0, 0))[1] else "plain fp32")
     pairs = None
     roof = None
     # candidate pairs of the timed search (exact count from the probe lists)
@@ -294,17 +294,20 @@ def run_gpu(args):
     pr = ix.probes(Yd, P)
     sizes = (off[1:] - off[:-1])
     pairs = int(sizes[pr].sum().item())
+    ix.search(Yd, P, K, out=(out_ids, out_d2), workspace=work)
+    screen = ix.screen_stats() if path_used.startswith("tensor") else None
     ix.close()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     dom_ms = stage_ms[dom]
     if dom == "tc_scan":
-        # the contraction: 2d flops per (query, candidate) pair on bf16 tensor cores
+        # the contraction: 2d flops per (query, candidate) pair on 16-bit tensor
+        # cores (fp16 and bf16 share the dense rate)
         flops = 2.0 * D * pairs
         peak = peaks.get("bf16_tflops", 1900.0)
         achieved = flops / (dom_ms / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"{peak_src} bf16 dense (burst)",
+                "peak_source": f"{peak_src} bf16 dense (burst; fp16 has the same nominal rate)",
                 "algorithmic": f"{pairs} (query, candidate) pairs x 2d flops per launch "
                                f"(issued MMA work is larger: padded tiles and one extra K block of 16)",
                 "avg_launch_ms": round(dom_ms, 4)}
@@ -349,6 +352,7 @@ def run_gpu(args):
                        "p99": round(float(np.percentile(times, 99)), 4),
                        "note": "per batch step of Q queries"},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "screen": screen,
         "stage_launches_per_step": stage_n,
         "plain_fp32": {"value": round(Q_FULL / (np.mean(plain_times) / 1e3), 1), "unit": "queries/s",
                        "ms_per_step": round(float(np.mean(plain_times)), 4)},
@@ -441,7 +445,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
-    ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16"])
+    ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16", "fp16"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

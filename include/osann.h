@@ -45,6 +45,9 @@ extern "C" {
 #define OSANN_PATH_BATCHED 2 /* cone-major work list, persistent fp32 tile scan */
 #define OSANN_PATH_BF16 3    /* cone-major work list, bf16 tensor-core screening with a
                                 certified error bound, exact fp32 rerank (d <= 128) */
+#define OSANN_PATH_FP16 4    /* as OSANN_PATH_BF16 with fp16 operands (data and queries
+                                scaled by an exact power of two): an 8x tighter bound,
+                                fewer candidates to rerank; the default when batched */
 
 /* Status flags returned by osann_status. */
 #define OSANN_STATUS_NONFINITE_DATA 1u
@@ -87,8 +90,11 @@ int osann_query_order(const float *d_queries, int64_t Q, int32_t d, uint8_t *d_o
 
 /* Build the index of one basis (Sec. 4, preparation phase; Table II):
  * cone keys of all points, cone histogram and exclusive scan (CSR offsets),
- * stable counting sort of point ids by cone, and the permuted fp32 copy of
- * the vectors (zero padded to d_pad in {16, 32, 64, 128, 256}).
+ * stable counting sort of point ids by cone, the permuted fp32 copy of the
+ * vectors (zero padded to d_pad in {16, 32, 64, 128, 256}) and, for
+ * d <= 128, the scaled fp16 operands of the tensor-core screen (the bf16
+ * ones are made on the first OSANN_PATH_BF16 search, which then
+ * synchronises its stream once).
  * d_data: N x d fp32, read only (the index keeps its own copy).
  * Synchronises `stream` once.  Errors: INVALID (N < 1, d outside [1,256],
  * L outside [1, min(d,16)], out == NULL), UNSUPPORTED (N >= 2^31 or

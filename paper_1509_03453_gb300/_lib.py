@@ -22,7 +22,7 @@ ERRORS = {
     -5: "CUDA error",
     -6: "device wait timed out",
 }
-PATHS = {"auto": 0, "plain": 1, "batched": 2, "bf16": 3}
+PATHS = {"auto": 0, "plain": 1, "batched": 2, "bf16": 3, "fp16": 4}
 STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
           "plain_scan", "bruteforce", "tc_prep", "tc_scan", "tc_rerank"]
 STATUS_NONFINITE_DATA = 1

@@ -6,13 +6,16 @@
 //   offsets[N_C + 1]  exclusive prefix sum of the cone counts,
 //   perm[N]           point ids, ascending inside every cone (stable order),
 //   xs[N x d_pad]     the vectors in perm order, fp32, zero padded,
-//   xb[N x d_pad]     the same in bf16 (tensor-core screening path),
-//   norm2[N]          fp32 squared norms of the xs rows.
+//   rowstat[N]        ((1-B)|x|^2, |x|, |x|^2, 0) for the tensor-core screen,
+//   x16, xe16         (optional) the screen's fp16 operands, written here so
+//                     the vectors are read once.
 // Nothing here spins on another block: the scan is reduce-then-scan, the sort
 // is a least-significant-digit radix sort whose passes are stable by lane
 // rank inside each warp chunk and by chunk order across chunks.
 #include "osann_device.cuh"
 #include "osann_launch.h"
+
+#include <cuda_fp16.h>
 
 namespace osann {
 
@@ -308,10 +311,11 @@ int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t
 template <int LPV, bool VEC>
 __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restrict__ X, int64_t N, int d, int d_pad,
                                                          const uint32_t* __restrict__ perm, float* __restrict__ xs,
-                                                         __nv_bfloat16* __restrict__ xb, float* __restrict__ norm2,
-                                                         float4* __restrict__ rowstat, __nv_bfloat16* __restrict__ xe,
-                                                         float Bn)
+                                                         float4* __restrict__ rowstat, float Bn,
+                                                         const float* __restrict__ tcs, uint16_t* __restrict__ x16,
+                                                         uint16_t* __restrict__ xe16)
 {
+    const float sc = tcs ? tcs[0] : 1.0f, sc2 = tcs ? tcs[1] : 1.0f;
     const int lane = threadIdx.x & 31;
     const int glane = lane & (LPV - 1);
     const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / LPV;
@@ -339,13 +343,13 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restric
                     v.w = c + 3 < d ? __ldg(xr + c + 3) : 0.0f;
                 }
                 reinterpret_cast<float4*>(xs + r * int64_t(d_pad))[i4] = v;
-                if (xb) {
-                    __nv_bfloat162 lo = __floats2bfloat162_rn(v.x, v.y);
-                    __nv_bfloat162 hi = __floats2bfloat162_rn(v.z, v.w);
-                    uint2 packed;
-                    packed.x = *reinterpret_cast<uint32_t*>(&lo);
-                    packed.y = *reinterpret_cast<uint32_t*>(&hi);
-                    reinterpret_cast<uint2*>(xb + r * int64_t(d_pad))[i4] = packed;
+                if (x16) {
+                    // fp16 operands of the tensor-core screen: s x, s a power of two
+                    const __half2 lo = __floats2half2_rn(sc * v.x, sc * v.y), hi = __floats2half2_rn(sc * v.z, sc * v.w);
+                    uint2 pk;
+                    pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+                    pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+                    reinterpret_cast<uint2*>(x16 + r * int64_t(d_pad))[i4] = pk;
                 }
                 s = fmaf(v.x, v.x, s);
                 s = fmaf(v.y, v.y, s);
@@ -356,33 +360,23 @@ __global__ void __launch_bounds__(256) gather_rows_kernel(const float* __restric
 #pragma unroll
         for (int m = LPV / 2; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
         if (live && glane == 0) {
-            norm2[r] = s;
-            const float xn1 = s * (1.0f - Bn), nrm = sqrtf(s);
-            if (rowstat) rowstat[r] = make_float4(xn1, nrm, s, 0.0f);
-            if (xe) {
-                // extra K block of the tensor-core screen: bf16 hi/lo splits of
-                // (1-B)|x|^2 and |x|, then zeros
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(xn1);
-                const __nv_bfloat16 l0 = __float2bfloat16_rn(xn1 - __bfloat162float(h0));
-                const __nv_bfloat16 h1 = __float2bfloat16_rn(nrm);
-                const __nv_bfloat16 l1 = __float2bfloat16_rn(nrm - __bfloat162float(h1));
-                const __nv_bfloat162 p0 = __halves2bfloat162(h0, l0), p1 = __halves2bfloat162(h1, l1);
-                uint4 e0;
-                e0.x = *reinterpret_cast<const uint32_t*>(&p0);
-                e0.y = *reinterpret_cast<const uint32_t*>(&p1);
-                e0.z = 0;
-                e0.w = 0;
-                uint4* dst = reinterpret_cast<uint4*>(xe + r * 16);
-                dst[0] = e0;
-                dst[1] = make_uint4(0, 0, 0, 0);
+            rowstat[r] = make_float4(s * (1.0f - Bn), sqrtf(s), s, 0.0f);
+            if (xe16) {
+                // extra K block: fp16 hi/lo of (1-B) s^2 |x|^2 and s |x|, then zeros
+                const float a = sc2 * s * (1.0f - Bn), b = sc * sqrtf(s);
+                const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
+                const __half al = __float2half_rn(a - __half2float(ah)), bl = __float2half_rn(b - __half2float(bh));
+                uint4* dst = reinterpret_cast<uint4*>(xe16 + r * 16);
+                dst[0] = make_uint4(uint32_t(__half_as_ushort(ah)) | (uint32_t(__half_as_ushort(al)) << 16),
+                                    uint32_t(__half_as_ushort(bh)) | (uint32_t(__half_as_ushort(bl)) << 16), 0u, 0u);
+                dst[1] = make_uint4(0u, 0u, 0u, 0u);
             }
         }
     }
 }
 
-int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
-                       __nv_bfloat16* xb, float* norm2, float4* rowstat, __nv_bfloat16* xe, float Bn, cudaStream_t st,
-                       int num_sms)
+int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs, float4* rowstat,
+                       float Bn, const float* tcs, uint16_t* x16, uint16_t* xe16, cudaStream_t st, int num_sms)
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -394,9 +388,9 @@ int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32
     const dim3 g(static_cast<unsigned>(blocks)), b(256u);
 #define OSANN_GATHER(LP)                                                                                 \
     if (vec)                                                                                             \
-        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, xe, Bn); \
+        gather_rows_kernel<LP, true><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, rowstat, Bn, tcs, x16, xe16); \
     else                                                                                                 \
-        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, xb, norm2, rowstat, xe, Bn);
+        gather_rows_kernel<LP, false><<<g, b, 0, st>>>(X, N, d, d_pad, perm, xs, rowstat, Bn, tcs, x16, xe16);
     switch (lpv) {
     case 4: OSANN_GATHER(4); break;
     case 8: OSANN_GATHER(8); break;

@@ -59,7 +59,8 @@ __device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], 
 template <int LPV, bool VEC, int LC>
 __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                        const uint64_t* __restrict__ binom,
-                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ status)
+                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ status,
+                                                       uint32_t* __restrict__ maxn2_bits)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
     const int lane = threadIdx.x & 31;
@@ -67,67 +68,90 @@ __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict_
     const int64_t gid = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) / LPV;
     const int64_t ngroups = int64_t(gridDim.x) * blockDim.x / LPV;
     bool bad = false;
-    // every group of the warp runs the same trip count so shuffles stay converged
-    const int64_t iters = (N + ngroups - 1) / ngroups;
+    float nmax = 0.0f;  // largest squared row norm seen by this lane's group
+    // rows are taken two at a time per group (both loads in flight before
+    // either is processed); every group of the warp runs the same trip count
+    // so shuffles stay converged
+    const int64_t iters = (N + 2 * ngroups - 1) / (2 * ngroups);
     for (int64_t it = 0; it < iters; ++it) {
-        const int64_t row = gid + it * ngroups;
-        const bool live = row < N;
-        uint64_t v[8];
+        uint64_t v[2][8];
+        int64_t rows[2];
+        float nsq[2] = {0.0f, 0.0f};
 #pragma unroll
-        for (int f = 0; f < 8; ++f) v[f] = 0;  // 0 = empty slot (real keys are > 0)
-        if (VEC) {
-            const float4* xr = reinterpret_cast<const float4*>(X + (live ? row : 0) * int64_t(d));
-            const int n4 = d >> 2;
+        for (int h = 0; h < 2; ++h) {
+            const int64_t row = gid + (2 * it + h) * ngroups;
+            rows[h] = row;
+            const bool live = row < N;
 #pragma unroll
-            for (int f = 0; f < 2; ++f) {
-                int i4 = glane + f * LPV;
-                if (live && i4 < n4) {
-                    float4 t = __ldg(xr + i4);
-                    bad |= !(finite_f(t.x) && finite_f(t.y) && finite_f(t.z) && finite_f(t.w));
-                    v[4 * f + 0] = sel_key(t.x, 4 * i4 + 0);
-                    v[4 * f + 1] = sel_key(t.y, 4 * i4 + 1);
-                    v[4 * f + 2] = sel_key(t.z, 4 * i4 + 2);
-                    v[4 * f + 3] = sel_key(t.w, 4 * i4 + 3);
+            for (int f = 0; f < 8; ++f) v[h][f] = 0;  // 0 = empty slot (real keys are > 0)
+            if (VEC) {
+                const float4* xr = reinterpret_cast<const float4*>(X + (live ? row : 0) * int64_t(d));
+                const int n4 = d >> 2;
+#pragma unroll
+                for (int f = 0; f < 2; ++f) {
+                    int i4 = glane + f * LPV;
+                    if (live && i4 < n4) {
+                        float4 t = __ldg(xr + i4);
+                        bad |= !(finite_f(t.x) && finite_f(t.y) && finite_f(t.z) && finite_f(t.w));
+                        nsq[h] = fmaf(t.x, t.x, fmaf(t.y, t.y, fmaf(t.z, t.z, fmaf(t.w, t.w, nsq[h]))));
+                        v[h][4 * f + 0] = sel_key(t.x, 4 * i4 + 0);
+                        v[h][4 * f + 1] = sel_key(t.y, 4 * i4 + 1);
+                        v[h][4 * f + 2] = sel_key(t.z, 4 * i4 + 2);
+                        v[h][4 * f + 3] = sel_key(t.w, 4 * i4 + 3);
+                    }
                 }
-            }
-        } else {
-            const float* xr = X + (live ? row : 0) * int64_t(d);
+            } else {
+                const float* xr = X + (live ? row : 0) * int64_t(d);
 #pragma unroll
-            for (int f = 0; f < 8; ++f) {
-                int c = glane + f * 32;
-                if (live && c < d) {
-                    float t = __ldg(xr + c);
-                    bad |= !finite_f(t);
-                    v[f] = sel_key(t, c);
+                for (int f = 0; f < 8; ++f) {
+                    int c = glane + f * 32;
+                    if (live && c < d) {
+                        float t = __ldg(xr + c);
+                        bad |= !finite_f(t);
+                        nsq[h] = fmaf(t, t, nsq[h]);
+                        v[h][f] = sel_key(t, c);
+                    }
                 }
             }
         }
-        int comp[MAX_L];
-        uint32_t sgn[MAX_L];
 #pragma unroll
-        for (int r = 0; r < MAX_L; ++r) {
-            comp[r] = 0;
-            sgn[r] = 0;
-        }
+        for (int h = 0; h < 2; ++h) {
+            int comp[MAX_L];
+            uint32_t sgn[MAX_L];
 #pragma unroll
-        for (int r = 0; r < LM; ++r) {
-            if (LC > 0 || r < L) {
-                uint64_t best = 0;
-#pragma unroll
-                for (int f = 0; f < 8; ++f) best = v[f] > best ? v[f] : best;
-#pragma unroll
-                for (int m = LPV / 2; m > 0; m >>= 1) {
-                    uint64_t o = shfl_xor_u64(best, m);
-                    best = o > best ? o : best;
-                }
-#pragma unroll
-                for (int f = 0; f < 8; ++f)
-                    if (v[f] == best) v[f] = 0;  // taken (keys are unique per row)
-                comp[r] = sel_comp(best);
-                sgn[r] = sel_sign(best);
+            for (int r = 0; r < MAX_L; ++r) {
+                comp[r] = 0;
+                sgn[r] = 0;
             }
+#pragma unroll
+            for (int r = 0; r < LM; ++r) {
+                if (LC > 0 || r < L) {
+                    uint64_t best = 0;
+#pragma unroll
+                    for (int f = 0; f < 8; ++f) best = v[h][f] > best ? v[h][f] : best;
+#pragma unroll
+                    for (int m = LPV / 2; m > 0; m >>= 1) {
+                        uint64_t o = shfl_xor_u64(best, m);
+                        best = o > best ? o : best;
+                    }
+#pragma unroll
+                    for (int f = 0; f < 8; ++f)
+                        if (v[h][f] == best) v[h][f] = 0;  // taken (keys are unique per row)
+                    comp[r] = sel_comp(best);
+                    sgn[r] = sel_sign(best);
+                }
+            }
+            if (rows[h] < N && glane == 0) keys[rows[h]] = cone_from_members<LC>(comp, sgn, L, binom);
+#pragma unroll
+            for (int m = LPV / 2; m > 0; m >>= 1) nsq[h] += __shfl_xor_sync(0xffffffffu, nsq[h], m);
+            nmax = fmaxf(nmax, nsq[h]);  // non-finite rows are reported separately
         }
-        if (live && glane == 0) keys[row] = cone_from_members<LC>(comp, sgn, L, binom);
+    }
+    if (maxn2_bits) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        // nonnegative floats order like their bits
+        if (lane == 0 && nmax > 0.0f && finite_f(nmax)) atomicMax(maxn2_bits, __float_as_uint(nmax));
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_DATA);
 }
@@ -168,22 +192,22 @@ __global__ void __launch_bounds__(128) query_order_kernel(const float* __restric
 
 template <int LC>
 static void launch_keys_lc(bool vec, int lpv, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d,
-                           int L, const uint64_t* binom, uint32_t* keys, uint32_t* status)
+                           int L, const uint64_t* binom, uint32_t* keys, uint32_t* status, uint32_t* maxn2)
 {
     if (vec) {
         switch (lpv) {
-        case 4: data_keys_kernel<4, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        case 8: data_keys_kernel<8, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        case 16: data_keys_kernel<16, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
-        default: data_keys_kernel<32, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status); break;
+        case 4: data_keys_kernel<4, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
+        case 8: data_keys_kernel<8, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
+        case 16: data_keys_kernel<16, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
+        default: data_keys_kernel<32, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
         }
     } else {
-        data_keys_kernel<32, false, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status);
+        data_keys_kernel<32, false, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2);
     }
 }
 
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
-                     uint32_t* status, cudaStream_t st, int num_sms)
+                     uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms)
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -196,11 +220,11 @@ int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* bi
     if (blocks > cap) blocks = cap;
     const dim3 g(static_cast<unsigned>(blocks)), b(static_cast<unsigned>(threads));
     switch (L) {
-    case 1: launch_keys_lc<1>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
-    case 2: launch_keys_lc<2>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
-    case 3: launch_keys_lc<3>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
-    case 4: launch_keys_lc<4>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
-    default: launch_keys_lc<0>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status); break;
+    case 1: launch_keys_lc<1>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 2: launch_keys_lc<2>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 3: launch_keys_lc<3>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 4: launch_keys_lc<4>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    default: launch_keys_lc<0>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
     }
     return count_launch();
 }

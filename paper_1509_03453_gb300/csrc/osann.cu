@@ -207,31 +207,40 @@ struct osann_index {
     uint32_t* offsets = nullptr;
     uint32_t* perm = nullptr;
     float* xs = nullptr;
-    float* norm2 = nullptr;
-    __nv_bfloat16* xb = nullptr;  // bf16 copy of xs (tensor-core screening)
     float4* rowstat = nullptr;    // per row (1-B)|x|^2, |x|, |x|^2; N + TC_N rows
-    __nv_bfloat16* xe = nullptr;  // per row extra K block of the screen (16 bf16)
-    uint32_t* status = nullptr;   // [0] flags, [1] largest cone
+    // tensor-core screening operands per precision (0 bf16, 1 fp16): the
+    // 16-bit scaled copy of xs, the extra K block of each row, the scale
+    // (s, s^2, 1/s^2, 0) and the TMA tensor maps over both arrays
+    uint16_t* x16[2] = {nullptr, nullptr};
+    uint16_t* xe16[2] = {nullptr, nullptr};
+    float* tcs = nullptr;  // 2 x 4 floats
+    bool tc_ready[2] = {false, false};
+    alignas(64) unsigned char tmap[2][256];
+    uint32_t* status = nullptr;   // [0] flags, [1] largest cone, [2] largest |x|^2 (bits)
     unsigned long long* diag = nullptr;  // screening counters (survivors, fallbacks, checks, violations)
     uint64_t* binom = nullptr;
-    float cdot2 = 0.f, Bn = 0.f;  // screening error-bound coefficients
-    bool tc_ok = false;           // tensor map encoded
-    alignas(64) unsigned char tmap[256];  // tensor maps over xb and xe
+    float cdot2[2] = {0.f, 0.f}, cabs[2] = {0.f, 0.f}, Bn = 0.f;  // screening error-bound coefficients
+    std::mutex tc_mu;
     std::vector<std::pair<void*, size_t>> allocs;
 };
 
-// Coefficients of the screening bound E = cdot2 |q||x| + Bn (|q|^2 + |x|^2):
-// bf16 rounding of both operands (unit roundoff u = 2^-8) and the fp32
-// accumulation of d_pad products (taken as d_pad 2^-20, sixteen times the
-// round-to-nearest bound); for Bn the fp32 norms, the accumulation of the
-// folded norm terms over d_pad + 16 columns, their bf16 hi/lo split (2^-15)
-// and a cushion of 4e-6 for the fp32 rounding of the exact distances
-// compared at the end.
-static void screen_coefficients(int d_pad, float* cdot2, float* Bn)
+// Coefficients of the screening bound
+//     E = cdot2 |q||x| + Bn (|q|^2 + |x|^2) + cabs (|q| + |x|):
+// 16-bit rounding of both operands (unit roundoff u = 2^-8 for bf16, 2^-11
+// for fp16) and the fp32 accumulation of d_pad products (taken as
+// d_pad 2^-20, sixteen times the round-to-nearest bound); for Bn the fp32
+// norms, the accumulation of the folded norm terms over d_pad + 16 columns,
+// their 16-bit hi/lo split (2^-15) and a cushion of 4e-6 for the fp32
+// rounding of the exact distances compared at the end; for cabs the
+// absolute rounding error of fp16 subnormals (half spacing 2^-25, times
+// 2 sqrt(d) from Cauchy-Schwarz, with a factor 4 to spare; bf16 has fp32's
+// exponent range, so its term is negligible but kept nonzero).
+static void screen_coefficients(int d_pad, int prec, float* cdot2, float* cabs, float* Bn)
 {
-    const double u = std::ldexp(1.0, -8);
+    const double u = std::ldexp(1.0, prec == 0 ? -8 : -11);
     const double c = 2 * u + u * u + d_pad * std::ldexp(1.0, -20) * (1 + u) * (1 + u);
     *cdot2 = float(2 * c);
+    *cabs = float(prec == 0 ? std::ldexp(1.0, -120) : std::ldexp(1.0, -22) * std::sqrt(double(d_pad)));
     *Bn = float(d_pad * std::ldexp(1.0, -23) + (d_pad + 16) * std::ldexp(1.0, -20) + std::ldexp(1.0, -15) + 4e-6);
 }
 
@@ -290,12 +299,45 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv, hbuf;
+    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, items_sorted, kcount, kfill;
     size_t total;
     int64_t max_items;
 };
 
-enum SearchMode { MODE_PLAIN = 0, MODE_BATCHED = 1, MODE_BF16 = 2 };
+enum SearchMode { MODE_PLAIN = 0, MODE_BATCHED = 1, MODE_BF16 = 2, MODE_FP16 = 3 };
+
+static bool tc_mode(int mode) { return mode == MODE_BF16 || mode == MODE_FP16; }
+
+// Prepare the screening operands of a precision on first use (bf16; fp16 is
+// made with the index).  Synchronises `st` once so that later searches on
+// any stream see them.
+static int ensure_tc(osann_index* ix, int prec, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(ix->tc_mu);
+    if (ix->tc_ready[prec]) return 0;
+    if (ix->d_pad > 128) {
+        set_error("the tensor-core path needs d <= 128");
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    if (!ix->x16[prec]) {
+        ix->x16[prec] = index_alloc<uint16_t>(ix, size_t(ix->N) * ix->d_pad);
+        ix->xe16[prec] = index_alloc<uint16_t>(ix, size_t(ix->N) * 16);
+        if (!ix->x16[prec] || !ix->xe16[prec]) {
+            set_error("tensor-core operands: device allocation failed");
+            return OSANN_ERR_OOM;
+        }
+    }
+    int rc = launch_tc_rows(prec, ix->xs, ix->rowstat, ix->N, ix->d_pad, ix->status + 2, ix->tcs + 4 * prec,
+                            ix->x16[prec], ix->xe16[prec], st, ix->num_sms);
+    if (rc) return rc;
+    if (tc_encode_rows_map(ix->tmap[prec], ix->x16[prec], ix->N, ix->d_pad, prec) != 0 ||
+        tc_encode_rows_map(ix->tmap[prec] + tc_map_bytes() / 2, ix->xe16[prec], ix->N, 0, prec) != 0)
+        return OSANN_ERR_UNSUPPORTED;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core operands");
+    ix->tc_ready[prec] = true;
+    return 0;
+}
 
 static int group_size(int d_pad) { return 128 / (d_pad == 16 ? 1 : d_pad / 32); }
 
@@ -312,7 +354,7 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
     w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
     if (mode != MODE_PLAIN) {
-        const int G = mode == MODE_BF16 ? TC_GROUP : group_size(ix->d_pad);
+        const int G = tc_mode(mode) ? TC_GROUP : group_size(ix->d_pad);
         const int64_t n = Q * P_eff;
         int64_t mi = n / G + ix->NC + 1;
         if (mi > n) mi = n;
@@ -327,14 +369,19 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         w.items = take(size_t(mi > 0 ? mi : 1) * 16);
         w.counters = take(256);
         w.hbuf = take(size_t(wl_hist_entries(ix->NC, n, ix->num_sms)) * 4 + 4);
+        w.probesT = take(size_t(n) * 4);
         w.scan_temp = take(batched_scan_temp_bytes(ix->NC, n, ix->num_sms));
     }
-    if (mode == MODE_BF16) {
+    if (tc_mode(mode)) {
+        w.items_sorted = take(size_t(w.max_items > 0 ? w.max_items : 1) * 16);
+        w.kcount = take(size_t(P_eff + 1) * 4);
+        w.kfill = take(size_t(P_eff) * 4);
         w.yb = take(size_t(Q) * ix->d_pad * 2);
         w.qstat = take(size_t(Q) * 16);
         w.ubits = take(size_t(Q) * 4);
         w.scnt = take(size_t(Q) * 4);
         w.surv = take(size_t(Q) * TC_SURV_CAP * 4);
+        w.ovf = take(size_t(Q + 1) * 4);
     }
     w.total = off + 256;
     return w;
@@ -345,8 +392,9 @@ static int choose_mode(const osann_index* ix, int64_t Q, int64_t P_eff, int path
     if (path == OSANN_PATH_PLAIN) return MODE_PLAIN;
     if (path == OSANN_PATH_BATCHED) return MODE_BATCHED;
     if (path == OSANN_PATH_BF16) return MODE_BF16;
+    if (path == OSANN_PATH_FP16) return MODE_FP16;
     const double per_cone = double(Q) * double(P_eff) / double(ix->NC);
-    if (ix->tc_ok && per_cone >= 64.0) return MODE_BF16;
+    if (ix->tc_ready[1] && per_cone >= 64.0) return MODE_FP16;
     return per_cone >= 16.0 ? MODE_BATCHED : MODE_PLAIN;
 }
 
@@ -419,7 +467,7 @@ int osann_keys(const float* d_vectors, int64_t n, int32_t d, int32_t L, uint32_t
     DeviceState* ds;
     int rc = device_state(&ds);
     if (rc) return rc;
-    return launch_data_keys(d_vectors, n, d, L, ds->binom, d_keys, ds->scratch_status,
+    return launch_data_keys(d_vectors, n, d, L, ds->binom, d_keys, ds->scratch_status, nullptr,
                             static_cast<cudaStream_t>(stream), ds->num_sms);
 }
 
@@ -473,20 +521,24 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     ix->offsets = index_alloc<uint32_t>(ix, size_t(NC + 1));
     ix->perm = index_alloc<uint32_t>(ix, size_t(N));
     ix->xs = index_alloc<float>(ix, size_t(N) * ix->d_pad);
-    ix->norm2 = index_alloc<float>(ix, size_t(N));
-    ix->xb = index_alloc<__nv_bfloat16>(ix, size_t(N) * ix->d_pad);
     ix->rowstat = index_alloc<float4>(ix, size_t(N) + TC_N_ROWS);
-    ix->xe = index_alloc<__nv_bfloat16>(ix, size_t(N) * 16);
     ix->status = index_alloc<uint32_t>(ix, 64);
     ix->diag = index_alloc<unsigned long long>(ix, 8);
-    screen_coefficients(ix->d_pad, &ix->cdot2, &ix->Bn);
+    ix->tcs = index_alloc<float>(ix, 8);
+    for (int p = 0; p < 2; ++p) screen_coefficients(ix->d_pad, p, &ix->cdot2[p], &ix->cabs[p], &ix->Bn);
+    const bool tc_possible = ix->d_pad <= 128;
+    if (tc_possible) {
+        // the default screening precision (fp16) is prepared with the index
+        ix->x16[1] = index_alloc<uint16_t>(ix, size_t(N) * ix->d_pad);
+        ix->xe16[1] = index_alloc<uint16_t>(ix, size_t(N) * 16);
+    }
     const size_t counts_bytes = al256(size_t(NC + 1) * 4);
     const size_t scan_bytes = al256(scan_temp_bytes(NC + 1));
     const size_t radix_bytes = al256(radix_temp_bytes(N, NC));
     const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes;
     char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
-    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->norm2 || !ix->xb || !ix->rowstat || !ix->xe ||
-        !ix->status || !ix->diag || !temp) {
+    if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->rowstat || !ix->status ||
+        !ix->diag || !ix->tcs || (tc_possible && (!ix->x16[1] || !ix->xe16[1])) || !temp) {
         if (temp) dev_free(temp, temp_bytes, st);
         index_release(ix);
         set_error("osann_build: device allocation failed");
@@ -502,7 +554,8 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
     {
         StageScope s(OSANN_STAGE_DATA_KEYS, st);
-        rc = launch_data_keys(d_data, N, d, L, ix->binom, ix->keys, ix->status, st, ix->num_sms);
+        rc = launch_data_keys(d_data, N, d, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms);
+        if (!rc && tc_possible) rc = launch_tc_scale(1, ix->status + 2, ix->tcs + 4, st);
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_BUCKETS, st);
@@ -512,8 +565,8 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_GATHER, st);
-        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->xb, ix->norm2, ix->rowstat, ix->xe,
-                                ix->Bn, st, ix->num_sms);
+        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->rowstat, ix->Bn,
+                                tc_possible ? ix->tcs + 4 : nullptr, ix->x16[1], ix->xe16[1], st, ix->num_sms);
     }
     if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st);
     dev_free(temp, temp_bytes, st);
@@ -537,10 +590,9 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     cudaMemsetAsync(ix->status, 0, 4, st);
     ix->max_bucket = host_status[1];
-    static_assert(sizeof(ix->tmap) >= 128, "tensor map storage");
-    ix->tc_ok = tc_map_bytes() <= sizeof(ix->tmap) && ix->d_pad <= 128 &&
-                tc_encode_rows_map(ix->tmap, ix->xb, N, ix->d_pad) == 0 &&
-                tc_encode_rows_map(ix->tmap + tc_map_bytes() / 2, ix->xe, N, 0) == 0;
+    ix->tc_ready[1] = tc_possible && tc_map_bytes() <= sizeof(ix->tmap[1]) &&
+                      tc_encode_rows_map(ix->tmap[1], ix->x16[1], N, ix->d_pad, 1) == 0 &&
+                      tc_encode_rows_map(ix->tmap[1] + tc_map_bytes() / 2, ix->xe16[1], N, 0, 1) == 0;
     *out = ix;
     return OSANN_OK;
 }
@@ -602,13 +654,13 @@ int osann_status(const osann_index* ix, void* stream, uint32_t* flags)
 size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path)
 {
     if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K) return 0;
-    if (path < 0 || path > OSANN_PATH_BF16) return 0;
+    if (path < 0 || path > OSANN_PATH_FP16) return 0;
     const int64_t P_eff = P < ix->NC ? P : ix->NC;
     return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path)).total;
 }
 
 static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_eff, const WsLayout& L, char* w,
-                       bool init_partial, int k, cudaStream_t st)
+                       bool init_partial, bool transposed, int k, cudaStream_t st)
 {
     int rc;
     {
@@ -620,6 +672,7 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
     StageScope s(OSANN_STAGE_PROBES, st);
     return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Q, ix->d,
                          ix->L, P_eff, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
+                         transposed ? reinterpret_cast<uint32_t*>(w + L.probesT) : nullptr,
                          init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st);
 }
 
@@ -646,7 +699,7 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, d_queries, Q, P_eff, L, w, false, 1, st);
+    int rc = query_front(ix, d_queries, Q, P_eff, L, w, false, false, 1, st);
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(d_probes, w + L.probes, size_t(Q) * P_eff * 4, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "osann_probes");
@@ -659,7 +712,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
                        int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
                        float* dists, void* stream)
 {
-    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_BF16 ||
+    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 ||
         (Q > 0 && (!Y || !ids || !dists))) {
         set_error("osann_search: invalid arguments (Q=%lld P=%d k=%d path=%d)", (long long)Q, P, k, path);
         return OSANN_ERR_INVALID;
@@ -676,9 +729,10 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int mode = choose_mode(ix, Q, P_eff, path);
-    if (mode == MODE_BF16 && !ix->tc_ok) {
-        set_error("osann_search: the tensor-core path needs d <= 128 and a TMA tensor map (unavailable)");
-        return OSANN_ERR_UNSUPPORTED;
+    const int prec = mode == MODE_FP16 ? 1 : 0;
+    if (tc_mode(mode)) {
+        int trc = ensure_tc(const_cast<osann_index*>(ix), prec, st);
+        if (trc) return trc;
     }
     const bool batched = mode != MODE_PLAIN;
     const WsLayout L = ws_layout(ix, Q, P_eff, k, mode);
@@ -694,7 +748,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, Y, Q, P_eff, L, w, mode == MODE_BATCHED, k, st);
+    int rc = query_front(ix, Y, Q, P_eff, L, w, mode == MODE_BATCHED, batched, k, st);
     if (!rc && batched) {
         BatchedBuffers b{};
         b.qcount = reinterpret_cast<uint32_t*>(w + L.qcount);
@@ -705,42 +759,53 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         b.qlist = reinterpret_cast<uint32_t*>(w + L.qlist);
         b.items = reinterpret_cast<uint4*>(w + L.items);
         b.hbuf = reinterpret_cast<uint32_t*>(w + L.hbuf);
+        if (tc_mode(mode)) {
+            b.items_sorted = reinterpret_cast<uint4*>(w + L.items_sorted);
+            b.kcount = reinterpret_cast<uint32_t*>(w + L.kcount);
+            b.kfill = reinterpret_cast<uint32_t*>(w + L.kfill);
+        }
         b.counters = reinterpret_cast<uint32_t*>(w + L.counters);
         b.n_items_dev = b.item_off + ix->NC;
         b.scan_temp = w + L.scan_temp;
         b.max_items = L.max_items;
-        const int G = mode == MODE_BF16 ? TC_GROUP : group_size(ix->d_pad);
+        const int G = tc_mode(mode) ? TC_GROUP : group_size(ix->d_pad);
         uint64_t* partial = reinterpret_cast<uint64_t*>(w + L.partial);
         const uint32_t* probes = reinterpret_cast<uint32_t*>(w + L.probes);
-        if (mode == MODE_BF16) {
+        if (tc_mode(mode)) {
             StageScope s(OSANN_STAGE_TC_PREP, st);
-            rc = launch_tc_query_prep(Y, Q, ix->d, ix->d_pad, probes, P_eff, ix->offsets, uint32_t(ix->NC), ix->xs, k,
-                                      true, ix->cdot2, ix->perm, src, grid_w, radius,
-                                      reinterpret_cast<__nv_bfloat16*>(w + L.yb),
-                                      reinterpret_cast<float4*>(w + L.qstat), reinterpret_cast<uint32_t*>(w + L.ubits),
-                                      reinterpret_cast<uint32_t*>(w + L.scnt), st);
+            rc = launch_tc_query_prep(prec, Y, Q, ix->d, ix->d_pad, probes, P_eff, ix->offsets, uint32_t(ix->NC), ix->xs,
+                                      k, ix->cdot2[prec], ix->cabs[prec], ix->tcs + 4 * prec, ix->perm, src, grid_w,
+                                      radius, TC_SURV_CAP, w + L.yb, reinterpret_cast<float4*>(w + L.qstat),
+                                      reinterpret_cast<uint32_t*>(w + L.ubits), reinterpret_cast<uint32_t*>(w + L.scnt),
+                                      st);
         }
         if (!rc) {
             StageScope s(OSANN_STAGE_WORKLIST, st);
-            rc = launch_worklist(probes, Q, P_eff, ix->offsets, ix->NC, G, b, st, ix->num_sms);
+            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probesT), Q, P_eff, ix->offsets, ix->NC, G,
+                                 tc_mode(mode), b, st, ix->num_sms);
         }
-        if (!rc && mode == MODE_BF16) {
+        if (!rc && tc_mode(mode)) {
             {
                 StageScope s(OSANN_STAGE_TC_SCAN, st);
-                rc = launch_tc_scan(ix->tmap, ix->offsets, ix->perm, ix->rowstat,
-                                    reinterpret_cast<const __nv_bfloat16*>(w + L.yb),
-                                    reinterpret_cast<const float4*>(w + L.qstat), src, grid_w, radius, b,
-                                    reinterpret_cast<uint32_t*>(w + L.ubits), reinterpret_cast<uint32_t*>(w + L.scnt),
-                                    reinterpret_cast<uint32_t*>(w + L.surv), TC_SURV_CAP, ix->status, ix->diag, ix->xs,
-                                    Y, P_eff, ix->d, ix->d_pad, k, ix->cdot2, ix->Bn, debug_checks(), st,
-                                    ix->num_sms);
+                rc = launch_tc_scan(prec, ix->tmap[prec], ix->perm, ix->rowstat, w + L.yb,
+                                    reinterpret_cast<const float4*>(w + L.qstat), ix->tcs + 4 * prec, src, grid_w,
+                                    radius, b, reinterpret_cast<uint32_t*>(w + L.ubits),
+                                    reinterpret_cast<uint32_t*>(w + L.scnt), reinterpret_cast<uint32_t*>(w + L.surv),
+                                    TC_SURV_CAP, ix->status, ix->diag, ix->xs, Y, P_eff, ix->d, ix->d_pad, k,
+                                    ix->cdot2[prec], ix->Bn, ix->cabs[prec], debug_checks(), st, ix->num_sms);
             }
             if (!rc) {
                 StageScope s(OSANN_STAGE_TC_RERANK, st);
                 rc = launch_tc_rerank(ix->xs, ix->d_pad, ix->perm, ix->offsets, uint32_t(ix->NC), Y, ix->d, Q, probes,
                                       P_eff, reinterpret_cast<uint32_t*>(w + L.scnt),
                                       reinterpret_cast<uint32_t*>(w + L.surv), TC_SURV_CAP, k, src, grid_w, radius,
-                                      ix->diag, ids, dists, st);
+                                      ix->diag, reinterpret_cast<uint32_t*>(w + L.ovf), ids, dists, st);
+                // queries whose survivor list overflowed: exact scan of their probed cones
+                if (!rc)
+                    rc = launch_plain_scan(ix->xs, ix->offsets, ix->perm, ix->d_pad, Y, ix->d, Q, probes, P_eff,
+                                           uint32_t(ix->NC), k, src, grid_w, radius,
+                                           reinterpret_cast<const uint32_t*>(w + L.ovf), ix->num_sms, ids, dists,
+                                           ix->status, st);
             }
         } else if (!rc) {
             {
@@ -757,8 +822,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         StageScope s(OSANN_STAGE_PLAIN_SCAN, st);
         rc = launch_plain_scan(ix->xs, ix->offsets, ix->perm, ix->d_pad, Y, ix->d, Q,
                                reinterpret_cast<uint32_t*>(w + L.probes), P_eff, uint32_t(ix->NC), k, src, grid_w,
-                               radius, ids, dists,
-                               ix->status, st);
+                               radius, nullptr, ix->num_sms, ids, dists, ix->status, st);
     }
     if (owned) dev_free(owned, L.total, st);
     return rc;

@@ -16,7 +16,7 @@ void set_error(const char* fmt, ...);
 
 // keys.cu
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
-                     uint32_t* status, cudaStream_t st, int num_sms);
+                     uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms);  // maxn2 may be null
 int launch_query_order(const float* Y, int64_t Q, int d, uint8_t* qorder, uint32_t* qsign, uint32_t* status,
                        cudaStream_t st);
 
@@ -28,20 +28,23 @@ int launch_key_histogram(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* 
 size_t radix_temp_bytes(int64_t N, int64_t NC);
 int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
                            cudaStream_t st);
-int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs,
-                       __nv_bfloat16* xb, float* norm2, float4* rowstat, __nv_bfloat16* xe, float Bn, cudaStream_t st,
-                       int num_sms);  // xb, rowstat, xe may be null
+int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs, float4* rowstat,
+                       float Bn, const float* tcs, uint16_t* x16, uint16_t* xe16, cudaStream_t st,
+                       int num_sms);  // tcs, x16, xe16 null: no fp16 operands
+int launch_tc_scale(int prec, const uint32_t* maxn2_bits, float* tcs, cudaStream_t st);
 int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st);
 
 // probes.cu
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* probes, uint64_t* partial, int k, cudaStream_t st);
+                  const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
+                  cudaStream_t st);  // probesT (p-major copy) may be null
 
 // scan_plain.cu
 int launch_plain_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad,
                       const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, uint32_t NC, int k,
-                      const int64_t* query_src, int64_t grid_w, int radius, int64_t* out_ids, float* out_d,
-                      uint32_t* status, cudaStream_t st);
+                      const int64_t* query_src, int64_t grid_w, int radius, const uint32_t* qlist, int num_sms,
+                      int64_t* out_ids, float* out_d, uint32_t* status, cudaStream_t st);
+// qlist (nullable): device list [count, q_0, ...] of the queries to scan
 
 // scan_batched.cu
 struct BatchedBuffers {
@@ -53,6 +56,9 @@ struct BatchedBuffers {
     uint32_t* qlist;      // Q * P_eff
     uint4* items;         // max_items descriptors (first row, end row, first slot, slot count)
     uint32_t* hbuf;       // per-block cone histograms (N_C <= 12288)
+    uint4* items_sorted;  // tensor-core path: items ordered by their smallest probe position
+    uint32_t* kcount;     // P + 1 counters of that ordering
+    uint32_t* kfill;      // P cursors
     uint32_t* counters;   // word 0: work counter of the tile scan
     const uint32_t* n_items_dev;  // device word holding the item count (item_off + NC)
     void* scan_temp;
@@ -60,8 +66,11 @@ struct BatchedBuffers {
 };
 size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms);
 int wl_hist_entries(int64_t NC, int64_t n, int num_sms);
-int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
-                    int group, BatchedBuffers& b, cudaStream_t st, int num_sms);
+// probesT: probe lists in probe-position-major order (probesT[p * Q + q]);
+// slots are still numbered q * P_eff + p.  order_by_probe: also produce
+// items_sorted (items by the smallest probe position of their queries).
+int launch_worklist(const uint32_t* probesT, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
+                    int group, bool order_by_probe, BatchedBuffers& b, cudaStream_t st, int num_sms);
 int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y,
                      int d, int64_t slots_per_query, int k, const int64_t* query_src, int64_t grid_w, int radius,
                      const BatchedBuffers& b, int group, uint64_t* partial, uint32_t* status, cudaStream_t st,
@@ -76,23 +85,29 @@ int launch_bruteforce_rows(const float* xs, const uint32_t* perm, int64_t N, int
                            uint32_t* counter, int64_t* out_ids, float* out_d, uint32_t* status, cudaStream_t st,
                            int num_sms);
 
-// tc_scan.cu: bf16 tensor-core screening + fp32 rerank
+// tc_scan.cu: 16-bit tensor-core screening + fp32 rerank.  prec 0 = bf16,
+// 1 = fp16 (with an exact power-of-two scale of the data and queries)
 constexpr int TC_GROUP = 128;
 constexpr int TC_SURV_CAP = 256;
 size_t tc_map_bytes();
-int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_pad);  // d_pad 0: extra block
-int launch_tc_query_prep(const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes, int64_t P_eff,
-                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, float cdot2,
-                         const uint32_t* perm, const int64_t* query_src, int64_t grid_w, int radius,
-                         __nv_bfloat16* Yb, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st);
-int launch_tc_scan(const void* map, const uint32_t* offsets, const uint32_t* perm, const float4* rowstat,
-                   const __nv_bfloat16* Yb, const float4* qstat, const int64_t* query_src, int64_t grid_w, int radius,
+int tc_encode_rows_map(void* map_out, const void* x16, int64_t N, int d_pad, int prec);  // d_pad 0: extra block
+int launch_tc_rows(int prec, const float* xs, const float4* rowstat, int64_t N, int d_pad, const uint32_t* maxn2_bits,
+                   float* tcs, void* x16, void* xe16, cudaStream_t st, int num_sms);
+int launch_tc_query_prep(int prec, const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes,
+                         int64_t P_eff, const uint32_t* offsets, uint32_t NC, const float* xs, int k, float cdot2,
+                         float cabs, const float* tcs, const uint32_t* perm, const int64_t* query_src, int64_t grid_w,
+                         int radius, int cap, void* Y16, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt,
+                         cudaStream_t st);
+int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float4* rowstat, const void* Y16,
+                   const float4* qstat, const float* tcs, const int64_t* query_src, int64_t grid_w, int radius,
                    const BatchedBuffers& b, uint32_t* Ubits, uint32_t* surv_cnt, uint32_t* surv, int cap,
                    uint32_t* status, unsigned long long* diag, const float* xs, const float* Y, int64_t S, int d,
-                   int d_pad, int k, float cdot2, float Bn, int debug, cudaStream_t st, int num_sms);
+                   int d_pad, int k, float cdot2, float Bn, float cabs, int debug, cudaStream_t st, int num_sms);
 int launch_tc_rerank(const float* xs, int d_pad, const uint32_t* perm, const uint32_t* offsets, uint32_t NC,
                      const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, const uint32_t* surv_cnt,
                      const uint32_t* surv, int cap, int k, const int64_t* query_src, int64_t grid_w, int radius,
-                     unsigned long long* diag, int64_t* out_ids, float* out_d, cudaStream_t st);
+                     unsigned long long* diag, uint32_t* ovf, int64_t* out_ids, float* out_d, cudaStream_t st);
+// ovf: device list [count, q_0, ...] of the queries whose survivor list
+// overflowed (Q + 1 words); they are left to the plain scan
 
 }  // namespace osann

@@ -25,31 +25,30 @@ __device__ __forceinline__ uint64_t C(const uint64_t* __restrict__ binom, int n,
     return __ldg(binom + n * (MAX_L + 1) + k);
 }
 
-// t-th m-subset of {0..n-1} in lexicographic order, written as ascending
-// values into out[0..m-1].
-__device__ __forceinline__ void unrank_lex(const uint64_t* __restrict__ binom, uint64_t t, int n, int m,
-                                           int (&out)[MAX_L], int out_base)
+// Smallest r' >= r with t < C(n - r' - 1, m - 1): the next member of the
+// t-th m-subset (lexicographic) of {0..n-1} after value r - 1; t is reduced
+// by the subsets skipped.  Bounded by n - m.
+__device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, uint64_t& t, int r, int n, int m)
 {
-    int r = 0;
-    for (int j = 0; j < m; ++j) {
-        // bounded: r never passes n - (m - j) for an in-range t
-        while (r < n - (m - j)) {
-            const uint64_t cnt = C(binom, n - r - 1, m - j - 1);
-            if (t < cnt) break;
-            t -= cnt;
-            ++r;
-        }
-        out[out_base + j] = r;
+    while (r < n - m) {
+        const uint64_t cnt = C(binom, n - r - 1, m - 1);
+        if (t < cnt) break;
+        t -= cnt;
         ++r;
     }
+    return r;
 }
 
+// LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
+template <int LC>
 __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
                                                      const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
                                                      int64_t P_eff, const uint64_t* __restrict__ binom,
-                                                     uint32_t* __restrict__ probes, uint64_t* __restrict__ partial,
-                                                     int k)
+                                                     uint32_t* __restrict__ probes, uint32_t* __restrict__ probesT,
+                                                     uint64_t* __restrict__ partial, int k)
 {
+    constexpr int LM = LC > 0 ? LC : MAX_L;
+    if (LC > 0) L = LC;
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= Q * P_eff) return;
     const int64_t q = t / P_eff;
@@ -65,60 +64,84 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
             const uint64_t per = C(binom, L, h);
             const uint64_t blk = nprof * per;
             if (idx < blk) {
-                const uint64_t fs = idx % per;
+                uint64_t fs = idx % per;
                 idx /= per;
-                int f[MAX_L];
-                unrank_lex(binom, fs, L, h, f, 0);
-                for (int j = 0; j < h; ++j) flip |= 1u << f[j];
+                int r = 0;
+                for (int j = 0; j < h; ++j) {
+                    r = next_member(binom, fs, r, L, h - j);
+                    flip |= 1u << r;
+                    ++r;
+                }
                 break;
             }
             idx -= blk;
         }
     }
-    // unrank the profile: class delta, then the substituted rank tuple
-    int rk[MAX_L];  // member ranks, 0-based positions into the query's order
-    for (int j = 0; j < MAX_L; ++j) rk[j] = j;
-    for (int delta = 0; delta <= L; ++delta) {
+    // profile class delta, then the idx-th delta-subset of the ranks after keep
+    int delta = 0;
+    for (; delta < L; ++delta) {
         const uint64_t cnt = delta == 0 ? 1 : C(binom, d - L + delta - 1, delta);
-        if (idx < cnt) {
-            const int keep = L - delta;
-            for (int j = 0; j < keep; ++j) rk[j] = j;
-            if (delta > 0) {
-                unrank_lex(binom, idx, d - keep - 1, delta, rk, keep);
-                for (int j = 0; j < delta; ++j) rk[keep + j] += keep + 1;
-            }
-            break;
-        }
+        if (idx < cnt) break;
         idx -= cnt;
+    }
+    const int keep = L - delta;
+    const int n = d - keep - 1;  // candidate ranks keep+1 .. d-1
+    int rk[LM];                  // member ranks (0-based positions into the query's order)
+    int cm[LM];                  // member components
+    int r = 0;
+#pragma unroll
+    for (int j = 0; j < LM; ++j) {
+        if (LC > 0 || j < L) {
+            if (j < keep) {
+                rk[j] = j;
+            } else {
+                r = next_member(binom, idx, r, n, L - j);
+                rk[j] = keep + 1 + r;
+                ++r;
+            }
+            cm[j] = ord[rk[j]];
+        }
     }
     // cone id of the profile with the query's signs (and the chosen flips)
     uint64_t rank = 0;
     uint32_t code = 0;
-    for (int j = 0; j < L; ++j) {
-        const int cj = ord[rk[j]];
-        int pos = 0, asc = 0;
-        for (int u = 0; u < L; ++u) {
-            const int cu = ord[rk[u]];
-            pos += cu < cj ? 1 : 0;          // ascending component index
-            asc += rk[u] > rk[j] ? 1 : 0;    // ascending magnitude
+#pragma unroll
+    for (int j = 0; j < LM; ++j) {
+        if (LC > 0 || j < L) {
+            int pos = 0, asc = 0;
+#pragma unroll
+            for (int u = 0; u < LM; ++u) {
+                if (LC > 0 || u < L) {
+                    pos += cm[u] < cm[j] ? 1 : 0;  // ascending component index
+                    asc += rk[u] > rk[j] ? 1 : 0;  // ascending magnitude
+                }
+            }
+            uint32_t bit = (sg[cm[j] >> 5] >> (cm[j] & 31)) & 1u;
+            bit ^= (flip >> asc) & 1u;
+            rank += C(binom, cm[j], pos + 1);
+            code |= bit << (L - 1 - pos);
         }
-        uint32_t bit = (sg[cj >> 5] >> (cj & 31)) & 1u;
-        bit ^= (flip >> asc) & 1u;
-        rank += C(binom, cj, pos + 1);
-        code |= bit << (L - 1 - pos);
     }
-    probes[t] = uint32_t((rank << L) | code);
+    const uint32_t cone = uint32_t((rank << L) | code);
+    probes[t] = cone;
+    if (probesT) probesT[int64_t(t - q * P_eff) * Q + q] = cone;  // probe-position-major copy
     if (partial)
         for (int j = 0; j < k; ++j) partial[t * k + j] = EMPTY_DI;
 }
 
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* probes, uint64_t* partial, int k, cudaStream_t st)
+                  const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k, cudaStream_t st)
 {
     const int64_t n = Q * P_eff;
     if (n == 0) return 0;
-    probes_kernel<<<unsigned((n + 255) / 256), 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, partial,
-                                                             k);
+    const unsigned g = unsigned((n + 255) / 256);
+    switch (L) {
+    case 1: probes_kernel<1><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
+    case 2: probes_kernel<2><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
+    case 3: probes_kernel<3><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
+    case 4: probes_kernel<4><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
+    default: probes_kernel<0><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
+    }
     return count_launch();
 }
 

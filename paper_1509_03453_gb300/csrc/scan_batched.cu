@@ -44,18 +44,25 @@ __global__ void wl_count_global_kernel(const uint32_t* __restrict__ probes, int6
                                        uint32_t* __restrict__ qcount)
 {
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t b = probes[t];
+        const uint32_t b = probes[t];  // order does not matter for counting
         if (cone_nonempty(offsets, b, NC)) atomicAdd(&qcount[b], 1u);
     }
 }
 
+// slot number q * P + p of position t = p * Q + q of the probe-major array
+__device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t Q, uint32_t P)
+{
+    const uint32_t p = t / Q;
+    return (t - p * Q) * P + p;
+}
+
 __global__ void wl_fill_kernel(const uint32_t* __restrict__ probes, int64_t n, const uint32_t* __restrict__ offsets,
                                uint32_t NC, const uint32_t* __restrict__ qoff, uint32_t* __restrict__ fill,
-                               uint32_t* __restrict__ qlist)
+                               uint32_t* __restrict__ qlist, uint32_t Q, uint32_t P)
 {
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, NC)) qlist[qoff[b] + atomicAdd(&fill[b], 1u)] = uint32_t(t);
+        if (cone_nonempty(offsets, b, NC)) qlist[qoff[b] + atomicAdd(&fill[b], 1u)] = slot_of(uint32_t(t), Q, P);
     }
 }
 
@@ -81,7 +88,7 @@ __global__ void __launch_bounds__(512) wl_block_hist_kernel(const uint32_t* __re
 __global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __restrict__ probes, int64_t n,
                                                             int64_t chunk, const uint32_t* __restrict__ offsets,
                                                             int NC, const uint32_t* __restrict__ Hs,
-                                                            uint32_t* __restrict__ qlist)
+                                                            uint32_t* __restrict__ qlist, uint32_t Q, uint32_t P)
 {
     extern __shared__ uint32_t cur[];
     for (int c = threadIdx.x; c < NC; c += blockDim.x) cur[c] = Hs[int64_t(c) * gridDim.x + blockIdx.x];
@@ -89,7 +96,7 @@ __global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __re
     const int64_t t0 = int64_t(blockIdx.x) * chunk, t1 = t0 + chunk < n ? t0 + chunk : n;
     for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
         const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = uint32_t(t);
+        if (cone_nonempty(offsets, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = slot_of(uint32_t(t), Q, P);
     }
 }
 
@@ -141,16 +148,41 @@ int wl_hist_entries(int64_t NC, int64_t n, int num_sms)
     return NC <= 12288 ? int(NC * wl_blocks_impl(n, num_sms) + 1) : 0;
 }
 
+// Order the items by the smallest probe position of their queries (the
+// first slot of an item, since a cone's slots are filled in probe-position
+// order): every query's best cones are screened early, which tightens its
+// bound for the rest.  Counting sort over the P positions.
+__global__ void wl_item_keys_kernel(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items_dev,
+                                    const uint32_t* __restrict__ qlist, uint32_t P, uint32_t* __restrict__ kcount)
+{
+    const uint32_t n = *n_items_dev;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        atomicAdd(&kcount[qlist[items[i].z] % P], 1u);
+}
+
+__global__ void wl_item_sort_kernel(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items_dev,
+                                    const uint32_t* __restrict__ qlist, uint32_t P, const uint32_t* __restrict__ koff,
+                                    uint32_t* __restrict__ kfill, uint4* __restrict__ out)
+{
+    const uint32_t n = *n_items_dev;
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint4 it = items[i];
+        const uint32_t key = qlist[it.z] % P;
+        out[koff[key] + atomicAdd(&kfill[key], 1u)] = it;
+    }
+}
+
 size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms)
 {
     const int64_t hn = NC <= 12288 ? NC * wl_blocks_impl(n, num_sms) + 1 : 0;
-    const int64_t m = hn > NC + 1 ? hn : NC + 1;
+    int64_t m = hn > NC + 1 ? hn : NC + 1;
+    if (n + 1 > m) m = n + 1;  // the probe-position counters (P + 1 <= n + 1)
     return scan_temp_bytes(m);
 }
 
 
 int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC, int group,
-                    BatchedBuffers& b, cudaStream_t st, int num_sms)
+                    bool order_by_probe, BatchedBuffers& b, cudaStream_t st, int num_sms)
 {
     const int64_t n = Q * P_eff;
     int rc;
@@ -169,7 +201,7 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         wl_counts_from_H_kernel<<<unsigned(cb), 256, 0, st>>>(b.hbuf, NC, nb, b.qcount, b.qoff);
         if ((rc = count_launch())) return rc;
         wl_block_fill_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf,
-                                                                         b.qlist);
+                                                                         b.qlist, uint32_t(Q), uint32_t(P_eff));
         if ((rc = count_launch())) return rc;
     } else {
         cudaMemsetAsync(b.qcount, 0, size_t(NC + 1) * 4, st);
@@ -180,7 +212,8 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         wl_count_global_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qcount);
         if ((rc = count_launch())) return rc;
         if ((rc = launch_exclusive_scan(b.qcount, b.qoff, NC + 1, b.scan_temp, st))) return rc;
-        wl_fill_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qoff, b.fill, b.qlist);
+        wl_fill_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qoff, b.fill, b.qlist,
+                                                      uint32_t(Q), uint32_t(P_eff));
         if ((rc = count_launch())) return rc;
     }
     wl_nitems_kernel<<<unsigned(cb), 256, 0, st>>>(b.qcount, NC, group, b.nitems);
@@ -188,7 +221,19 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
     if ((rc = launch_exclusive_scan(b.nitems, b.item_off, NC + 1, b.scan_temp, st))) return rc;
     wl_items_kernel<<<unsigned(cb), 256, 0, st>>>(b.nitems, b.item_off, offsets, b.qcount, b.qoff, NC, group,
                                                    b.items, b.counters);
-    return count_launch();
+    if ((rc = count_launch())) return rc;
+    if (order_by_probe) {
+        cudaMemsetAsync(b.kcount, 0, size_t(P_eff + 1) * 4, st);
+        cudaMemsetAsync(b.kfill, 0, size_t(P_eff) * 4, st);
+        const unsigned ib = unsigned(2 * num_sms);
+        wl_item_keys_kernel<<<ib, 256, 0, st>>>(b.items, b.n_items_dev, b.qlist, uint32_t(P_eff), b.kcount);
+        if ((rc = count_launch())) return rc;
+        if ((rc = launch_exclusive_scan(b.kcount, b.kcount, P_eff + 1, b.scan_temp, st))) return rc;
+        wl_item_sort_kernel<<<ib, 256, 0, st>>>(b.items, b.n_items_dev, b.qlist, uint32_t(P_eff), b.kcount, b.kfill,
+                                                b.items_sorted);
+        if ((rc = count_launch())) return rc;
+    }
+    return 0;
 }
 
 // ---------------------------------------------------------------- tile scan

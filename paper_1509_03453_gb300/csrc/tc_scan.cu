@@ -1,5 +1,10 @@
-// Batched candidate scan with bf16 tensor-core screening and an exact fp32
-// rerank (the batched path's precision option).
+// Batched candidate scan with 16-bit tensor-core screening and an exact fp32
+// rerank.  The 16-bit operands are bf16 (unit roundoff u = 2^-8) or fp16
+// (u = 2^-11, eight times tighter bound); for fp16 the data and queries are
+// first multiplied by an exact power of two s, chosen from the largest row
+// norm so that |s x|^2 <= 2^14, and all screening quantities are in those
+// scaled units (distances scale by s^2, exactly).  Subnormal fp16 rounding
+// adds an absolute error, covered by the terms Cabs(|x| + |q|).
 //
 // For a work item (cone c, group of up to 128 queries that probe it) the
 // squared distances are first estimated on the 5th-generation tensor cores
@@ -9,8 +14,8 @@
 // the permuted vectors, swizzled K-major tiles).  Each query keeps an upper
 // bound U on its k-th best exact distance; a row survives the screen when
 //     d~ - E(q, x) <= U,   E = 2 c |q| |x| + B (|q|^2 + |x|^2),
-// where c bounds the bf16 rounding of both operands plus the fp32
-// accumulation (c = 2u + u^2 + K 2^-20, u = 2^-8) and B the fp32 error of
+// where c bounds the 16-bit rounding of both operands plus the fp32
+// accumulation (c = 2u + u^2 + K 2^-20) and B the fp32 error of
 // the norms, of their bf16 hi/lo split and a cushion for the fp32 rounding of
 // the exact distance.  The per-row terms are folded into the product by one
 // extra K block of 16 columns: the query side holds (1, 1, -A', -A') with
@@ -35,6 +40,27 @@ namespace osann {
 constexpr int TC_M = 128;  // queries per item = MMA M
 constexpr int TC_N = 128;  // cone rows per tile = MMA N = TMEM columns
 
+// 16-bit conversions: PREC 0 = bf16, 1 = fp16 (round to nearest or up)
+template <int PREC>
+__device__ __forceinline__ uint16_t to16_rn(float f)
+{
+    if (PREC == 0) return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+    return __half_as_ushort(__float2half_rn(f));
+}
+template <int PREC>
+__device__ __forceinline__ uint16_t to16_ru(float f)
+{
+    if (PREC == 0) return __bfloat16_as_ushort(__float2bfloat16_ru(f));
+    return __half_as_ushort(__float2half_ru(f));
+}
+template <int PREC>
+__device__ __forceinline__ float from16(uint16_t h)
+{
+    if (PREC == 0) return __bfloat162float(__ushort_as_bfloat16(h));
+    return __half2float(__ushort_as_half(h));
+}
+__device__ __forceinline__ uint32_t pack16(uint16_t lo, uint16_t hi) { return uint32_t(lo) | (uint32_t(hi) << 16); }
+
 __host__ __device__ inline int tc_row_bytes(int d_pad) { return d_pad >= 64 ? 128 : d_pad * 2; }
 __host__ __device__ inline int tc_kblocks(int d_pad) { return d_pad >= 64 ? d_pad / 64 : 1; }
 __host__ inline int tc_stages(int d_pad) { return d_pad <= 32 ? 4 : (d_pad == 64 ? 3 : 2); }
@@ -43,8 +69,9 @@ struct TcArgs {
     const uint32_t* offsets;
     const uint32_t* perm;
     const float4* rowstat;    // per row: ((1-B)|x|^2, |x|, |x|^2, 0); N + TC_N rows
-    const __nv_bfloat16* Yb;  // Q x d_pad, holds bf16(-2 y)
-    const float4* qstat;      // per query: (|q|^2, |q|, -A' (bf16 value, A' >= A = 2c|q|), 0)
+    const uint16_t* Y16;      // Q x d_pad, 16-bit -2 s y
+    const float4* qstat;      // per query, scaled: (|q|^2, |q|, -A' (16-bit value, A' >= 2c|q| + Cabs), Cabs |q|)
+    const float* tcs;         // (s, s^2, 1/s^2, 0)
     const int64_t* query_src;
     const uint4* items;  // (first row, end row, first slot, slot count)
     const uint32_t* n_items_dev;
@@ -64,6 +91,7 @@ struct TcArgs {
     int d, d_pad, k, radius, cap, stages, debug;
     float cdot2;  // 2c
     float Bn;     // B
+    float cabs;   // coefficient of the subnormal rounding terms
 };
 
 // Item descriptor passed from the producer warp to the MMA and epilogue warps.
@@ -89,25 +117,14 @@ constexpr int TC_SBUF = 16;  // survivors buffered per thread before a flush
 
 // per-query constants of a query tile, written by the loaders
 struct TcQConst {
-    float qn2;   // |q|^2
-    float Uthr;  // U - (1-B)|q|^2
-    float Aq1;   // A'
-    float U;     // upper bound on the k-th best exact distance
+    float qn2;   // |q|^2 (scaled)
+    float Uthr;  // s^2 U - (1-B)|q|^2 + Cq (scaled)
+    float Aq1;   // A' (scaled)
+    float U;     // upper bound on the k-th best exact distance (unscaled)
+    float Cq;    // Cabs |q| (scaled)
 };
 
-__device__ __forceinline__ float min32_tree(const float (&v)[32])
-{
-    float a[16];
-#pragma unroll
-    for (int j = 0; j < 16; ++j) a[j] = fminf(v[2 * j], v[2 * j + 1]);
-#pragma unroll
-    for (int w = 8; w > 0; w >>= 1)
-#pragma unroll
-        for (int j = 0; j < w; ++j) a[j] = fminf(a[j], a[j + w]);
-    return a[0];
-}
-
-template <int KMAX, bool EXCL>
+template <int KMAX, bool EXCL, int PREC>
 __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_x,
                    const TcArgs a)
@@ -136,8 +153,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     const int S = a.stages;
     unsigned char* sA = base;                             // 2 x (mainA + extA)
     unsigned char* sB = base + 2 * size_t(mainA + extA);  // S x (mainB + extB)
-    const uint32_t idesc = idesc_bf16_f32(TC_M, TC_N);
+    const uint32_t idesc = idesc_f16_f32(TC_M, TC_N, PREC == 0 ? 1u : 0u);
     const uint32_t tx_bytes = uint32_t(mainB + extB);
+    const float sc = a.tcs[0], sc2 = a.tcs[1], inv_sc2 = a.tcs[2];
 
     if (warp == 1) {
         tmem_alloc(&tmem_base_sh, 2 * TC_N);
@@ -290,7 +308,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                     qs = a.qstat[q];
                     U = __uint_as_float(a.Ubits[q]);
                 }
-                const uint4* src = reinterpret_cast<const uint4*>(a.Yb + int64_t(q) * a.d_pad);
+                const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(q) * a.d_pad);
                 for (int kb = 0; kb < kblocks; ++kb)
                     for (int c = 0; c < chunks; ++c) {
                         const uint4 v = active ? src[kb * chunks + c] : make_uint4(0, 0, 0, 0);
@@ -299,17 +317,17 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 // extra block: (1, 1, -A', -A', 0, ...) against (|x|^2 hi, lo, |x| hi, lo, 0, ...)
                 uint4 e0 = make_uint4(0, 0, 0, 0);
                 if (active) {
-                    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), na = __float2bfloat16_rn(qs.z);
-                    const __nv_bfloat162 p0 = __halves2bfloat162(one, one), p1 = __halves2bfloat162(na, na);
-                    e0.x = *reinterpret_cast<const uint32_t*>(&p0);
-                    e0.y = *reinterpret_cast<const uint32_t*>(&p1);
+                    const uint16_t one = to16_rn<PREC>(1.0f), na = to16_rn<PREC>(qs.z);  // exact
+                    e0.x = pack16(one, one);
+                    e0.y = pack16(na, na);
                 }
                 *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 0, 32)) = e0;
                 *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 1, 32)) = make_uint4(0, 0, 0, 0);
                 TcQConst c;
                 c.qn2 = qs.x;
                 c.U = U;
-                c.Uthr = U - (1.0f - a.Bn) * qs.x;
+                c.Cq = qs.w;
+                c.Uthr = sc2 * U - (1.0f - a.Bn) * qs.x + qs.w;
                 c.Aq1 = -qs.z;
                 qc[ab][r] = c;
                 qidx[ab][r] = active ? q : 0xFFFFFFFFu;
@@ -363,11 +381,11 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                         const uint32_t row = sbuf_row[i * 128 + er];
                         const float D = sbuf_val[i * 128 + er];
                         if (pos + uint32_t(i) < uint32_t(a.cap)) a.surv[q * a.cap + pos + i] = row;
-                        // d~ + E <= D + (1+B)|q|^2 + 2B|x|^2 + 2A'|x|
+                        // d~ + E <= D + (1+B)|q|^2 + 2B|x|^2 + 2A'|x| + Cq (scaled units)
                         const float4 rs = __ldg(a.rowstat + row);
-                        const float ub = fmaxf((D + (1.0f + a.Bn) * cur.qn2 + 2.0f * a.Bn * rs.z +
-                                                2.0f * cur.Aq1 * rs.y) * (1.0f + 1e-6f),
-                                               0.0f);
+                        const float ubs = (D + (1.0f + a.Bn) * cur.qn2 + 2.0f * a.Bn * sc2 * rs.z +
+                                           2.0f * cur.Aq1 * sc * rs.y + cur.Cq) * (1.0f + 1e-6f);
+                        const float ub = fmaxf(ubs * inv_sc2, 0.0f);
                         if (ub < ubl[KMAX - 1]) {
 #pragma unroll
                             for (int u = KMAX - 1; u > 0; --u) {
@@ -385,7 +403,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                         if (u == a.k - 1) kth = ubl[u];
                     if (kth < cur.U) {
                         cur.U = kth;
-                        cur.Uthr = cur.U - (1.0f - a.Bn) * cur.qn2;
+                        cur.Uthr = sc2 * cur.U - (1.0f - a.Bn) * cur.qn2 + cur.Cq;
                     }
                 }
                 nb = 0;
@@ -397,51 +415,57 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 tc_fence_after();
                 const int y0 = int(dc.r0) + t * TC_N;
                 const int nvalid = min(TC_N, int(dc.r1) - y0);
-                for (int c0 = 0; c0 < nvalid; c0 += 32) {
-                    float v[32];
-                    tmem_ld32(tl + uint32_t(acc * TC_N + c0), v);
+                for (int c0 = 0; c0 < nvalid; c0 += 64) {
+                    float v[64], vmin;
+                    tmem_ld32x2_min(tl + uint32_t(acc * TC_N + c0), v, vmin);
                     const int lim = nvalid - c0;
-                    if (lim < 32) {
+                    // columns past the item's rows (the next cone's, in the last
+                    // tile) can only lower the minimum: the exact mask below drops them
+                    if (active && vmin <= cur.Uthr) {
 #pragma unroll
-                        for (int j = 0; j < 32; ++j)
-                            if (j >= lim) v[j] = INFINITY;  // rows of the next cone
-                    }
-                    if (active && min32_tree(v) <= cur.Uthr) {
-                        uint32_t mask = 0;
+                        for (int h = 0; h < 2; ++h) {
+                            uint32_t mask = 0;
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) mask |= (v[j] <= cur.Uthr ? 1u : 0u) << j;
-                        // a masked column is +inf, which an unbounded U would admit
-                        if (lim < 32) mask &= (1u << lim) - 1u;
-                        while (mask) {
-                            const int j = __ffs(int(mask)) - 1;
-                            mask &= mask - 1u;
-                            float val = v[0];
+                            for (int j = 0; j < 32; ++j) mask |= (v[32 * h + j] <= cur.Uthr ? 1u : 0u) << j;
+                            // a masked column is +inf, which an unbounded U would admit
+                            const int limh = lim - 32 * h;
+                            if (limh < 32) mask &= limh <= 0 ? 0u : (1u << limh) - 1u;
+                            while (mask) {
+                                const int j = __ffs(int(mask)) - 1;
+                                mask &= mask - 1u;
+                                float val = v[32 * h];
 #pragma unroll
-                            for (int u = 1; u < 32; ++u) val = u == j ? v[u] : val;
-                            if (nb == TC_SBUF) flush();
-                            sbuf_row[nb * 128 + er] = uint32_t(y0 + c0 + j);
-                            sbuf_val[nb * 128 + er] = val;
-                            ++nb;
+                                for (int u = 1; u < 32; ++u) val = u == j ? v[32 * h + u] : val;
+                                if (nb == TC_SBUF) flush();
+                                sbuf_row[nb * 128 + er] = uint32_t(y0 + c0 + 32 * h + j);
+                                sbuf_val[nb * 128 + er] = val;
+                                ++nb;
+                            }
                         }
                     }
-                    if (a.debug && active && lane < lim) {
+                    if (a.debug && active) {
                         // folded product against an fp32 evaluation, one column per thread
-                        const int row = y0 + c0 + lane;
-                        const float* xr = a.xs + size_t(row) * a.d_pad;
-                        const float* yr = a.Y + q * int64_t(a.d);
-                        float dot = 0.f;
-                        for (int i = 0; i < a.d; ++i) dot = fmaf(xr[i], yr[i], dot);
-                        const float4 rs = __ldg(a.rowstat + row);
-                        float mine = v[0];
+                        const int col = lane + 32 * (c0 / 64 % 2);
+                        if (col < lim) {
+                            const int row = y0 + c0 + col;
+                            const float* xr = a.xs + size_t(row) * a.d_pad;
+                            const float* yr = a.Y + q * int64_t(a.d);
+                            float dot = 0.f;
+                            for (int i = 0; i < a.d; ++i) dot = fmaf(xr[i], yr[i], dot);
+                            const float4 rs = __ldg(a.rowstat + row);
+                            float mine = v[0];
 #pragma unroll
-                        for (int u = 1; u < 32; ++u) mine = u == lane ? v[u] : mine;
-                        const float ref = -2.0f * dot + rs.x - cur.Aq1 * rs.y;
-                        const float qnorm = sqrtf(cur.qn2);
-                        const float lim2 = a.cdot2 * qnorm * rs.y * 1.001f + 4.0f * a.Bn * (cur.qn2 + rs.z) + 1e-30f;
-                        atomicAdd(a.diag + 2, 1ull);
-                        if (fabsf(mine - ref) > lim2) {
-                            atomicAdd(a.diag + 3, 1ull);
-                            atomicOr(a.status, ST_BOUND);
+                            for (int u = 1; u < 64; ++u) mine = u == col ? v[u] : mine;
+                            const float ref = -2.0f * sc2 * dot + sc2 * rs.x - cur.Aq1 * sc * rs.y;
+                            const float qnorm = sqrtf(cur.qn2);
+                            const float lim2 = a.cdot2 * qnorm * sc * rs.y * 1.001f +
+                                               4.0f * a.Bn * (cur.qn2 + sc2 * rs.z) +
+                                               2.0f * a.cabs * (sc * rs.y + qnorm) + 1e-30f;
+                            atomicAdd(a.diag + 2, 1ull);
+                            if (fabsf(mine - ref) > lim2) {
+                                atomicAdd(a.diag + 3, 1ull);
+                                atomicOr(a.status, ST_BOUND);
+                            }
                         }
                     }
                 }
@@ -464,49 +488,57 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
 
 // ---------------------------------------------------------------- query prep
 
-// One warp per query: bf16 copy of -2y, norms and A', survivor counter reset,
-// and the initial upper bound U: the k-th smallest canonical fp32 distance
-// among up to TC_SEED rows of the first probed cones (in probe order, excluded
-// rows skipped), inflated by the fp32 error bound; +inf if fewer than k rows.
-constexpr int TC_SEED = 128;
+// One warp per query: 16-bit copy of -2 s y, scaled norms and A', survivor
+// counter reset, and the initial upper bound U: the k-th smallest canonical
+// fp32 distance over the rows of the first probed cones (in probe order,
+// excluded rows skipped, at least TC_SEED rows when the cones hold them),
+// inflated by the fp32 error bound; +inf if fewer than k rows.  A query too large for the 16-bit range is left to the
+// rerank's full scan (its survivor count is set above the capacity).
+constexpr int TC_SEED = 512;  // rows scanned exactly for the initial bound
 
-template <int F>
+template <int F, int PREC, int KMAX>
 __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restrict__ Y, int64_t Q, int d, int d_pad,
                                                             const uint32_t* __restrict__ probes, int64_t P_eff,
                                                             const uint32_t* __restrict__ offsets, uint32_t NC,
                                                             const float* __restrict__ xs, int k, float cdot2,
+                                                            float cabs, const float* __restrict__ tcs,
                                                             const uint32_t* __restrict__ perm,
                                                             const int64_t* __restrict__ query_src, int64_t grid_w,
-                                                            int radius, __nv_bfloat16* __restrict__ Yb,
+                                                            int radius, int cap, uint16_t* __restrict__ Y16,
                                                             float4* __restrict__ qstat, uint32_t* __restrict__ Ubits,
                                                             uint32_t* __restrict__ surv_cnt)
 {
-    __shared__ float seed[4][TC_SEED];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
     if (q >= Q) return;  // whole warp
     const float* y = Y + q * int64_t(d);
-    float s = 0.f;
+    const float sc = tcs[0];
+    float s = 0.f, amax = 0.f;
     for (int c = lane * 4; c < d_pad; c += 128) {
         float4 v;
         v.x = c + 0 < d ? y[c + 0] : 0.f;
         v.y = c + 1 < d ? y[c + 1] : 0.f;
         v.z = c + 2 < d ? y[c + 2] : 0.f;
         v.w = c + 3 < d ? y[c + 3] : 0.f;
-        // bf16(-2 y) = -2 bf16(y) exactly: the scale is a power of two
-        __nv_bfloat162 lo = __floats2bfloat162_rn(-2.f * v.x, -2.f * v.y),
-                       hi = __floats2bfloat162_rn(-2.f * v.z, -2.f * v.w);
+        // -2 s y: the factor is a power of two, so the 16-bit value is exact
+        // up to the 16-bit rounding of s y itself
         uint2 pk;
-        pk.x = *reinterpret_cast<uint32_t*>(&lo);
-        pk.y = *reinterpret_cast<uint32_t*>(&hi);
-        *reinterpret_cast<uint2*>(Yb + q * int64_t(d_pad) + c) = pk;
+        pk.x = pack16(to16_rn<PREC>(-2.f * sc * v.x), to16_rn<PREC>(-2.f * sc * v.y));
+        pk.y = pack16(to16_rn<PREC>(-2.f * sc * v.z), to16_rn<PREC>(-2.f * sc * v.w));
+        *reinterpret_cast<uint2*>(Y16 + q * int64_t(d_pad) + c) = pk;
         s = fmaf(v.x, v.x, s);
         s = fmaf(v.y, v.y, s);
         s = fmaf(v.z, v.z, s);
         s = fmaf(v.w, v.w, s);
+        amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    for (int o = 16; o > 0; o >>= 1) {
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    // fp16 holds |v| < 65504; keep 2 |s y| and the norm terms well inside
+    const bool unscreenable = PREC == 1 && (2.f * sc * amax > 16384.f || sc * sc * s > 32768.f);
 
     // seed rows: TPR lanes per row (canonical distance, as in the rerank)
     const int n4 = d_pad >> 2;
@@ -522,76 +554,150 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
         qv[f].w = c + 3 < d ? y[c + 3] : 0.f;
     }
     const int64_t src = query_src ? query_src[q] : -1;
-    int n = 0;  // seed slots used (multiple of CPP)
-    for (int64_t p = 0; p < P_eff && n < TC_SEED; ++p) {
+    uint64_t list[KMAX];
+    topk_init<KMAX>(list, k);
+    int scanned = 0;
+    for (int64_t p = 0; p < P_eff && scanned < TC_SEED; ++p) {
         const uint32_t b = probes[q * P_eff + p];
         if (b >= NC) continue;
         const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
-        for (uint32_t r0 = o0; r0 < o1 && n < TC_SEED; r0 += CPP) {
-            const uint32_t r = r0 + g;
-            bool usable = r < o1;
-            const float4* xr = reinterpret_cast<const float4*>(xs + size_t(usable ? r : o0) * d_pad) + sub * F;
-            float cpart[F];
+        for (uint32_t r0 = o0; r0 < o1 && scanned < TC_SEED; r0 += 4 * CPP) {
+            // four row groups per iteration: all loads in flight before the arithmetic
+            float4 xv[4][F];
+            uint32_t rr[4];
 #pragma unroll
-            for (int f = 0; f < F; ++f) cpart[f] = sq4(xr[f], qv[f]);
-            const float dist = lane_tree(pair_tree<F>(cpart), TPR);
-            if (usable && src >= 0) {
-                // an excluded row is not a candidate and cannot seed the bound
-                const int64_t id = int64_t(perm[r]);
-                int64_t dr = id / grid_w - src / grid_w, dc = id % grid_w - src % grid_w;
-                dr = dr < 0 ? -dr : dr;
-                dc = dc < 0 ? -dc : dc;
-                usable = (dr > dc ? dr : dc) > radius;
+            for (int u = 0; u < 4; ++u) {
+                rr[u] = r0 + uint32_t(u * CPP + g);
+                const float4* xr =
+                    reinterpret_cast<const float4*>(xs + size_t(rr[u] < o1 ? rr[u] : o0) * d_pad) + sub * F;
+#pragma unroll
+                for (int f = 0; f < F; ++f) xv[u][f] = xr[f];
             }
-            if (sub == 0) seed[w][n + g] = usable ? dist : INFINITY;
-            n += CPP;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                float cpart[F];
+#pragma unroll
+                for (int f = 0; f < F; ++f) cpart[f] = sq4(xv[u][f], qv[f]);
+                const float dist = lane_tree(pair_tree<F>(cpart), TPR);
+                bool usable = rr[u] < o1;
+                if (usable && src >= 0) {
+                    // an excluded row is not a candidate and cannot seed the bound
+                    const int64_t id = int64_t(perm[rr[u]]);
+                    int64_t dr = id / grid_w - src / grid_w, dc = id % grid_w - src % grid_w;
+                    dr = dr < 0 ? -dr : dr;
+                    dc = dc < 0 ? -dc : dc;
+                    usable = (dr > dc ? dr : dc) > radius;
+                }
+                if (sub == 0 && usable) {
+                    const uint64_t v = pack_di(dist, rr[u]);
+                    if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
+                }
+            }
+            scanned += 4 * CPP;
         }
     }
-    __syncwarp();
-    // k rounds of warp minimum over the seed distances
+    // k-th smallest over the warp: k rounds of warp minimum over the lists
     float U = INFINITY;
     {
-        float mine[TC_SEED / 32];
-#pragma unroll
-        for (int i = 0; i < TC_SEED / 32; ++i) {
-            const int slot = lane + 32 * i;
-            mine[i] = slot < n ? seed[w][slot] : INFINITY;
-        }
         float kth = INFINITY;
         int found = 0;
         for (int j = 0; j < k; ++j) {
-            float m = mine[0];
-            int mi = 0;
-#pragma unroll
-            for (int i = 1; i < TC_SEED / 32; ++i)
-                if (mine[i] < m) {
-                    m = mine[i];
-                    mi = i;
-                }
-            float wm = m;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wm = fminf(wm, __shfl_xor_sync(0xffffffffu, wm, o));
-            if (wm == INFINITY) break;
-            const unsigned owner = __ballot_sync(0xffffffffu, m == wm);
-            if (lane == __ffs(owner) - 1) {
-#pragma unroll
-                for (int i = 0; i < TC_SEED / 32; ++i)
-                    if (i == mi) mine[i] = INFINITY;
-            }
-            kth = wm;
+            const uint64_t head = topk_head<KMAX>(list, k);
+            const uint64_t best = warp_min_u64(head);
+            if (best == EMPTY_DI) break;
+            if (head == best) topk_remove<KMAX>(list, k, best);
+            kth = di_dist(best);
             ++found;
         }
         // the canonical fp32 distance is within 6.6e-7 relative of the exact one
         if (found == k) U = kth * (1.0f + 2e-6f) + 1e-30f;
     }
     if (lane == 0) {
-        // A' = 2c|q| inflated by 2^-14 (bf16 hi/lo split of |x|) and rounded up to bf16
-        const float A = cdot2 * sqrtf(s) * (1.0f + 6.1035156e-5f);
-        const float Ap = __bfloat162float(__float2bfloat16_ru(A));
-        qstat[q] = make_float4(s, sqrtf(s), -Ap, 0.f);
+        // scaled units: |q'| = s |q|; A' = 2c|q'| + Cabs, inflated by 2^-14
+        // (16-bit hi/lo split of |x|) and rounded up to the 16-bit format
+        const float qn = sc * sc * s, qnorm = sc * sqrtf(s);
+        const float A = (cdot2 * qnorm + cabs) * (1.0f + 6.1035156e-5f);
+        const float Ap = from16<PREC>(to16_ru<PREC>(A));
+        qstat[q] = make_float4(qn, qnorm, -Ap, cabs * qnorm);
         Ubits[q] = __float_as_uint(U);
-        surv_cnt[q] = 0;
+        surv_cnt[q] = unscreenable ? uint32_t(cap) + 1u : 0u;
     }
+}
+
+// ---------------------------------------------------------------- rows
+
+// The data scale of the screen: s = 1 for bf16; for fp16 the power of two
+// with s^2 max|x|^2 <= 2^14 (all-zero data: 1).  tcs = (s, s^2, 1/s^2, 0).
+template <int PREC>
+__global__ void tc_scale_kernel(const uint32_t* __restrict__ maxn2_bits, float* __restrict__ tcs)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int e = 0;
+    const float m = __uint_as_float(*maxn2_bits);
+    if (PREC == 1 && m > 0.0f) {
+        int x;
+        frexpf(m, &x);  // m < 2^x
+        const int t = 14 - x;
+        e = t >= 0 ? t / 2 : -((1 - t) / 2);
+        e = e > 40 ? 40 : (e < -40 ? -40 : e);
+    }
+    const float sc = ldexpf(1.0f, e);
+    tcs[0] = sc;
+    tcs[1] = sc * sc;
+    tcs[2] = 1.0f / (sc * sc);
+    tcs[3] = 0.0f;
+}
+
+// 16-bit copy of s x (row-major, d_pad per row) and the extra K block of each
+// row: 16-bit hi/lo splits of (1-B) s^2 |x|^2 and s |x|, then zeros.
+template <int PREC>
+__global__ void __launch_bounds__(256) tc_rows_kernel(const float* __restrict__ xs, const float4* __restrict__ rowstat,
+                                                      int64_t N, int d_pad, const float* __restrict__ tcs,
+                                                      uint16_t* __restrict__ x16, uint16_t* __restrict__ xe16)
+{
+    const float sc = tcs[0], sc2 = tcs[1];
+    const int64_t n4 = N * (d_pad / 4);
+    for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n4; i += int64_t(gridDim.x) * blockDim.x) {
+        const float4 v = reinterpret_cast<const float4*>(xs)[i];
+        uint2 pk;
+        pk.x = pack16(to16_rn<PREC>(sc * v.x), to16_rn<PREC>(sc * v.y));
+        pk.y = pack16(to16_rn<PREC>(sc * v.z), to16_rn<PREC>(sc * v.w));
+        reinterpret_cast<uint2*>(x16)[i] = pk;
+    }
+    for (int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; r < N; r += int64_t(gridDim.x) * blockDim.x) {
+        const float4 rs = rowstat[r];
+        const float a = sc2 * rs.x, b = sc * rs.y;
+        const uint16_t ah = to16_rn<PREC>(a), bh = to16_rn<PREC>(b);
+        const uint16_t al = to16_rn<PREC>(a - from16<PREC>(ah)), bl = to16_rn<PREC>(b - from16<PREC>(bh));
+        uint4* dst = reinterpret_cast<uint4*>(xe16 + r * 16);
+        dst[0] = make_uint4(pack16(ah, al), pack16(bh, bl), 0u, 0u);
+        dst[1] = make_uint4(0u, 0u, 0u, 0u);
+    }
+}
+
+int launch_tc_scale(int prec, const uint32_t* maxn2_bits, float* tcs, cudaStream_t st)
+{
+    if (prec == 0) tc_scale_kernel<0><<<1, 32, 0, st>>>(maxn2_bits, tcs);
+    else tc_scale_kernel<1><<<1, 32, 0, st>>>(maxn2_bits, tcs);
+    return count_launch();
+}
+
+int launch_tc_rows(int prec, const float* xs, const float4* rowstat, int64_t N, int d_pad, const uint32_t* maxn2_bits,
+                   float* tcs, void* x16, void* xe16, cudaStream_t st, int num_sms)
+{
+    if (prec == 0) tc_scale_kernel<0><<<1, 32, 0, st>>>(maxn2_bits, tcs);
+    else tc_scale_kernel<1><<<1, 32, 0, st>>>(maxn2_bits, tcs);
+    int rc = count_launch();
+    if (rc || N == 0) return rc;
+    int64_t blocks = (N * (d_pad / 4) + 255) / 256;
+    if (blocks > int64_t(num_sms) * 16) blocks = int64_t(num_sms) * 16;
+    if (prec == 0)
+        tc_rows_kernel<0><<<unsigned(blocks), 256, 0, st>>>(xs, rowstat, N, d_pad, tcs, static_cast<uint16_t*>(x16),
+                                                             static_cast<uint16_t*>(xe16));
+    else
+        tc_rows_kernel<1><<<unsigned(blocks), 256, 0, st>>>(xs, rowstat, N, d_pad, tcs, static_cast<uint16_t*>(x16),
+                                                             static_cast<uint16_t*>(xe16));
+    return count_launch();
 }
 
 // ---------------------------------------------------------------- rerank
@@ -608,7 +714,8 @@ __global__ void __launch_bounds__(128) tc_rerank_kernel(const float* __restrict_
                                                         const uint32_t* __restrict__ surv, int cap, int k,
                                                         const int64_t* __restrict__ query_src, int64_t grid_w,
                                                         int radius, unsigned long long* __restrict__ diag,
-                                                        int64_t* __restrict__ out_ids, float* __restrict__ out_d)
+                                                        uint32_t* __restrict__ ovf, int64_t* __restrict__ out_ids,
+                                                        float* __restrict__ out_d)
 {
     const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -659,16 +766,12 @@ __global__ void __launch_bounds__(128) tc_rerank_kernel(const float* __restrict_
         }
         if (lane == 0) atomicAdd(diag, (unsigned long long)n);
     } else {
-        if (lane == 0) atomicAdd(diag + 1, 1ull);
-        for (int64_t p = 0; p < P_eff; ++p) {
-            const uint32_t b = probes[q * P_eff + p];
-            if (b >= NC) continue;
-            const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
-            for (uint32_t b0 = o0; b0 < o1; b0 += CPP) {
-                const uint32_t r = b0 + g;
-                consider(r, r < o1);
-            }
+        // survivor list overflowed: the query is rescanned by the plain scan
+        if (lane == 0) {
+            atomicAdd(diag + 1, 1ull);
+            ovf[1 + atomicAdd(ovf, 1u)] = uint32_t(q);
         }
+        return;
     }
     for (int j = 0; j < k; ++j) {
         const uint64_t head = topk_head<KMAX>(list, k);
@@ -688,7 +791,7 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_pad)
+int tc_encode_rows_map(void* map_out, const void* x16, int64_t N, int d_pad, int prec)
 {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -713,8 +816,9 @@ int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_
     const CUtensorMapSwizzle sw = row_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
                                                    : (row_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
                                                                       : CU_TENSOR_MAP_SWIZZLE_32B);
-    CUresult r = fn(static_cast<CUtensorMap*>(map_out), CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
-                    const_cast<__nv_bfloat16*>(xb), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+    CUresult r = fn(static_cast<CUtensorMap*>(map_out),
+                    prec == 0 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    const_cast<void*>(x16), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         set_error("cuTensorMapEncodeTiled failed (%d)", int(r));
@@ -725,20 +829,33 @@ int tc_encode_rows_map(void* map_out, const __nv_bfloat16* xb, int64_t N, int d_
 
 size_t tc_map_bytes() { return 2 * sizeof(CUtensorMap); }
 
-int launch_tc_query_prep(const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes, int64_t P_eff,
-                         const uint32_t* offsets, uint32_t NC, const float* xs, int k, bool seed, float cdot2,
-                         const uint32_t* perm, const int64_t* query_src, int64_t grid_w, int radius,
-                         __nv_bfloat16* Yb, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt, cudaStream_t st)
+int launch_tc_query_prep(int prec, const float* Y, int64_t Q, int d, int d_pad, const uint32_t* probes,
+                         int64_t P_eff, const uint32_t* offsets, uint32_t NC, const float* xs, int k, float cdot2,
+                         float cabs, const float* tcs, const uint32_t* perm, const int64_t* query_src, int64_t grid_w,
+                         int radius, int cap, void* Y16, float4* qstat, uint32_t* Ubits, uint32_t* surv_cnt,
+                         cudaStream_t st)
 {
     if (Q == 0) return 0;
     const unsigned blocks = unsigned((Q * 32 + 127) / 128);
-    const int64_t pe = seed ? P_eff : 0;
-    if (d_pad <= 128)
-        tc_query_prep_kernel<1><<<blocks, 128, 0, st>>>(Y, Q, d, d_pad, probes, pe, offsets, NC, xs, k, cdot2, perm,
-                                                        query_src, grid_w, radius, Yb, qstat, Ubits, surv_cnt);
-    else
-        tc_query_prep_kernel<2><<<blocks, 128, 0, st>>>(Y, Q, d, d_pad, probes, pe, offsets, NC, xs, k, cdot2, perm,
-                                                        query_src, grid_w, radius, Yb, qstat, Ubits, surv_cnt);
+    uint16_t* y16 = static_cast<uint16_t*>(Y16);
+#define OSANN_PREP(F, PR, KM)                                                                                       \
+    tc_query_prep_kernel<F, PR, KM><<<blocks, 128, 0, st>>>(Y, Q, d, d_pad, probes, P_eff, offsets, NC, xs, k, cdot2, \
+                                                            cabs, tcs, perm, query_src, grid_w, radius, cap, y16,    \
+                                                            qstat, Ubits, surv_cnt)
+#define OSANN_PREP_K(F, PR)             \
+    if (k <= 1) OSANN_PREP(F, PR, 1);      \
+    else if (k <= 4) OSANN_PREP(F, PR, 4); \
+    else if (k <= 16) OSANN_PREP(F, PR, 16); \
+    else OSANN_PREP(F, PR, 32);
+    if (d_pad <= 128) {
+        if (prec == 0) { OSANN_PREP_K(1, 0) }
+        else { OSANN_PREP_K(1, 1) }
+    } else {
+        if (prec == 0) { OSANN_PREP_K(2, 0) }
+        else { OSANN_PREP_K(2, 1) }
+    }
+#undef OSANN_PREP_K
+#undef OSANN_PREP
     return count_launch();
 }
 
@@ -750,11 +867,11 @@ size_t tc_smem_bytes(int d_pad)
     return need < 80u * 1024u ? 80u * 1024u : need;
 }
 
-template <int KMAX, bool EXCL>
+template <int KMAX, bool EXCL, int PREC>
 static int launch_tc_t(const void* maps, const TcArgs& a, cudaStream_t st, int num_sms)
 {
     const size_t smem = tc_smem_bytes(a.d_pad);
-    auto kern = tc_scan_kernel<KMAX, EXCL>;
+    auto kern = tc_scan_kernel<KMAX, EXCL, PREC>;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     // resident CTAs per SM: registers, shared memory (228 KB per SM, 1 KB
     // reserved per CTA) and TMEM (512 columns, 256 per CTA)
@@ -772,20 +889,20 @@ static int launch_tc_t(const void* maps, const TcArgs& a, cudaStream_t st, int n
     return count_launch();
 }
 
-int launch_tc_scan(const void* map, const uint32_t* offsets, const uint32_t* perm, const float4* rowstat,
-                   const __nv_bfloat16* Yb, const float4* qstat, const int64_t* query_src, int64_t grid_w, int radius,
+int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float4* rowstat, const void* Y16,
+                   const float4* qstat, const float* tcs, const int64_t* query_src, int64_t grid_w, int radius,
                    const BatchedBuffers& b, uint32_t* Ubits, uint32_t* surv_cnt, uint32_t* surv, int cap,
                    uint32_t* status, unsigned long long* diag, const float* xs, const float* Y, int64_t S, int d,
-                   int d_pad, int k, float cdot2, float Bn, int debug, cudaStream_t st, int num_sms)
+                   int d_pad, int k, float cdot2, float Bn, float cabs, int debug, cudaStream_t st, int num_sms)
 {
     TcArgs a{};
-    a.offsets = offsets;
     a.perm = perm;
     a.rowstat = rowstat;
-    a.Yb = Yb;
+    a.Y16 = static_cast<const uint16_t*>(Y16);
     a.qstat = qstat;
+    a.tcs = tcs;
     a.query_src = query_src;
-    a.items = b.items;
+    a.items = b.items_sorted;
     a.n_items_dev = b.n_items_dev;
     a.qcount = b.qcount;
     a.qoff = b.qoff;
@@ -809,9 +926,16 @@ int launch_tc_scan(const void* map, const uint32_t* offsets, const uint32_t* per
     a.debug = debug;
     a.cdot2 = cdot2;
     a.Bn = Bn;
+    a.cabs = cabs;
     const bool excl = query_src != nullptr;
-#define OSANN_TC(KM)                                                                                     \
-    return excl ? launch_tc_t<KM, true>(map, a, st, num_sms) : launch_tc_t<KM, false>(map, a, st, num_sms)
+#define OSANN_TC(KM)                                                                                 \
+    do {                                                                                             \
+        if (prec == 0)                                                                               \
+            return excl ? launch_tc_t<KM, true, 0>(maps, a, st, num_sms)                             \
+                        : launch_tc_t<KM, false, 0>(maps, a, st, num_sms);                           \
+        return excl ? launch_tc_t<KM, true, 1>(maps, a, st, num_sms)                                 \
+                    : launch_tc_t<KM, false, 1>(maps, a, st, num_sms);                               \
+    } while (0)
     if (k <= 1) OSANN_TC(1);
     if (k <= 4) OSANN_TC(4);
     if (k <= 16) OSANN_TC(16);
@@ -822,9 +946,10 @@ int launch_tc_scan(const void* map, const uint32_t* offsets, const uint32_t* per
 int launch_tc_rerank(const float* xs, int d_pad, const uint32_t* perm, const uint32_t* offsets, uint32_t NC,
                      const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, const uint32_t* surv_cnt,
                      const uint32_t* surv, int cap, int k, const int64_t* query_src, int64_t grid_w, int radius,
-                     unsigned long long* diag, int64_t* out_ids, float* out_d, cudaStream_t st)
+                     unsigned long long* diag, uint32_t* ovf, int64_t* out_ids, float* out_d, cudaStream_t st)
 {
     if (Q == 0) return 0;
+    cudaMemsetAsync(ovf, 0, 4, st);
     const unsigned blocks = unsigned((Q * 32 + 127) / 128);
     const bool excl = query_src != nullptr;
 #define OSANN_RR(F, KM)                                                                                           \
@@ -832,11 +957,11 @@ int launch_tc_rerank(const float* xs, int d_pad, const uint32_t* perm, const uin
         if (excl)                                                                                                 \
             tc_rerank_kernel<F, KM, true><<<blocks, 128, 0, st>>>(xs, d_pad, perm, offsets, NC, Y, d, Q, probes,  \
                                                                   P_eff, surv_cnt, surv, cap, k, query_src,       \
-                                                                  grid_w, radius, diag, out_ids, out_d);          \
+                                                                  grid_w, radius, diag, ovf, out_ids, out_d);     \
         else                                                                                                      \
             tc_rerank_kernel<F, KM, false><<<blocks, 128, 0, st>>>(xs, d_pad, perm, offsets, NC, Y, d, Q, probes, \
                                                                    P_eff, surv_cnt, surv, cap, k, query_src,      \
-                                                                   grid_w, radius, diag, out_ids, out_d);         \
+                                                                   grid_w, radius, diag, ovf, out_ids, out_d);    \
     } while (0)
 #define OSANN_RR_K(F)              \
     if (k <= 1) OSANN_RR(F, 1);    \

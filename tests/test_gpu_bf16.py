@@ -1,6 +1,7 @@
-"""Tensor-core screening path (bf16 tcgen05 tiles + certified bound + fp32
-rerank): same bits as the fp32 paths, parity with the oracle, and the
-on-device check of the error bound (OSANN_DEBUG_CHECKS=1) never fails."""
+"""Tensor-core screening paths (bf16 or scaled fp16 tcgen05 tiles + certified
+bound + fp32 rerank): same bits as the fp32 paths, parity with the oracle,
+and the on-device check of the error bound (OSANN_DEBUG_CHECKS=1) never
+fails."""
 import os
 
 import numpy as np
@@ -43,6 +44,11 @@ def _cases():
                 rng.standard_normal((700, 20), dtype=np.float32), 2, [40], 3, None))
     out.append(("d100", rng.standard_normal((20_011, 100), dtype=np.float32),
                 rng.standard_normal((300, 100), dtype=np.float32), 1, [30], 2, None))
+    # magnitudes far from 1: the fp16 scale must bring them into range exactly
+    out.append(("tiny", (1e-6 * rng.standard_normal((30_011, 32))).astype(np.float32),
+                (1e-6 * rng.standard_normal((600, 32))).astype(np.float32), 2, [48], 2, None))
+    out.append(("huge", (3e4 * rng.standard_normal((30_011, 32))).astype(np.float32),
+                (3e4 * rng.standard_normal((600, 32))).astype(np.float32), 2, [48], 2, None))
     return out
 
 
@@ -56,8 +62,9 @@ def case(i):
     return CASES[i]
 
 
-@pytest.mark.parametrize("i", range(7))
-def test_bf16_screen_is_exact(osann, i):
+@pytest.mark.parametrize("path", ["bf16", "fp16"])
+@pytest.mark.parametrize("i", range(9))
+def test_tensor_screen_is_exact(osann, i, path):
     name, X, Y, L, Ps, k, ex = case(i)
     idx = osann.Index(to_dev(X), L)
     Yd = to_dev(Y)
@@ -68,7 +75,7 @@ def test_bf16_screen_is_exact(osann, i):
     ref = oracle.Index(X, L)
     idx.screen_stats()
     for P in Ps:
-        a = idx.search(Yd, P, k, path="bf16", **kw)
+        a = idx.search(Yd, P, k, path=path, **kw)
         b = idx.search(Yd, P, k, path="batched", **kw)
         assert np.array_equal(to_np(a[0]), to_np(b[0])), name
         assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(b[1]).view(np.uint32)), name
@@ -78,15 +85,32 @@ def test_bf16_screen_is_exact(osann, i):
     assert st["bound_checks"] > 0
     assert st["bound_violations"] == 0, st
     assert idx.status() == 0
-    print(name, st)
+    print(name, path, st)
 
 
-def test_bf16_full_budget_is_linear_search(osann):
+@pytest.mark.parametrize("path", ["bf16", "fp16"])
+def test_tensor_full_budget_is_linear_search(osann, path):
     name, X, Y, L, Ps, k, ex = case(0)
     idx = osann.Index(to_dev(X), L)
     Yd = to_dev(Y)
-    a = idx.search(Yd, idx.NC, k, path="bf16")
+    a = idx.search(Yd, idx.NC, k, path=path)
     bf = idx.bruteforce(Yd, k)
     assert np.array_equal(to_np(a[0]), to_np(bf[0]))
     assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(bf[1]).view(np.uint32))
     assert idx.screen_stats()["bound_violations"] == 0
+
+
+def test_fp16_out_of_range_query_takes_the_full_scan(osann):
+    """A query too large for the scaled fp16 range is rescanned in fp32."""
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((20_011, 32)).astype(np.float32)
+    Y = rng.standard_normal((300, 32)).astype(np.float32)
+    Y[7] *= 1e5
+    idx = osann.Index(to_dev(X), 2)
+    Yd = to_dev(Y)
+    idx.screen_stats()
+    a = idx.search(Yd, 64, 3, path="fp16")
+    b = idx.search(Yd, 64, 3, path="batched")
+    assert np.array_equal(to_np(a[0]), to_np(b[0]))
+    assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(b[1]).view(np.uint32))
+    assert idx.screen_stats()["fallbacks"] >= 1
