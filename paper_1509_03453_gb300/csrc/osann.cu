@@ -210,7 +210,7 @@ struct osann_index {
     float4* rowstat = nullptr;    // per row (1-B)|x|^2, |x|, |x|^2; N + TC_N rows
     // tensor-core screening operands per precision (0 bf16, 1 fp16): the
     // 16-bit scaled copy of xs, the extra K block of each row, the scale
-    // (s, s^2, 1/s^2, 0) and the TMA tensor maps over both arrays
+    // (s, s^2, 1/s^2, X) and the TMA tensor maps over both arrays
     uint16_t* x16[2] = {nullptr, nullptr};
     uint16_t* xe16[2] = {nullptr, nullptr};
     float* tcs = nullptr;  // 2 x 4 floats
@@ -299,7 +299,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, items_sorted, kcount, kfill;
+    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT;
     size_t total;
     int64_t max_items;
 };
@@ -373,9 +373,6 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         w.scan_temp = take(batched_scan_temp_bytes(ix->NC, n, ix->num_sms));
     }
     if (tc_mode(mode)) {
-        w.items_sorted = take(size_t(w.max_items > 0 ? w.max_items : 1) * 16);
-        w.kcount = take(size_t(P_eff + 1) * 4);
-        w.kfill = take(size_t(P_eff) * 4);
         w.yb = take(size_t(Q) * ix->d_pad * 2);
         w.qstat = take(size_t(Q) * 16);
         w.ubits = take(size_t(Q) * 4);
@@ -759,11 +756,6 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         b.qlist = reinterpret_cast<uint32_t*>(w + L.qlist);
         b.items = reinterpret_cast<uint4*>(w + L.items);
         b.hbuf = reinterpret_cast<uint32_t*>(w + L.hbuf);
-        if (tc_mode(mode)) {
-            b.items_sorted = reinterpret_cast<uint4*>(w + L.items_sorted);
-            b.kcount = reinterpret_cast<uint32_t*>(w + L.kcount);
-            b.kfill = reinterpret_cast<uint32_t*>(w + L.kfill);
-        }
         b.counters = reinterpret_cast<uint32_t*>(w + L.counters);
         b.n_items_dev = b.item_off + ix->NC;
         b.scan_temp = w + L.scan_temp;
@@ -781,8 +773,8 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         }
         if (!rc) {
             StageScope s(OSANN_STAGE_WORKLIST, st);
-            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probesT), Q, P_eff, ix->offsets, ix->NC, G,
-                                 tc_mode(mode), b, st, ix->num_sms);
+            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probesT), Q, P_eff, ix->offsets, ix->NC, G, b, st,
+                                 ix->num_sms);
         }
         if (!rc && tc_mode(mode)) {
             {

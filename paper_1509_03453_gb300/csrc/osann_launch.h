@@ -56,9 +56,6 @@ struct BatchedBuffers {
     uint32_t* qlist;      // Q * P_eff
     uint4* items;         // max_items descriptors (first row, end row, first slot, slot count)
     uint32_t* hbuf;       // per-block cone histograms (N_C <= 12288)
-    uint4* items_sorted;  // tensor-core path: items ordered by their smallest probe position
-    uint32_t* kcount;     // P + 1 counters of that ordering
-    uint32_t* kfill;      // P cursors
     uint32_t* counters;   // word 0: work counter of the tile scan
     const uint32_t* n_items_dev;  // device word holding the item count (item_off + NC)
     void* scan_temp;
@@ -67,10 +64,10 @@ struct BatchedBuffers {
 size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms);
 int wl_hist_entries(int64_t NC, int64_t n, int num_sms);
 // probesT: probe lists in probe-position-major order (probesT[p * Q + q]);
-// slots are still numbered q * P_eff + p.  order_by_probe: also produce
-// items_sorted (items by the smallest probe position of their queries).
+// slots are still numbered q * P_eff + p, and each cone's slot list is in
+// probe-position order.  Items are in cone order.
 int launch_worklist(const uint32_t* probesT, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
-                    int group, bool order_by_probe, BatchedBuffers& b, cudaStream_t st, int num_sms);
+                    int group, BatchedBuffers& b, cudaStream_t st, int num_sms);
 int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y,
                      int d, int64_t slots_per_query, int k, const int64_t* query_src, int64_t grid_w, int radius,
                      const BatchedBuffers& b, int group, uint64_t* partial, uint32_t* status, cudaStream_t st,

@@ -148,41 +148,16 @@ int wl_hist_entries(int64_t NC, int64_t n, int num_sms)
     return NC <= 12288 ? int(NC * wl_blocks_impl(n, num_sms) + 1) : 0;
 }
 
-// Order the items by the smallest probe position of their queries (the
-// first slot of an item, since a cone's slots are filled in probe-position
-// order): every query's best cones are screened early, which tightens its
-// bound for the rest.  Counting sort over the P positions.
-__global__ void wl_item_keys_kernel(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items_dev,
-                                    const uint32_t* __restrict__ qlist, uint32_t P, uint32_t* __restrict__ kcount)
-{
-    const uint32_t n = *n_items_dev;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        atomicAdd(&kcount[qlist[items[i].z] % P], 1u);
-}
-
-__global__ void wl_item_sort_kernel(const uint4* __restrict__ items, const uint32_t* __restrict__ n_items_dev,
-                                    const uint32_t* __restrict__ qlist, uint32_t P, const uint32_t* __restrict__ koff,
-                                    uint32_t* __restrict__ kfill, uint4* __restrict__ out)
-{
-    const uint32_t n = *n_items_dev;
-    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const uint4 it = items[i];
-        const uint32_t key = qlist[it.z] % P;
-        out[koff[key] + atomicAdd(&kfill[key], 1u)] = it;
-    }
-}
-
 size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms)
 {
     const int64_t hn = NC <= 12288 ? NC * wl_blocks_impl(n, num_sms) + 1 : 0;
     int64_t m = hn > NC + 1 ? hn : NC + 1;
-    if (n + 1 > m) m = n + 1;  // the probe-position counters (P + 1 <= n + 1)
     return scan_temp_bytes(m);
 }
 
 
 int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC, int group,
-                    bool order_by_probe, BatchedBuffers& b, cudaStream_t st, int num_sms)
+                    BatchedBuffers& b, cudaStream_t st, int num_sms)
 {
     const int64_t n = Q * P_eff;
     int rc;
@@ -222,17 +197,6 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
     wl_items_kernel<<<unsigned(cb), 256, 0, st>>>(b.nitems, b.item_off, offsets, b.qcount, b.qoff, NC, group,
                                                    b.items, b.counters);
     if ((rc = count_launch())) return rc;
-    if (order_by_probe) {
-        cudaMemsetAsync(b.kcount, 0, size_t(P_eff + 1) * 4, st);
-        cudaMemsetAsync(b.kfill, 0, size_t(P_eff) * 4, st);
-        const unsigned ib = unsigned(2 * num_sms);
-        wl_item_keys_kernel<<<ib, 256, 0, st>>>(b.items, b.n_items_dev, b.qlist, uint32_t(P_eff), b.kcount);
-        if ((rc = count_launch())) return rc;
-        if ((rc = launch_exclusive_scan(b.kcount, b.kcount, P_eff + 1, b.scan_temp, st))) return rc;
-        wl_item_sort_kernel<<<ib, 256, 0, st>>>(b.items, b.n_items_dev, b.qlist, uint32_t(P_eff), b.kcount, b.kfill,
-                                                b.items_sorted);
-        if ((rc = count_launch())) return rc;
-    }
     return 0;
 }
 

@@ -63,7 +63,11 @@ __device__ __forceinline__ uint32_t pack16(uint16_t lo, uint16_t hi) { return ui
 
 __host__ __device__ inline int tc_row_bytes(int d_pad) { return d_pad >= 64 ? 128 : d_pad * 2; }
 __host__ __device__ inline int tc_kblocks(int d_pad) { return d_pad >= 64 ? d_pad / 64 : 1; }
-__host__ inline int tc_stages(int d_pad) { return d_pad <= 32 ? 4 : (d_pad == 64 ? 3 : 2); }
+// tile stages and query buffers per CTA: two CTAs per SM (each with its own
+// MMA issuer) while the shared memory allows, else one
+__host__ inline int tc_stages(int d_pad) { return d_pad <= 16 ? 6 : (d_pad == 32 ? 4 : (d_pad == 64 ? 2 : 3)); }
+__host__ inline int tc_abufs(int d_pad) { return d_pad <= 16 ? 4 : (d_pad == 32 ? 3 : 2); }
+// (both within TC_STAGES_MAX and TC_NA_MAX, the sizes of the kernel's barrier arrays)
 
 struct TcArgs {
     const uint32_t* offsets;
@@ -71,7 +75,7 @@ struct TcArgs {
     const float4* rowstat;    // per row: ((1-B)|x|^2, |x|, |x|^2, 0); N + TC_N rows
     const uint16_t* Y16;      // Q x d_pad, 16-bit -2 s y
     const float4* qstat;      // per query, scaled: (|q|^2, |q|, -A' (16-bit value, A' >= 2c|q| + Cabs), Cabs |q|)
-    const float* tcs;         // (s, s^2, 1/s^2, 0)
+    const float* tcs;         // (s, s^2, 1/s^2, X): X bounds every row norm (unscaled)
     const int64_t* query_src;
     const uint4* items;  // (first row, end row, first slot, slot count)
     const uint32_t* n_items_dev;
@@ -88,7 +92,7 @@ struct TcArgs {
     const float* Y;
     int64_t S;
     int64_t grid_w;
-    int d, d_pad, k, radius, cap, stages, debug;
+    int d, d_pad, k, radius, cap, stages, abufs, debug;
     float cdot2;  // 2c
     float Bn;     // B
     float cabs;   // coefficient of the subnormal rounding terms
@@ -113,7 +117,9 @@ struct TcItem {
 // sets ST_TIMEOUT and makes all roles drop out.
 constexpr int TC_ROLE_THREADS = 256;
 constexpr int TC_IQ = 4;
-constexpr int TC_SBUF = 16;  // survivors buffered per thread before a flush
+constexpr int TC_SBUF = 8;  // survivors buffered per thread before a flush
+constexpr int TC_NA_MAX = 4;
+constexpr int TC_STAGES_MAX = 8;
 
 // per-query constants of a query tile, written by the loaders
 struct TcQConst {
@@ -122,6 +128,7 @@ struct TcQConst {
     float Aq1;   // A' (scaled)
     float U;     // upper bound on the k-th best exact distance (unscaled)
     float Cq;    // Cabs |q| (scaled)
+    float Uoff;  // (1+B)|q|^2 + 2B s^2 X^2 + 2A' s X + Cq, X >= every row norm (scaled)
 };
 
 template <int KMAX, bool EXCL, int PREC>
@@ -133,11 +140,11 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     unsigned char* base =
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t iq_full[TC_IQ], iq_empty[TC_IQ];
-    __shared__ __align__(8) uint64_t bfull[4], bempty[4];
-    __shared__ __align__(8) uint64_t afull[2], aempty[2], accfull[2], accempty[2];
+    __shared__ __align__(8) uint64_t bfull[TC_STAGES_MAX], bempty[TC_STAGES_MAX];
+    __shared__ __align__(8) uint64_t afull[TC_NA_MAX], aempty[TC_NA_MAX], accfull[2], accempty[2];
     __shared__ TcItem iq[TC_IQ];
-    __shared__ TcQConst qc[2][TC_M];
-    __shared__ uint32_t qidx[2][TC_M];  // query index, 0xFFFFFFFF for an unused row
+    __shared__ TcQConst qc[TC_NA_MAX][TC_M];
+    __shared__ uint32_t qidx[TC_NA_MAX][TC_M];  // query index, 0xFFFFFFFF for an unused row
     __shared__ uint32_t tmem_base_sh;
     __shared__ volatile int abort_sh;
     __shared__ uint32_t sbuf_row[TC_SBUF * 128];  // survivors buffered per screening thread
@@ -151,11 +158,15 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     const int mainA = TC_M * a.d_pad * 2, mainB = TC_N * a.d_pad * 2;
     const int extA = TC_M * 32, extB = TC_N * 32;  // extra K block: 16 bf16 per row
     const int S = a.stages;
-    unsigned char* sA = base;                             // 2 x (mainA + extA)
-    unsigned char* sB = base + 2 * size_t(mainA + extA);  // S x (mainB + extB)
+    const uint32_t NA = uint32_t(a.abufs);
+    unsigned char* sA = base;                              // NA x (mainA + extA)
+    unsigned char* sB = base + NA * size_t(mainA + extA);  // S x (mainB + extB)
     const uint32_t idesc = idesc_f16_f32(TC_M, TC_N, PREC == 0 ? 1u : 0u);
     const uint32_t tx_bytes = uint32_t(mainB + extB);
-    const float sc = a.tcs[0], sc2 = a.tcs[1], inv_sc2 = a.tcs[2];
+    const float sc = a.tcs[0], sc2 = a.tcs[1], inv_sc2 = a.tcs[2], xmax = a.tcs[3];
+    // k = 1 without exclusion: the minimum of a full chunk bounds the best
+    // candidate directly, and survivors need only their row
+    constexpr bool FAST = KMAX == 1 && !EXCL;
 
     if (warp == 1) {
         tmem_alloc(&tmem_base_sh, 2 * TC_N);
@@ -170,9 +181,11 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             mbar_init(&bfull[s], 1);
             mbar_init(&bempty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (uint32_t b = 0; b < NA; ++b) {
             mbar_init(&afull[b], 64);
             mbar_init(&aempty[b], 128);
+        }
+        for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
             mbar_init(&accempty[b], 128);
         }
@@ -185,6 +198,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     const uint32_t tmem = tmem_base_sh;
 
     auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
+        if (mbar_try_wait(bar, parity)) return true;
         if (abort_sh) return false;
         if (mbar_wait_bounded(bar, parity)) return true;
         if (!abort_sh) atomicOr(a.status, ST_TIMEOUT);
@@ -196,7 +210,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         // ------------------------------------------------ producer
         if (lane == 0) {
             const uint32_t n_items = *a.n_items_dev;
-            uint32_t it = 0, tc = 0;
+            uint32_t it = 0, tc = 0, s = 0, s_ph = 0;
             // the next item's index and descriptor are fetched one publish
             // ahead, so their latency overlaps the current item's tiles
             uint32_t pf_item = atomicAdd(a.counter, 1u);
@@ -225,14 +239,18 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 const bool have_next = publish(nxt);  // one item ahead of its tiles
                 const int ntiles = int((cur.r1 - cur.r0 + TC_N - 1) / TC_N);
                 for (int t = 0; t < ntiles; ++t, ++tc) {
-                    const int s = int(tc % uint32_t(S));
-                    if (tc >= uint32_t(S) && !wait(&bempty[s], ((tc / uint32_t(S)) - 1) & 1u)) break;
+                    // stage s = tc mod S, s_ph = (tc / S) & 1: wait for the stage's previous use
+                    if (tc >= uint32_t(S) && !wait(&bempty[s], s_ph ^ 1u)) break;
                     const int y0 = int(cur.r0) + t * TC_N;
                     unsigned char* dst = sB + size_t(s) * (mainB + extB);
                     mbar_arrive_expect_tx(&bfull[s], tx_bytes);
                     for (int kb = 0; kb < kblocks; ++kb)
                         tma_load_2d(dst + size_t(kb) * TC_N * row_bytes, &tmap, kb * epb, y0, &bfull[s]);
                     tma_load_2d(dst + mainB, &tmap_x, 0, y0, &bfull[s]);
+                    if (++s == uint32_t(S)) {
+                        s = 0;
+                        s_ph ^= 1u;
+                    }
                 }
                 if (abort_sh) break;
                 cur = nxt;
@@ -247,41 +265,55 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     } else if (warp == 1) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
-            uint32_t it = 0, tc = 0;
-            const int ksteps = kblocks * ksteps_pb;
+            const int ksteps = kblocks * ksteps_pb;  // <= 8
+            // descriptors of query buffer 0 and tile stage 0; a buffer, a stage
+            // and a K step add their byte offset / 16 to the 14-bit start-address
+            // field, which never carries (shared memory is below 2^18 bytes)
+            const uint64_t da0 = smem_desc_kmajor(smem_u32(sA), row_bytes);
+            const uint64_t db0 = smem_desc_kmajor(smem_u32(sB), row_bytes);
+            const uint64_t dax0 = smem_desc_kmajor(smem_u32(sA + mainA), 32);
+            const uint64_t dbx0 = smem_desc_kmajor(smem_u32(sB + mainB), 32);
+            const uint32_t a_step = uint32_t(mainA + extA) >> 4, b_step = uint32_t(mainB + extB) >> 4;
+            uint32_t koff[8];
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk)
+                koff[kk] = uint32_t((kk / ksteps_pb) * TC_M * row_bytes + (kk % ksteps_pb) * 32) >> 4;
+            uint32_t it = 0, tc = 0, s = 0, s_ph = 0, ab = 0, ab_ph = 0;
             for (;;) {
                 const int slot = int(it % TC_IQ);
                 if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
                 const TcItem d = iq[slot];
                 if (d.r0 == 0xFFFFFFFFu) break;
-                const int ab = int(it & 1u);
-                if (!wait(&afull[ab], (it >> 1) & 1u)) break;
+                if (!wait(&afull[ab], ab_ph)) break;
                 const int ntiles = int((d.r1 - d.r0 + TC_N - 1) / TC_N);
-                const uint32_t a_main = smem_u32(sA + size_t(ab) * (mainA + extA));
+                const uint64_t da = da0 + ab * a_step, dax = dax0 + ab * a_step;
                 bool ok = true;
                 for (int t = 0; t < ntiles; ++t, ++tc) {
-                    const int s = int(tc % uint32_t(S));
-                    const int acc = int(tc & 1u);
-                    if (!wait(&bfull[s], (tc / uint32_t(S)) & 1u)) { ok = false; break; }
+                    const uint32_t acc = tc & 1u;
+                    if (!wait(&bfull[s], s_ph)) { ok = false; break; }
                     if (tc >= 2 && !wait(&accempty[acc], ((tc >> 1) - 1) & 1u)) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t b_main = smem_u32(sB + size_t(s) * (mainB + extB));
-                    const uint32_t dt = tmem + uint32_t(acc * TC_N);
-                    for (int kk = 0; kk < ksteps; ++kk) {
-                        const int kb = kk / ksteps_pb, w = kk % ksteps_pb;
-                        mma_bf16_ss(dt, smem_desc_kmajor(a_main + uint32_t(kb * TC_M * row_bytes + w * 32), row_bytes),
-                                    smem_desc_kmajor(b_main + uint32_t(kb * TC_N * row_bytes + w * 32), row_bytes), idesc,
-                                    kk > 0 ? 1u : 0u);
-                    }
+                    const uint64_t db = db0 + s * b_step, dbx = dbx0 + s * b_step;
+                    const uint32_t dt = tmem + acc * TC_N;
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk)
+                        if (kk < ksteps) mma_bf16_ss(dt, da + koff[kk], db + koff[kk], idesc, kk > 0 ? 1u : 0u);
                     // extra K block: |x|^2 and |x| terms folded into the product
-                    mma_bf16_ss(dt, smem_desc_kmajor(a_main + uint32_t(mainA), 32),
-                                smem_desc_kmajor(b_main + uint32_t(mainB), 32), idesc, 1u);
+                    mma_bf16_ss(dt, dax, dbx, idesc, 1u);
                     mma_commit(&bempty[s]);
                     mma_commit(&accfull[acc]);
+                    if (++s == uint32_t(S)) {
+                        s = 0;
+                        s_ph ^= 1u;
+                    }
                 }
                 if (!ok) break;
                 mbar_arrive(&iq_empty[slot]);
                 ++it;
+                if (++ab == NA) {
+                    ab = 0;
+                    ab_ph ^= 1u;
+                }
             }
             if (abort_sh && tc > 0) mbar_wait_bounded(&accfull[(tc - 1) & 1u], ((tc - 1) >> 1) & 1u);
         }
@@ -294,21 +326,33 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
             const TcItem d = iq[slot];
             if (d.r0 == 0xFFFFFFFFu) break;
-            const int ab = int(it & 1u);
-            if (it >= 2 && !wait(&aempty[ab], ((it >> 1) - 1) & 1u)) break;
+            const uint32_t ab = it % NA;
+            if (it >= NA && !wait(&aempty[ab], ((it / NA) - 1) & 1u)) break;
             unsigned char* dstA = sA + size_t(ab) * (mainA + extA);
+            // both rows' query indices, then both rows' constants, so that the
+            // dependent loads of the two rows overlap
+            uint32_t qr[2];
+            float4 qs[2];
+            float Ur[2];
+#pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const int r = lt + 64 * h;
-                const bool active = uint32_t(r) < d.qn;
-                uint32_t q = 0;
-                float4 qs = make_float4(0.f, 0.f, 0.f, 0.f);
-                float U = INFINITY;
-                if (active) {
-                    q = uint32_t(int64_t(a.qlist[d.qbeg + r]) / a.S);
-                    qs = a.qstat[q];
-                    U = __uint_as_float(a.Ubits[q]);
+                qr[h] = uint32_t(r) < d.qn ? uint32_t(int64_t(a.qlist[d.qbeg + r]) / a.S) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                qs[h] = make_float4(0.f, 0.f, 0.f, 0.f);
+                Ur[h] = INFINITY;
+                if (qr[h] != 0xFFFFFFFFu) {
+                    qs[h] = a.qstat[qr[h]];
+                    Ur[h] = __uint_as_float(a.Ubits[qr[h]]);
                 }
-                const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(q) * a.d_pad);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = lt + 64 * h;
+                const bool active = qr[h] != 0xFFFFFFFFu;
+                const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(active ? qr[h] : 0u) * a.d_pad);
                 for (int kb = 0; kb < kblocks; ++kb)
                     for (int c = 0; c < chunks; ++c) {
                         const uint4 v = active ? src[kb * chunks + c] : make_uint4(0, 0, 0, 0);
@@ -317,20 +361,21 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 // extra block: (1, 1, -A', -A', 0, ...) against (|x|^2 hi, lo, |x| hi, lo, 0, ...)
                 uint4 e0 = make_uint4(0, 0, 0, 0);
                 if (active) {
-                    const uint16_t one = to16_rn<PREC>(1.0f), na = to16_rn<PREC>(qs.z);  // exact
+                    const uint16_t one = to16_rn<PREC>(1.0f), na = to16_rn<PREC>(qs[h].z);  // exact
                     e0.x = pack16(one, one);
                     e0.y = pack16(na, na);
                 }
                 *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 0, 32)) = e0;
                 *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 1, 32)) = make_uint4(0, 0, 0, 0);
                 TcQConst c;
-                c.qn2 = qs.x;
-                c.U = U;
-                c.Cq = qs.w;
-                c.Uthr = sc2 * U - (1.0f - a.Bn) * qs.x + qs.w;
-                c.Aq1 = -qs.z;
+                c.qn2 = qs[h].x;
+                c.U = Ur[h];
+                c.Cq = qs[h].w;
+                c.Uthr = sc2 * Ur[h] - (1.0f - a.Bn) * qs[h].x + qs[h].w;
+                c.Aq1 = -qs[h].z;
+                c.Uoff = (1.0f + a.Bn) * qs[h].x + 2.0f * a.Bn * sc2 * xmax * xmax + 2.0f * c.Aq1 * sc * xmax + qs[h].w;
                 qc[ab][r] = c;
-                qidx[ab][r] = active ? q : 0xFFFFFFFFu;
+                qidx[ab][r] = qr[h];
             }
             fence_proxy_async_smem();
             mbar_arrive(&afull[ab]);
@@ -345,8 +390,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
             const TcItem dc = iq[slot];
             if (dc.r0 == 0xFFFFFFFFu) break;
-            const int ab = int(it & 1u);
-            if (!wait(&afull[ab], (it >> 1) & 1u)) break;
+            const uint32_t ab = it % NA;
+            if (!wait(&afull[ab], (it / NA) & 1u)) break;
             TcQConst cur = qc[ab][er];
             const uint32_t qi = qidx[ab][er];
             const bool active = qi != 0xFFFFFFFFu;
@@ -361,6 +406,15 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             // list, then tighten U with their upper bounds (deferred: a stale U
             // only admits more rows)
             auto flush = [&]() {
+                if (FAST) {
+                    if (nb > 0) {
+                        const uint32_t pos = atomicAdd(a.surv_cnt + q, uint32_t(nb));
+                        for (int i = 0; i < nb; ++i)
+                            if (pos + uint32_t(i) < uint32_t(a.cap)) a.surv[q * a.cap + pos + i] = sbuf_row[i * 128 + er];
+                    }
+                    nb = 0;
+                    return;
+                }
                 int keep = 0;
                 for (int i = 0; i < nb; ++i) {
                     const uint32_t row = sbuf_row[i * 128 + er];
@@ -422,6 +476,15 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                     // columns past the item's rows (the next cone's, in the last
                     // tile) can only lower the minimum: the exact mask below drops them
                     if (active && vmin <= cur.Uthr) {
+                        if (FAST && lim >= 64) {
+                            // every column is a row of the item's cone, so the row at
+                            // the minimum is a candidate within this bound
+                            const float ub = fmaxf((vmin + cur.Uoff) * (1.0f + 1e-6f) * inv_sc2, 0.0f);
+                            if (ub < cur.U) {
+                                cur.U = ub;
+                                cur.Uthr = sc2 * cur.U - (1.0f - a.Bn) * cur.qn2 + cur.Cq;
+                            }
+                        }
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             uint32_t mask = 0;
@@ -433,12 +496,14 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                             while (mask) {
                                 const int j = __ffs(int(mask)) - 1;
                                 mask &= mask - 1u;
-                                float val = v[32 * h];
-#pragma unroll
-                                for (int u = 1; u < 32; ++u) val = u == j ? v[32 * h + u] : val;
                                 if (nb == TC_SBUF) flush();
                                 sbuf_row[nb * 128 + er] = uint32_t(y0 + c0 + 32 * h + j);
-                                sbuf_val[nb * 128 + er] = val;
+                                if (!FAST) {
+                                    float val = v[32 * h];
+#pragma unroll
+                                    for (int u = 1; u < 32; ++u) val = u == j ? v[32 * h + u] : val;
+                                    sbuf_val[nb * 128 + er] = val;
+                                }
                                 ++nb;
                             }
                         }
@@ -494,7 +559,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
 // excluded rows skipped, at least TC_SEED rows when the cones hold them),
 // inflated by the fp32 error bound; +inf if fewer than k rows.  A query too large for the 16-bit range is left to the
 // rerank's full scan (its survivor count is set above the capacity).
-constexpr int TC_SEED = 512;  // rows scanned exactly for the initial bound
+constexpr int TC_SEED = 256;    // rows scanned exactly for the initial bound
+constexpr int TC_SEED_ILP = 8;  // row groups loaded per iteration
 
 template <int F, int PREC, int KMAX>
 __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restrict__ Y, int64_t Q, int d, int d_pad,
@@ -561,12 +627,12 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
         const uint32_t b = probes[q * P_eff + p];
         if (b >= NC) continue;
         const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
-        for (uint32_t r0 = o0; r0 < o1 && scanned < TC_SEED; r0 += 4 * CPP) {
-            // four row groups per iteration: all loads in flight before the arithmetic
-            float4 xv[4][F];
-            uint32_t rr[4];
+        for (uint32_t r0 = o0; r0 < o1 && scanned < TC_SEED; r0 += TC_SEED_ILP * CPP) {
+            // TC_SEED_ILP row groups per iteration: all loads in flight before the arithmetic
+            float4 xv[TC_SEED_ILP][F];
+            uint32_t rr[TC_SEED_ILP];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < TC_SEED_ILP; ++u) {
                 rr[u] = r0 + uint32_t(u * CPP + g);
                 const float4* xr =
                     reinterpret_cast<const float4*>(xs + size_t(rr[u] < o1 ? rr[u] : o0) * d_pad) + sub * F;
@@ -574,7 +640,7 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
                 for (int f = 0; f < F; ++f) xv[u][f] = xr[f];
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < TC_SEED_ILP; ++u) {
                 float cpart[F];
 #pragma unroll
                 for (int f = 0; f < F; ++f) cpart[f] = sq4(xv[u][f], qv[f]);
@@ -593,7 +659,7 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
                     if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
                 }
             }
-            scanned += 4 * CPP;
+            scanned += TC_SEED_ILP * CPP;
         }
     }
     // k-th smallest over the warp: k rounds of warp minimum over the lists
@@ -627,7 +693,7 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
 // ---------------------------------------------------------------- rows
 
 // The data scale of the screen: s = 1 for bf16; for fp16 the power of two
-// with s^2 max|x|^2 <= 2^14 (all-zero data: 1).  tcs = (s, s^2, 1/s^2, 0).
+// with s^2 max|x|^2 <= 2^14 (all-zero data: 1).  tcs = (s, s^2, 1/s^2, X), X >= every row norm.
 template <int PREC>
 __global__ void tc_scale_kernel(const uint32_t* __restrict__ maxn2_bits, float* __restrict__ tcs)
 {
@@ -645,7 +711,9 @@ __global__ void tc_scale_kernel(const uint32_t* __restrict__ maxn2_bits, float* 
     tcs[0] = sc;
     tcs[1] = sc * sc;
     tcs[2] = 1.0f / (sc * sc);
-    tcs[3] = 0.0f;
+    // a bound on every row norm, with room for the differently ordered fp32
+    // sums of the per-row norms
+    tcs[3] = sqrtf(m * (1.0f + 1e-4f)) * (1.0f + 1e-6f);
 }
 
 // 16-bit copy of s x (row-major, d_pad per row) and the extra K block of each
@@ -862,7 +930,7 @@ int launch_tc_query_prep(int prec, const float* Y, int64_t Q, int d, int d_pad, 
 size_t tc_smem_bytes(int d_pad)
 {
     const size_t tileA = size_t(TC_M) * d_pad * 2 + TC_M * 32, tileB = size_t(TC_N) * d_pad * 2 + TC_N * 32;
-    const size_t need = 1024 + 2 * tileA + size_t(tc_stages(d_pad)) * tileB;
+    const size_t need = 1024 + size_t(tc_abufs(d_pad)) * tileA + size_t(tc_stages(d_pad)) * tileB;
     // at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
     return need < 80u * 1024u ? 80u * 1024u : need;
 }
@@ -902,7 +970,7 @@ int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float
     a.qstat = qstat;
     a.tcs = tcs;
     a.query_src = query_src;
-    a.items = b.items_sorted;
+    a.items = b.items;
     a.n_items_dev = b.n_items_dev;
     a.qcount = b.qcount;
     a.qoff = b.qoff;
@@ -923,6 +991,8 @@ int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float
     a.radius = radius;
     a.cap = cap;
     a.stages = tc_stages(d_pad);
+    a.abufs = tc_abufs(d_pad);
+    if (a.stages > TC_STAGES_MAX || a.abufs > TC_NA_MAX) return -2;  // unsupported shape
     a.debug = debug;
     a.cdot2 = cdot2;
     a.Bn = Bn;
