@@ -182,8 +182,9 @@ int launch_key_histogram(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* 
 
 // ---------------------------------------------------------------- radix sort
 
-constexpr int RADIX_CHUNK = 2048;  // elements per warp chunk
-constexpr int RADIX_WARPS = 4;     // warps per block
+constexpr int RADIX_CHUNK = 2048;  // elements per chunk (one CTA)
+constexpr int RADIX_WARPS = 8;     // warps per CTA, RADIX_CHUNK / RADIX_WARPS elements each
+constexpr int RADIX_WE = RADIX_CHUNK / RADIX_WARPS;
 
 struct RadixPlan {
     int passes, bits_per_pass, B;
@@ -202,54 +203,85 @@ static RadixPlan radix_plan(int64_t N, int64_t NC)
     return p;
 }
 
+// Digit counts of one chunk: H[digit * nchunks + chunk].
 __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t N,
                                                                       int shift, int B, int64_t nchunks,
                                                                       uint32_t* __restrict__ H)
 {
     extern __shared__ uint32_t sh[];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t chunk = int64_t(blockIdx.x) * RADIX_WARPS + warp;
-    if (chunk >= nchunks) return;
-    uint32_t* h = sh + warp * B;
-    for (int i = lane; i < B; i += 32) h[i] = 0;
-    __syncwarp();
+    const int64_t chunk = blockIdx.x;
+    for (int i = threadIdx.x; i < B; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
     const int64_t begin = chunk * RADIX_CHUNK;
     const int64_t end = begin + RADIX_CHUNK < N ? begin + RADIX_CHUNK : N;
     const uint32_t mask = uint32_t(B - 1);
-    for (int64_t i = begin + lane; i < end; i += 32) atomicAdd(&h[(keys[i] >> shift) & mask], 1u);
-    __syncwarp();
-    for (int dg = lane; dg < B; dg += 32) H[int64_t(dg) * nchunks + chunk] = h[dg];
+    for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
+    __syncthreads();
+    for (int dg = threadIdx.x; dg < B; dg += blockDim.x) H[int64_t(dg) * nchunks + chunk] = sh[dg];
 }
 
+// Stable scatter of one chunk.  Warp w owns elements [w * RADIX_WE, (w + 1) *
+// RADIX_WE) of the chunk: (1) per-warp digit counts in shared memory, (2) for
+// each digit a running sum over the warps from the chunk's scanned base, (3)
+// each warp places its elements in order (match_any ranks within a round).
 __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_scatter_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ ids_in, int64_t N, int shift, int B,
-    int64_t nchunks, const uint32_t* __restrict__ Hs, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ ids_out)
+    int64_t nchunks, const uint32_t* __restrict__ Hs, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ ids_out,
+    uint32_t* __restrict__ offsets_out, int64_t NC)
 {
-    extern __shared__ uint32_t sh[];
+    extern __shared__ uint32_t sh[];  // [RADIX_WARPS][B]
+    // single pass over all key bits: the scanned counts at chunk 0 are the
+    // bucket starts (CSR offsets)
+    if (offsets_out && blockIdx.x == 0)
+        for (int64_t dg = threadIdx.x; dg <= NC; dg += blockDim.x)
+            offsets_out[dg] = dg < NC ? Hs[dg * nchunks] : uint32_t(N);
+    constexpr int R = RADIX_WE / 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t chunk = int64_t(blockIdx.x) * RADIX_WARPS + warp;
-    if (chunk >= nchunks) return;
-    uint32_t* run = sh + warp * B;
-    for (int dg = lane; dg < B; dg += 32) run[dg] = Hs[int64_t(dg) * nchunks + chunk];
-    __syncwarp();
-    const int64_t begin = chunk * RADIX_CHUNK;
-    const int64_t end = begin + RADIX_CHUNK < N ? begin + RADIX_CHUNK : N;
+    const int64_t chunk = blockIdx.x;
+    const int64_t wbeg = chunk * RADIX_CHUNK + int64_t(warp) * RADIX_WE;
+    const int64_t wend = wbeg + RADIX_WE < N ? wbeg + RADIX_WE : N;
     const uint32_t mask = uint32_t(B - 1);
     const unsigned lt = (1u << lane) - 1u;
-    for (int64_t base = begin; base < end; base += 32) {
-        const int64_t i = base + lane;
-        const bool live = i < end;
-        uint32_t key = live ? keys_in[i] : 0u;
-        uint32_t id = live ? (ids_in ? ids_in[i] : uint32_t(i)) : 0u;
-        uint32_t digit = live ? ((key >> shift) & mask) : 0xFFFFFFFFu;
-        unsigned peers = __match_any_sync(0xffffffffu, digit);
+    for (int i = threadIdx.x; i < RADIX_WARPS * B; i += blockDim.x) sh[i] = 0;
+    uint32_t key[R], id[R], digit[R];
+    unsigned peers[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = wbeg + 32 * r + lane;
+        const bool live = i < wend;
+        key[r] = live ? keys_in[i] : 0u;
+        id[r] = live ? (ids_in ? ids_in[i] : uint32_t(i)) : 0u;
+        digit[r] = live ? ((key[r] >> shift) & mask) : 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    uint32_t* cnt = sh + warp * B;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        peers[r] = __match_any_sync(0xffffffffu, digit[r]);
+        if (digit[r] != 0xFFFFFFFFu && lane == __ffs(peers[r]) - 1) cnt[digit[r]] += __popc(peers[r]);
+        __syncwarp();
+    }
+    __syncthreads();
+    for (int dg = threadIdx.x; dg < B; dg += blockDim.x) {
+        uint32_t run = Hs[int64_t(dg) * nchunks + chunk];
+#pragma unroll
+        for (int w = 0; w < RADIX_WARPS; ++w) {
+            const uint32_t c = sh[w * B + dg];
+            sh[w * B + dg] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool live = digit[r] != 0xFFFFFFFFu;
         if (live) {
-            uint32_t pos = run[digit] + __popc(peers & lt);
-            ids_out[pos] = id;
-            if (keys_out) keys_out[pos] = key;
+            const uint32_t pos = cnt[digit[r]] + __popc(peers[r] & lt);
+            ids_out[pos] = id[r];
+            if (keys_out) keys_out[pos] = key[r];
         }
         __syncwarp();
-        if (live && lane == __ffs(peers) - 1) run[digit] += __popc(peers);
+        if (live && lane == __ffs(peers[r]) - 1) cnt[digit[r]] += __popc(peers[r]);
         __syncwarp();
     }
 }
@@ -264,10 +296,15 @@ size_t radix_temp_bytes(int64_t N, int64_t NC)
     return b + 1024;
 }
 
-int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
+bool radix_single_pass(int64_t NC) { return radix_plan(1, NC).passes == 1; }
+
+int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, uint32_t* offsets, void* temp,
                            cudaStream_t st)
 {
-    if (N == 0) return 0;
+    if (N == 0) {
+        if (offsets && cudaMemsetAsync(offsets, 0, size_t(NC + 1) * 4, st) != cudaSuccess) return -5;
+        return 0;
+    }
     RadixPlan p = radix_plan(N, NC);
     const int64_t hn = int64_t(p.B) * p.nchunks;
     char* t = static_cast<char*>(temp);
@@ -280,8 +317,13 @@ int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t
     uint32_t* ia = reinterpret_cast<uint32_t*>(t + nb);
     uint32_t* kb = reinterpret_cast<uint32_t*>(t + 2 * nb);
     uint32_t* ib = reinterpret_cast<uint32_t*>(t + 3 * nb);
-    const unsigned blocks = unsigned((p.nchunks + RADIX_WARPS - 1) / RADIX_WARPS);
-    const size_t smem = size_t(RADIX_WARPS) * p.B * 4;
+    const unsigned blocks = unsigned(p.nchunks);
+    const size_t hsmem = size_t(p.B) * 4, smem = size_t(RADIX_WARPS) * p.B * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RADIX_WARPS * 2048 * 4));
+        attr_set = true;
+    }
     const uint32_t* kin = keys;
     const uint32_t* iin = nullptr;
     for (int pass = 0; pass < p.passes; ++pass) {
@@ -289,13 +331,13 @@ int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t
         const bool last = pass == p.passes - 1;
         uint32_t* kout = last ? nullptr : (pass % 2 == 0 ? ka : kb);
         uint32_t* iout = last ? perm : (pass % 2 == 0 ? ia : ib);
-        radix_hist_kernel<<<blocks, RADIX_WARPS * 32, smem, st>>>(kin, N, shift, p.B, p.nchunks, H);
+        radix_hist_kernel<<<blocks, RADIX_WARPS * 32, hsmem, st>>>(kin, N, shift, p.B, p.nchunks, H);
         int rc = count_launch();
         if (rc) return rc;
         rc = launch_exclusive_scan(H, H, hn, stemp, st);
         if (rc) return rc;
         radix_scatter_kernel<<<blocks, RADIX_WARPS * 32, smem, st>>>(kin, iin, N, shift, p.B, p.nchunks, H, kout,
-                                                                     iout);
+                                                                     iout, p.passes == 1 ? offsets : nullptr, NC);
         rc = count_launch();
         if (rc) return rc;
         kin = kout;

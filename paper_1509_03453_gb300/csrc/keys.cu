@@ -53,6 +53,91 @@ __device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], 
     return uint32_t((rank << L) | code);
 }
 
+// Vector path (d % 4 == 0, 16-byte aligned rows): one lane per row.  The
+// lane streams its row in pieces of up to KC float4 (the first line fetch
+// brings the piece's cache lines into L1 for the rest of the warp's loads)
+// and keeps the L largest selection keys in a sorted register list, so the
+// selection needs no shuffles: one 64-bit compare per component, and an
+// insertion only when a component beats the current L-th.
+template <int LC>
+__global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restrict__ X, int64_t N, int d, int L,
+                                                           const uint64_t* __restrict__ binom,
+                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ status,
+                                                           uint32_t* __restrict__ maxn2_bits)
+{
+    constexpr int LM = LC > 0 ? LC : MAX_L;
+    constexpr int KC = 8;  // float4 per piece
+    const int lane = threadIdx.x & 31;
+    const int n4 = d >> 2;
+    bool bad = false;
+    float nmax = 0.0f;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < N; row += stride) {
+        const float4* xr = reinterpret_cast<const float4*>(X + row * int64_t(d));
+        uint64_t top[LM];  // descending; 0 = empty (a real selection key is > 0)
+#pragma unroll
+        for (int r = 0; r < LM; ++r) top[r] = 0;
+        float nsq = 0.0f;
+        for (int c0 = 0; c0 < n4; c0 += KC) {
+            float4 t[KC];
+#pragma unroll
+            for (int f = 0; f < KC; ++f) t[f] = c0 + f < n4 ? __ldg(xr + c0 + f) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int f = 0; f < KC; ++f) {
+                if (c0 + f < n4) {
+                    const float x4[4] = {t[f].x, t[f].y, t[f].z, t[f].w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float x = x4[e];
+                        bad |= !finite_f(x);
+                        nsq = fmaf(x, x, nsq);
+                        uint64_t k = sel_key(x, 4 * (c0 + f) + e);
+                        uint64_t last = top[LM - 1];  // the L-th (compile-time index)
+                        if (LC == 0) {
+#pragma unroll
+                            for (int r = 0; r < LM; ++r)
+                                if (r == L - 1) last = top[r];
+                        }
+                        if (k > last) {
+                            // insertion into the sorted list (rare after the first few)
+#pragma unroll
+                            for (int r = 0; r < LM; ++r) {
+                                if (LC > 0 || r < L) {
+                                    const uint64_t hi = k > top[r] ? k : top[r];
+                                    k = k > top[r] ? top[r] : k;
+                                    top[r] = hi;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        int comp[MAX_L];
+        uint32_t sgn[MAX_L];
+#pragma unroll
+        for (int r = 0; r < MAX_L; ++r) {
+            comp[r] = 0;
+            sgn[r] = 0;
+        }
+#pragma unroll
+        for (int r = 0; r < LM; ++r)
+            if (LC > 0 || r < L) {
+                comp[r] = sel_comp(top[r]);
+                sgn[r] = sel_sign(top[r]);
+            }
+        keys[row] = cone_from_members<LC>(comp, sgn, L, binom);
+        nmax = fmaxf(nmax, nsq);  // non-finite rows are reported separately
+    }
+    if (maxn2_bits) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) nmax = fmaxf(nmax, __shfl_xor_sync(0xffffffffu, nmax, o));
+        // nonnegative floats order like their bits
+        if (lane == 0 && nmax > 0.0f && finite_f(nmax)) atomicMax(maxn2_bits, __float_as_uint(nmax));
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_DATA);
+}
+
 // One group of LPV lanes per row.  VEC: d % 4 == 0 and 16-byte aligned rows,
 // lane l holds float4 number l, l+LPV (128-bit loads); else lane l holds the
 // scalars l, l+32, ... (LPV = 32).  At most 8 values per lane (d <= 256).
@@ -191,19 +276,11 @@ __global__ void __launch_bounds__(128) query_order_kernel(const float* __restric
 }
 
 template <int LC>
-static void launch_keys_lc(bool vec, int lpv, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d,
-                           int L, const uint64_t* binom, uint32_t* keys, uint32_t* status, uint32_t* maxn2)
+static void launch_keys_lc(bool vec, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d, int L,
+                           const uint64_t* binom, uint32_t* keys, uint32_t* status, uint32_t* maxn2)
 {
-    if (vec) {
-        switch (lpv) {
-        case 4: data_keys_kernel<4, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
-        case 8: data_keys_kernel<8, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
-        case 16: data_keys_kernel<16, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
-        default: data_keys_kernel<32, true, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2); break;
-        }
-    } else {
-        data_keys_kernel<32, false, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2);
-    }
+    if (vec) data_keys_row_kernel<LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2);
+    else data_keys_kernel<32, false, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2);
 }
 
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
@@ -211,20 +288,18 @@ int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* bi
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
-    int n4 = d / 4, lpv = 4;
-    while (lpv < n4 && lpv < 32) lpv <<= 1;
-    if (!vec) lpv = 32;
     const int threads = 256;
-    int64_t blocks = (N * lpv + threads - 1) / threads;
-    const int64_t cap = int64_t(num_sms) * 16;
+    // vector path: one lane per row; scalar path: a warp per row
+    int64_t blocks = vec ? (N + threads - 1) / threads : (N * 32 + threads - 1) / threads;
+    const int64_t cap = int64_t(num_sms) * (vec ? 8 : 16);
     if (blocks > cap) blocks = cap;
     const dim3 g(static_cast<unsigned>(blocks)), b(static_cast<unsigned>(threads));
     switch (L) {
-    case 1: launch_keys_lc<1>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    case 2: launch_keys_lc<2>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    case 3: launch_keys_lc<3>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    case 4: launch_keys_lc<4>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    default: launch_keys_lc<0>(vec, lpv, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 1: launch_keys_lc<1>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 2: launch_keys_lc<2>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 3: launch_keys_lc<3>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 4: launch_keys_lc<4>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    default: launch_keys_lc<0>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
     }
     return count_launch();
 }

@@ -556,9 +556,13 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_BUCKETS, st);
-        rc = launch_key_histogram(ix->keys, N, NC, counts, st, ix->num_sms);
-        if (!rc) rc = launch_exclusive_scan(counts, ix->offsets, NC + 1, scan_temp, st);
-        if (!rc) rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, radix_temp, st);
+        if (radix_single_pass(NC)) {
+            rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, ix->offsets, radix_temp, st);
+        } else {
+            rc = launch_key_histogram(ix->keys, N, NC, counts, st, ix->num_sms);
+            if (!rc) rc = launch_exclusive_scan(counts, ix->offsets, NC + 1, scan_temp, st);
+            if (!rc) rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, nullptr, radix_temp, st);
+        }
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_GATHER, st);

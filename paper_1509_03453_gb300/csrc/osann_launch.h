@@ -26,7 +26,10 @@ int launch_exclusive_scan(const uint32_t* in, uint32_t* out, int64_t n, void* te
 int launch_key_histogram(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* counts, cudaStream_t st,
                          int num_sms);
 size_t radix_temp_bytes(int64_t N, int64_t NC);
-int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, void* temp,
+// offsets (nullable): with radix_single_pass(NC), also written: the CSR
+// bucket starts (NC + 1 values), so no separate histogram is needed
+bool radix_single_pass(int64_t NC);
+int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, uint32_t* offsets, void* temp,
                            cudaStream_t st);
 int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs, float4* rowstat,
                        float Bn, const float* tcs, uint16_t* x16, uint16_t* xe16, cudaStream_t st,
