@@ -145,6 +145,20 @@ size_t osann_search_workspace_size(const osann_index *index, int64_t Q, int32_t 
 int osann_search(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k, int32_t path,
                  void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists, void *stream);
 
+/* As osann_search, with the work list's query group size chosen by the
+ * caller (the paper has no counterpart: a tuning knob of the batched
+ * paths).  group = 0 takes the default; otherwise it is used when it lies in
+ * 1..128 on the tensor-core paths (the MMA tile's query rows) or in
+ * 1..128 / max(1, d_pad / 32) on OSANN_PATH_BATCHED, and the default is
+ * taken when it does not; the plain path ignores it.  Results are those of
+ * osann_search, bit for bit, whatever the group.  The workspace is
+ * osann_search_workspace_size_group(...) bytes. */
+int osann_search_group(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k,
+                       int32_t path, int32_t group, void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists,
+                       void *stream);
+size_t osann_search_workspace_size_group(const osann_index *index, int64_t Q, int32_t P, int32_t k, int32_t path,
+                                         int32_t group);
+
 /* As osann_search, skipping for query q every point n whose grid position
  * (n / grid_w, n % grid_w) is within Chebyshev distance `radius` of
  * d_query_src[q]'s position (self and near-duplicates of an image patch).
@@ -218,6 +232,60 @@ int osann_stats_enable(int on);
 int osann_stats_reset(void);
 int osann_stats_get(int32_t stage, double *total_ms, int64_t *count);
 int64_t osann_launch_count(void);
+
+/* ---------------------------------------------------------------- serving
+ *
+ * A request server over indexes resident on the device (the paper has no
+ * counterpart: this is the serving layer around Algorithm 1).  Requests wait
+ * in arrival order; whenever one of the server's slots is free, waiting
+ * queries of the oldest request's index are gathered into one batch of at
+ * most max_batch queries (across requests; a larger request is split over
+ * several batches) and searched on that slot's stream, so batches of
+ * different slots overlap on the device.  Each slot holds its own workspace
+ * and buffers; the number of slots is `slots`, reduced to what mem_budget
+ * bytes hold when mem_budget > 0 (OSANN_ERR_OOM when it holds none).  With
+ * use_graphs, a batch is a CUDA graph replay (one graph per slot, index and
+ * batch-size bucket 64, 128, ... max_batch, captured on first use, the batch
+ * padded to its bucket).  Every query's result equals that of osann_search
+ * with the index's P and k, bit for bit, whatever batch it ran in. */
+typedef struct osann_server osann_server;
+
+/* indexes[n_indexes] must outlive the server; P[i], k[i] (1..32) are index
+ * i's probe budget and neighbour count. */
+int osann_server_create(const osann_index *const *indexes, int32_t n_indexes, const int32_t *P, const int32_t *k,
+                        int32_t slots, int64_t max_batch, size_t mem_budget, int32_t use_graphs,
+                        osann_server **out);
+/* Number of slots the memory budget allowed. */
+int osann_server_slots(const osann_server *server);
+/* Queue Q queries (device, Q x d of index `index`, ready on the device when
+ * submitted, left untouched until the request finishes) whose results go to
+ * the caller's device buffers d_ids (Q x k int64) and d_sqdists (Q x k fp32),
+ * complete when the ticket is reported by osann_server_progress.
+ * Non-blocking. */
+int osann_server_submit(osann_server *server, int32_t index, const float *d_queries, int64_t Q, int64_t *d_ids,
+                        float *d_sqdists, uint64_t *ticket);
+/* Retire completed batches, admit waiting queries into free slots and
+ * launch them; write up to max_done finished tickets to done and their
+ * count to *n_done.  wait != 0 blocks on the oldest batch in flight when
+ * nothing has finished yet. */
+int osann_server_progress(osann_server *server, int32_t wait, uint64_t *done, int32_t max_done, int32_t *n_done);
+/* Queries still waiting for a slot, and slots busy. */
+int osann_server_pending(const osann_server *server, int64_t *waiting_queries, int32_t *busy_slots);
+/* Autotuner: for every index and batch bucket, time each candidate (path,
+ * work-list group size) -- plain; batched with the default and 32-query
+ * groups; fp16 screening with 128- and 64-query groups -- on max_batch rows
+ * sampled from the index itself, reps timed runs each, and keep the
+ * fastest.  out_choices (nullable) receives (path, group) per (index,
+ * bucket).  Call with no request in the server. */
+int osann_server_tune(osann_server *server, int32_t reps, int32_t *out_choices);
+/* Batch buckets in use (returns their count; writes up to max_out). */
+int osann_server_buckets(const osann_server *server, int64_t *out, int32_t max_out);
+/* Counters since creation: batches run, queries run (padding excluded),
+ * graph replays, graphs captured, captures that failed (those batches run
+ * directly). */
+int osann_server_stats(const osann_server *server, int64_t out5[5]);
+/* Synchronise the slots and release everything (NULL ok). */
+int osann_server_free(osann_server *server);
 
 #ifdef __cplusplus
 }

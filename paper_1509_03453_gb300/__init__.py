@@ -15,7 +15,7 @@ import ctypes
 from . import _lib
 from ._lib import OsannError, PATHS, STAGES, load
 
-__all__ = ["Index", "OsannError", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
+__all__ = ["Index", "Server", "OsannError", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
 
 
 def _torch():
@@ -122,13 +122,15 @@ class Index:
         self.close()
 
     # -- queries
-    def workspace_size(self, Q: int, P: int, k: int, path: str = "auto") -> int:
-        return int(load().osann_search_workspace_size(self._h, Q, P, k, PATHS[path]))
+    def workspace_size(self, Q: int, P: int, k: int, path: str = "auto", group: int = 0) -> int:
+        return int(load().osann_search_workspace_size_group(self._h, Q, P, k, PATHS[path], group))
 
     def search(self, queries, P: int, k: int, path: str = "auto", query_src=None, grid_w: int = 0,
-               radius: int = 0, stream=None, out=None, workspace=None):
+               radius: int = 0, stream=None, out=None, workspace=None, group: int = 0):
         """Top-k by exact squared distance over the first min(P, N_C)
-        probed cones.  Returns (ids int64 [Q,k], sqdists float32 [Q,k])."""
+        probed cones.  Returns (ids int64 [Q,k], sqdists float32 [Q,k]).
+        ``group``: queries per work-list item on the batched paths (0 =
+        default); it changes the speed, not the result."""
         torch = _torch()
         q = _dev_f32(queries, "queries")
         Q = q.shape[0]
@@ -139,12 +141,12 @@ class Index:
             d2 = torch.empty((Q, k), dtype=torch.float32, device=q.device)
         else:
             ids, d2 = out
-        ws_bytes = self.workspace_size(Q, P, k, path)
+        ws_bytes = self.workspace_size(Q, P, k, path, 0 if query_src is not None else group)
         ws = workspace if workspace is not None else torch.empty(ws_bytes, dtype=torch.uint8, device=q.device)
         L = load()
         if query_src is None:
-            rc = L.osann_search(self._h, _ptr(q), Q, P, k, PATHS[path], _ptr(ws), ws.numel(), _ptr(ids),
-                                _ptr(d2), _stream_ptr(stream))
+            rc = L.osann_search_group(self._h, _ptr(q), Q, P, k, PATHS[path], group, _ptr(ws), ws.numel(),
+                                      _ptr(ids), _ptr(d2), _stream_ptr(stream))
         else:
             src = query_src.contiguous()
             rc = L.osann_search_excl(self._h, _ptr(q), _ptr(src), Q, P, k, grid_w, radius, PATHS[path],
@@ -200,3 +202,107 @@ class Index:
         f = ctypes.c_uint32()
         _lib.check(load().osann_status(self._h, _stream_ptr(stream), ctypes.byref(f)))
         return f.value
+
+
+class Server:
+    """Continuous-batching request loop over resident indexes (osann_server_*
+    in include/osann.h).  ``indexes``: list of Index; ``P``, ``k``: per index.
+
+        srv = Server([ia, ib], P=[64, 32], k=[1, 1], slots=4, max_batch=4096)
+        t = srv.submit(0, queries_cuda)          # -> ticket; results in srv.result(t)
+        done = srv.progress(wait=True)           # finished tickets
+    """
+
+    def __init__(self, indexes, P, k, slots: int = 4, max_batch: int = 4096, mem_budget: int = 0,
+                 graphs: bool = True):
+        n = len(indexes)
+        self.indexes = list(indexes)
+        self.P, self.k = list(P), list(k)
+        arr = (ctypes.c_void_p * n)(*[ix._h.value for ix in indexes])
+        Pa = (ctypes.c_int32 * n)(*self.P)
+        ka = (ctypes.c_int32 * n)(*self.k)
+        h = ctypes.c_void_p()
+        _lib.check(load().osann_server_create(arr, n, Pa, ka, slots, max_batch, mem_budget, 1 if graphs else 0,
+                                              ctypes.byref(h)))
+        self._h = h
+        self._req = {}  # ticket -> (queries, ids, dists): kept alive until finished
+        self._out = {}
+
+    @property
+    def slots(self) -> int:
+        return int(load().osann_server_slots(self._h))
+
+    def buckets(self):
+        out = (ctypes.c_int64 * 64)()
+        n = load().osann_server_buckets(self._h, out, 64)
+        return [int(out[i]) for i in range(n)]
+
+    def tune(self, reps: int = 3):
+        """Autotune (path, group) per (index, bucket); returns the choices."""
+        nb = len(self.buckets())
+        n = len(self.indexes)
+        out = (ctypes.c_int32 * (2 * n * nb))()
+        _lib.check(load().osann_server_tune(self._h, reps, out))
+        names = {v: k for k, v in PATHS.items()}
+        return [[(names[out[2 * (i * nb + b)]], int(out[2 * (i * nb + b) + 1])) for b in range(nb)]
+                for i in range(n)]
+
+    def submit(self, index: int, queries, out=None) -> int:
+        torch = _torch()
+        q = _dev_f32(queries, "queries")
+        Q = q.shape[0]
+        kk = self.k[index]
+        if out is None:
+            ids = torch.empty((Q, kk), dtype=torch.int64, device=q.device)
+            d2 = torch.empty((Q, kk), dtype=torch.float32, device=q.device)
+        else:
+            ids, d2 = out
+        t = ctypes.c_uint64()
+        _lib.check(load().osann_server_submit(self._h, index, _ptr(q), Q, _ptr(ids), _ptr(d2), ctypes.byref(t)))
+        self._req[t.value] = (q, ids, d2)
+        return t.value
+
+    def progress(self, wait: bool = False, max_done: int = 1024):
+        done = (ctypes.c_uint64 * max_done)()
+        n = ctypes.c_int32()
+        _lib.check(load().osann_server_progress(self._h, 1 if wait else 0, done, max_done, ctypes.byref(n)))
+        out = []
+        for i in range(n.value):
+            t = int(done[i])
+            q, ids, d2 = self._req.pop(t)
+            self._out[t] = (ids, d2)
+            out.append(t)
+        return out
+
+    def pending(self):
+        w, b = ctypes.c_int64(), ctypes.c_int32()
+        _lib.check(load().osann_server_pending(self._h, ctypes.byref(w), ctypes.byref(b)))
+        return w.value, b.value
+
+    def stats(self) -> dict:
+        out = (ctypes.c_int64 * 5)()
+        _lib.check(load().osann_server_stats(self._h, out))
+        return {"batches": out[0], "queries": out[1], "graph_replays": out[2], "graphs_captured": out[3],
+                "capture_failures": out[4]}
+
+    def result(self, ticket: int):
+        """(ids, sqdists) of a finished request (removed from the server)."""
+        return self._out.pop(ticket)
+
+    def drain(self):
+        """Progress until every submitted request has finished; returns their tickets."""
+        got = []
+        while self._req:
+            got += self.progress(wait=True)
+        return got
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().osann_server_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

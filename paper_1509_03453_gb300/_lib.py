@@ -62,6 +62,23 @@ SIGNATURES = {
     "osann_stats_reset": (c.c_int, []),
     "osann_stats_get": (c.c_int, [c.c_int32, c.POINTER(c.c_double), c.POINTER(c.c_int64)]),
     "osann_launch_count": (c.c_int64, []),
+    "osann_search_group": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
+                                     c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_search_workspace_size_group": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
+                                                       c.c_int32]),
+    "osann_server_create": (c.c_int, [c.POINTER(c.c_void_p), c.c_int32, c.POINTER(c.c_int32),
+                                      c.POINTER(c.c_int32), c.c_int32, c.c_int64, c.c_size_t, c.c_int32,
+                                      c.POINTER(c.c_void_p)]),
+    "osann_server_slots": (c.c_int, [c.c_void_p]),
+    "osann_server_submit": (c.c_int, [c.c_void_p, c.c_int32, c.c_void_p, c.c_int64, c.c_void_p, c.c_void_p,
+                                      c.POINTER(c.c_uint64)]),
+    "osann_server_progress": (c.c_int, [c.c_void_p, c.c_int32, c.POINTER(c.c_uint64), c.c_int32,
+                                        c.POINTER(c.c_int32)]),
+    "osann_server_pending": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32)]),
+    "osann_server_tune": (c.c_int, [c.c_void_p, c.c_int32, c.POINTER(c.c_int32)]),
+    "osann_server_buckets": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.c_int32]),
+    "osann_server_free": (c.c_int, [c.c_void_p]),
+    "osann_server_stats": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64)]),
 }
 
 

@@ -37,6 +37,13 @@ void set_error(const char* fmt, ...)
     va_end(ap);
 }
 
+// A thread capturing a search into a CUDA graph records no stage events;
+// the kernels counted while capturing are credited per replay instead.
+static thread_local bool t_capturing = false;
+void set_capturing(bool on) { t_capturing = on; }
+void add_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launch_total() { return g_launches.load(std::memory_order_relaxed); }
+
 int count_launch()
 {
     cudaError_t e = cudaGetLastError();
@@ -166,7 +173,7 @@ struct StageScope {
     cudaEvent_t a = nullptr;
     StageScope(int s, cudaStream_t stream) : stage(s), st(stream)
     {
-        if (!g_stats_on) return;
+        if (!g_stats_on || t_capturing) return;
         std::lock_guard<std::mutex> lk(g_stats_mu);
         a = take_event();
         cudaEventRecord(a, st);
@@ -223,6 +230,19 @@ struct osann_index {
     std::mutex tc_mu;
     std::vector<std::pair<void*, size_t>> allocs;
 };
+
+namespace osann {
+// The permuted fp32 rows of an index (the request server samples them as
+// tuning queries).
+const float* index_rows(const osann_index* ix, int64_t* N, int* d, int* d_pad)
+{
+    *N = ix->N;
+    *d = ix->d;
+    *d_pad = ix->d_pad;
+    return ix->xs;
+}
+int index_device(const osann_index* ix) { return ix->device; }
+}  // namespace osann
 
 // Coefficients of the screening bound
 //     E = cdot2 |q||x| + Bn (|q|^2 + |x|^2) + cabs (|q| + |x|):
@@ -341,7 +361,16 @@ static int ensure_tc(osann_index* ix, int prec, cudaStream_t st)
 
 static int group_size(int d_pad) { return 128 / (d_pad == 16 ? 1 : d_pad / 32); }
 
-static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, int mode)
+// Queries per work-list item: the default, or `group` when it is in range
+// (1..128 for the tensor-core screen, whose MMA tile has 128 query rows;
+// 1..group_size for the fp32 tile scan, whose thread layout fixes the most).
+static int item_group(const osann_index* ix, int mode, int group)
+{
+    const int gmax = tc_mode(mode) ? TC_GROUP : group_size(ix->d_pad);
+    return group >= 1 && group <= gmax ? group : gmax;
+}
+
+static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, int mode, int group = 0)
 {
     WsLayout w{};
     size_t off = 0;
@@ -354,7 +383,7 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
     w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
     if (mode != MODE_PLAIN) {
-        const int G = tc_mode(mode) ? TC_GROUP : group_size(ix->d_pad);
+        const int G = item_group(ix, mode, group);
         const int64_t n = Q * P_eff;
         int64_t mi = n / G + ix->NC + 1;
         if (mi > n) mi = n;
@@ -652,12 +681,18 @@ int osann_status(const osann_index* ix, void* stream, uint32_t* flags)
     return OSANN_OK;
 }
 
-size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path)
+size_t osann_search_workspace_size_group(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path,
+                                         int32_t group)
 {
     if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K) return 0;
-    if (path < 0 || path > OSANN_PATH_FP16) return 0;
+    if (path < 0 || path > OSANN_PATH_FP16 || group < 0) return 0;
     const int64_t P_eff = P < ix->NC ? P : ix->NC;
-    return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path)).total;
+    return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path), group).total;
+}
+
+size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path)
+{
+    return osann_search_workspace_size_group(ix, Q, P, k, path, 0);
 }
 
 static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_eff, const WsLayout& L, char* w,
@@ -711,9 +746,9 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
 
 static int search_impl(const osann_index* ix, const float* Y, const int64_t* src, int64_t Q, int32_t P, int32_t k,
                        int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
-                       float* dists, void* stream)
+                       float* dists, void* stream, int32_t group = 0)
 {
-    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 ||
+    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 || group < 0 ||
         (Q > 0 && (!Y || !ids || !dists))) {
         set_error("osann_search: invalid arguments (Q=%lld P=%d k=%d path=%d)", (long long)Q, P, k, path);
         return OSANN_ERR_INVALID;
@@ -736,7 +771,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         if (trc) return trc;
     }
     const bool batched = mode != MODE_PLAIN;
-    const WsLayout L = ws_layout(ix, Q, P_eff, k, mode);
+    const WsLayout L = ws_layout(ix, Q, P_eff, k, mode, group);
     void* owned = nullptr;
     if (!d_ws) {
         owned = d_ws = dev_alloc(L.total, st);
@@ -764,7 +799,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         b.n_items_dev = b.item_off + ix->NC;
         b.scan_temp = w + L.scan_temp;
         b.max_items = L.max_items;
-        const int G = tc_mode(mode) ? TC_GROUP : group_size(ix->d_pad);
+        const int G = item_group(ix, mode, group);
         uint64_t* partial = reinterpret_cast<uint64_t*>(w + L.partial);
         const uint32_t* probes = reinterpret_cast<uint32_t*>(w + L.probes);
         if (tc_mode(mode)) {
@@ -828,6 +863,13 @@ int osann_search(const osann_index* index, const float* d_queries, int64_t Q, in
                  void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists, void* stream)
 {
     return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream);
+}
+
+int osann_search_group(const osann_index* index, const float* d_queries, int64_t Q, int32_t P, int32_t k,
+                       int32_t path, int32_t group, void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists,
+                       void* stream)
+{
+    return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, group);
 }
 
 int osann_search_excl(const osann_index* index, const float* d_queries, const int64_t* d_query_src, int64_t Q,

@@ -13,6 +13,11 @@ namespace osann {
 // Launch bookkeeping: checks cudaGetLastError, bumps the launch counter.
 int count_launch();
 void set_error(const char* fmt, ...);
+// Graph capture: a capturing thread records no stage events; the launches
+// counted while capturing are moved to the replays (add_launches).
+void set_capturing(bool on);
+void add_launches(int64_t n);
+int64_t launch_total();
 
 // keys.cu
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
