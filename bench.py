@@ -374,6 +374,19 @@ def run_gpu(args):
     }
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(P, budget_s=args.cpu_budget)
+    if rank == 0 and ws == 1 and args.serve_requests > 0:
+        # the serving workload (three resident indexes), shortened: its own
+        # numbers, reported beside the step throughput
+        try:
+            del Xd, Yd, work, flush
+            torch.cuda.empty_cache()
+            args_s = argparse.Namespace(**vars(args))
+            args_s.serve_requests = min(args.serve_requests, 2000)
+            sv = run_serving(args_s, emit=False)
+            line["serving"] = {k: sv[k] for k in ("indexes", "requests", "queries", "slots", "max_batch",
+                                                  "capacity_qps", "loads", "server")}
+        except Exception as exc:  # reported, never fatal to the main line
+            line["serving"] = {"error": repr(exc)[:300]}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -440,6 +453,123 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+# ---------------------------------------------------------------- serving
+
+SERVE_SEED = 5000
+SERVE_POOL = 8192
+SERVE_LADDER = [16, 32, 64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192, 12288,
+                16384]
+
+
+def serve_indexes():
+    """The three resident indexes of the serving workload: (name, X, query
+    pool, L).  Gaussian rows iid N(0,1); descriptor rows as the descriptor
+    recipe; query pools are fresh draws (seeds 5001..5003)."""
+    from paper_1509_03453_gb300 import datagen
+    return [
+        ("gauss32 N=1M", datagen.gaussian(1_000_000, 32, 1002), datagen.gaussian(SERVE_POOL, 32, 5001), 2),
+        ("gauss64 N=4M", datagen.gaussian(4_000_000, 64, 1005), datagen.gaussian(SERVE_POOL, 64, 5002), 2),
+        ("desc128 N=2M", datagen.descriptors(2_000_000, 1004), datagen.descriptor_queries(SERVE_POOL, 5003), 3),
+    ]
+
+
+def run_serving(args, emit=True):
+    """Poisson-arriving requests of 1..4096 queries (log-uniform sizes,
+    uniform index) through the request server; capacity first (all requests
+    at once), then open-loop loads at 50/80/95% of it."""
+    import torch
+
+    import paper_1509_03453_gb300 as osann
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    osann.load()
+    specs = serve_indexes()
+    idx, pools, Ps, names, recalls = [], [], [], [], []
+    for name, X, Y, Lk in specs:
+        ix = osann.Index(torch.from_numpy(X).to(dev), Lk)
+        pool = torch.from_numpy(Y).to(dev)
+        gt_ids, gt_d2 = (t.cpu().numpy() for t in ix.bruteforce(pool[:1000], 1))
+        P, rec = SERVE_LADDER[-1], 0.0
+        for cand in SERVE_LADDER:
+            ids, d2 = (t.cpu().numpy() for t in ix.search(pool[:1000], cand, 1))
+            rec = recall1(ids, d2, gt_ids, gt_d2)
+            if rec >= 0.9:
+                P = cand
+                break
+        idx.append(ix)
+        pools.append(pool)
+        Ps.append(P)
+        names.append(name)
+        recalls.append(round(rec, 4))
+    srv = osann.Server(idx, P=Ps, k=[1] * len(idx), slots=args.serve_slots, max_batch=4096,
+                       mem_budget=int(args.serve_mem_gb * (1 << 30)), graphs=True)
+    choices = srv.tune(reps=2)
+    rng = np.random.default_rng(SERVE_SEED)
+    n_req = args.serve_requests
+    sizes = np.floor(np.exp(rng.uniform(0.0, np.log(4096.0), n_req))).astype(np.int64).clip(1, 4096)
+    which = rng.integers(0, len(idx), n_req)
+    offs = np.array([rng.integers(0, SERVE_POOL - s + 1) for s in sizes], dtype=np.int64)
+    total_q = int(sizes.sum())
+
+    def drive(arrivals):
+        lat = np.zeros(n_req)
+        t0 = time.perf_counter()
+        nxt, done = 0, 0
+        owner = {}
+        while done < n_req:
+            now = time.perf_counter() - t0
+            while nxt < n_req and arrivals[nxt] <= now:
+                i = int(which[nxt])
+                t = srv.submit(i, pools[i][offs[nxt]:offs[nxt] + sizes[nxt]])
+                owner[t] = nxt
+                nxt += 1
+            got = srv.progress(wait=False)
+            tn = time.perf_counter() - t0
+            for t in got:
+                j = owner.pop(t)
+                srv.result(t)
+                lat[j] = tn - arrivals[j]
+                done += 1
+        return time.perf_counter() - t0, lat
+
+    # warm-up: capture every graph the run needs
+    for i in range(len(idx)):
+        for b in srv.buckets():
+            ts = [srv.submit(i, pools[i][:b]) for _ in range(srv.slots)]  # one graph per slot
+            srv.drain()
+            for t in ts:
+                srv.result(t)
+    el, _ = drive(np.zeros(n_req))
+    capacity = total_q / el
+    loads = []
+    mean_size = total_q / n_req
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * capacity / mean_size
+        arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        arr -= arr[0]
+        el, lat = drive(arr)
+        loads.append({"offered_frac": frac, "offered_qps": round(frac * capacity, 1),
+                      "qps": round(total_q / el, 1), "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)})
+    st = srv.stats()
+    out = {
+        "serving": True,
+        "metric": "request latency p50/p99 and queries/s at recall@1>=0.9",
+        "indexes": [{"name": n, "P": p, "recall_at_1": r, "tuned": [list(c) for c in ch]}
+                    for n, p, r, ch in zip(names, Ps, recalls, choices)],
+        "requests": n_req, "queries": total_q, "sizes": "floor(exp(U(0, ln 4096))), index uniform",
+        "slots": srv.slots, "max_batch": 4096, "graphs": True,
+        "capacity_qps": round(capacity, 1), "loads": loads,
+        "server": st,
+    }
+    srv.close()
+    for ix in idx:
+        ix.close()
+    if emit:
+        print(json.dumps(out))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -451,6 +581,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16", "fp16"])
+    ap.add_argument("--serving", action="store_true", help="the request-server workload (three resident indexes)")
+    ap.add_argument("--serve-requests", type=int, default=10_000,
+                    help="requests of the serving workload (0: skip it in the default run)")
+    ap.add_argument("--serve-slots", type=int, default=4)
+    ap.add_argument("--serve-mem-gb", type=float, default=8.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -458,6 +593,8 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
+    elif args.serving:
+        run_serving(args)
     else:
         run_gpu(args)
 

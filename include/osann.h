@@ -233,6 +233,17 @@ int osann_stats_reset(void);
 int osann_stats_get(int32_t stage, double *total_ms, int64_t *count);
 int64_t osann_launch_count(void);
 
+/* Merge of per-shard results (the exchange step of a search sharded by data
+ * rows; the paper has no counterpart).  d_ids / d_sqdists hold G lists laid
+ * out [G][Q][k] (as osann_search returns them, ids already global, -1 and
+ * +inf as padding); the result is the k best of each query's G*k entries by
+ * (distance, id), padded with -1 / +inf.  Since keys depend only on a row,
+ * the shards' candidate sets partition the unsharded one, and the merge of
+ * their k-best lists equals the unsharded search bit for bit.  Ids must be
+ * below 2^32 - 1.  1 <= k <= 32.  Asynchronous on `stream`. */
+int osann_merge_topk(const int64_t *d_ids, const float *d_sqdists, int32_t G, int64_t Q, int32_t k,
+                     int64_t *d_out_ids, float *d_out_sqdists, void *stream);
+
 /* ---------------------------------------------------------------- serving
  *
  * A request server over indexes resident on the device (the paper has no

@@ -15,7 +15,7 @@ import ctypes
 from . import _lib
 from ._lib import OsannError, PATHS, STAGES, load
 
-__all__ = ["Index", "Server", "OsannError", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
+__all__ = ["Index", "Server", "OsannError", "merge_topk", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
 
 
 def _torch():
@@ -80,6 +80,22 @@ def stats(enable: bool | None = None, reset: bool = False) -> dict:
     if reset:
         L.osann_stats_reset()
     return out
+
+
+def merge_topk(ids, sqdists, stream=None):
+    """k best by (distance, id) of G per-shard result lists: ids int64 and
+    sqdists float32 CUDA tensors of shape [G, Q, k]."""
+    torch = _torch()
+    if ids.dim() != 3 or sqdists.shape != ids.shape:
+        raise ValueError("ids and sqdists must both be [G, Q, k]")
+    G, Q, k = ids.shape
+    ids = ids.contiguous()
+    d2 = sqdists.contiguous()
+    out_ids = torch.empty((Q, k), dtype=torch.int64, device=ids.device)
+    out_d = torch.empty((Q, k), dtype=torch.float32, device=ids.device)
+    _lib.check(load().osann_merge_topk(_ptr(ids), _ptr(d2), G, Q, k, _ptr(out_ids), _ptr(out_d),
+                                       _stream_ptr(stream)))
+    return out_ids, out_d
 
 
 def launch_count() -> int:

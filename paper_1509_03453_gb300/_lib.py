@@ -79,6 +79,8 @@ SIGNATURES = {
     "osann_server_buckets": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.c_int32]),
     "osann_server_free": (c.c_int, [c.c_void_p]),
     "osann_server_stats": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64)]),
+    "osann_merge_topk": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int32, c.c_int64, c.c_int32, c.c_void_p,
+                                   c.c_void_p, c.c_void_p]),
 }
 
 
