@@ -113,6 +113,27 @@ def recall1(ids, d2, gt_ids, gt_d2):
     return float(np.mean(hit | near))
 
 
+def profiled_traffic(kernel_md, sources):
+    """DRAM bytes per launch from a committed ncu summary under profiles/,
+    or None when the kernel's sources changed since the capture (the
+    summary records a hash of them)."""
+    import hashlib
+    try:
+        txt = open(os.path.join(ROOT, "profiles", kernel_md)).read()
+        h = hashlib.sha1(b"".join(open(os.path.join(ROOT, f), "rb").read() for f in sources)).hexdigest()[:16]
+        rec = dict(line.split(":", 1) for line in txt.splitlines() if line.startswith(("traffic_bytes_per_launch:",
+                                                                                    "kernel_source_sha1_16:")))
+        if rec.get("kernel_source_sha1_16", "").split()[0] != h:
+            return None
+        return int(rec["traffic_bytes_per_launch"].split()[0])
+    except Exception:
+        return None
+
+
+TC_SOURCES = ["paper_1509_03453_gb300/csrc/tc_scan.cu", "paper_1509_03453_gb300/csrc/osann_tc.cuh",
+              "paper_1509_03453_gb300/csrc/osann_device.cuh"]
+
+
 def run_profile(args):
     """Only the warm-up and timed steps (fixed P, chosen path): the command
     the ncu captures under profiles/ run, so that the launch list holds
@@ -311,7 +332,9 @@ def run_gpu(args):
         peak = peaks.get("bf16_tflops", 1900.0)
         achieved = flops / (dom_ms / 1e3) / 1e12
         roof = {"kernel": dom, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic("tc_scan_gauss32_N1M_Q10k_P224.md", TC_SOURCES),
+                "traffic_source": "ncu capture in profiles/tc_scan_gauss32_N1M_Q10k_P224.md (null if the kernel changed)",
                 "peak_source": f"{peak_src} bf16 dense (burst; fp16 has the same nominal rate)",
                 "algorithmic": f"{pairs} (query, candidate) pairs x 2d flops per launch "
                                f"(issued MMA work is larger: padded tiles and one extra K block of 16)",
