@@ -56,9 +56,9 @@ __device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], 
 // Vector path (d % 4 == 0, 16-byte aligned rows): one lane per row.  The
 // lane streams its row in pieces of up to KC float4 (the first line fetch
 // brings the piece's cache lines into L1 for the rest of the warp's loads)
-// and keeps the L largest selection keys in a sorted register list, so the
-// selection needs no shuffles: one 64-bit compare per component, and an
-// insertion only when a component beats the current L-th.
+// and keeps the L largest selection keys in a sorted register list: one
+// 32-bit magnitude compare per component, the 64-bit key and an insertion
+// only when the component can enter the list.
 template <int LC>
 __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                            const uint64_t* __restrict__ binom,
@@ -77,6 +77,10 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
         uint64_t top[LM];  // descending; 0 = empty (a real selection key is > 0)
 #pragma unroll
         for (int r = 0; r < LM; ++r) top[r] = 0;
+        // magnitude bits of the current L-th key: a component with a smaller
+        // magnitude cannot enter the list (equal ones are decided by the full key)
+        uint32_t lastmag = 0;
+        uint32_t amax = 0;  // largest magnitude bits of the row: >= 0x7F800000 iff non-finite
         float nsq = 0.0f;
         for (int c0 = 0; c0 < n4; c0 += KC) {
             float4 t[KC];
@@ -89,30 +93,40 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const float x = x4[e];
-                        bad |= !finite_f(x);
+                        const uint32_t a = __float_as_uint(x) & 0x7FFFFFFFu;
+                        amax = a > amax ? a : amax;
                         nsq = fmaf(x, x, nsq);
-                        uint64_t k = sel_key(x, 4 * (c0 + f) + e);
-                        uint64_t last = top[LM - 1];  // the L-th (compile-time index)
-                        if (LC == 0) {
+                        if (a >= lastmag) {
+                            uint64_t k = sel_key(x, 4 * (c0 + f) + e);
+                            uint64_t last = top[LM - 1];  // the L-th (compile-time index)
+                            if (LC == 0) {
 #pragma unroll
-                            for (int r = 0; r < LM; ++r)
-                                if (r == L - 1) last = top[r];
-                        }
-                        if (k > last) {
-                            // insertion into the sorted list (rare after the first few)
+                                for (int r = 0; r < LM; ++r)
+                                    if (r == L - 1) last = top[r];
+                            }
+                            if (k > last) {
 #pragma unroll
-                            for (int r = 0; r < LM; ++r) {
-                                if (LC > 0 || r < L) {
-                                    const uint64_t hi = k > top[r] ? k : top[r];
-                                    k = k > top[r] ? top[r] : k;
-                                    top[r] = hi;
+                                for (int r = 0; r < LM; ++r) {
+                                    if (LC > 0 || r < L) {
+                                        const uint64_t hi = k > top[r] ? k : top[r];
+                                        k = k > top[r] ? top[r] : k;
+                                        top[r] = hi;
+                                    }
                                 }
+                                last = top[LM - 1];
+                                if (LC == 0) {
+#pragma unroll
+                                    for (int r = 0; r < LM; ++r)
+                                        if (r == L - 1) last = top[r];
+                                }
+                                lastmag = uint32_t(last >> 32);
                             }
                         }
                     }
                 }
             }
         }
+        bad |= amax >= 0x7F800000u;
         int comp[MAX_L];
         uint32_t sgn[MAX_L];
 #pragma unroll

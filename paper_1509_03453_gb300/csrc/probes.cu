@@ -30,6 +30,13 @@ __device__ __forceinline__ uint64_t C(const uint64_t* __restrict__ binom, int n,
 // by the subsets skipped.  Bounded by n - m.
 __device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, uint64_t& t, int r, int n, int m)
 {
+    if (m == 1) {
+        // every candidate value accounts for exactly one subset: step t values at once
+        const uint64_t room = r < n - 1 ? uint64_t(n - 1 - r) : 0;
+        const uint64_t step = t < room ? t : room;
+        t -= step;
+        return r + int(step);
+    }
     while (r < n - m) {
         const uint64_t cnt = C(binom, n - r - 1, m - 1);
         if (t < cnt) break;
