@@ -361,6 +361,42 @@ static int ensure_tc(osann_index* ix, int prec, cudaStream_t st)
 
 static int group_size(int d_pad) { return 128 / (d_pad == 16 ? 1 : d_pad / 32); }
 
+// Side streams for independent stages of one search (fork on an event of the
+// caller's stream, join back before the dependent stage): a small pool per
+// device, chosen by the caller's stream, and a fork/join event pair per host
+// thread.  Event fork/join is also how a capturing stream pulls the side
+// stream into its CUDA graph.
+struct SideStream {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static int side_stream(int device, cudaStream_t caller, SideStream* out)
+{
+    constexpr int POOL = 8, MAXDEV = 64;
+    static std::mutex mu;
+    static cudaStream_t pool[MAXDEV][POOL] = {};
+    thread_local int ev_dev[MAXDEV] = {};
+    thread_local cudaEvent_t ev[MAXDEV][2] = {};
+    if (device < 0 || device >= MAXDEV) return OSANN_ERR_UNSUPPORTED;
+    const int slot = int((reinterpret_cast<uintptr_t>(caller) >> 4) % POOL);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pool[device][slot] && cudaStreamCreateWithFlags(&pool[device][slot], cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "side stream");
+    }
+    if (!ev_dev[device]) {
+        if (cudaEventCreateWithFlags(&ev[device][0], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ev[device][1], cudaEventDisableTiming) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "side stream events");
+        ev_dev[device] = 1;
+    }
+    out->st = pool[device][slot];
+    out->fork = ev[device][0];
+    out->join = ev[device][1];
+    return 0;
+}
+
 // Queries per work-list item: the default, or `group` when it is in range
 // (1..128 for the tensor-core screen, whose MMA tile has 128 query rows;
 // 1..group_size for the fp32 tile scan, whose thread layout fixes the most).
@@ -802,18 +838,33 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         const int G = item_group(ix, mode, group);
         uint64_t* partial = reinterpret_cast<uint64_t*>(w + L.partial);
         const uint32_t* probes = reinterpret_cast<uint32_t*>(w + L.probes);
+        // the query constants and seed bounds (tensor-core paths) and the work
+        // list depend only on the probe lists: the former runs on a side stream
+        SideStream side{};
         if (tc_mode(mode)) {
-            StageScope s(OSANN_STAGE_TC_PREP, st);
-            rc = launch_tc_query_prep(prec, Y, Q, ix->d, ix->d_pad, probes, P_eff, ix->offsets, uint32_t(ix->NC), ix->xs,
-                                      k, ix->cdot2[prec], ix->cabs[prec], ix->tcs + 4 * prec, ix->perm, src, grid_w,
-                                      radius, TC_SURV_CAP, w + L.yb, reinterpret_cast<float4*>(w + L.qstat),
-                                      reinterpret_cast<uint32_t*>(w + L.ubits), reinterpret_cast<uint32_t*>(w + L.scnt),
-                                      st);
+            rc = side_stream(ix->device, st, &side);
+            if (!rc && (cudaEventRecord(side.fork, st) != cudaSuccess ||
+                        cudaStreamWaitEvent(side.st, side.fork, 0) != cudaSuccess))
+                rc = cuda_fail(cudaGetLastError(), "osann_search: fork");
+            if (!rc) {
+                StageScope s(OSANN_STAGE_TC_PREP, side.st);
+                rc = launch_tc_query_prep(prec, Y, Q, ix->d, ix->d_pad, probes, P_eff, ix->offsets, uint32_t(ix->NC),
+                                          ix->xs, k, ix->cdot2[prec], ix->cabs[prec], ix->tcs + 4 * prec, ix->perm,
+                                          src, grid_w, radius, TC_SURV_CAP, w + L.yb,
+                                          reinterpret_cast<float4*>(w + L.qstat),
+                                          reinterpret_cast<uint32_t*>(w + L.ubits),
+                                          reinterpret_cast<uint32_t*>(w + L.scnt), side.st);
+            }
         }
         if (!rc) {
             StageScope s(OSANN_STAGE_WORKLIST, st);
             rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probesT), Q, P_eff, ix->offsets, ix->NC, G, b, st,
                                  ix->num_sms);
+        }
+        if (side.st) {
+            // join (also after an error, so that the side stream's work stays ordered before the caller's)
+            if (cudaEventRecord(side.join, side.st) != cudaSuccess || cudaStreamWaitEvent(st, side.join, 0) != cudaSuccess)
+                if (!rc) rc = cuda_fail(cudaGetLastError(), "osann_search: join");
         }
         if (!rc && tc_mode(mode)) {
             {

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     if (tid == 0) {
         for (int i = 0; i < TC_IQ; ++i) {
             mbar_init(&iq_full[i], 1);
-            mbar_init(&iq_empty[i], 1 + 64 + 128);
+            mbar_init(&iq_empty[i], 1 + 64 + 4);  // MMA issuer, 64 loader threads, 4 screening warps
         }
         for (int s = 0; s < S; ++s) {
             mbar_init(&bfull[s], 1);
@@ -183,11 +183,11 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         }
         for (uint32_t b = 0; b < NA; ++b) {
             mbar_init(&afull[b], 64);
-            mbar_init(&aempty[b], 128);
+            mbar_init(&aempty[b], 4);  // one arrival per screening warp
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
-            mbar_init(&accempty[b], 128);
+            mbar_init(&accempty[b], 4);
         }
         fence_mbar_init();
         abort_sh = 0;
@@ -393,6 +393,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             const uint32_t ab = it % NA;
             if (!wait(&afull[ab], (it / NA) & 1u)) break;
             TcQConst cur = qc[ab][er];
+            const float U0 = cur.U;
             const uint32_t qi = qidx[ab][er];
             const bool active = qi != 0xFFFFFFFFu;
             const int64_t q = active ? int64_t(qi) : 0;
@@ -534,16 +535,22 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                         }
                     }
                 }
+                // every lane's loads of this accumulator are complete: one arrival per warp
                 tc_fence_before();
-                mbar_arrive(&accempty[acc]);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&accempty[acc]);
             }
             if (!ok) break;
             if (active) {
                 flush();
-                atomicMin(a.Ubits + q, __float_as_uint(fmaxf(cur.U, 0.0f)));
+                if (cur.U < U0) atomicMin(a.Ubits + q, __float_as_uint(fmaxf(cur.U, 0.0f)));
             }
-            mbar_arrive(&aempty[ab]);
-            mbar_arrive(&iq_empty[slot]);
+            // the warp has read its query constants and the item descriptor
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&aempty[ab]);
+                mbar_arrive(&iq_empty[slot]);
+            }
         }
     }
     tc_fence_before();
