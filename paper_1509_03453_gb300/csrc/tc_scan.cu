@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
 // excluded rows skipped, at least TC_SEED rows when the cones hold them),
 // inflated by the fp32 error bound; +inf if fewer than k rows.  A query too large for the 16-bit range is left to the
 // rerank's full scan (its survivor count is set above the capacity).
-constexpr int TC_SEED = 256;    // rows scanned exactly for the initial bound
+constexpr int TC_SEED = 64;     // rows scanned exactly for the initial bound
 constexpr int TC_SEED_ILP = 8;  // row groups loaded per iteration
 
 template <int F, int PREC, int KMAX>
