@@ -212,9 +212,15 @@ def run_gpu(args):
     out_d2 = torch.empty((Q_FULL, K), dtype=torch.float32, device=dev)
 
     def step(path="auto"):
-        ix = osann.Index(Xd, L)
+        # build without its synchronisation (osann_build_async): the search
+        # follows in stream order; the build's status is read after the step
+        ix = osann.Index(Xd, L, sync=False)
         ix.search(Yd, P, K, path=path, out=(out_ids, out_d2), workspace=work)
         return ix
+
+    def check(ix):
+        if ix.status() & 5:  # non-finite data or a device wait timeout
+            raise RuntimeError("index build reported an error status")
 
     def timed(path, steps, warmup, with_stats=False):
         times = []
@@ -227,6 +233,7 @@ def run_gpu(args):
             ix = step(path)
             b.record(stream)
             b.synchronize()
+            check(ix)
             ix.close()
             if i >= warmup:
                 times.append(a.elapsed_time(b))
@@ -236,7 +243,9 @@ def run_gpu(args):
     # warm-up, then exactly `steps` timed steps bracketed by barrier + sync
     for _ in range(args.warmup):
         flush.zero_()
-        step().close()
+        ix = step()
+        check(ix)
+        ix.close()
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
@@ -290,12 +299,13 @@ def run_gpu(args):
         a.record(stream)
         xd = Xh.to(dev, non_blocking=True)
         yd = Yh.to(dev, non_blocking=True)
-        ix = osann.Index(xd, L)
+        ix = osann.Index(xd, L, sync=False)
         ix.search(yd, P, K, out=(out_ids, out_d2), workspace=work)
         ids_h.copy_(out_ids, non_blocking=True)
         d2_h.copy_(out_d2, non_blocking=True)
         b.record(stream)
         b.synchronize()
+        check(ix)
         ix.close()
         if i >= args.warmup:
             e2e_times.append(a.elapsed_time(b))
@@ -372,7 +382,7 @@ def run_gpu(args):
         "data": "synthetic (seeded iid N(0,1), generated on the host)",
         "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P,
                    "path": f"auto -> {path_used}",
-                   "step": "index build + search of the Q queries",
+                   "step": "index build (asynchronous; its status read after the step) + search of the Q queries",
                    "l2": "flushed before every step by a 256 MiB device write (untimed)",
                    "parallelism": f"replicas x{ws} (independent data per rank)"},
         "recall_at_1": round(rec, 4),

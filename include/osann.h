@@ -101,6 +101,14 @@ int osann_query_order(const float *d_queries, int64_t Q, int32_t d, uint8_t *d_o
  * N_C >= 2^31), NONFINITE (NaN/Inf in d_data), OOM, CUDA. */
 int osann_build(const float *d_data, int64_t N, int32_t d, int32_t L, void *stream, osann_index **out);
 
+/* As osann_build, without the final synchronisation (the paper has no
+ * counterpart: for pipelines that build and search back to back).  The
+ * index is usable at once in stream order on `stream`; its status bits
+ * (OSANN_STATUS_NONFINITE_DATA, OSANN_STATUS_TIMEOUT) are left for the next
+ * osann_status call, which must be checked before the results are trusted,
+ * and max_bucket reads -1 in osann_info until that call. */
+int osann_build_async(const float *d_data, int64_t N, int32_t d, int32_t L, void *stream, osann_index **out);
+
 /* Release an index.  NULL is accepted.  The caller must ensure that no
  * work using the index is still pending on any stream. */
 int osann_free(osann_index *index);

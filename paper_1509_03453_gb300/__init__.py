@@ -105,16 +105,21 @@ def launch_count() -> int:
 class Index:
     """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
 
-    def __init__(self, data, L: int, stream=None):
+    def __init__(self, data, L: int, stream=None, sync: bool = True):
+        """sync=False: osann_build_async (no synchronisation; call status()
+        before trusting results)."""
         torch = _torch()
         x = _dev_f32(data, "data")
         self.N, self.d = x.shape
         self.L = L
         self.device = x.device
         h = ctypes.c_void_p()
+        build = load().osann_build if sync else load().osann_build_async
         with torch.cuda.device(x.device):
-            _lib.check(load().osann_build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
+            _lib.check(build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
+        # an asynchronous build may still be reading the input: keep it until status()
+        self._src = None if sync else x
         NC, mb = ctypes.c_int64(), ctypes.c_int64()
         _lib.check(load().osann_info(h, None, None, None, ctypes.byref(NC), ctypes.byref(mb)))
         self.NC, self.max_bucket = NC.value, mb.value
@@ -217,6 +222,11 @@ class Index:
         """Synchronise and return (and clear) the device status flags."""
         f = ctypes.c_uint32()
         _lib.check(load().osann_status(self._h, _stream_ptr(stream), ctypes.byref(f)))
+        self._src = None
+        if self.max_bucket < 0:
+            mb = ctypes.c_int64()
+            _lib.check(load().osann_info(self._h, None, None, None, None, ctypes.byref(mb)))
+            self.max_bucket = mb.value
         return f.value
 
 

@@ -546,7 +546,8 @@ int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_o
                               static_cast<cudaStream_t>(stream));
 }
 
-int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
+static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, bool async,
+                      osann_index** out)
 {
     if (!out || !d_data || N < 1) {
         set_error("osann_build: invalid arguments (data=%p N=%lld out=%p)", (const void*)d_data, (long long)N,
@@ -636,6 +637,18 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st);
     dev_free(temp, temp_bytes, st);
+    // the tensor maps need only addresses and sizes: encode them while the device works
+    const bool maps_ok = !rc && tc_possible && tc_map_bytes() <= sizeof(ix->tmap[1]) &&
+                         tc_encode_rows_map(ix->tmap[1], ix->x16[1], N, ix->d_pad, 1) == 0 &&
+                         tc_encode_rows_map(ix->tmap[1] + tc_map_bytes() / 2, ix->xe16[1], N, 0, 1) == 0;
+    if (!rc && async) {
+        // status (non-finite data, timeouts) and the largest cone are read by
+        // the next osann_status call
+        ix->max_bucket = -1;
+        ix->tc_ready[1] = maps_ok;
+        *out = ix;
+        return OSANN_OK;
+    }
     uint32_t host_status[2] = {0, 0};
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(host_status, ix->status, 8, cudaMemcpyDeviceToHost, st);
@@ -656,11 +669,19 @@ int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stre
     }
     cudaMemsetAsync(ix->status, 0, 4, st);
     ix->max_bucket = host_status[1];
-    ix->tc_ready[1] = tc_possible && tc_map_bytes() <= sizeof(ix->tmap[1]) &&
-                      tc_encode_rows_map(ix->tmap[1], ix->x16[1], N, ix->d_pad, 1) == 0 &&
-                      tc_encode_rows_map(ix->tmap[1] + tc_map_bytes() / 2, ix->xe16[1], N, 0, 1) == 0;
+    ix->tc_ready[1] = maps_ok;
     *out = ix;
     return OSANN_OK;
+}
+
+int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
+{
+    return build_impl(d_data, N, d, L, stream, false, out);
+}
+
+int osann_build_async(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
+{
+    return build_impl(d_data, N, d, L, stream, true, out);
 }
 
 int osann_free(osann_index* index)
@@ -708,12 +729,14 @@ int osann_status(const osann_index* ix, void* stream, uint32_t* flags)
         return OSANN_ERR_INVALID;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    uint32_t h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, ix->status, 4, cudaMemcpyDeviceToHost, st);
+    uint32_t h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, ix->status, 8, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(ix->status, 0, 4, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(e, "osann_status");
-    *flags = h;
+    *flags = h[0];
+    // an index built asynchronously learns its largest cone here
+    if (ix->max_bucket < 0) const_cast<osann_index*>(ix)->max_bucket = h[1];
     return OSANN_OK;
 }
 

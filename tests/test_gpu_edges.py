@@ -128,3 +128,29 @@ def test_many_queries_small_budget_and_big_groups(osann):
     for path in ("plain", "batched"):
         gids, gd = idx.search(to_dev(Y), 3, 2, path=path)
         assert_knn_match(X, Y, to_np(gids), to_np(gd), oids, od)
+
+
+def test_async_build_same_index_and_deferred_status(osann):
+    rng = np.random.default_rng(41)
+    X = rng.standard_normal((30_011, 32)).astype(np.float32)
+    Y = rng.standard_normal((500, 32)).astype(np.float32)
+    a = osann.Index(to_dev(X), 2)
+    b = osann.Index(to_dev(X), 2, sync=False)
+    assert b.max_bucket == -1
+    ia, da = a.search(to_dev(Y), 40, 3)
+    ib, db = b.search(to_dev(Y), 40, 3)
+    assert b.status() == 0 and b.max_bucket == a.max_bucket
+    for ta, tb in zip(a.export(), b.export()):
+        assert np.array_equal(to_np(ta), to_np(tb))
+    assert np.array_equal(to_np(ia), to_np(ib))
+    assert np.array_equal(to_np(da).view(np.uint32), to_np(db).view(np.uint32))
+    # non-finite data: the synchronous build refuses it, the asynchronous one
+    # reports it at the status read
+    X[123, 5] = np.nan
+    with pytest.raises(osann.OsannError):
+        osann.Index(to_dev(X), 2)
+    c = osann.Index(to_dev(X), 2, sync=False)
+    assert c.status() & 1
+    a.close()
+    b.close()
+    c.close()
