@@ -100,16 +100,6 @@ __global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __re
     }
 }
 
-__global__ void wl_counts_from_H_kernel(const uint32_t* __restrict__ Hs, int64_t NC, int64_t nb,
-                                        uint32_t* __restrict__ qcount, uint32_t* __restrict__ qoff)
-{
-    for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < NC; c += int64_t(gridDim.x) * blockDim.x) {
-        const uint32_t o = Hs[c * nb], e = Hs[(c + 1) * nb];  // Hs[NC * nb] is the total
-        qoff[c] = o;
-        qcount[c] = e - o;
-    }
-}
-
 __global__ void wl_nitems_kernel(const uint32_t* __restrict__ qcount, int64_t NC, int G, uint32_t* __restrict__ nitems)
 {
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c <= NC; c += int64_t(gridDim.x) * blockDim.x)
@@ -134,6 +124,62 @@ __global__ void wl_items_kernel(const uint32_t* __restrict__ nitems, const uint3
             items[o + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
         }
     }
+}
+
+// One CTA over all cones (N_C <= 12288, at most 12 per thread): per-cone
+// counts and first slots from the scanned per-block histograms, the number of
+// items of each cone, their exclusive scan and the item descriptors, in one
+// launch.  item_off[N_C] receives the total.
+constexpr int WL_CONES_THREADS = 1024;
+
+__global__ void __launch_bounds__(WL_CONES_THREADS) wl_cones_kernel(
+    const uint32_t* __restrict__ Hs, int NC, int64_t nb, const uint32_t* __restrict__ offsets, int G,
+    uint32_t* __restrict__ qcount, uint32_t* __restrict__ qoff, uint32_t* __restrict__ item_off,
+    uint4* __restrict__ items, uint32_t* __restrict__ counters)
+{
+    __shared__ uint32_t wsum[WL_CONES_THREADS / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (NC + WL_CONES_THREADS - 1) / WL_CONES_THREADS;
+    const int c0 = tid * per < NC ? tid * per : NC, c1 = c0 + per < NC ? c0 + per : NC;
+    uint32_t mine = 0;
+    for (int c = c0; c < c1; ++c) {
+        const uint32_t o = Hs[int64_t(c) * nb], e = Hs[int64_t(c + 1) * nb];  // Hs[N_C * nb] is the total
+        qoff[c] = o;
+        qcount[c] = e - o;
+        mine += (e - o + uint32_t(G) - 1) / uint32_t(G);
+    }
+    // exclusive scan of the per-thread item counts over the CTA
+    uint32_t incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = wsum[lane], wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += v;
+        }
+        wsum[lane] = wi - w;  // exclusive over warps
+    }
+    __syncthreads();
+    uint32_t off = wsum[warp] + incl - mine;
+    for (int c = c0; c < c1; ++c) {
+        const uint32_t cnt = qcount[c], n = (cnt + uint32_t(G) - 1) / uint32_t(G);
+        item_off[c] = off;
+        const uint32_t r0 = offsets[c], r1 = offsets[c + 1], q0 = qoff[c];
+        for (uint32_t g = 0; g < n; ++g) {
+            const uint32_t rest = cnt - g * uint32_t(G);
+            items[off + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
+        }
+        off += n;
+    }
+    if (tid == WL_CONES_THREADS - 1) item_off[NC] = off;
+    if (tid == 0) counters[0] = 0;  // work counter of the scan that follows
 }
 
 static int wl_blocks_impl(int64_t n, int num_sms)
@@ -173,11 +219,12 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         wl_block_hist_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf);
         if ((rc = count_launch())) return rc;
         if ((rc = launch_exclusive_scan(b.hbuf, b.hbuf, hn, b.scan_temp, st))) return rc;
-        wl_counts_from_H_kernel<<<unsigned(cb), 256, 0, st>>>(b.hbuf, NC, nb, b.qcount, b.qoff);
+        wl_cones_kernel<<<1, WL_CONES_THREADS, 0, st>>>(b.hbuf, int(NC), nb, offsets, group, b.qcount, b.qoff,
+                                                          b.item_off, b.items, b.counters);
         if ((rc = count_launch())) return rc;
         wl_block_fill_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf,
                                                                          b.qlist, uint32_t(Q), uint32_t(P_eff));
-        if ((rc = count_launch())) return rc;
+        return count_launch();
     } else {
         cudaMemsetAsync(b.qcount, 0, size_t(NC + 1) * 4, st);
         cudaMemsetAsync(b.fill, 0, size_t(NC) * 4, st);
