@@ -70,6 +70,12 @@ def lib():
         L.oracle_bruteforce.argtypes = [
             _f32p, c.c_int64, c.c_int, _f32p, c.c_int64, c.c_int, c.c_void_p,
             c.c_int64, c.c_int64, _i64p, _f64p]
+        L.oracle_rotate.restype = None
+        L.oracle_rotate.argtypes = [_f32p, _f32p, c.c_int64, c.c_int, _f32p]
+        L.oracle_search_multi.restype = None
+        L.oracle_search_multi.argtypes = [
+            _f32p, c.c_int64, c.c_int, c.c_int, c.c_int, _f32p, _u32p, _u32p, _f32p, c.c_int64,
+            c.c_int64, c.c_int, _i64p, _f64p, c.c_void_p]
         L.oracle_pair_dists.restype = None
         L.oracle_pair_dists.argtypes = [_f32p, c.c_int, _f32p, c.c_int64,
                                         c.c_int, _i64p, _f64p]
@@ -157,6 +163,48 @@ class Index:
             src, grid_w, radius, ids, dists,
             counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
         del keep
+        ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
+        return (ids, dists, counts) if want_counts else (ids, dists)
+
+
+def rotate(Rm, X) -> np.ndarray:
+    """Coordinates of the rows of X on the basis Rm (fp32, in-order FMAs)."""
+    Rm, X = _f32(Rm), _f32(X)
+    n, d = X.shape
+    out = np.empty((n, d), np.float32)
+    lib().oracle_rotate(Rm, X, n, d, out)
+    return out
+
+
+class MultiIndex:
+    """Oracle index over R bases: per basis, keys of the rotated rows and a
+    stable counting sort; the search visits the bases' cones in Algorithm 1's
+    order with the "analyzed" flag."""
+
+    def __init__(self, X, L: int, rots):
+        self.X = _f32(X)
+        self.N, self.d = self.X.shape
+        self.L = L
+        self.rots = _f32(np.asarray(rots).reshape(-1, self.d, self.d))
+        self.R = self.rots.shape[0]
+        self.NC = num_cones(self.d, L)
+        offs, perms = [], []
+        for r in range(self.R):
+            o, p = buckets(keys(rotate(self.rots[r], self.X), L), self.NC)
+            offs.append(o)
+            perms.append(p)
+        self.offsets = np.ascontiguousarray(np.stack(offs), np.uint32)
+        self.perms = np.ascontiguousarray(np.stack(perms), np.uint32)
+
+    def search(self, Y, P: int, k: int, want_counts: bool = False):
+        Y = _f32(Y)
+        Q = Y.shape[0]
+        ids = np.empty(Q * k, np.int64)
+        dists = np.empty(Q * k, np.float64)
+        counts = np.empty(Q, np.int64) if want_counts else None
+        lib().oracle_search_multi(self.X, self.N, self.d, self.L, self.R, self.rots, self.offsets, self.perms,
+                                  Y, Q, P, k, ids, dists,
+                                  counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
         ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
         return (ids, dists, counts) if want_counts else (ids, dists)
 

@@ -2,7 +2,8 @@
  * osann_oracle.c -- plain, slow, single-threaded CPU oracle for the
  * order-statistics cone-hash ANN search of Verdoliva, Cozzolino and Poggi,
  * "A reliable order-statistics-based approximate nearest neighbor search
- * algorithm" (ROSANNA), restricted to one basis (R = 1).
+ * algorithm" (ROSANNA): one basis (R = 1), and R bases (Algorithm 1 with
+ * its "analyzed" flag) for the multi-basis search of Sec. 3-D.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark may load this library.  The product path
@@ -27,6 +28,11 @@
  *     cone carrying the query's own signs; after all C(K,G) profiles the
  *     sign-flipped cones follow (h flips ascending, profile order, flip
  *     subsets lexicographic over the members sorted by |y| ascending).
+ *   - the coordinates of x on basis r are y_i = sum_j R_r[i][j] x_j, each
+ *     accumulated in fp32 by fused multiply-adds in order j = 0, 1, ...
+ *     (the rotated coordinates only decide integers -- keys and query
+ *     orders -- so both sides compute them in the same fp32 order);
+ *     distances always use the original vectors.
  * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
  * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
  * The intra-class probe order and the sign-flip extension are this
@@ -326,6 +332,71 @@ void oracle_search(const float *X, int64_t N, int d, int L,
         if (cand_count) cand_count[q] = cands;
     }
     free(probes);
+}
+
+/* Coordinates on a rotated basis (Sec. 3-D, "projection of y on the r-th
+ * basis"): out[i][r] = sum_j Rm[r][j] X[i][j] in fp32, fused multiply-adds in
+ * order j = 0..d-1 from 0.  Rm: d x d row-major (row r = basis vector r). */
+void oracle_rotate(const float *Rm, const float *X, int64_t n, int d, float *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int r = 0; r < d; ++r) {
+            float acc = 0.0f;
+            for (int j = 0; j < d; ++j) acc = fmaf(Rm[(int64_t)r * d + j], X[i * d + j], acc);
+            out[i * d + r] = acc;
+        }
+}
+
+/* Search over R bases (Algorithm 1): basis r has its own cone index
+ * (offsets_r, perm_r, built from the rotated data) and its own probe list,
+ * made from the query's coordinates on that basis.  Cones are visited in
+ * the algorithm's order -- for l = 1..C, for r = 1..R, cone c_l^(r) -- and a
+ * point is analysed once (the "analyzed" flag); distances are exact (Eq. 1)
+ * on the original vectors.  rots: R x d x d; offsets: R x (N_C + 1);
+ * perms: R x N.  Outputs as oracle_search. */
+void oracle_search_multi(const float *X, int64_t N, int d, int L, int R, const float *rots,
+                         const uint32_t *offsets, const uint32_t *perms, const float *Y, int64_t Q,
+                         int64_t P, int k, int64_t *ids, double *dists, int64_t *cand_count)
+{
+    int64_t NC = oracle_num_cones(d, L);
+    if (P > NC) P = NC;
+    uint32_t *probes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(R * (P > 0 ? P : 1)));
+    int64_t *np = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
+    float *yr = (float *)malloc(sizeof(float) * (size_t)d);
+    unsigned char *analyzed = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
+    int64_t *touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    for (int64_t q = 0; q < Q; ++q) {
+        const float *y = Y + q * d;
+        double *bd = dists + q * k;
+        int64_t *bi = ids + q * k;
+        topk_init(bd, bi, k);
+        for (int r = 0; r < R; ++r) {
+            oracle_rotate(rots + (int64_t)r * d * d, y, 1, d, yr);
+            np[r] = oracle_probes(yr, d, L, P, probes + (int64_t)r * P);
+        }
+        int64_t nt = 0;
+        for (int64_t l = 0; l < P; ++l)
+            for (int r = 0; r < R; ++r) {
+                if (l >= np[r]) continue;
+                const uint32_t c = probes[(int64_t)r * P + l];
+                const uint32_t *off = offsets + (int64_t)r * (NC + 1);
+                const uint32_t *perm = perms + (int64_t)r * N;
+                for (uint32_t row = off[c]; row < off[c + 1]; ++row) {
+                    const int64_t n = perm[row];
+                    if (analyzed[n]) continue;
+                    analyzed[n] = 1;
+                    touched[nt++] = n;
+                    topk_insert(bd, bi, k, sqdist(X + n * d, y, d), n);
+                }
+            }
+        if (cand_count) cand_count[q] = nt;
+        for (int64_t t = 0; t < nt; ++t) analyzed[touched[t]] = 0;
+    }
+    free(probes);
+    free(np);
+    free(yr);
+    free(analyzed);
+    free(touched);
 }
 
 /* Exact linear search (Eq. 1): the k nearest of all N points. */

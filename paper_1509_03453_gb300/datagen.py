@@ -86,6 +86,21 @@ def descriptor_queries(q: int, seed: int, d: int = 128) -> np.ndarray:
     return np.clip(noisy, 0.0, 512.0).astype(np.float32)
 
 
+def rotations(R: int, d: int, seed: int) -> np.ndarray:
+    """R orthonormal d x d bases (float32, row i = basis vector i) for the
+    multi-basis search: basis 0 is the identity, the others are random
+    rotations (QR of a Gaussian matrix, signs fixed by the diagonal of R)."""
+    rng = np.random.default_rng(seed)
+    out = np.empty((R, d, d), np.float32)
+    out[0] = np.eye(d, dtype=np.float32)
+    for r in range(1, R):
+        a = rng.standard_normal((d, d))
+        q, t = np.linalg.qr(a)
+        q = q * np.sign(np.diag(t))[None, :]
+        out[r] = q.T.astype(np.float32)
+    return out
+
+
 def workload(name: str, n: int | None = None, q: int | None = None) -> dict:
     """Named workload.  ``n``/``q`` shrink it (same recipe, prefix of the
     draws for Gaussian data) for tests that need a smaller case."""
