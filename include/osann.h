@@ -101,6 +101,20 @@ int osann_query_order(const float *d_queries, int64_t Q, int32_t d, uint8_t *d_o
  * N_C >= 2^31), NONFINITE (NaN/Inf in d_data), OOM, CUDA. */
 int osann_build(const float *d_data, int64_t N, int32_t d, int32_t L, void *stream, osann_index **out);
 
+/* One basis of the multi-basis search (Sec. 3-D, Algorithm 1 with R > 1):
+ * as osann_build, but the cone keys -- and, in every later search, the
+ * query's magnitude order -- come from the coordinates on the basis d_rot
+ * (d x d fp32, row-major, row r = basis vector r, orthonormal; the index
+ * keeps a copy): y_r = sum_j d_rot[r][j] x_j, accumulated in fp32 by fused
+ * multiply-adds in order j = 0, 1, ... from 0.  Distances still use the
+ * original vectors.  d <= 128 (else UNSUPPORTED).  async != 0: as
+ * osann_build_async.  The R bases of a search are R such indexes; their
+ * per-basis results merge with osann_merge_topk, which drops repeated ids
+ * (a point found on several bases is one candidate: the "analyzed" flag of
+ * Algorithm 1). */
+int osann_build_rot(const float *d_data, int64_t N, int32_t d, int32_t L, const float *d_rot, int32_t async,
+                    void *stream, osann_index **out);
+
 /* As osann_build, without the final synchronisation (the paper has no
  * counterpart: for pipelines that build and search back to back).  The
  * index is usable at once in stream order on `stream`; its status bits
@@ -245,7 +259,9 @@ int64_t osann_launch_count(void);
  * rows; the paper has no counterpart).  d_ids / d_sqdists hold G lists laid
  * out [G][Q][k] (as osann_search returns them, ids already global, -1 and
  * +inf as padding); the result is the k best of each query's G*k entries by
- * (distance, id), padded with -1 / +inf.  Since keys depend only on a row,
+ * (distance, id), padded with -1 / +inf; an id present in several lists
+ * (the same point found on several bases) counts once.  Since keys depend
+ * only on a row,
  * the shards' candidate sets partition the unsharded one, and the merge of
  * their k-best lists equals the unsharded search bit for bit.  Ids must be
  * below 2^32 - 1.  1 <= k <= 32.  Asynchronous on `stream`. */

@@ -15,7 +15,7 @@ import ctypes
 from . import _lib
 from ._lib import OsannError, PATHS, STAGES, load
 
-__all__ = ["Index", "Server", "OsannError", "merge_topk", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
+__all__ = ["Index", "MultiIndex", "Server", "OsannError", "merge_topk", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
 
 
 def _torch():
@@ -105,18 +105,26 @@ def launch_count() -> int:
 class Index:
     """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
 
-    def __init__(self, data, L: int, stream=None, sync: bool = True):
+    def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None):
         """sync=False: osann_build_async (no synchronisation; call status()
-        before trusting results)."""
+        before trusting results).  rot: d x d float32 CUDA tensor, the basis
+        of the keys and query orders (osann_build_rot)."""
         torch = _torch()
         x = _dev_f32(data, "data")
         self.N, self.d = x.shape
         self.L = L
         self.device = x.device
         h = ctypes.c_void_p()
-        build = load().osann_build if sync else load().osann_build_async
         with torch.cuda.device(x.device):
-            _lib.check(build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
+            if rot is not None:
+                r = _dev_f32(rot, "rot")
+                if tuple(r.shape) != (self.d, self.d):
+                    raise ValueError("rot must be d x d")
+                _lib.check(load().osann_build_rot(_ptr(x), self.N, self.d, L, _ptr(r), 0 if sync else 1,
+                                                  _stream_ptr(stream), ctypes.byref(h)))
+            else:
+                build = load().osann_build if sync else load().osann_build_async
+                _lib.check(build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
         self._h = h
         # an asynchronous build may still be reading the input: keep it until status()
         self._src = None if sync else x
@@ -228,6 +236,46 @@ class Index:
             _lib.check(load().osann_info(self._h, None, None, None, None, ctypes.byref(mb)))
             self.max_bucket = mb.value
         return f.value
+
+
+class MultiIndex:
+    """R bases (Sec. 3-D, Algorithm 1 with R > 1): one rotated index per basis
+    (``rots``: R x d x d, basis 0 usually the identity), a search on each and
+    the merge of the per-basis k-best lists with repeated ids dropped.
+
+        mi = MultiIndex(X, L, datagen.rotations(4, d, seed))
+        ids, d2 = mi.search(Y, P, k)    # P cones per basis
+    """
+
+    def __init__(self, data, L: int, rots, stream=None, sync: bool = True):
+        torch = _torch()
+        x = _dev_f32(data, "data")
+        r = rots if isinstance(rots, torch.Tensor) else torch.as_tensor(rots)
+        r = r.to(device=x.device, dtype=torch.float32).contiguous()
+        self.R = r.shape[0]
+        self.rots = r
+        self.bases = [Index(x, L, stream=stream, sync=sync, rot=r[i]) for i in range(self.R)]
+        self.N, self.d, self.L = x.shape[0], x.shape[1], L
+
+    def search(self, queries, P: int, k: int, path: str = "auto", stream=None):
+        torch = _torch()
+        q = _dev_f32(queries, "queries")
+        Q = q.shape[0]
+        ids = torch.empty((self.R, Q, k), dtype=torch.int64, device=q.device)
+        d2 = torch.empty((self.R, Q, k), dtype=torch.float32, device=q.device)
+        for i, ix in enumerate(self.bases):
+            ix.search(q, P, k, path=path, stream=stream, out=(ids[i], d2[i]))
+        return merge_topk(ids, d2, stream=stream)
+
+    def status(self, stream=None) -> int:
+        f = 0
+        for ix in self.bases:
+            f |= ix.status(stream)
+        return f
+
+    def close(self):
+        for ix in self.bases:
+            ix.close()
 
 
 class Server:

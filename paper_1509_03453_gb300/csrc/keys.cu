@@ -289,6 +289,55 @@ __global__ void __launch_bounds__(128) query_order_kernel(const float* __restric
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_QUERY);
 }
 
+// Coordinates on a rotated basis (Sec. 3-D): out[i][r] = sum_j R[r][j] x_i[j],
+// accumulated in fp32 by fused multiply-adds in order j = 0, 1, ... from 0
+// (the order the keys' parity depends on).  A CTA takes ROT_ROWS rows; R is
+// held transposed in shared memory (lanes read consecutive outputs of one
+// column: no bank conflicts), the rows' inputs are broadcast.  d <= 128.
+constexpr int ROT_ROWS = 32;
+
+__global__ void __launch_bounds__(256) rotate_rows_kernel(const float* __restrict__ Rm, const float* __restrict__ X,
+                                                          int64_t n, int d, float* __restrict__ out)
+{
+    extern __shared__ float rsh[];
+    float* Rt = rsh;              // d x d, Rt[j * d + r] = R[r][j]
+    float* xt = rsh + d * d;      // ROT_ROWS x d
+    for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+        const int r = e / d, j = e - r * d;
+        Rt[j * d + r] = Rm[e];
+    }
+    for (int64_t base = int64_t(blockIdx.x) * ROT_ROWS; base < n; base += int64_t(gridDim.x) * ROT_ROWS) {
+        const int rows = n - base < ROT_ROWS ? int(n - base) : ROT_ROWS;
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * d; e += blockDim.x) xt[e] = X[base * d + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < rows * d; e += blockDim.x) {
+            const int i = e / d, r = e - i * d;
+            const float* x = xt + i * d;
+            float acc = 0.0f;
+            for (int j = 0; j < d; ++j) acc = fmaf(Rt[j * d + r], x[j], acc);
+            out[base * d + e] = acc;
+        }
+    }
+}
+
+int launch_rotate_rows(const float* Rm, const float* X, int64_t n, int d, float* out, cudaStream_t st, int num_sms)
+{
+    if (n == 0) return 0;
+    if (d > 128) return -2;  // the transposed basis must fit shared memory
+    const size_t smem = size_t(d) * d * 4 + size_t(ROT_ROWS) * d * 4;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(rotate_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(128 * 128 * 4 + ROT_ROWS * 128 * 4));
+        attr = true;
+    }
+    int64_t blocks = (n + ROT_ROWS - 1) / ROT_ROWS;
+    if (blocks > int64_t(num_sms) * 8) blocks = int64_t(num_sms) * 8;
+    rotate_rows_kernel<<<unsigned(blocks), 256, smem, st>>>(Rm, X, n, d, out);
+    return count_launch();
+}
+
 template <int LC>
 static void launch_keys_lc(bool vec, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d, int L,
                            const uint64_t* binom, uint32_t* keys, uint32_t* status, uint32_t* maxn2)

@@ -224,6 +224,7 @@ struct osann_index {
     bool tc_ready[2] = {false, false};
     alignas(64) unsigned char tmap[2][256];
     uint32_t* status = nullptr;   // [0] flags, [1] largest cone, [2] largest |x|^2 (bits)
+    float* rot = nullptr;         // d x d basis of the keys and query orders (null: the identity)
     unsigned long long* diag = nullptr;  // screening counters (survivors, fallbacks, checks, violations)
     uint64_t* binom = nullptr;
     float cdot2[2] = {0.f, 0.f}, cabs[2] = {0.f, 0.f}, Bn = 0.f;  // screening error-bound coefficients
@@ -319,7 +320,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT;
+    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, yrot;
     size_t total;
     int64_t max_items;
 };
@@ -416,6 +417,7 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         return o;
     };
     w.qorder = take(size_t(Q) * ix->d);
+    if (ix->rot) w.yrot = take(size_t(Q) * ix->d * 4);
     w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
     if (mode != MODE_PLAIN) {
@@ -546,8 +548,8 @@ int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_o
                               static_cast<cudaStream_t>(stream));
 }
 
-static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, bool async,
-                      osann_index** out)
+static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, void* stream,
+                      bool async, osann_index** out)
 {
     if (!out || !d_data || N < 1) {
         set_error("osann_build: invalid arguments (data=%p N=%lld out=%p)", (const void*)d_data, (long long)N,
@@ -617,7 +619,30 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, void
     cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
     {
         StageScope s(OSANN_STAGE_DATA_KEYS, st);
-        rc = launch_data_keys(d_data, N, d, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms);
+        // keys come from the rows' coordinates on the index's basis
+        const float* key_src = d_data;
+        float* xr = nullptr;
+        if (d_rot) {
+            if (d > 128) {
+                set_error("osann_build_rot: rotated bases need d <= 128");
+                rc = OSANN_ERR_UNSUPPORTED;
+            } else {
+                ix->rot = index_alloc<float>(ix, size_t(d) * d);
+                xr = static_cast<float*>(dev_alloc(size_t(N) * d * 4, st));
+                if (!ix->rot || !xr) {
+                    set_error("osann_build_rot: device allocation failed");
+                    rc = OSANN_ERR_OOM;
+                } else {
+                    cudaError_t e = cudaMemcpyAsync(ix->rot, d_rot, size_t(d) * d * 4, cudaMemcpyDeviceToDevice, st);
+                    rc = e != cudaSuccess ? cuda_fail(e, "osann_build_rot")
+                                          : launch_rotate_rows(ix->rot, d_data, N, d, xr, st, ix->num_sms);
+                    key_src = xr;
+                }
+            }
+        }
+        if (!rc)
+            rc = launch_data_keys(key_src, N, d, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms);
+        if (xr) dev_free(xr, size_t(N) * d * 4, st);
         if (!rc && tc_possible) rc = launch_tc_scale(1, ix->status + 2, ix->tcs + 4, st);
     }
     if (!rc) {
@@ -676,12 +701,18 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, void
 
 int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, stream, false, out);
+    return build_impl(d_data, N, d, L, nullptr, stream, false, out);
 }
 
 int osann_build_async(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, stream, true, out);
+    return build_impl(d_data, N, d, L, nullptr, stream, true, out);
+}
+
+int osann_build_rot(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, int32_t async,
+                    void* stream, osann_index** out)
+{
+    return build_impl(d_data, N, d, L, d_rot, stream, async != 0, out);
 }
 
 int osann_free(osann_index* index)
@@ -757,11 +788,18 @@ size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, 
 static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_eff, const WsLayout& L, char* w,
                        bool init_partial, bool transposed, int k, cudaStream_t st)
 {
-    int rc;
+    int rc = 0;
     {
         StageScope s(OSANN_STAGE_QUERY_ORDER, st);
-        rc = launch_query_order(Y, Q, ix->d, reinterpret_cast<uint8_t*>(w + L.qorder),
-                                reinterpret_cast<uint32_t*>(w + L.qsign), ix->status, st);
+        // on a rotated basis the magnitude order is that of the query's coordinates there
+        const float* Yk = Y;
+        if (ix->rot) {
+            rc = launch_rotate_rows(ix->rot, Y, Q, ix->d, reinterpret_cast<float*>(w + L.yrot), st, ix->num_sms);
+            Yk = reinterpret_cast<const float*>(w + L.yrot);
+        }
+        if (!rc)
+            rc = launch_query_order(Yk, Q, ix->d, reinterpret_cast<uint8_t*>(w + L.qorder),
+                                    reinterpret_cast<uint32_t*>(w + L.qsign), ix->status, st);
     }
     if (rc) return rc;
     StageScope s(OSANN_STAGE_PROBES, st);

@@ -1,10 +1,12 @@
 // Top-k merge of per-shard results (the exchange step of a row-sharded
-// search).  Cone keys depend only on a row, so a shard holding rows
-// [lo, hi) builds exactly the part of every cone that falls in its rows, and
-// a query probes the same cones on every shard; the union of the shards'
-// candidates is the unsharded candidate set, and the k best of the shards'
-// k-best lists (by distance, then global id) are the unsharded answer, bit
-// for bit (a pair's distance does not depend on the sharding).
+// search) and of per-basis results (multi-basis search, where one point can
+// come from several lists and counts once).  Cone keys depend only on a row,
+// so a shard holding rows [lo, hi) builds exactly the part of every cone that
+// falls in its rows, and a query probes the same cones on every shard; the
+// union of the shards' candidates is the unsharded candidate set, and the k
+// best of the shards' k-best lists (by distance, then global id) are the
+// unsharded answer, bit for bit (a pair's distance does not depend on the
+// sharding).
 #include "osann.h"
 #include "osann_device.cuh"
 #include "osann_launch.h"
@@ -30,7 +32,14 @@ __global__ void __launch_bounds__(128) merge_lists_kernel(const int64_t* __restr
         const int64_t id = ids[at];
         if (id < 0) continue;  // padding
         const uint64_t v = pack_di(d2[at], uint32_t(id));
-        if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
+        if (v < list[KMAX - 1]) {
+            // the same point from another list (another basis) is one candidate;
+            // copies held by other lanes leave together when extracted below
+            bool dup = false;
+#pragma unroll
+            for (int u = 0; u < KMAX; ++u) dup |= u >= KMAX - k && list[u] == v;  // live slots only
+            if (!dup) topk_insert<KMAX>(list, v);
+        }
     }
     for (int j = 0; j < k; ++j) {
         const uint64_t head = topk_head<KMAX>(list, k);
