@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 N_FULL, Q_FULL, D, L, K = 1_000_000, 10_000, 32, 2, 1
 P_LADDER = [64, 96, 128, 160, 192, 224, 256, 320, 384, 512]
+MB_LADDER = [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256]
 WORKLOAD = "gauss32: N=1,000,000 x d=32 data, Q=10,000 queries, iid N(0,1), L=2 (N_C=1984), k=1"
 METRIC = "queries/s at recall@1>=0.9"
 FP32_LANES_PER_SM = 128
@@ -267,6 +268,42 @@ def run_gpu(args):
     ms_step = float(ms_max.item())
     value = ws * Q_FULL / (ms_step / 1e3)
 
+    # multi-basis search (Sec. 3-D): R rotated indexes, P per basis the
+    # smallest of a ladder with recall@1 >= 0.9; step = R asynchronous builds
+    # + R searches + the duplicate-free merge, timed the same way
+    multi = []
+    if rank == 0 and ws == 1 and not args.no_multi:
+        from paper_1509_03453_gb300 import datagen
+        for R in (2, 4):
+            rots = torch.from_numpy(datagen.rotations(R, D, 6000 + R)).to(dev)
+            mi = osann.MultiIndex(Xd, L, rots)
+            Pm, recm = None, 0.0
+            for cand in MB_LADDER:
+                ids, d2 = mi.search(Yd, cand, K)
+                recm = recall1(ids.cpu().numpy(), d2.cpu().numpy(), gt_ids, gt_d2)
+                Pm = cand
+                if recm >= 0.9:
+                    break
+            mi.close()
+            mt = []
+            for i in range(args.warmup + args.steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                mi = osann.MultiIndex(Xd, L, rots, sync=False)
+                mi.search(Yd, Pm, K)
+                b.record(stream)
+                b.synchronize()
+                if mi.status() & 5:
+                    raise RuntimeError("multi-basis build reported an error status")
+                mi.close()
+                if i >= args.warmup:
+                    mt.append(a.elapsed_time(b))
+            mms = float(np.mean(mt))
+            multi.append({"R": R, "P_per_basis": Pm, "recall_at_1": round(recm, 4),
+                          "value": round(Q_FULL / (mms / 1e3), 1), "unit": "queries/s", "ms_per_step": round(mms, 4),
+                          "bases": "identity + seeded random rotations (QR of Gaussian, seed 6000 + R)"})
+
     # per-stage device times, from a separate pass (the stage events stay out
     # of the timed steps above)
     n_stat = max(3, args.steps // 2)
@@ -390,6 +427,7 @@ def run_gpu(args):
                        "p99": round(float(np.percentile(times, 99)), 4),
                        "note": "per batch step of Q queries"},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "multi_basis": multi,
         "screen": screen,
         "stage_launches_per_step": stage_n,
         "plain_fp32": {"value": round(Q_FULL / (np.mean(plain_times) / 1e3), 1), "unit": "queries/s",
@@ -615,6 +653,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16", "fp16"])
     ap.add_argument("--serving", action="store_true", help="the request-server workload (three resident indexes)")
+    ap.add_argument("--no-multi", action="store_true", help="skip the multi-basis (R > 1) measurement")
     ap.add_argument("--serve-requests", type=int, default=10_000,
                     help="requests of the serving workload (0: skip it in the default run)")
     ap.add_argument("--serve-slots", type=int, default=4)
