@@ -115,6 +115,16 @@ int osann_build(const float *d_data, int64_t N, int32_t d, int32_t L, void *stre
 int osann_build_rot(const float *d_data, int64_t N, int32_t d, int32_t L, const float *d_rot, int32_t async,
                     void *stream, osann_index **out);
 
+/* The PCA front-end of Sec. 4-B ("classify on the first PCA components,
+ * search on all"): as osann_build_rot with a projection on m <= d
+ * components, d_proj (m x d fp32, row r = axis r) and optional offsets d_off
+ * (m fp32, the projected mean; NULL: none): keys and query orders come from
+ * y_r = (sum_j d_proj[r][j] x_j) - d_off[r] (fp32 in-order fused
+ * multiply-adds, then one subtraction), so N_C = C(m, L) 2^L; distances use
+ * all d original components.  1 <= m <= d <= 128. */
+int osann_build_proj(const float *d_data, int64_t N, int32_t d, int32_t L, const float *d_proj, const float *d_off,
+                     int32_t m, int32_t async, void *stream, osann_index **out);
+
 /* As osann_build, without the final synchronisation (the paper has no
  * counterpart: for pipelines that build and search back to back).  The
  * index is usable at once in stream order on `stream`; its status bits

@@ -72,6 +72,12 @@ def lib():
             c.c_int64, c.c_int64, _i64p, _f64p]
         L.oracle_rotate.restype = None
         L.oracle_rotate.argtypes = [_f32p, _f32p, c.c_int64, c.c_int, _f32p]
+        L.oracle_project.restype = None
+        L.oracle_project.argtypes = [_f32p, c.c_void_p, _f32p, c.c_int64, c.c_int, c.c_int, _f32p]
+        L.oracle_search_multi_proj.restype = None
+        L.oracle_search_multi_proj.argtypes = [
+            _f32p, c.c_int64, c.c_int, c.c_int, c.c_int, c.c_int, _f32p, c.c_void_p, _u32p, _u32p, _f32p,
+            c.c_int64, c.c_int64, c.c_int, _i64p, _f64p, c.c_void_p]
         L.oracle_search_multi.restype = None
         L.oracle_search_multi.argtypes = [
             _f32p, c.c_int64, c.c_int, c.c_int, c.c_int, _f32p, _u32p, _u32p, _f32p, c.c_int64,
@@ -176,21 +182,37 @@ def rotate(Rm, X) -> np.ndarray:
     return out
 
 
-class MultiIndex:
-    """Oracle index over R bases: per basis, keys of the rotated rows and a
-    stable counting sort; the search visits the bases' cones in Algorithm 1's
-    order with the "analyzed" flag."""
+def project(Pm, X, off=None) -> np.ndarray:
+    """Rows of X projected on the m rows of Pm minus off (fp32, in-order FMAs,
+    one final subtraction)."""
+    Pm, X = _f32(Pm), _f32(X)
+    m = Pm.shape[0]
+    n, d = X.shape
+    out = np.empty((n, m), np.float32)
+    o = None if off is None else _f32(off)
+    lib().oracle_project(Pm, None if o is None else o.ctypes.data_as(ctypes.c_void_p), X, n, d, m, out)
+    return out
 
-    def __init__(self, X, L: int, rots):
+
+class MultiIndex:
+    """Oracle index over R bases: per basis, keys of the rows' coordinates on
+    the basis (R x m x d, m <= d: a projection, with optional offsets R x m)
+    and a stable counting sort; the search visits the bases' cones in
+    Algorithm 1's order with the "analyzed" flag."""
+
+    def __init__(self, X, L: int, rots, offsets=None):
         self.X = _f32(X)
         self.N, self.d = self.X.shape
         self.L = L
-        self.rots = _f32(np.asarray(rots).reshape(-1, self.d, self.d))
-        self.R = self.rots.shape[0]
-        self.NC = num_cones(self.d, L)
+        r = np.asarray(rots, np.float32)
+        self.rots = _f32(r.reshape(-1, r.shape[-2], self.d))
+        self.R, self.m = self.rots.shape[0], self.rots.shape[1]
+        self.off = None if offsets is None else _f32(np.asarray(offsets, np.float32).reshape(self.R, self.m))
+        self.NC = num_cones(self.m, L)
         offs, perms = [], []
-        for r in range(self.R):
-            o, p = buckets(keys(rotate(self.rots[r], self.X), L), self.NC)
+        for b in range(self.R):
+            ob = None if self.off is None else self.off[b]
+            o, p = buckets(keys(project(self.rots[b], self.X, ob), L), self.NC)
             offs.append(o)
             perms.append(p)
         self.offsets = np.ascontiguousarray(np.stack(offs), np.uint32)
@@ -202,9 +224,10 @@ class MultiIndex:
         ids = np.empty(Q * k, np.int64)
         dists = np.empty(Q * k, np.float64)
         counts = np.empty(Q, np.int64) if want_counts else None
-        lib().oracle_search_multi(self.X, self.N, self.d, self.L, self.R, self.rots, self.offsets, self.perms,
-                                  Y, Q, P, k, ids, dists,
-                                  counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+        lib().oracle_search_multi_proj(
+            self.X, self.N, self.d, self.L, self.R, self.m, self.rots,
+            None if self.off is None else self.off.ctypes.data_as(ctypes.c_void_p), self.offsets, self.perms,
+            Y, Q, P, k, ids, dists, counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
         ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
         return (ids, dists, counts) if want_counts else (ids, dists)
 

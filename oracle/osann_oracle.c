@@ -31,8 +31,11 @@
  *   - the coordinates of x on basis r are y_i = sum_j R_r[i][j] x_j, each
  *     accumulated in fp32 by fused multiply-adds in order j = 0, 1, ...
  *     (the rotated coordinates only decide integers -- keys and query
- *     orders -- so both sides compute them in the same fp32 order);
- *     distances always use the original vectors.
+ *     orders -- so both sides compute them in the same fp32 order); a
+ *     projection on m < d components (the PCA front-end of Sec. 4-B) keeps
+ *     the first m rows of the basis and subtracts an offset c_i (the
+ *     projected mean) in one final fp32 subtraction; distances always use the
+ *     original vectors.
  * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
  * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
  * The intra-class probe order and the sign-flip extension are this
@@ -347,6 +350,25 @@ void oracle_rotate(const float *Rm, const float *X, int64_t n, int d, float *out
         }
 }
 
+/* Projection on m <= d components (Sec. 4-B, PCA front-end): out[i][r] =
+ * (sum_j Pm[r][j] X[i][j]) - off[r], the sum in fp32 fused multiply-adds in
+ * order j = 0..d-1 from 0, then one fp32 subtraction (off may be NULL: no
+ * offset).  Pm: m x d row-major. */
+void oracle_project(const float *Pm, const float *off, const float *X, int64_t n, int d, int m, float *out)
+{
+    for (int64_t i = 0; i < n; ++i)
+        for (int r = 0; r < m; ++r) {
+            float acc = 0.0f;
+            for (int j = 0; j < d; ++j) acc = fmaf(Pm[(int64_t)r * d + j], X[i * d + j], acc);
+            out[i * m + r] = off ? acc - off[r] : acc;
+        }
+}
+
+void oracle_search_multi_proj(const float *X, int64_t N, int d, int L, int R, int m, const float *projs,
+                              const float *projoff, const uint32_t *offsets, const uint32_t *perms,
+                              const float *Y, int64_t Q, int64_t P, int k, int64_t *ids, double *dists,
+                              int64_t *cand_count);
+
 /* Search over R bases (Algorithm 1): basis r has its own cone index
  * (offsets_r, perm_r, built from the rotated data) and its own probe list,
  * made from the query's coordinates on that basis.  Cones are visited in
@@ -358,7 +380,18 @@ void oracle_search_multi(const float *X, int64_t N, int d, int L, int R, const f
                          const uint32_t *offsets, const uint32_t *perms, const float *Y, int64_t Q,
                          int64_t P, int k, int64_t *ids, double *dists, int64_t *cand_count)
 {
-    int64_t NC = oracle_num_cones(d, L);
+    oracle_search_multi_proj(X, N, d, L, R, d, rots, NULL, offsets, perms, Y, Q, P, k, ids, dists, cand_count);
+}
+
+/* As oracle_search_multi, on R projections of m components each (m x d
+ * matrices projs, offsets projoff R x m or NULL): keys and probes on the m
+ * projected coordinates (N_C = C(m, G) 2^G), distances on the d originals. */
+void oracle_search_multi_proj(const float *X, int64_t N, int d, int L, int R, int m, const float *projs,
+                              const float *projoff, const uint32_t *offsets, const uint32_t *perms,
+                              const float *Y, int64_t Q, int64_t P, int k, int64_t *ids, double *dists,
+                              int64_t *cand_count)
+{
+    int64_t NC = oracle_num_cones(m, L);
     if (P > NC) P = NC;
     uint32_t *probes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(R * (P > 0 ? P : 1)));
     int64_t *np = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
@@ -371,8 +404,8 @@ void oracle_search_multi(const float *X, int64_t N, int d, int L, int R, const f
         int64_t *bi = ids + q * k;
         topk_init(bd, bi, k);
         for (int r = 0; r < R; ++r) {
-            oracle_rotate(rots + (int64_t)r * d * d, y, 1, d, yr);
-            np[r] = oracle_probes(yr, d, L, P, probes + (int64_t)r * P);
+            oracle_project(projs + (int64_t)r * m * d, projoff ? projoff + (int64_t)r * m : NULL, y, 1, d, m, yr);
+            np[r] = oracle_probes(yr, m, L, P, probes + (int64_t)r * P);
         }
         int64_t nt = 0;
         for (int64_t l = 0; l < P; ++l)

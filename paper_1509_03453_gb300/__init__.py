@@ -105,10 +105,12 @@ def launch_count() -> int:
 class Index:
     """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
 
-    def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None):
+    def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None, rot_offset=None):
         """sync=False: osann_build_async (no synchronisation; call status()
-        before trusting results).  rot: d x d float32 CUDA tensor, the basis
-        of the keys and query orders (osann_build_rot)."""
+        before trusting results).  rot: d x d (a rotated basis,
+        osann_build_rot) or m x d (a projection on m components, e.g. PCA
+        axes, osann_build_proj) float32 CUDA tensor, the basis of the keys and
+        query orders; rot_offset: m offsets subtracted after projecting."""
         torch = _torch()
         x = _dev_f32(data, "data")
         self.N, self.d = x.shape
@@ -118,10 +120,16 @@ class Index:
         with torch.cuda.device(x.device):
             if rot is not None:
                 r = _dev_f32(rot, "rot")
-                if tuple(r.shape) != (self.d, self.d):
-                    raise ValueError("rot must be d x d")
-                _lib.check(load().osann_build_rot(_ptr(x), self.N, self.d, L, _ptr(r), 0 if sync else 1,
-                                                  _stream_ptr(stream), ctypes.byref(h)))
+                if r.shape[1] != self.d or not 1 <= r.shape[0] <= self.d:
+                    raise ValueError("rot must be m x d with 1 <= m <= d")
+                off = None
+                if rot_offset is not None:
+                    off = rot_offset.to(device=x.device, dtype=torch.float32).contiguous().reshape(-1)
+                    if off.numel() != r.shape[0]:
+                        raise ValueError("rot_offset must hold m values")
+                self._basis = (r, off)  # read by the build in stream order
+                _lib.check(load().osann_build_proj(_ptr(x), self.N, self.d, L, _ptr(r), _ptr(off), r.shape[0],
+                                                   0 if sync else 1, _stream_ptr(stream), ctypes.byref(h)))
             else:
                 build = load().osann_build if sync else load().osann_build_async
                 _lib.check(build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
@@ -247,14 +255,21 @@ class MultiIndex:
         ids, d2 = mi.search(Y, P, k)    # P cones per basis
     """
 
-    def __init__(self, data, L: int, rots, stream=None, sync: bool = True):
+    def __init__(self, data, L: int, rots, stream=None, sync: bool = True, offsets=None):
         torch = _torch()
         x = _dev_f32(data, "data")
         r = rots if isinstance(rots, torch.Tensor) else torch.as_tensor(rots)
         r = r.to(device=x.device, dtype=torch.float32).contiguous()
+        if r.dim() == 2:
+            r = r.unsqueeze(0)
+        o = None
+        if offsets is not None:
+            o = offsets if isinstance(offsets, torch.Tensor) else torch.as_tensor(offsets)
+            o = o.to(device=x.device, dtype=torch.float32).reshape(r.shape[0], r.shape[1]).contiguous()
         self.R = r.shape[0]
         self.rots = r
-        self.bases = [Index(x, L, stream=stream, sync=sync, rot=r[i]) for i in range(self.R)]
+        self.bases = [Index(x, L, stream=stream, sync=sync, rot=r[i], rot_offset=None if o is None else o[i])
+                      for i in range(self.R)]
         self.N, self.d, self.L = x.shape[0], x.shape[1], L
 
     def search(self, queries, P: int, k: int, path: str = "auto", stream=None):

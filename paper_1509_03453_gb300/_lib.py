@@ -42,6 +42,8 @@ SIGNATURES = {
                                     c.POINTER(c.c_void_p)]),
     "osann_build_rot": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_int32,
                                   c.c_void_p, c.POINTER(c.c_void_p)]),
+    "osann_build_proj": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p,
+                                   c.c_int32, c.c_int32, c.c_void_p, c.POINTER(c.c_void_p)]),
     "osann_free": (c.c_int, [c.c_void_p]),
     "osann_info": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
                              c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),

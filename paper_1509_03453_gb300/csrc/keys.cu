@@ -289,43 +289,47 @@ __global__ void __launch_bounds__(128) query_order_kernel(const float* __restric
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_NONFINITE_QUERY);
 }
 
-// Coordinates on a rotated basis (Sec. 3-D): out[i][r] = sum_j R[r][j] x_i[j],
-// accumulated in fp32 by fused multiply-adds in order j = 0, 1, ... from 0
-// (the order the keys' parity depends on).  A CTA takes ROT_ROWS rows; R is
-// held transposed in shared memory (lanes read consecutive outputs of one
-// column: no bank conflicts), the rows' inputs are broadcast.  d <= 128.
+// Coordinates on a rotated basis (Sec. 3-D) or a projection on m <= d
+// components (Sec. 4-B): out[i][r] = (sum_j P[r][j] x_i[j]) - off[r],
+// the sum in fp32 fused multiply-adds in order j = 0, 1, ... from 0, then one
+// subtraction (off may be null) -- the order the keys' parity depends on.
+// A CTA takes ROT_ROWS rows; P is held transposed in shared memory (lanes
+// read consecutive outputs of one column: no bank conflicts), the rows'
+// inputs are broadcast.  d <= 128.
 constexpr int ROT_ROWS = 32;
 
-__global__ void __launch_bounds__(256) rotate_rows_kernel(const float* __restrict__ Rm, const float* __restrict__ X,
-                                                          int64_t n, int d, float* __restrict__ out)
+__global__ void __launch_bounds__(256) rotate_rows_kernel(const float* __restrict__ Pm, const float* __restrict__ off,
+                                                          const float* __restrict__ X, int64_t n, int d, int m,
+                                                          float* __restrict__ out)
 {
     extern __shared__ float rsh[];
-    float* Rt = rsh;              // d x d, Rt[j * d + r] = R[r][j]
-    float* xt = rsh + d * d;      // ROT_ROWS x d
-    for (int e = threadIdx.x; e < d * d; e += blockDim.x) {
+    float* Pt = rsh;              // d x m, Pt[j * m + r] = P[r][j]
+    float* xt = rsh + d * m;      // ROT_ROWS x d
+    for (int e = threadIdx.x; e < m * d; e += blockDim.x) {
         const int r = e / d, j = e - r * d;
-        Rt[j * d + r] = Rm[e];
+        Pt[j * m + r] = Pm[e];
     }
     for (int64_t base = int64_t(blockIdx.x) * ROT_ROWS; base < n; base += int64_t(gridDim.x) * ROT_ROWS) {
         const int rows = n - base < ROT_ROWS ? int(n - base) : ROT_ROWS;
         __syncthreads();
         for (int e = threadIdx.x; e < rows * d; e += blockDim.x) xt[e] = X[base * d + e];
         __syncthreads();
-        for (int e = threadIdx.x; e < rows * d; e += blockDim.x) {
-            const int i = e / d, r = e - i * d;
+        for (int e = threadIdx.x; e < rows * m; e += blockDim.x) {
+            const int i = e / m, r = e - i * m;
             const float* x = xt + i * d;
             float acc = 0.0f;
-            for (int j = 0; j < d; ++j) acc = fmaf(Rt[j * d + r], x[j], acc);
-            out[base * d + e] = acc;
+            for (int j = 0; j < d; ++j) acc = fmaf(Pt[j * m + r], x[j], acc);
+            out[base * m + e] = off ? acc - off[r] : acc;
         }
     }
 }
 
-int launch_rotate_rows(const float* Rm, const float* X, int64_t n, int d, float* out, cudaStream_t st, int num_sms)
+int launch_rotate_rows(const float* Pm, const float* off, const float* X, int64_t n, int d, int m, float* out,
+                       cudaStream_t st, int num_sms)
 {
     if (n == 0) return 0;
-    if (d > 128) return -2;  // the transposed basis must fit shared memory
-    const size_t smem = size_t(d) * d * 4 + size_t(ROT_ROWS) * d * 4;
+    if (d > 128 || m < 1 || m > d) return -2;  // the transposed basis must fit shared memory
+    const size_t smem = size_t(d) * m * 4 + size_t(ROT_ROWS) * d * 4;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(rotate_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -334,7 +338,34 @@ int launch_rotate_rows(const float* Rm, const float* X, int64_t n, int d, float*
     }
     int64_t blocks = (n + ROT_ROWS - 1) / ROT_ROWS;
     if (blocks > int64_t(num_sms) * 8) blocks = int64_t(num_sms) * 8;
-    rotate_rows_kernel<<<unsigned(blocks), 256, smem, st>>>(Rm, X, n, d, out);
+    rotate_rows_kernel<<<unsigned(blocks), 256, smem, st>>>(Pm, off, X, n, d, m, out);
+    return count_launch();
+}
+
+// Largest squared row norm of X (fp32 sums, any order: it only sizes the fp16
+// scale and a norm bound, both with slack), as float bits for atomicMax.
+__global__ void __launch_bounds__(256) row_norm_max_kernel(const float* __restrict__ X, int64_t n, int d,
+                                                           uint32_t* __restrict__ maxn2_bits)
+{
+    float best = 0.0f;
+    const int64_t stride = int64_t(gridDim.x) * blockDim.x;
+    for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < n; row += stride) {
+        const float* x = X + row * d;
+        float s = 0.0f;
+        for (int j = 0; j < d; ++j) s = fmaf(x[j], x[j], s);
+        best = fmaxf(best, s);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, o));
+    if ((threadIdx.x & 31) == 0 && best > 0.0f && finite_f(best)) atomicMax(maxn2_bits, __float_as_uint(best));
+}
+
+int launch_row_norm_max(const float* X, int64_t n, int d, uint32_t* maxn2_bits, cudaStream_t st, int num_sms)
+{
+    if (n == 0) return 0;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > int64_t(num_sms) * 8) blocks = int64_t(num_sms) * 8;
+    row_norm_max_kernel<<<unsigned(blocks), 256, 0, st>>>(X, n, d, maxn2_bits);
     return count_launch();
 }
 

@@ -224,7 +224,9 @@ struct osann_index {
     bool tc_ready[2] = {false, false};
     alignas(64) unsigned char tmap[2][256];
     uint32_t* status = nullptr;   // [0] flags, [1] largest cone, [2] largest |x|^2 (bits)
-    float* rot = nullptr;         // d x d basis of the keys and query orders (null: the identity)
+    float* rot = nullptr;         // dk x d basis of the keys and query orders (null: the identity)
+    float* rot_off = nullptr;     // dk offsets subtracted from the projected coordinates (null: none)
+    int dk = 0;                   // key coordinates: d, or m for a projection
     unsigned long long* diag = nullptr;  // screening counters (survivors, fallbacks, checks, violations)
     uint64_t* binom = nullptr;
     float cdot2[2] = {0.f, 0.f}, cabs[2] = {0.f, 0.f}, Bn = 0.f;  // screening error-bound coefficients
@@ -416,8 +418,8 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         off = al256(off + bytes);
         return o;
     };
-    w.qorder = take(size_t(Q) * ix->d);
-    if (ix->rot) w.yrot = take(size_t(Q) * ix->d * 4);
+    w.qorder = take(size_t(Q) * ix->dk);
+    if (ix->rot) w.yrot = take(size_t(Q) * ix->dk * 4);
     w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
     if (mode != MODE_PLAIN) {
@@ -548,16 +550,21 @@ int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_o
                               static_cast<cudaStream_t>(stream));
 }
 
-static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, void* stream,
-                      bool async, osann_index** out)
+static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, const float* d_off,
+                      int32_t m, void* stream, bool async, osann_index** out)
 {
+    if (!d_rot) m = d;
+    if (d_rot && (m < 1 || m > d || d > 128)) {
+        set_error("osann_build_proj: need 1 <= m <= d <= 128 (m=%d d=%d)", m, d);
+        return OSANN_ERR_INVALID;
+    }
     if (!out || !d_data || N < 1) {
         set_error("osann_build: invalid arguments (data=%p N=%lld out=%p)", (const void*)d_data, (long long)N,
                   (void*)out);
         return OSANN_ERR_INVALID;
     }
     *out = nullptr;
-    const int64_t NC = cones_or_error(d, L);
+    const int64_t NC = cones_or_error(m, L);
     if (NC < 0) {
         set_error("osann_build: unsupported (d=%d, L=%d): need 1<=d<=%d, 1<=L<=min(d,%d), N_C < 2^31", d, L, MAX_D,
                   MAX_L);
@@ -575,6 +582,7 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     ix->N = N;
     ix->NC = NC;
     ix->d = d;
+    ix->dk = m;
     ix->d_pad = pad_dim(d);
     ix->L = L;
     ix->stream = st;
@@ -623,26 +631,30 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         const float* key_src = d_data;
         float* xr = nullptr;
         if (d_rot) {
-            if (d > 128) {
-                set_error("osann_build_rot: rotated bases need d <= 128");
-                rc = OSANN_ERR_UNSUPPORTED;
+            ix->rot = index_alloc<float>(ix, size_t(m) * d);
+            if (d_off) ix->rot_off = index_alloc<float>(ix, size_t(m));
+            xr = static_cast<float*>(dev_alloc(size_t(N) * m * 4, st));
+            if (!ix->rot || (d_off && !ix->rot_off) || !xr) {
+                set_error("osann_build_proj: device allocation failed");
+                rc = OSANN_ERR_OOM;
             } else {
-                ix->rot = index_alloc<float>(ix, size_t(d) * d);
-                xr = static_cast<float*>(dev_alloc(size_t(N) * d * 4, st));
-                if (!ix->rot || !xr) {
-                    set_error("osann_build_rot: device allocation failed");
-                    rc = OSANN_ERR_OOM;
-                } else {
-                    cudaError_t e = cudaMemcpyAsync(ix->rot, d_rot, size_t(d) * d * 4, cudaMemcpyDeviceToDevice, st);
-                    rc = e != cudaSuccess ? cuda_fail(e, "osann_build_rot")
-                                          : launch_rotate_rows(ix->rot, d_data, N, d, xr, st, ix->num_sms);
-                    key_src = xr;
-                }
+                cudaError_t e = cudaMemcpyAsync(ix->rot, d_rot, size_t(m) * d * 4, cudaMemcpyDeviceToDevice, st);
+                if (e == cudaSuccess && d_off)
+                    e = cudaMemcpyAsync(ix->rot_off, d_off, size_t(m) * 4, cudaMemcpyDeviceToDevice, st);
+                rc = e != cudaSuccess ? cuda_fail(e, "osann_build_proj")
+                                      : launch_rotate_rows(ix->rot, ix->rot_off, d_data, N, d, m, xr, st, ix->num_sms);
+                key_src = xr;
             }
         }
         if (!rc)
-            rc = launch_data_keys(key_src, N, d, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms);
-        if (xr) dev_free(xr, size_t(N) * d * 4, st);
+            rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms);
+        // the fp16 scale and the norm bound need the original rows' norms, which
+        // a projection or an offset does not keep
+        if (!rc && d_rot && (m < d || d_off)) {
+            cudaMemsetAsync(ix->status + 2, 0, 4, st);
+            rc = launch_row_norm_max(d_data, N, d, ix->status + 2, st, ix->num_sms);
+        }
+        if (xr) dev_free(xr, size_t(N) * m * 4, st);
         if (!rc && tc_possible) rc = launch_tc_scale(1, ix->status + 2, ix->tcs + 4, st);
     }
     if (!rc) {
@@ -701,18 +713,32 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
 
 int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, nullptr, stream, false, out);
+    return build_impl(d_data, N, d, L, nullptr, nullptr, d, stream, false, out);
 }
 
 int osann_build_async(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, nullptr, stream, true, out);
+    return build_impl(d_data, N, d, L, nullptr, nullptr, d, stream, true, out);
 }
 
 int osann_build_rot(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, int32_t async,
                     void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, d_rot, stream, async != 0, out);
+    if (!d_rot) {
+        set_error("osann_build_rot: null basis");
+        return OSANN_ERR_INVALID;
+    }
+    return build_impl(d_data, N, d, L, d_rot, nullptr, d, stream, async != 0, out);
+}
+
+int osann_build_proj(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_proj, const float* d_off,
+                     int32_t m, int32_t async, void* stream, osann_index** out)
+{
+    if (!d_proj) {
+        set_error("osann_build_proj: null projection");
+        return OSANN_ERR_INVALID;
+    }
+    return build_impl(d_data, N, d, L, d_proj, d_off, m, stream, async != 0, out);
 }
 
 int osann_free(osann_index* index)
@@ -794,16 +820,17 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
         // on a rotated basis the magnitude order is that of the query's coordinates there
         const float* Yk = Y;
         if (ix->rot) {
-            rc = launch_rotate_rows(ix->rot, Y, Q, ix->d, reinterpret_cast<float*>(w + L.yrot), st, ix->num_sms);
+            rc = launch_rotate_rows(ix->rot, ix->rot_off, Y, Q, ix->d, ix->dk, reinterpret_cast<float*>(w + L.yrot), st,
+                                    ix->num_sms);
             Yk = reinterpret_cast<const float*>(w + L.yrot);
         }
         if (!rc)
-            rc = launch_query_order(Yk, Q, ix->d, reinterpret_cast<uint8_t*>(w + L.qorder),
+            rc = launch_query_order(Yk, Q, ix->dk, reinterpret_cast<uint8_t*>(w + L.qorder),
                                     reinterpret_cast<uint32_t*>(w + L.qsign), ix->status, st);
     }
     if (rc) return rc;
     StageScope s(OSANN_STAGE_PROBES, st);
-    return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Q, ix->d,
+    return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Q, ix->dk,
                          ix->L, P_eff, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
                          transposed ? reinterpret_cast<uint32_t*>(w + L.probesT) : nullptr,
                          init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st);

@@ -22,9 +22,12 @@ int64_t launch_total();
 // keys.cu
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
                      uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms);  // maxn2 may be null
-// out = rows of X on the basis Rm (d x d, row r = basis vector r), fp32
-// in-order FMAs; d <= 128 (else -2)
-int launch_rotate_rows(const float* Rm, const float* X, int64_t n, int d, float* out, cudaStream_t st, int num_sms);
+// out (n x m) = rows of X on the m basis rows of Pm (m x d) minus off (null:
+// none), fp32 in-order FMAs then one subtraction; d <= 128, m <= d (else -2)
+int launch_rotate_rows(const float* Pm, const float* off, const float* X, int64_t n, int d, int m, float* out,
+                       cudaStream_t st, int num_sms);
+// atomicMax of the largest squared row norm into *maxn2_bits
+int launch_row_norm_max(const float* X, int64_t n, int d, uint32_t* maxn2_bits, cudaStream_t st, int num_sms);
 int launch_query_order(const float* Y, int64_t Q, int d, uint8_t* qorder, uint32_t* qsign, uint32_t* status,
                        cudaStream_t st);
 

@@ -73,3 +73,29 @@ def test_merge_drops_repeated_points(osann):
     m_ids, m_d = osann.merge_topk(ids, d)
     assert to_np(m_ids).tolist() == [[0, 5, 7]]
     assert to_np(m_d).tolist() == [[0.0, 1.0, 2.0]]
+
+
+@pytest.mark.parametrize("d,m,L,P,k", [(64, 16, 3, 24, 4), (128, 16, 3, 32, 10), (40, 9, 2, 8, 1)])
+def test_pca_front_end_matches_oracle(osann, d, m, L, P, k):
+    from paper_1509_03453_gb300.pca import pca_basis
+    rng = np.random.default_rng(200 + d)
+    A = rng.standard_normal((d, d)).astype(np.float32)
+    X = (rng.standard_normal((30_000, d)).astype(np.float32) @ A) + 3.0
+    Y = (rng.standard_normal((300, d)).astype(np.float32) @ A) + 3.0
+    X, Y = X.astype(np.float32), Y.astype(np.float32)
+    axes, off = pca_basis(X, m, seed=2)
+    ix = osann.Index(to_dev(X), L, rot=to_dev(axes), rot_offset=to_dev(off))
+    om = oracle.MultiIndex(X, L, axes[None], off[None])
+    assert ix.NC == oracle.num_cones(m, L)
+    keys, offs, perm = (to_np(t) for t in ix.export())
+    assert np.array_equal(keys, oracle.keys(oracle.project(axes, X, off), L))
+    assert np.array_equal(offs, om.offsets[0])
+    assert np.array_equal(perm, om.perms[0])
+    ids, d2 = ix.search(to_dev(Y), P, k)
+    oids, od = om.search(Y, P, k)
+    assert_knn_match(X, Y, to_np(ids), to_np(d2), oids, od)
+    for path in ("plain", "batched", "fp16"):
+        pi, pd = ix.search(to_dev(Y), P, k, path=path)
+        assert np.array_equal(to_np(pi), to_np(ids))
+        assert np.array_equal(to_np(pd).view(np.uint32), to_np(d2).view(np.uint32))
+    ix.close()

@@ -97,3 +97,36 @@ def test_more_bases_never_lose_the_best_candidate():
         if prev is not None:
             assert np.all(dist[:, 0] <= prev)
         prev = dist[:, 0]
+
+
+def test_projection_selects_and_offsets_exactly():
+    X = np.random.default_rng(60).standard_normal((300, 20)).astype(np.float32)
+    m = 7
+    Pm = np.eye(20, dtype=np.float32)[:m]
+    off = np.random.default_rng(61).standard_normal(m).astype(np.float32)
+    assert np.array_equal(oracle.project(Pm, X), X[:, :m])
+    assert np.array_equal(oracle.project(Pm, X, off), (X[:, :m] - off).astype(np.float32))
+
+
+def test_projected_multibasis_is_exact_topk_over_union():
+    from paper_1509_03453_gb300.pca import pca_basis
+    d, m, L, P, k = 24, 8, 2, 6, 3
+    rng = np.random.default_rng(70)
+    # correlated data: a few strong directions
+    X = (rng.standard_normal((3000, d)) @ rng.standard_normal((d, d))).astype(np.float32)
+    Y = (rng.standard_normal((30, d)) @ rng.standard_normal((d, d))).astype(np.float32)
+    axes, off = pca_basis(X, m, seed=1)
+    assert np.allclose(axes.astype(np.float64) @ axes.T.astype(np.float64), np.eye(m), atol=1e-5)
+    mi = oracle.MultiIndex(X, L, axes[None], off[None])
+    assert mi.NC == oracle.num_cones(m, L)
+    ids, dist, cnt = mi.search(Y, P, k, want_counts=True)
+    Xp = oracle.project(axes, X, off)
+    keys = oracle.keys(Xp, L)
+    for q in range(Y.shape[0]):
+        yp = oracle.project(axes, Y[q:q + 1], off)[0]
+        cones = set(int(c) for c in oracle.probes(yp, L, P))
+        u = np.array([n for n in range(X.shape[0]) if int(keys[n]) in cones], np.int64)
+        assert cnt[q] == len(u)
+        dd = ((X[u].astype(np.float64) - Y[q].astype(np.float64)) ** 2).sum(1)
+        order = np.lexsort((u, dd))[:k]
+        assert np.array_equal(ids[q, :len(order)], u[order])
