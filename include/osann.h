@@ -291,8 +291,9 @@ int osann_merge_topk(const int64_t *d_ids, const float *d_sqdists, int32_t G, in
  * bytes hold when mem_budget > 0 (OSANN_ERR_OOM when it holds none).  With
  * use_graphs, a batch is a CUDA graph replay (one graph per slot, index and
  * batch-size bucket 64, 128, ... max_batch, captured on first use, the batch
- * padded to its bucket).  Every query's result equals that of osann_search
- * with the index's P and k, bit for bit, whatever batch it ran in. */
+ * padded to its bucket with zero queries whose results are dropped).
+ * Every query's result equals that of osann_search with the index's P and
+ * k, bit for bit, whatever batch it ran in. */
 typedef struct osann_server osann_server;
 
 /* indexes[n_indexes] must outlive the server; P[i], k[i] (1..32) are index
@@ -323,6 +324,15 @@ int osann_server_pending(const osann_server *server, int64_t *waiting_queries, i
  * fastest.  out_choices (nullable) receives (path, group) per (index,
  * bucket).  Call with no request in the server. */
 int osann_server_tune(osann_server *server, int32_t reps, int32_t *out_choices);
+/* As osann_server_tune, timing each index i on the caller's sample queries
+ * d_queries[i] (n_queries[i] rows, device; a NULL entry: rows of the index),
+ * which tunes for the query distribution actually served. */
+int osann_server_tune_queries(osann_server *server, const float *const *d_queries, const int64_t *n_queries,
+                              int32_t reps, int32_t *out_choices);
+/* Run every slot, index and batch bucket once (capturing the graphs when
+ * they are on), so that no capture happens while serving.  Call after
+ * osann_server_tune (tuning drops the graphs) with no request in flight. */
+int osann_server_warmup(osann_server *server);
 /* Batch buckets in use (returns their count; writes up to max_out). */
 int osann_server_buckets(const osann_server *server, int64_t *out, int32_t max_out);
 /* Counters since creation: batches run, queries run (padding excluded),

@@ -326,15 +326,26 @@ class Server:
         n = load().osann_server_buckets(self._h, out, 64)
         return [int(out[i]) for i in range(n)]
 
-    def tune(self, reps: int = 3):
-        """Autotune (path, group) per (index, bucket); returns the choices."""
+    def tune(self, reps: int = 3, queries=None):
+        """Autotune (path, group) per (index, bucket); returns the choices.
+        queries: optional list (per index) of sample query tensors."""
         nb = len(self.buckets())
         n = len(self.indexes)
         out = (ctypes.c_int32 * (2 * n * nb))()
-        _lib.check(load().osann_server_tune(self._h, reps, out))
+        if queries is None:
+            _lib.check(load().osann_server_tune(self._h, reps, out))
+        else:
+            qs = [None if q is None else _dev_f32(q, "queries") for q in queries]
+            ptrs = (ctypes.c_void_p * n)(*[None if q is None else q.data_ptr() for q in qs])
+            cnt = (ctypes.c_int64 * n)(*[0 if q is None else q.shape[0] for q in qs])
+            _lib.check(load().osann_server_tune_queries(self._h, ptrs, cnt, reps, out))
         names = {v: k for k, v in PATHS.items()}
         return [[(names[out[2 * (i * nb + b)]], int(out[2 * (i * nb + b) + 1])) for b in range(nb)]
                 for i in range(n)]
+
+    def warmup(self):
+        """Capture every (slot, index, bucket) graph now rather than while serving."""
+        _lib.check(load().osann_server_warmup(self._h))
 
     def submit(self, index: int, queries, out=None) -> int:
         torch = _torch()

@@ -82,7 +82,10 @@ SIGNATURES = {
                                         c.POINTER(c.c_int32)]),
     "osann_server_pending": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32)]),
     "osann_server_tune": (c.c_int, [c.c_void_p, c.c_int32, c.POINTER(c.c_int32)]),
+    "osann_server_tune_queries": (c.c_int, [c.c_void_p, c.POINTER(c.c_void_p), c.POINTER(c.c_int64), c.c_int32,
+                                            c.POINTER(c.c_int32)]),
     "osann_server_buckets": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.c_int32]),
+    "osann_server_warmup": (c.c_int, [c.c_void_p]),
     "osann_server_free": (c.c_int, [c.c_void_p]),
     "osann_server_stats": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64)]),
     "osann_merge_topk": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int32, c.c_int64, c.c_int32, c.c_void_p,

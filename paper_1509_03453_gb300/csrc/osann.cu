@@ -459,9 +459,14 @@ static int choose_mode(const osann_index* ix, int64_t Q, int64_t P_eff, int path
     if (path == OSANN_PATH_BATCHED) return MODE_BATCHED;
     if (path == OSANN_PATH_BF16) return MODE_BF16;
     if (path == OSANN_PATH_FP16) return MODE_FP16;
+    // queries per probed cone decide whether cone-major batching pays; the
+    // candidates per query decide whether one CTA per query (plain) finishes
+    // soon enough: a small batch with a large budget goes cone-major too
     const double per_cone = double(Q) * double(P_eff) / double(ix->NC);
-    if (ix->tc_ready[1] && per_cone >= 64.0) return MODE_FP16;
-    return per_cone >= 16.0 ? MODE_BATCHED : MODE_PLAIN;
+    const double per_query = double(P_eff) * double(ix->N) / double(ix->NC);
+    const bool big_queries = per_query >= 16384.0;
+    if (ix->tc_ready[1] && (per_cone >= 64.0 || big_queries)) return MODE_FP16;
+    return per_cone >= 16.0 || big_queries ? MODE_BATCHED : MODE_PLAIN;
 }
 
 // ---------------------------------------------------------------- C ABI

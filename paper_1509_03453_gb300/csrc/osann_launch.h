@@ -99,7 +99,7 @@ int launch_bruteforce_rows(const float* xs, const uint32_t* perm, int64_t N, int
 // tc_scan.cu: 16-bit tensor-core screening + fp32 rerank.  prec 0 = bf16,
 // 1 = fp16 (with an exact power-of-two scale of the data and queries)
 constexpr int TC_GROUP = 128;
-constexpr int TC_SURV_CAP = 256;
+constexpr int TC_SURV_CAP = 1024;
 size_t tc_map_bytes();
 int tc_encode_rows_map(void* map_out, const void* x16, int64_t N, int d_pad, int prec);  // d_pad 0: extra block
 int launch_tc_rows(int prec, const float* xs, const float4* rowstat, int64_t N, int d_pad, const uint32_t* maxn2_bits,

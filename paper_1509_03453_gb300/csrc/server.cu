@@ -10,8 +10,8 @@
 // overlap on the device; the number of slots is bounded by the memory budget
 // (admission by memory).  A batch runs as a CUDA graph replay when graphs
 // are on (one graph per slot, index and batch-size bucket, captured on first
-// use; the batch is padded to the bucket with the buffer's previous rows,
-// whose results are discarded), and its path and work-list group size come
+// use; the batch is padded to the bucket with zero rows, whose results are
+// discarded), and its path and work-list group size come
 // from the tuner when it has run.  Results are copied to the callers'
 // buffers on the slot's stream; a request is reported finished when the
 // last of its batches has completed.  Every query's result is independent
@@ -176,6 +176,12 @@ int run_batch(osann_server* s, Slot& sl, int i, int64_t nq)
         if (graph) cudaGraphDestroy(graph);
     }
     if (g.failed) return run_search(s, sl, i, nq, c);
+    // the padding rows are searched too (their results are dropped): zeros,
+    // cheap and in range, rather than stale rows of another index or width
+    if (nb > nq) {
+        cudaError_t z = cudaMemsetAsync(sl.qbuf + nq * s->d[i], 0, size_t(nb - nq) * s->d[i] * 4, sl.st);
+        if (z != cudaSuccess) return cuda_err(z, "osann_server: padding");
+    }
     cudaError_t e = cudaGraphLaunch(g.exec, sl.st);
     if (e != cudaSuccess) return cuda_err(e, "osann_server: graph launch");
     add_launches(g.launches);
@@ -434,7 +440,16 @@ int osann_server_pending(const osann_server* s, int64_t* waiting_queries, int32_
     return OSANN_OK;
 }
 
+int osann_server_tune_queries(osann_server* s, const float* const* d_queries, const int64_t* n_queries, int32_t reps,
+                              int32_t* out_choices);
+
 int osann_server_tune(osann_server* s, int32_t reps, int32_t* out_choices)
+{
+    return osann_server_tune_queries(s, nullptr, nullptr, reps, out_choices);
+}
+
+int osann_server_tune_queries(osann_server* s, const float* const* d_queries, const int64_t* n_queries, int32_t reps,
+                              int32_t* out_choices)
 {
     if (!s || reps < 1) return fail(OSANN_ERR_INVALID, "osann_server_tune: invalid arguments");
     std::lock_guard<std::mutex> lk(s->mu);
@@ -451,16 +466,25 @@ int osann_server_tune(osann_server* s, int32_t reps, int32_t* out_choices)
     int rc = 0;
     const size_t nb = nbuckets(s);
     for (size_t i = 0; i < s->idx.size() && !rc; ++i) {
-        // tuning queries: max_batch rows spread over the whole index
+        // tuning queries: the caller's sample of index i, else max_batch rows
+        // spread over the index (whose nearest neighbours are themselves: a
+        // representative sample tunes better)
         int64_t N = 0;
         int d = 0, dp = 0;
         const float* rows = index_rows(s->idx[i], &N, &d, &dp);
-        const int64_t n = std::min(s->max_batch, N);
-        const int64_t step = n > 0 ? N / n : 1;
-        if (n > 0) {
-            cudaError_t e = cudaMemcpy2DAsync(sl.qbuf, size_t(d) * 4, rows, size_t(step) * dp * 4, size_t(d) * 4,
-                                              size_t(n), cudaMemcpyDeviceToDevice, sl.st);
+        int64_t n = 0;
+        if (d_queries && d_queries[i] && n_queries && n_queries[i] > 0) {
+            n = std::min(s->max_batch, n_queries[i]);
+            cudaError_t e = cudaMemcpyAsync(sl.qbuf, d_queries[i], size_t(n) * d * 4, cudaMemcpyDeviceToDevice, sl.st);
             if (e != cudaSuccess) rc = cuda_err(e, "osann_server_tune: sample");
+        } else {
+            n = std::min(s->max_batch, N);
+            const int64_t step = n > 0 ? N / n : 1;
+            if (n > 0) {
+                cudaError_t e = cudaMemcpy2DAsync(sl.qbuf, size_t(d) * 4, rows, size_t(step) * dp * 4, size_t(d) * 4,
+                                                  size_t(n), cudaMemcpyDeviceToDevice, sl.st);
+                if (e != cudaSuccess) rc = cuda_err(e, "osann_server_tune: sample");
+            }
         }
         for (size_t bk = 0; bk < nb && !rc; ++bk) {
             const int64_t q = std::min(s->buckets[bk], n);
@@ -498,6 +522,27 @@ int osann_server_tune(osann_server* s, int32_t reps, int32_t* out_choices)
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     drop_graphs(s);  // captured with the previous choices
+    cudaSetDevice(cur);
+    return rc;
+}
+
+int osann_server_warmup(osann_server* s)
+{
+    if (!s) return fail(OSANN_ERR_INVALID, "osann_server_warmup: null server");
+    std::lock_guard<std::mutex> lk(s->mu);
+    for (const auto& sl : s->slots)
+        if (sl.busy) return fail(OSANN_ERR_INVALID, "osann_server_warmup: batches in flight");
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(s->device);
+    int rc = 0;
+    // every slot, index and bucket once (captures the graphs when they are on);
+    // the query buffers hold finite rows, whose results are dropped
+    for (auto& sl : s->slots)
+        for (size_t i = 0; i < s->idx.size() && !rc; ++i)
+            for (size_t b = 0; b < s->buckets.size() && !rc; ++b) rc = run_batch(s, sl, int(i), s->buckets[b]);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (!rc && e != cudaSuccess) rc = cuda_err(e, "osann_server_warmup");
     cudaSetDevice(cur);
     return rc;
 }

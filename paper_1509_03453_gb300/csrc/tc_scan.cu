@@ -563,11 +563,21 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
 // One warp per query: 16-bit copy of -2 s y, scaled norms and A', survivor
 // counter reset, and the initial upper bound U: the k-th smallest canonical
 // fp32 distance over the rows of the first probed cones (in probe order,
-// excluded rows skipped, at least TC_SEED rows when the cones hold them),
+// excluded rows skipped, at least `seed_rows` rows when the cones hold them),
 // inflated by the fp32 error bound; +inf if fewer than k rows.  A query too large for the 16-bit range is left to the
 // rerank's full scan (its survivor count is set above the capacity).
-constexpr int TC_SEED = 64;     // rows scanned exactly for the initial bound
 constexpr int TC_SEED_ILP = 8;  // row groups loaded per iteration
+
+// Rows scanned exactly for a query's initial bound.  A large batch keeps
+// tightening its bounds as items finish, so a short seed suffices (64 rows
+// at 10^4 queries); in a small batch every item runs at once on the first
+// bound, which must then be tighter (up to 1024 rows, a few cones): about
+// 2^16 * 10 / Q rows, clamped.
+static int tc_seed_rows(int64_t Q)
+{
+    const int64_t r = Q > 0 ? (int64_t(655360) + Q - 1) / Q : 1024;
+    return int(r < 64 ? 64 : (r > 1024 ? 1024 : r));
+}
 
 template <int F, int PREC, int KMAX>
 __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restrict__ Y, int64_t Q, int d, int d_pad,
@@ -579,7 +589,7 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
                                                             const int64_t* __restrict__ query_src, int64_t grid_w,
                                                             int radius, int cap, uint16_t* __restrict__ Y16,
                                                             float4* __restrict__ qstat, uint32_t* __restrict__ Ubits,
-                                                            uint32_t* __restrict__ surv_cnt)
+                                                            uint32_t* __restrict__ surv_cnt, int seed_rows)
 {
     const int lane = threadIdx.x & 31;
     const int64_t q = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
@@ -630,11 +640,11 @@ __global__ void __launch_bounds__(128) tc_query_prep_kernel(const float* __restr
     uint64_t list[KMAX];
     topk_init<KMAX>(list, k);
     int scanned = 0;
-    for (int64_t p = 0; p < P_eff && scanned < TC_SEED; ++p) {
+    for (int64_t p = 0; p < P_eff && scanned < seed_rows; ++p) {
         const uint32_t b = probes[q * P_eff + p];
         if (b >= NC) continue;
         const uint32_t o0 = offsets[b], o1 = offsets[b + 1];
-        for (uint32_t r0 = o0; r0 < o1 && scanned < TC_SEED; r0 += TC_SEED_ILP * CPP) {
+        for (uint32_t r0 = o0; r0 < o1 && scanned < seed_rows; r0 += TC_SEED_ILP * CPP) {
             // TC_SEED_ILP row groups per iteration: all loads in flight before the arithmetic
             float4 xv[TC_SEED_ILP][F];
             uint32_t rr[TC_SEED_ILP];
@@ -913,10 +923,11 @@ int launch_tc_query_prep(int prec, const float* Y, int64_t Q, int d, int d_pad, 
     if (Q == 0) return 0;
     const unsigned blocks = unsigned((Q * 32 + 127) / 128);
     uint16_t* y16 = static_cast<uint16_t*>(Y16);
+    const int seed_rows = tc_seed_rows(Q);
 #define OSANN_PREP(F, PR, KM)                                                                                       \
     tc_query_prep_kernel<F, PR, KM><<<blocks, 128, 0, st>>>(Y, Q, d, d_pad, probes, P_eff, offsets, NC, xs, k, cdot2, \
                                                             cabs, tcs, perm, query_src, grid_w, radius, cap, y16,    \
-                                                            qstat, Ubits, surv_cnt)
+                                                            qstat, Ubits, surv_cnt, seed_rows)
 #define OSANN_PREP_K(F, PR)             \
     if (k <= 1) OSANN_PREP(F, PR, 1);      \
     else if (k <= 4) OSANN_PREP(F, PR, 4); \
