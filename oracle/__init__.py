@@ -82,6 +82,19 @@ def lib():
         L.oracle_search_multi.argtypes = [
             _f32p, c.c_int64, c.c_int, c.c_int, c.c_int, _f32p, _u32p, _u32p, _f32p, c.c_int64,
             c.c_int64, c.c_int, _i64p, _f64p, c.c_void_p]
+        _u64p = np.ctypeslib.ndpointer(np.uint64, flags="C_CONTIGUOUS")
+        L.oracle_num_cones_wide.restype = c.c_int
+        L.oracle_num_cones_wide.argtypes = [c.c_int, c.c_int, _u64p]
+        L.oracle_keys_wide.restype = None
+        L.oracle_keys_wide.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _u64p]
+        L.oracle_probes_wide.restype = c.c_int64
+        L.oracle_probes_wide.argtypes = [_f32p, c.c_int, c.c_int, c.c_int64, _u64p]
+        L.oracle_buckets_wide.restype = c.c_int64
+        L.oracle_buckets_wide.argtypes = [_u64p, c.c_int64, _u32p, _u64p, _u32p]
+        L.oracle_search_wide.restype = None
+        L.oracle_search_wide.argtypes = [
+            _f32p, c.c_int64, c.c_int, c.c_int, c.c_int64, _u64p, _u32p, _u32p, _f32p, c.c_int64,
+            c.c_int64, c.c_int, c.c_void_p, c.c_int64, c.c_int64, _i64p, _f64p, c.c_void_p]
         L.oracle_pair_dists.restype = None
         L.oracle_pair_dists.argtypes = [_f32p, c.c_int, _f32p, c.c_int64,
                                         c.c_int, _i64p, _f64p]
@@ -136,6 +149,35 @@ def probes(y, L: int, P: int) -> np.ndarray:
     return out[:n].copy()
 
 
+def num_cones_wide(d: int, L: int) -> int:
+    """N_C = C(d, L) 2^L as a Python int, or -1 when it reaches 2^127."""
+    out = np.zeros(2, np.uint64)
+    if lib().oracle_num_cones_wide(d, L, out) != 0:
+        return -1
+    return int(out[0]) | (int(out[1]) << 64)
+
+
+def _wide_ints(w: np.ndarray) -> list:
+    return [int(a) | (int(b) << 64) for a, b in w.reshape(-1, 2)]
+
+
+def keys_wide(X, L: int) -> list:
+    """128-bit cone ids of the rows of X, as Python ints."""
+    X = _f32(X)
+    N, d = X.shape
+    out = np.empty(2 * N, np.uint64)
+    lib().oracle_keys_wide(X, N, d, L, out)
+    return _wide_ints(out)
+
+
+def probes_wide(y, L: int, P: int) -> list:
+    """The ordered cone list of y with 128-bit ids (Python ints)."""
+    y = _f32(y)
+    out = np.empty(2 * max(P, 1), np.uint64)
+    n = lib().oracle_probes_wide(y, y.shape[-1], L, P, out)
+    return _wide_ints(out[:2 * n])
+
+
 def _src_ptr(query_src):
     if query_src is None:
         return None, None
@@ -166,6 +208,45 @@ class Index:
         keep, src = _src_ptr(query_src)
         lib().oracle_search(
             self.X, self.N, self.d, self.L, self.offsets, self.perm, Y, Q, P, k,
+            src, grid_w, radius, ids, dists,
+            counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+        del keep
+        ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
+        return (ids, dists, counts) if want_counts else (ids, dists)
+
+
+class WideIndex:
+    """Oracle index over the second-level table: 128-bit cone ids, points
+    sorted by (id, point), only the occupied cones stored (ascending ids)."""
+
+    def __init__(self, X, L: int):
+        self.X = _f32(X)
+        self.N, self.d = self.X.shape
+        self.L = L
+        self.NC = num_cones_wide(self.d, L)
+        if self.NC < 0:
+            raise ValueError("N_C does not fit in 127 bits")
+        kw = np.empty(2 * self.N, np.uint64)
+        lib().oracle_keys_wide(self.X, self.N, self.d, L, kw)
+        self.keys = _wide_ints(kw)
+        self.perm = np.empty(self.N, np.uint32)
+        uniq = np.empty(2 * max(self.N, 1), np.uint64)
+        offs = np.empty(self.N + 1, np.uint32)
+        self.n_occ = int(lib().oracle_buckets_wide(kw, self.N, self.perm, uniq, offs))
+        self._uniq = np.ascontiguousarray(uniq[:2 * max(self.n_occ, 1)])
+        self.uniq = _wide_ints(uniq[:2 * self.n_occ])
+        self.offsets = offs[:self.n_occ + 1].copy()
+
+    def search(self, Y, P: int, k: int, query_src=None, grid_w: int = 0,
+               radius: int = 0, want_counts: bool = False):
+        Y = _f32(Y)
+        Q = Y.shape[0]
+        ids = np.empty(Q * k, np.int64)
+        dists = np.empty(Q * k, np.float64)
+        counts = np.empty(Q, np.int64) if want_counts else None
+        keep, src = _src_ptr(query_src)
+        lib().oracle_search_wide(
+            self.X, self.N, self.d, self.L, self.n_occ, self._uniq, self.offsets, self.perm, Y, Q, P, k,
             src, grid_w, radius, ids, dists,
             counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
         del keep

@@ -36,6 +36,11 @@
  *     the first m rows of the basis and subtracts an offset c_i (the
  *     projected mean) in one final fp32 subtraction; distances always use the
  *     original vectors.
+ *   - when N_C is too large for a direct table (the "second-level hash
+ *     table" of Sec. 4), the cone id is the same number rank(S) * 2^G +
+ *     sign code held in 128 bits; only the occupied cones are stored, in
+ *     ascending id order, and a probed cone that holds no point is skipped
+ *     (it still counts against the budget C).
  * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
  * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
  * The intra-class probe order and the sign-flip extension are this
@@ -61,6 +66,36 @@ uint64_t oracle_binom(int64_t n, int64_t k)
         if (r > (unsigned __int128)UINT64_MAX) return UINT64_MAX;
     }
     return (uint64_t)r;
+}
+
+typedef unsigned __int128 u128;
+#define U128_MAX (~(u128)0)
+
+/* C(n, k) in 128 bits, exact, saturating at the 128-bit maximum. */
+static u128 binom_wide(int64_t n, int64_t k)
+{
+    if (k < 0 || n < 0 || k > n) return 0;
+    if (k > n - k) k = n - k;
+    u128 r = 1;
+    for (int64_t i = 1; i <= k; ++i) {
+        u128 f = (u128)(n - k + i);
+        if (r > U128_MAX / f) return U128_MAX;
+        r = r * f / (u128)i;
+    }
+    return r;
+}
+
+/* N_C = C(K, G) * 2^G in 128 bits (lo, hi words).  Returns -1 (and writes
+ * nothing) when N_C >= 2^127. */
+int oracle_num_cones_wide(int d, int L, uint64_t *lohi)
+{
+    if (d < 1 || L < 1 || L > d || L > ORACLE_MAX_L || d > ORACLE_MAX_D) return -1;
+    u128 c = binom_wide(d, L);
+    if (c == U128_MAX || c > (((u128)1 << 127) - 1) >> L) return -1;
+    u128 nc = c << L;
+    lohi[0] = (uint64_t)nc;
+    lohi[1] = (uint64_t)(nc >> 64);
+    return 0;
 }
 
 /* Number of cones N_C = C(K, G) * 2^G (Sec. 2, Table I).  -1 if it does not
@@ -95,8 +130,8 @@ void oracle_magnitude_order(const float *y, int d, int32_t *order)
  * signs of y on its members, optionally with the members listed in
  * flip_mask (bit m set = flip the sign of the member whose position in the
  * ascending-|y| ordering of S is m) sign-inverted. */
-static uint32_t cone_of_profile(const int32_t *S_in, int L, const float *y,
-                                const int32_t *rank_of, uint32_t flip_mask)
+static u128 cone_of_profile_wide(const int32_t *S_in, int L, const float *y,
+                                 const int32_t *rank_of, uint32_t flip_mask)
 {
     int32_t s[ORACLE_MAX_L];
     memcpy(s, S_in, sizeof(int32_t) * (size_t)L);
@@ -107,9 +142,9 @@ static uint32_t cone_of_profile(const int32_t *S_in, int L, const float *y,
         while (b >= 0 && s[b] > v) { s[b + 1] = s[b]; --b; }
         s[b + 1] = v;
     }
-    uint64_t rank = 0;
-    for (int j = 0; j < L; ++j) rank += oracle_binom(s[j], j + 1);
-    uint32_t code = 0;
+    u128 rank = 0;
+    for (int j = 0; j < L; ++j) rank += binom_wide(s[j], j + 1);
+    u128 code = 0;
     for (int j = 0; j < L; ++j) {
         uint32_t bit = (y[s[j]] >= 0.0f) ? 1u : 0u;
         if (flip_mask) {
@@ -120,9 +155,16 @@ static uint32_t cone_of_profile(const int32_t *S_in, int L, const float *y,
                 if (rank_of[s[t]] > rank_of[s[j]]) ++pos;
             if ((flip_mask >> pos) & 1u) bit ^= 1u;
         }
-        code |= bit << (L - 1 - j);
+        code |= (u128)bit << (L - 1 - j);
     }
-    return (uint32_t)((rank << L) | code);
+    return (rank << L) | code;
+}
+
+/* The same id when N_C < 2^31 (a direct table). */
+static uint32_t cone_of_profile(const int32_t *S_in, int L, const float *y,
+                                const int32_t *rank_of, uint32_t flip_mask)
+{
+    return (uint32_t)cone_of_profile_wide(S_in, L, y, rank_of, flip_mask);
 }
 
 /* Cone id of one vector (Sec. 2): profile = the G largest-magnitude
@@ -139,6 +181,18 @@ void oracle_keys(const float *X, int64_t N, int d, int L, uint32_t *keys)
     for (int64_t n = 0; n < N; ++n) keys[n] = oracle_key(X + n * d, d, L);
 }
 
+/* 128-bit cone ids of N vectors, two words (low, high) per vector. */
+void oracle_keys_wide(const float *X, int64_t N, int d, int L, uint64_t *keys)
+{
+    int32_t order[ORACLE_MAX_D];
+    for (int64_t n = 0; n < N; ++n) {
+        oracle_magnitude_order(X + n * d, d, order);
+        u128 k = cone_of_profile_wide(order, L, X + n * d, NULL, 0);
+        keys[2 * n] = (uint64_t)k;
+        keys[2 * n + 1] = (uint64_t)(k >> 64);
+    }
+}
+
 /* Bucket index: offsets[N_C + 1] (exclusive prefix sum of the cone counts)
  * and perm[N] (point ids, ascending inside each cone: a stable counting
  * sort).  The paper only says that one hash table per basis maps cones to
@@ -153,6 +207,63 @@ void oracle_buckets(const uint32_t *keys, int64_t N, int64_t NC,
     memcpy(cursor, offsets, sizeof(uint32_t) * (size_t)(NC + 1));
     for (int64_t n = 0; n < N; ++n) perm[cursor[keys[n]]++] = (uint32_t)n;
     free(cursor);
+}
+
+/* Second-level table for large N_C (Sec. 4: "a second-level hash table is
+ * used ... when the number of cones grows very large"): only occupied cones
+ * are kept.  perm[N] lists the point ids sorted by (128-bit cone id, id);
+ * uniq[2 * n_occ] holds the distinct ids in ascending order (low, high
+ * words) and offsets[n_occ + 1] the start of each one's points in perm.
+ * Returns n_occ.  The sort is the C library's qsort on (cone id, point id)
+ * pairs. */
+struct wide_pair {
+    u128 key;
+    uint32_t id;
+};
+
+static int cmp_wide_pair(const void *a, const void *b)
+{
+    const struct wide_pair *x = (const struct wide_pair *)a, *y = (const struct wide_pair *)b;
+    if (x->key != y->key) return x->key < y->key ? -1 : 1;
+    return x->id < y->id ? -1 : (x->id > y->id ? 1 : 0);
+}
+
+static u128 wide_at(const uint64_t *w, int64_t i) { return ((u128)w[2 * i + 1] << 64) | w[2 * i]; }
+
+int64_t oracle_buckets_wide(const uint64_t *keys, int64_t N, uint32_t *perm, uint64_t *uniq, uint32_t *offsets)
+{
+    struct wide_pair *v = (struct wide_pair *)malloc(sizeof(struct wide_pair) * (size_t)(N > 0 ? N : 1));
+    for (int64_t n = 0; n < N; ++n) {
+        v[n].key = wide_at(keys, n);
+        v[n].id = (uint32_t)n;
+    }
+    qsort(v, (size_t)N, sizeof(struct wide_pair), cmp_wide_pair);
+    int64_t n_occ = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        perm[i] = v[i].id;
+        if (i == 0 || v[i].key != v[i - 1].key) {
+            uniq[2 * n_occ] = (uint64_t)v[i].key;
+            uniq[2 * n_occ + 1] = (uint64_t)(v[i].key >> 64);
+            offsets[n_occ] = (uint32_t)i;
+            ++n_occ;
+        }
+    }
+    offsets[n_occ] = (uint32_t)N;
+    free(v);
+    return n_occ;
+}
+
+/* Position of cone id key among the n_occ ascending ids of uniq, or -1 if
+ * no point lies in that cone (binary search). */
+static int64_t find_cone(const uint64_t *uniq, int64_t n_occ, u128 key)
+{
+    int64_t lo = 0, hi = n_occ;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (wide_at(uniq, mid) < key) lo = mid + 1;
+        else hi = mid;
+    }
+    return (lo < n_occ && wide_at(uniq, lo) == key) ? lo : -1;
 }
 
 /* Advance comb[0..m-1] (strictly increasing values in [lo, hi]) to the next
@@ -206,17 +317,30 @@ struct probe_ctx {
     const int32_t *rank_of;
     int L;
     int64_t P, count;
-    uint32_t *out;
+    uint32_t *out;      /* direct-table ids, or */
+    uint64_t *out_wide; /* 128-bit ids, two words each */
     uint32_t flip_mask; /* 0 in the first sweep */
     int h;              /* flips per cone in the current sweep */
     int32_t F[ORACLE_MAX_L];
 };
 
+static void emit_cone(struct probe_ctx *c, const int32_t *S, uint32_t mask)
+{
+    u128 k = cone_of_profile_wide(S, c->L, c->y, c->rank_of, mask);
+    if (c->out) {
+        c->out[c->count] = (uint32_t)k;
+    } else {
+        c->out_wide[2 * c->count] = (uint64_t)k;
+        c->out_wide[2 * c->count + 1] = (uint64_t)(k >> 64);
+    }
+    c->count++;
+}
+
 static int emit_unflipped(const int32_t *S, void *vctx)
 {
     struct probe_ctx *c = (struct probe_ctx *)vctx;
     if (c->count >= c->P) return 1;
-    c->out[c->count++] = cone_of_profile(S, c->L, c->y, c->rank_of, 0);
+    emit_cone(c, S, 0);
     return c->count >= c->P;
 }
 
@@ -229,7 +353,7 @@ static int emit_flipped(const int32_t *S, void *vctx)
         if (c->count >= c->P) return 1;
         uint32_t mask = 0;
         for (int j = 0; j < c->h; ++j) mask |= 1u << F[j];
-        c->out[c->count++] = cone_of_profile(S, c->L, c->y, c->rank_of, mask);
+        emit_cone(c, S, mask);
     } while (next_combination(F, c->h, 0, c->L - 1));
     return c->count >= c->P;
 }
@@ -237,13 +361,13 @@ static int emit_flipped(const int32_t *S, void *vctx)
 /* Ordered list of cones to visit for query y (Algorithm 1, "find ordered
  * list of cones"), truncated at P entries.  Returns the number written,
  * min(P, N_C). */
-int64_t oracle_probes(const float *y, int d, int L, int64_t P, uint32_t *out)
+static int64_t probes_into(const float *y, int d, int L, int64_t P, uint32_t *out, uint64_t *out_wide)
 {
     int32_t order[ORACLE_MAX_D], rank_of[ORACLE_MAX_D];
     oracle_magnitude_order(y, d, order);
     for (int r = 0; r < d; ++r) rank_of[order[r]] = r;
     struct probe_ctx c;
-    c.y = y; c.rank_of = rank_of; c.L = L; c.P = P; c.count = 0; c.out = out;
+    c.y = y; c.rank_of = rank_of; c.L = L; c.P = P; c.count = 0; c.out = out; c.out_wide = out_wide;
     c.flip_mask = 0; c.h = 0;
     enumerate_profiles(order, d, L, emit_unflipped, &c);
     for (int h = 1; h <= L && c.count < P; ++h) {
@@ -251,6 +375,17 @@ int64_t oracle_probes(const float *y, int d, int L, int64_t P, uint32_t *out)
         enumerate_profiles(order, d, L, emit_flipped, &c);
     }
     return c.count;
+}
+
+int64_t oracle_probes(const float *y, int d, int L, int64_t P, uint32_t *out)
+{
+    return probes_into(y, d, L, P, out, NULL);
+}
+
+/* The same list with 128-bit ids (two words each), for N_C of any size. */
+int64_t oracle_probes_wide(const float *y, int d, int L, int64_t P, uint64_t *out)
+{
+    return probes_into(y, d, L, P, NULL, out);
 }
 
 /* Candidate exclusion used by the patch workload: data id n sits at grid
@@ -325,6 +460,44 @@ void oracle_search(const float *X, int64_t N, int d, int L,
         int64_t src = query_src ? query_src[q] : -1;
         for (int64_t l = 0; l < np; ++l) {
             uint32_t c = probes[l];
+            for (uint32_t r = offsets[c]; r < offsets[c + 1]; ++r) {
+                int64_t n = perm[r];
+                if (excluded(n, src, grid_w, radius)) continue;
+                ++cands;
+                topk_insert(bd, bi, k, sqdist(X + n * d, y, d), n);
+            }
+        }
+        if (cand_count) cand_count[q] = cands;
+    }
+    free(probes);
+}
+
+/* The search of oracle_search over the second-level table of
+ * oracle_buckets_wide: the same ordered cone list with 128-bit ids, each
+ * looked up among the occupied cones; P is clamped to N_C (128-bit). */
+void oracle_search_wide(const float *X, int64_t N, int d, int L, int64_t n_occ,
+                        const uint64_t *uniq, const uint32_t *offsets, const uint32_t *perm,
+                        const float *Y, int64_t Q, int64_t P, int k,
+                        const int64_t *query_src, int64_t grid_w, int64_t radius,
+                        int64_t *ids, double *dists, int64_t *cand_count)
+{
+    (void)N;
+    uint64_t nc[2];
+    if (oracle_num_cones_wide(d, L, nc) != 0) return;
+    u128 NC = ((u128)nc[1] << 64) | nc[0];
+    if ((u128)P > NC) P = (int64_t)NC;
+    uint64_t *probes = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (size_t)(P > 0 ? P : 1));
+    for (int64_t q = 0; q < Q; ++q) {
+        const float *y = Y + q * d;
+        double *bd = dists + q * k;
+        int64_t *bi = ids + q * k;
+        topk_init(bd, bi, k);
+        int64_t np = oracle_probes_wide(y, d, L, P, probes);
+        int64_t cands = 0;
+        int64_t src = query_src ? query_src[q] : -1;
+        for (int64_t l = 0; l < np; ++l) {
+            int64_t c = find_cone(uniq, n_occ, wide_at(probes, l));
+            if (c < 0) continue;
             for (uint32_t r = offsets[c]; r < offsets[c + 1]; ++r) {
                 int64_t n = perm[r];
                 if (excluded(n, src, grid_w, radius)) continue;
