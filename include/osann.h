@@ -33,7 +33,7 @@ extern "C" {
 
 #define OSANN_OK 0
 #define OSANN_ERR_INVALID (-1)     /* bad argument (sizes, null pointers, ranges) */
-#define OSANN_ERR_UNSUPPORTED (-2) /* N_C or N beyond the 31-bit index space */
+#define OSANN_ERR_UNSUPPORTED (-2) /* N beyond the 31-bit index space (or a size limit below) */
 #define OSANN_ERR_OOM (-3)         /* device allocation failed */
 #define OSANN_ERR_NONFINITE (-4)   /* NaN or Inf in the data */
 #define OSANN_ERR_CUDA (-5)        /* a CUDA call failed */
@@ -81,6 +81,12 @@ int osann_num_cones(int32_t d, int32_t L, int64_t *nc);
  * 1 <= L <= min(d, 16).  Non-finite inputs are not reported here. */
 int osann_keys(const float *d_vectors, int64_t n, int32_t d, int32_t L, uint32_t *d_keys, void *stream);
 
+/* The same cone ids for any N_C (the numbers of the second-level table,
+ * Sec. 4): rank(S) * 2^L + code exact in 128 bits, written as four uint32
+ * words per vector, least significant first (d_ids: n x 4, 16-byte
+ * aligned).  N_C < 2^100 for every d <= 256, L <= 16. */
+int osann_keys_wide(const float *d_vectors, int64_t n, int32_t d, int32_t L, uint32_t *d_ids, void *stream);
+
 /* Magnitude order i_1..i_d of each query (Sec. 3-B): d_order[q*d + r] is the
  * component with the (r+1)-th largest |y| (ties to the lower index), uint8.
  * d_signs[q*8 + w] bit b is set when y[32w + b] >= 0 (8 words per query).
@@ -96,9 +102,10 @@ int osann_query_order(const float *d_queries, int64_t Q, int32_t d, uint8_t *d_o
  * ones are made on the first OSANN_PATH_BF16 search, which then
  * synchronises its stream once).
  * d_data: N x d fp32, read only (the index keeps its own copy).
- * Synchronises `stream` once.  Errors: INVALID (N < 1, d outside [1,256],
- * L outside [1, min(d,16)], out == NULL), UNSUPPORTED (N >= 2^31 or
- * N_C >= 2^31), NONFINITE (NaN/Inf in d_data), OOM, CUDA. */
+ * With N_C >= 2^31 the index gets the second-level cone table (see
+ * osann_build_ex).  Synchronises `stream` once.  Errors: INVALID (N < 1, d
+ * outside [1,256], L outside [1, min(d,16)], out == NULL), UNSUPPORTED
+ * (N >= 2^31), NONFINITE (NaN/Inf in d_data), OOM, CUDA. */
 int osann_build(const float *d_data, int64_t N, int32_t d, int32_t L, void *stream, osann_index **out);
 
 /* One basis of the multi-basis search (Sec. 3-D, Algorithm 1 with R > 1):
@@ -133,21 +140,69 @@ int osann_build_proj(const float *d_data, int64_t N, int32_t d, int32_t L, const
  * and max_bucket reads -1 in osann_info until that call. */
 int osann_build_async(const float *d_data, int64_t N, int32_t d, int32_t L, void *stream, osann_index **out);
 
+/* Cone table kinds for osann_build_ex.  A direct table holds all N_C cones
+ * (CSR offsets over the cone ids) and needs N_C < 2^31.  The second-level
+ * table (Sec. 4: "a second-level hash table is used ... when the number of
+ * cones grows very large") keeps only the occupied cones: the point ids
+ * are sorted by 128-bit cone id (osann_keys_wide), the occupied cones are
+ * numbered 0..n_occ-1 in ascending id order ("compact" cones), offsets span
+ * NC_t = min(N, N_C) + 1 compact cones (those from n_occ on are empty), and
+ * a hash table maps a probed id to its compact cone -- or, for an id no
+ * point carries, to the empty cone NC_t - 1.  Both kinds give the same
+ * search results; AUTO takes the direct table when N_C < 2^31. */
+#define OSANN_CONES_AUTO 0
+#define OSANN_CONES_DENSE 1
+#define OSANN_CONES_HASHED 2
+
+typedef struct {
+    const float *d_basis;  /* m x d key basis (osann_build_rot / osann_build_proj), NULL: the identity */
+    const float *d_offset; /* m offsets subtracted after projecting, NULL: none (needs d_basis) */
+    int32_t m;             /* rows of d_basis (ignored without one) */
+    int32_t async;         /* nonzero: no final synchronisation (as osann_build_async) */
+    int32_t cone_table;    /* OSANN_CONES_* */
+} osann_build_opts;
+
+/* Build with explicit options (opts NULL: as osann_build).  Every other
+ * build entry point is this one with the matching options and
+ * OSANN_CONES_AUTO.  Errors as osann_build, plus: UNSUPPORTED for
+ * OSANN_CONES_DENSE with N_C >= 2^31, and for a second-level table of more
+ * than 2^30 cones. */
+int osann_build_ex(const float *d_data, int64_t N, int32_t d, int32_t L, const osann_build_opts *opts, void *stream,
+                   osann_index **out);
+
+/* The cone table of an index.  Any output may be NULL.  hashed: 1 for the
+ * second-level table.  n_cones[2]: N_C (low, high 64-bit words).
+ * table_cones: cones of the CSR table (the NC of osann_info: N_C, or NC_t).
+ * occupied: cones holding at least one point (synchronises `stream`). */
+int osann_cones(const osann_index *index, int32_t *hashed, uint64_t *n_cones, int64_t *table_cones,
+                int64_t *occupied, void *stream);
+
+/* The 128-bit id of every compact cone of a second-level table: d_ids is
+ * table_cones x 4 uint32 words (least significant first); entries past the
+ * occupied cones are all ones.  INVALID for a direct table. */
+int osann_export_cones(const osann_index *index, uint32_t *d_ids, void *stream);
+
 /* Release an index.  NULL is accepted.  The caller must ensure that no
  * work using the index is still pending on any stream. */
 int osann_free(osann_index *index);
 
 /* Sizes of an index.  Any output pointer may be NULL.  max_bucket is the
- * largest cone population. */
+ * largest cone population.  NC is the number of cones of the CSR table:
+ * N_C for a direct table, NC_t = min(N, N_C) + 1 for a second-level one
+ * (osann_cones gives N_C itself). */
 int osann_info(const osann_index *index, int64_t *N, int32_t *d, int32_t *L, int64_t *NC, int64_t *max_bucket);
 
 /* Copy the index's bucket structure out (for verification): d_keys[N]
- * (cone of each point, original order), d_offsets[N_C + 1], d_perm[N]
- * (point ids, ascending inside each cone).  Any pointer may be NULL. */
+ * (cone of each point, original order), d_offsets[NC + 1], d_perm[N]
+ * (point ids, ascending inside each cone), NC as in osann_info; with a
+ * second-level table the cones are the compact ones.  Any pointer may be
+ * NULL. */
 int osann_export(const osann_index *index, uint32_t *d_keys, uint32_t *d_offsets, uint32_t *d_perm, void *stream);
 
 /* Ordered list of cones to visit (Algorithm 1, "find ordered list of
- * cones"; Sec. 3-B): d_probes[q * P_eff + p], P_eff = min(P, N_C).  Order:
+ * cones"; Sec. 3-B): d_probes[q * P_eff + p], P_eff = min(P, N_C) (with a
+ * second-level table: the compact cone of each probed id, NC_t - 1 for an
+ * unoccupied one).  Order:
  * profile distance delta = L - (level of the closest common ancestor with
  * the query's profile {i_1..i_L}) ascending; inside a class the substituted
  * ranks in lexicographic order; each profile with the query's signs; then

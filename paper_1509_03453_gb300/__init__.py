@@ -15,7 +15,8 @@ import ctypes
 from . import _lib
 from ._lib import OsannError, PATHS, STAGES, load
 
-__all__ = ["Index", "MultiIndex", "Server", "OsannError", "merge_topk", "keys", "query_order", "num_cones", "stats", "launch_count", "load"]
+__all__ = ["Index", "MultiIndex", "Server", "OsannError", "merge_topk", "keys", "keys_wide", "query_order",
+           "num_cones", "stats", "launch_count", "load"]
 
 
 def _torch():
@@ -55,6 +56,21 @@ def keys(vectors, L: int, stream=None):
     out = torch.empty(v.shape[0], dtype=torch.int32, device=v.device)
     _lib.check(load().osann_keys(_ptr(v), v.shape[0], v.shape[1], L, _ptr(out), _stream_ptr(stream)))
     return out.to(torch.int64) & 0xFFFFFFFF
+
+
+def _wide_to_ints(w) -> list:
+    """[n, 4] uint32 words (least significant first, as int32) -> Python ints."""
+    a = w.cpu().numpy().astype("uint32").astype(object)
+    return [int(r[0]) | (int(r[1]) << 32) | (int(r[2]) << 64) | (int(r[3]) << 96) for r in a]
+
+
+def keys_wide(vectors, L: int, stream=None) -> list:
+    """128-bit cone id (Python int) of every row, for any N_C."""
+    torch = _torch()
+    v = _dev_f32(vectors, "vectors")
+    out = torch.empty((v.shape[0], 4), dtype=torch.int32, device=v.device)
+    _lib.check(load().osann_keys_wide(_ptr(v), v.shape[0], v.shape[1], L, _ptr(out), _stream_ptr(stream)))
+    return _wide_to_ints(out)
 
 
 def query_order(queries, stream=None):
@@ -105,18 +121,24 @@ def launch_count() -> int:
 class Index:
     """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
 
-    def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None, rot_offset=None):
-        """sync=False: osann_build_async (no synchronisation; call status()
-        before trusting results).  rot: d x d (a rotated basis,
-        osann_build_rot) or m x d (a projection on m components, e.g. PCA
-        axes, osann_build_proj) float32 CUDA tensor, the basis of the keys and
-        query orders; rot_offset: m offsets subtracted after projecting."""
+    def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None, rot_offset=None,
+                 cone_table: str = "auto"):
+        """sync=False: no final synchronisation (call status() before
+        trusting results).  rot: d x d (a rotated basis) or m x d (a
+        projection on m components, e.g. PCA axes) float32 CUDA tensor, the
+        basis of the keys and query orders; rot_offset: m offsets subtracted
+        after projecting.  cone_table: "auto" (a direct table when
+        N_C < 2^31), "dense" or "hashed" (the second-level table of occupied
+        cones); the results are the same."""
         torch = _torch()
         x = _dev_f32(data, "data")
         self.N, self.d = x.shape
         self.L = L
         self.device = x.device
         h = ctypes.c_void_p()
+        opts = _lib.BuildOpts()
+        opts.async_ = 0 if sync else 1
+        opts.cone_table = _lib.CONE_TABLES[cone_table]
         with torch.cuda.device(x.device):
             if rot is not None:
                 r = _dev_f32(rot, "rot")
@@ -128,17 +150,35 @@ class Index:
                     if off.numel() != r.shape[0]:
                         raise ValueError("rot_offset must hold m values")
                 self._basis = (r, off)  # read by the build in stream order
-                _lib.check(load().osann_build_proj(_ptr(x), self.N, self.d, L, _ptr(r), _ptr(off), r.shape[0],
-                                                   0 if sync else 1, _stream_ptr(stream), ctypes.byref(h)))
-            else:
-                build = load().osann_build if sync else load().osann_build_async
-                _lib.check(build(_ptr(x), self.N, self.d, L, _stream_ptr(stream), ctypes.byref(h)))
+                opts.d_basis = r.data_ptr()
+                opts.d_offset = off.data_ptr() if off is not None else None
+                opts.m = r.shape[0]
+            _lib.check(load().osann_build_ex(_ptr(x), self.N, self.d, L, ctypes.byref(opts), _stream_ptr(stream),
+                                             ctypes.byref(h)))
         self._h = h
         # an asynchronous build may still be reading the input: keep it until status()
         self._src = None if sync else x
         NC, mb = ctypes.c_int64(), ctypes.c_int64()
         _lib.check(load().osann_info(h, None, None, None, ctypes.byref(NC), ctypes.byref(mb)))
         self.NC, self.max_bucket = NC.value, mb.value
+        hashed, ncw = ctypes.c_int32(), (ctypes.c_uint64 * 2)()
+        _lib.check(load().osann_cones(h, ctypes.byref(hashed), ncw, None, None, None))
+        self.hashed = bool(hashed.value)
+        self.n_cones = int(ncw[0]) | (int(ncw[1]) << 64)  # N_C itself (NC: cones of the CSR table)
+
+    def occupied(self, stream=None) -> int:
+        """Cones holding at least one point (synchronises)."""
+        n = ctypes.c_int64()
+        _lib.check(load().osann_cones(self._h, None, None, None, ctypes.byref(n), _stream_ptr(stream)))
+        return n.value
+
+    def cone_ids(self, stream=None) -> list:
+        """128-bit id (Python int) of every compact cone of a second-level
+        table (all ones past the occupied cones)."""
+        torch = _torch()
+        out = torch.empty((self.NC, 4), dtype=torch.int32, device=self.device)
+        _lib.check(load().osann_export_cones(self._h, _ptr(out), _stream_ptr(stream)))
+        return _wide_to_ints(out)
 
     # -- lifetime
     def close(self):
@@ -211,7 +251,7 @@ class Index:
         torch = _torch()
         q = _dev_f32(queries, "queries")
         Q = q.shape[0]
-        P_eff = min(P, self.NC)
+        P_eff = min(P, self.n_cones)
         out = torch.empty((Q, P_eff), dtype=torch.int32, device=q.device)
         ws = torch.empty(self.workspace_size(Q, P, 1, "plain"), dtype=torch.uint8, device=q.device)
         _lib.check(load().osann_probes(self._h, _ptr(q), Q, P, _ptr(out), _ptr(ws), ws.numel(),
@@ -219,7 +259,8 @@ class Index:
         return out.to(torch.int64) & 0xFFFFFFFF
 
     def export(self, stream=None):
-        """(keys [N], offsets [N_C+1], perm [N]) as int64 tensors."""
+        """(keys [N], offsets [NC+1], perm [N]) as int64 tensors (NC: cones of
+        the CSR table; compact cones for a second-level table)."""
         torch = _torch()
         k = torch.empty(self.N, dtype=torch.int32, device=self.device)
         o = torch.empty(self.NC + 1, dtype=torch.int32, device=self.device)

@@ -23,6 +23,13 @@ ERRORS = {
     -6: "device wait timed out",
 }
 PATHS = {"auto": 0, "plain": 1, "batched": 2, "bf16": 3, "fp16": 4}
+CONE_TABLES = {"auto": 0, "dense": 1, "hashed": 2}
+
+
+class BuildOpts(c.Structure):
+    """osann_build_opts."""
+    _fields_ = [("d_basis", c.c_void_p), ("d_offset", c.c_void_p), ("m", c.c_int32), ("async_", c.c_int32),
+                ("cone_table", c.c_int32)]
 STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
           "plain_scan", "bruteforce", "tc_prep", "tc_scan", "tc_rerank"]
 STATUS_NONFINITE_DATA = 1
@@ -44,6 +51,12 @@ SIGNATURES = {
                                   c.c_void_p, c.POINTER(c.c_void_p)]),
     "osann_build_proj": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p,
                                    c.c_int32, c.c_int32, c.c_void_p, c.POINTER(c.c_void_p)]),
+    "osann_build_ex": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p,
+                                 c.POINTER(c.c_void_p)]),
+    "osann_cones": (c.c_int, [c.c_void_p, c.POINTER(c.c_int32), c.POINTER(c.c_uint64), c.POINTER(c.c_int64),
+                              c.POINTER(c.c_int64), c.c_void_p]),
+    "osann_export_cones": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_keys_wide": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p]),
     "osann_free": (c.c_int, [c.c_void_p]),
     "osann_info": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
                              c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),

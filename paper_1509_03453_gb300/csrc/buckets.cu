@@ -191,10 +191,8 @@ struct RadixPlan {
     int64_t nchunks;
 };
 
-static RadixPlan radix_plan(int64_t N, int64_t NC)
+static RadixPlan radix_plan_bits(int64_t N, int bits)
 {
-    int bits = 1;
-    while ((int64_t(1) << bits) < NC) ++bits;
     RadixPlan p;
     p.passes = (bits + 10) / 11;
     p.bits_per_pass = (bits + p.passes - 1) / p.passes;
@@ -203,8 +201,33 @@ static RadixPlan radix_plan(int64_t N, int64_t NC)
     return p;
 }
 
+static RadixPlan radix_plan(int64_t N, int64_t NC)
+{
+    int bits = 1;
+    while ((int64_t(1) << bits) < NC) ++bits;
+    return radix_plan_bits(N, bits);
+}
+
+// Digit of element i: bits [shift, shift + log2 B) of its key.  WIDE: the key
+// is the 128-bit id of the element's point (ids_in[i], or i in the first
+// pass), read from wkeys, instead of a carried 32-bit key.
+template <bool WIDE>
+__device__ __forceinline__ uint32_t radix_digit(const uint32_t* __restrict__ keys, const uint4* __restrict__ wkeys,
+                                                const uint32_t* __restrict__ ids_in, int64_t i, int shift,
+                                                uint32_t mask)
+{
+    if (WIDE) {
+        const uint32_t id = ids_in ? ids_in[i] : uint32_t(i);
+        return uint32_t(wide_value(wkeys[id]) >> shift) & mask;
+    }
+    return (keys[i] >> shift) & mask;
+}
+
 // Digit counts of one chunk: H[digit * nchunks + chunk].
-__global__ void __launch_bounds__(RADIX_WARPS * 32) radix_hist_kernel(const uint32_t* __restrict__ keys, int64_t N,
+template <bool WIDE>
+__global__ void __launch_bounds__(RADIX_WARPS * 32) radix_hist_kernel(const uint32_t* __restrict__ keys,
+                                                                      const uint4* __restrict__ wkeys,
+                                                                      const uint32_t* __restrict__ ids_in, int64_t N,
                                                                       int shift, int B, int64_t nchunks,
                                                                       uint32_t* __restrict__ H)
 {
@@ -215,7 +238,8 @@ __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_hist_kernel(const uint
     const int64_t begin = chunk * RADIX_CHUNK;
     const int64_t end = begin + RADIX_CHUNK < N ? begin + RADIX_CHUNK : N;
     const uint32_t mask = uint32_t(B - 1);
-    for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x) atomicAdd(&sh[(keys[i] >> shift) & mask], 1u);
+    for (int64_t i = begin + threadIdx.x; i < end; i += blockDim.x)
+        atomicAdd(&sh[radix_digit<WIDE>(keys, wkeys, ids_in, i, shift, mask)], 1u);
     __syncthreads();
     for (int dg = threadIdx.x; dg < B; dg += blockDim.x) H[int64_t(dg) * nchunks + chunk] = sh[dg];
 }
@@ -224,8 +248,10 @@ __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_hist_kernel(const uint
 // RADIX_WE) of the chunk: (1) per-warp digit counts in shared memory, (2) for
 // each digit a running sum over the warps from the chunk's scanned base, (3)
 // each warp places its elements in order (match_any ranks within a round).
+template <bool WIDE>
 __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_scatter_kernel(
-    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ ids_in, int64_t N, int shift, int B,
+    const uint32_t* __restrict__ keys_in, const uint4* __restrict__ wkeys, const uint32_t* __restrict__ ids_in,
+    int64_t N, int shift, int B,
     int64_t nchunks, const uint32_t* __restrict__ Hs, uint32_t* __restrict__ keys_out, uint32_t* __restrict__ ids_out,
     uint32_t* __restrict__ offsets_out, int64_t NC)
 {
@@ -249,9 +275,10 @@ __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_scatter_kernel(
     for (int r = 0; r < R; ++r) {
         const int64_t i = wbeg + 32 * r + lane;
         const bool live = i < wend;
-        key[r] = live ? keys_in[i] : 0u;
+        key[r] = live && !WIDE ? keys_in[i] : 0u;
         id[r] = live ? (ids_in ? ids_in[i] : uint32_t(i)) : 0u;
-        digit[r] = live ? ((key[r] >> shift) & mask) : 0xFFFFFFFFu;
+        digit[r] = !live ? 0xFFFFFFFFu
+                         : (WIDE ? radix_digit<true>(keys_in, wkeys, ids_in, i, shift, mask) : (key[r] >> shift) & mask);
     }
     __syncthreads();
     uint32_t* cnt = sh + warp * B;
@@ -278,7 +305,7 @@ __global__ void __launch_bounds__(RADIX_WARPS * 32) radix_scatter_kernel(
         if (live) {
             const uint32_t pos = cnt[digit[r]] + __popc(peers[r] & lt);
             ids_out[pos] = id[r];
-            if (keys_out) keys_out[pos] = key[r];
+            if (!WIDE && keys_out) keys_out[pos] = key[r];
         }
         __syncwarp();
         if (live && lane == __ffs(peers[r]) - 1) cnt[digit[r]] += __popc(peers[r]);
@@ -321,7 +348,8 @@ int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t
     const size_t hsmem = size_t(p.B) * 4, smem = size_t(RADIX_WARPS) * p.B * 4;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(radix_scatter_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(RADIX_WARPS * 2048 * 4));
+        cudaFuncSetAttribute(radix_scatter_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(RADIX_WARPS * 2048 * 4));
         attr_set = true;
     }
     const uint32_t* kin = keys;
@@ -331,16 +359,70 @@ int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t
         const bool last = pass == p.passes - 1;
         uint32_t* kout = last ? nullptr : (pass % 2 == 0 ? ka : kb);
         uint32_t* iout = last ? perm : (pass % 2 == 0 ? ia : ib);
-        radix_hist_kernel<<<blocks, RADIX_WARPS * 32, hsmem, st>>>(kin, N, shift, p.B, p.nchunks, H);
+        radix_hist_kernel<false><<<blocks, RADIX_WARPS * 32, hsmem, st>>>(kin, nullptr, nullptr, N, shift, p.B,
+                                                                         p.nchunks, H);
         int rc = count_launch();
         if (rc) return rc;
         rc = launch_exclusive_scan(H, H, hn, stemp, st);
         if (rc) return rc;
-        radix_scatter_kernel<<<blocks, RADIX_WARPS * 32, smem, st>>>(kin, iin, N, shift, p.B, p.nchunks, H, kout,
-                                                                     iout, p.passes == 1 ? offsets : nullptr, NC);
+        radix_scatter_kernel<false><<<blocks, RADIX_WARPS * 32, smem, st>>>(kin, nullptr, iin, N, shift, p.B,
+                                                                            p.nchunks, H, kout, iout,
+                                                                            p.passes == 1 ? offsets : nullptr, NC);
         rc = count_launch();
         if (rc) return rc;
         kin = kout;
+        iin = iout;
+    }
+    return 0;
+}
+
+size_t radix_temp_bytes_wide(int64_t N, int key_bits)
+{
+    RadixPlan p = radix_plan_bits(N, key_bits < 1 ? 1 : key_bits);
+    const int64_t hn = int64_t(p.B) * p.nchunks;
+    size_t b = size_t((hn + 63) / 64 * 64) * 4;
+    b += (scan_temp_bytes(hn) + 255) / 256 * 256;
+    b += size_t((N + 63) / 64 * 64) * 4 * 2;  // ids ping-pong
+    return b + 1024;
+}
+
+// Passes over the key_bits significant bits of the 128-bit ids, at most 11
+// bits each; ids are carried, keys read through them.
+int launch_stable_sort_wide(const uint4* wkeys, int64_t N, int key_bits, uint32_t* perm, void* temp, cudaStream_t st)
+{
+    if (N == 0) return 0;
+    RadixPlan p = radix_plan_bits(N, key_bits < 1 ? 1 : key_bits);
+    const int64_t hn = int64_t(p.B) * p.nchunks;
+    char* t = static_cast<char*>(temp);
+    uint32_t* H = reinterpret_cast<uint32_t*>(t);
+    t += size_t((hn + 63) / 64 * 64) * 4;
+    void* stemp = t;
+    t += (scan_temp_bytes(hn) + 255) / 256 * 256;
+    const size_t nb = size_t((N + 63) / 64 * 64) * 4;
+    uint32_t* ia = reinterpret_cast<uint32_t*>(t);
+    uint32_t* ib = reinterpret_cast<uint32_t*>(t + nb);
+    const unsigned blocks = unsigned(p.nchunks);
+    const size_t hsmem = size_t(p.B) * 4, smem = size_t(RADIX_WARPS) * p.B * 4;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(radix_scatter_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             int(RADIX_WARPS * 2048 * 4));
+        attr_set = true;
+    }
+    const uint32_t* iin = nullptr;
+    for (int pass = 0; pass < p.passes; ++pass) {
+        const int shift = pass * p.bits_per_pass;
+        uint32_t* iout = pass == p.passes - 1 ? perm : (pass % 2 == 0 ? ia : ib);
+        radix_hist_kernel<true><<<blocks, RADIX_WARPS * 32, hsmem, st>>>(nullptr, wkeys, iin, N, shift, p.B,
+                                                                        p.nchunks, H);
+        int rc = count_launch();
+        if (rc) return rc;
+        rc = launch_exclusive_scan(H, H, hn, stemp, st);
+        if (rc) return rc;
+        radix_scatter_kernel<true><<<blocks, RADIX_WARPS * 32, smem, st>>>(nullptr, wkeys, iin, N, shift, p.B,
+                                                                           p.nchunks, H, nullptr, iout, nullptr, 0);
+        rc = count_launch();
+        if (rc) return rc;
         iin = iout;
     }
     return 0;
@@ -443,27 +525,31 @@ int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32
     return count_launch();
 }
 
-__global__ void max_bucket_kernel(const uint32_t* __restrict__ offsets, int64_t NC, uint32_t* __restrict__ out)
+__global__ void max_bucket_kernel(const uint32_t* __restrict__ offsets, int64_t NC, uint32_t* __restrict__ out,
+                                  uint32_t* __restrict__ occ)
 {
-    uint32_t m = 0;
+    uint32_t m = 0, n = 0;
     for (int64_t c = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; c < NC; c += int64_t(gridDim.x) * blockDim.x) {
         uint32_t s = offsets[c + 1] - offsets[c];
         m = s > m ? s : m;
+        n += s > 0 ? 1u : 0u;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         uint32_t y = __shfl_xor_sync(0xffffffffu, m, o);
         m = y > m ? y : m;
+        n += __shfl_xor_sync(0xffffffffu, n, o);
     }
     if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
+    if ((threadIdx.x & 31) == 0 && occ && n) atomicAdd(occ, n);
 }
 
-int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st)
+int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st, uint32_t* out_occ)
 {
     int64_t blocks = (NC + 255) / 256;
     if (blocks > 1024) blocks = 1024;
     if (blocks < 1) blocks = 1;
-    max_bucket_kernel<<<unsigned(blocks), 256, 0, st>>>(offsets, NC, out_max);
+    max_bucket_kernel<<<unsigned(blocks), 256, 0, st>>>(offsets, NC, out_max, out_occ);
     return count_launch();
 }
 

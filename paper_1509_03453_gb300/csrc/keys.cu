@@ -53,16 +53,50 @@ __device__ __forceinline__ uint32_t cone_from_members(const int (&comp)[MAX_L], 
     return uint32_t((rank << L) | code);
 }
 
+// The same id in 128 bits (N_C >= 2^31: the second-level table).
+template <int LC>
+__device__ __forceinline__ uint4 cone_wide_from_members(const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L], int L,
+                                                        const ulonglong2* __restrict__ binom_w)
+{
+    constexpr int LM = LC > 0 ? LC : MAX_L;
+    u128 rank = 0;
+    uint32_t code = 0;
+#pragma unroll
+    for (int j = 0; j < LM; ++j) {
+        if (LC > 0 || j < L) {
+            int pos = 0;
+#pragma unroll
+            for (int t = 0; t < LM; ++t)
+                if ((LC > 0 || t < L) && comp[t] < comp[j]) ++pos;
+            rank += binom_wide(binom_w, comp[j], pos + 1);
+            code |= sgn[j] << (L - 1 - pos);
+        }
+    }
+    return wide_words((rank << L) | u128(code));
+}
+
+// Store the key of one row: a direct-table id, or (WIDE) a 128-bit id.
+template <int LC, bool WIDE>
+__device__ __forceinline__ void store_key(int64_t row, const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L], int L,
+                                          const uint64_t* __restrict__ binom, const ulonglong2* __restrict__ binom_w,
+                                          uint32_t* __restrict__ keys, uint4* __restrict__ wkeys)
+{
+    if (WIDE) wkeys[row] = cone_wide_from_members<LC>(comp, sgn, L, binom_w);
+    else keys[row] = cone_from_members<LC>(comp, sgn, L, binom);
+}
+
 // Vector path (d % 4 == 0, 16-byte aligned rows): one lane per row.  The
 // lane streams its row in pieces of up to KC float4 (the first line fetch
 // brings the piece's cache lines into L1 for the rest of the warp's loads)
 // and keeps the L largest selection keys in a sorted register list: one
 // 32-bit magnitude compare per component, the 64-bit key and an insertion
 // only when the component can enter the list.
-template <int LC>
+template <int LC, bool WIDE>
 __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                            const uint64_t* __restrict__ binom,
-                                                           uint32_t* __restrict__ keys, uint32_t* __restrict__ status,
+                                                           const ulonglong2* __restrict__ binom_w,
+                                                           uint32_t* __restrict__ keys, uint4* __restrict__ wkeys,
+                                                           uint32_t* __restrict__ status,
                                                            uint32_t* __restrict__ maxn2_bits)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
@@ -140,7 +174,7 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
                 comp[r] = sel_comp(top[r]);
                 sgn[r] = sel_sign(top[r]);
             }
-        keys[row] = cone_from_members<LC>(comp, sgn, L, binom);
+        store_key<LC, WIDE>(row, comp, sgn, L, binom, binom_w, keys, wkeys);
         nmax = fmaxf(nmax, nsq);  // non-finite rows are reported separately
     }
     if (maxn2_bits) {
@@ -155,10 +189,12 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
 // One group of LPV lanes per row.  VEC: d % 4 == 0 and 16-byte aligned rows,
 // lane l holds float4 number l, l+LPV (128-bit loads); else lane l holds the
 // scalars l, l+32, ... (LPV = 32).  At most 8 values per lane (d <= 256).
-template <int LPV, bool VEC, int LC>
+template <int LPV, bool VEC, int LC, bool WIDE>
 __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                        const uint64_t* __restrict__ binom,
-                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ status,
+                                                       const ulonglong2* __restrict__ binom_w,
+                                                       uint32_t* __restrict__ keys, uint4* __restrict__ wkeys,
+                                                       uint32_t* __restrict__ status,
                                                        uint32_t* __restrict__ maxn2_bits)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
@@ -240,7 +276,7 @@ __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict_
                     sgn[r] = sel_sign(best);
                 }
             }
-            if (rows[h] < N && glane == 0) keys[rows[h]] = cone_from_members<LC>(comp, sgn, L, binom);
+            if (rows[h] < N && glane == 0) store_key<LC, WIDE>(rows[h], comp, sgn, L, binom, binom_w, keys, wkeys);
 #pragma unroll
             for (int m = LPV / 2; m > 0; m >>= 1) nsq[h] += __shfl_xor_sync(0xffffffffu, nsq[h], m);
             nmax = fmaxf(nmax, nsq[h]);  // non-finite rows are reported separately
@@ -369,16 +405,18 @@ int launch_row_norm_max(const float* X, int64_t n, int d, uint32_t* maxn2_bits, 
     return count_launch();
 }
 
-template <int LC>
+template <int LC, bool WIDE = false>
 static void launch_keys_lc(bool vec, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d, int L,
-                           const uint64_t* binom, uint32_t* keys, uint32_t* status, uint32_t* maxn2)
+                           const uint64_t* binom, const ulonglong2* binom_w, uint32_t* keys, uint4* wkeys,
+                           uint32_t* status, uint32_t* maxn2)
 {
-    if (vec) data_keys_row_kernel<LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2);
-    else data_keys_kernel<32, false, LC><<<g, b, 0, st>>>(X, N, d, L, binom, keys, status, maxn2);
+    if (vec) data_keys_row_kernel<LC, WIDE><<<g, b, 0, st>>>(X, N, d, L, binom, binom_w, keys, wkeys, status, maxn2);
+    else data_keys_kernel<32, false, LC, WIDE><<<g, b, 0, st>>>(X, N, d, L, binom, binom_w, keys, wkeys, status, maxn2);
 }
 
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
-                     uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms)
+                     uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms,
+                     const ulonglong2* binom_w, uint4* wkeys)
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -388,12 +426,17 @@ int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* bi
     const int64_t cap = int64_t(num_sms) * (vec ? 8 : 16);
     if (blocks > cap) blocks = cap;
     const dim3 g(static_cast<unsigned>(blocks)), b(static_cast<unsigned>(threads));
+    if (wkeys) {
+        // 128-bit ids: one instantiation with a runtime L
+        launch_keys_lc<0, true>(vec, g, b, st, X, N, d, L, binom, binom_w, nullptr, wkeys, status, maxn2_bits);
+        return count_launch();
+    }
     switch (L) {
-    case 1: launch_keys_lc<1>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    case 2: launch_keys_lc<2>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    case 3: launch_keys_lc<3>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    case 4: launch_keys_lc<4>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
-    default: launch_keys_lc<0>(vec, g, b, st, X, N, d, L, binom, keys, status, maxn2_bits); break;
+    case 1: launch_keys_lc<1>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+    case 2: launch_keys_lc<2>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+    case 3: launch_keys_lc<3>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+    case 4: launch_keys_lc<4>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+    default: launch_keys_lc<0>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
     }
     return count_launch();
 }

@@ -21,6 +21,9 @@
 // Binomial coefficients C(n, k), n <= MAX_D, k <= MAX_L, saturated at
 // UINT64_MAX; used by the key (profile rank) and probe (unranking) kernels.
 __device__ uint64_t g_binom_table[(osann::MAX_D + 1) * (osann::MAX_L + 1)];
+// The same coefficients exact in 128 bits (low, high words): the ranks of
+// the second-level table's 128-bit cone ids.
+__device__ ulonglong2 g_binom_wide_table[(osann::MAX_D + 1) * (osann::MAX_L + 1)];
 // Status word for the stateless entry points (osann_keys, osann_query_order).
 __device__ uint32_t g_scratch_status[4];
 
@@ -92,6 +95,7 @@ struct DeviceState {
     bool ready = false;
     int num_sms = 0;
     uint64_t* binom = nullptr;
+    ulonglong2* binom_w = nullptr;
     uint32_t* scratch_status = nullptr;
 };
 static DeviceState g_dev[64];
@@ -123,6 +127,22 @@ static int device_state(DeviceState** out)
             }
         if ((e = cudaMemcpyToSymbol(g_binom_table, t.data(), t.size() * sizeof(uint64_t))) != cudaSuccess)
             return cuda_fail(e, "binomial table upload");
+        {
+            // Pascal's rule in 128 bits: C(256, 16) < 2^84, so nothing saturates
+            std::vector<unsigned __int128> w((MAX_D + 1) * (MAX_L + 1), 0);
+            std::vector<ulonglong2> wt(w.size());
+            for (int n = 0; n <= MAX_D; ++n)
+                for (int k = 0; k <= MAX_L; ++k) {
+                    unsigned __int128 v = k == 0 ? 1 : (n == 0 ? 0 : w[(n - 1) * (MAX_L + 1) + k - 1] +
+                                                                        w[(n - 1) * (MAX_L + 1) + k]);
+                    w[n * (MAX_L + 1) + k] = v;
+                    wt[n * (MAX_L + 1) + k] = make_ulonglong2(uint64_t(v), uint64_t(v >> 64));
+                }
+            if ((e = cudaMemcpyToSymbol(g_binom_wide_table, wt.data(), wt.size() * sizeof(ulonglong2))) != cudaSuccess)
+                return cuda_fail(e, "binomial table upload");
+            if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.binom_w), g_binom_wide_table)) != cudaSuccess)
+                return cuda_fail(e, "binomial table address");
+        }
         if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.binom), g_binom_table)) != cudaSuccess)
             return cuda_fail(e, "binomial table address");
         if ((e = cudaGetSymbolAddress(reinterpret_cast<void**>(&s.scratch_status), g_scratch_status)) != cudaSuccess)
@@ -207,7 +227,17 @@ static void stats_collect()
 using namespace osann;
 
 struct osann_index {
-    int64_t N = 0, NC = 0, max_bucket = 0;
+    // NC: cones of the CSR table (N_C for a direct table; min(N, N_C) + 1
+    // compact cones for the second-level table); nc_clamp: N_C itself,
+    // clamped to 2^62 (it bounds the probe budget)
+    int64_t N = 0, NC = 0, max_bucket = 0, nc_clamp = 0;
+    unsigned __int128 nc_true = 0;
+    bool hashed = false;          // second-level table (128-bit cone ids)
+    int key_bits = 0;             // significant bits of the 128-bit ids
+    uint4* ukeys = nullptr;       // [NC] 128-bit id of each compact cone (occupied ones first)
+    uint32_t* htab = nullptr;     // open-addressing table: id -> compact cone
+    uint32_t hmask = 0;
+    const ulonglong2* binom_w = nullptr;
     int d = 0, d_pad = 0, L = 0, device = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
     uint32_t* keys = nullptr;
@@ -291,20 +321,29 @@ static T* index_alloc(osann_index* ix, size_t count)
     return static_cast<T*>(p);
 }
 
-static int64_t cones_or_error(int d, int L)
+// N_C = C(d, L) 2^L, exact in 128 bits (below 2^100 for d <= MAX_D, L <= MAX_L).
+static int cone_count(int d, int L, unsigned __int128* nc)
 {
     if (d < 1 || L < 1 || L > d) return OSANN_ERR_INVALID;
     if (L > MAX_L || d > MAX_D) return OSANN_ERR_INVALID;
     // C(d, L) by the multiplicative formula; every prefix quotient is exact
     unsigned __int128 c = 1;
-    for (int i = 1; i <= L; ++i) {
-        c = c * (unsigned __int128)(d - L + i) / (unsigned __int128)i;
-        if (c > ((unsigned __int128)1 << 40)) return OSANN_ERR_UNSUPPORTED;
-    }
-    const unsigned __int128 nc = c << L;
+    for (int i = 1; i <= L; ++i) c = c * (unsigned __int128)(d - L + i) / (unsigned __int128)i;
+    *nc = c << L;
+    return OSANN_OK;
+}
+
+// N_C when a direct table can hold it (N_C < 2^31), else an error code.
+static int64_t cones_or_error(int d, int L)
+{
+    unsigned __int128 nc = 0;
+    const int rc = cone_count(d, L, &nc);
+    if (rc) return rc;
     if (nc >= ((unsigned __int128)1 << 31)) return OSANN_ERR_UNSUPPORTED;
     return int64_t(nc);
 }
+
+static int64_t p_eff(const osann_index* ix, int64_t P) { return P < ix->nc_clamp ? P : ix->nc_clamp; }
 
 static int pad_dim(int d)
 {
@@ -542,6 +581,25 @@ int osann_keys(const float* d_vectors, int64_t n, int32_t d, int32_t L, uint32_t
                             static_cast<cudaStream_t>(stream), ds->num_sms);
 }
 
+int osann_keys_wide(const float* d_vectors, int64_t n, int32_t d, int32_t L, uint32_t* d_ids, void* stream)
+{
+    unsigned __int128 nc = 0;
+    if (cone_count(d, L, &nc) != OSANN_OK || n < 0 || (n > 0 && (!d_vectors || !d_ids))) {
+        set_error("osann_keys_wide: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    if (reinterpret_cast<uintptr_t>(d_ids) & 15) {
+        set_error("osann_keys_wide: output must be 16-byte aligned");
+        return OSANN_ERR_INVALID;
+    }
+    DeviceState* ds;
+    int rc = device_state(&ds);
+    if (rc) return rc;
+    return launch_data_keys(d_vectors, n, d, L, ds->binom, nullptr, ds->scratch_status, nullptr,
+                            static_cast<cudaStream_t>(stream), ds->num_sms, ds->binom_w,
+                            reinterpret_cast<uint4*>(d_ids));
+}
+
 int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_order, uint32_t* d_signs, void* stream)
 {
     if (d < 1 || d > MAX_D || Q < 0 || (Q > 0 && (!d_queries || !d_order || !d_signs))) {
@@ -556,7 +614,7 @@ int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_o
 }
 
 static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, const float* d_off,
-                      int32_t m, void* stream, bool async, osann_index** out)
+                      int32_t m, void* stream, bool async, int32_t cone_table, osann_index** out)
 {
     if (!d_rot) m = d;
     if (d_rot && (m < 1 || m > d || d > 128)) {
@@ -569,16 +627,36 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         return OSANN_ERR_INVALID;
     }
     *out = nullptr;
-    const int64_t NC = cones_or_error(m, L);
-    if (NC < 0) {
-        set_error("osann_build: unsupported (d=%d, L=%d): need 1<=d<=%d, 1<=L<=min(d,%d), N_C < 2^31", d, L, MAX_D,
-                  MAX_L);
-        return int(NC);
+    if (cone_table < OSANN_CONES_AUTO || cone_table > OSANN_CONES_HASHED) {
+        set_error("osann_build: unknown cone table kind %d", cone_table);
+        return OSANN_ERR_INVALID;
+    }
+    unsigned __int128 nc_true = 0;
+    if (cone_count(m, L, &nc_true) != OSANN_OK) {
+        set_error("osann_build: unsupported (d=%d, L=%d): need 1<=d<=%d, 1<=L<=min(d,%d)", m, L, MAX_D, MAX_L);
+        return OSANN_ERR_INVALID;
     }
     if (N >= (int64_t(1) << 31)) {
         set_error("osann_build: N=%lld exceeds 2^31-1", (long long)N);
         return OSANN_ERR_UNSUPPORTED;
     }
+    // a direct table up to N_C < 2^31; beyond, the second-level table over
+    // the at most min(N, N_C) occupied cones (plus one empty cone)
+    const bool fits = nc_true < ((unsigned __int128)1 << 31);
+    if (cone_table == OSANN_CONES_DENSE && !fits) {
+        set_error("osann_build: N_C >= 2^31 (d=%d, L=%d) needs the second-level cone table", m, L);
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    const bool hashed = cone_table == OSANN_CONES_HASHED || (cone_table == OSANN_CONES_AUTO && !fits);
+    const int64_t NC = hashed ? (nc_true < (unsigned __int128)N ? int64_t(nc_true) : N) + 1 : int64_t(nc_true);
+    if (hashed && NC > (int64_t(1) << 30)) {
+        set_error("osann_build: a second-level table holds at most 2^30 cones (N=%lld)", (long long)N);
+        return OSANN_ERR_UNSUPPORTED;
+    }
+    int key_bits = 1;
+    while (key_bits < 127 && ((unsigned __int128)1 << key_bits) < nc_true) ++key_bits;
+    uint32_t hcap = 1;
+    while (int64_t(hcap) < 2 * NC) hcap <<= 1;
     DeviceState* ds;
     int rc = device_state(&ds);
     if (rc) return rc;
@@ -586,6 +664,12 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     osann_index* ix = new osann_index();
     ix->N = N;
     ix->NC = NC;
+    ix->nc_true = nc_true;
+    ix->nc_clamp = nc_true < ((unsigned __int128)1 << 62) ? int64_t(nc_true) : (int64_t(1) << 62);
+    ix->hashed = hashed;
+    ix->key_bits = key_bits;
+    ix->hmask = hcap - 1;
+    ix->binom_w = ds->binom_w;
     ix->d = d;
     ix->dk = m;
     ix->d_pad = pad_dim(d);
@@ -610,13 +694,21 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         ix->x16[1] = index_alloc<uint16_t>(ix, size_t(N) * ix->d_pad);
         ix->xe16[1] = index_alloc<uint16_t>(ix, size_t(N) * 16);
     }
-    const size_t counts_bytes = al256(size_t(NC + 1) * 4);
-    const size_t scan_bytes = al256(scan_temp_bytes(NC + 1));
-    const size_t radix_bytes = al256(radix_temp_bytes(N, NC));
-    const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes;
+    if (hashed) {
+        ix->ukeys = index_alloc<uint4>(ix, size_t(NC));
+        ix->htab = index_alloc<uint32_t>(ix, size_t(hcap));
+    }
+    // temporaries: direct table (counts, scan, radix) or second-level table
+    // (128-bit ids, wide radix sort, run heads and their scan)
+    const size_t counts_bytes = hashed ? 0 : al256(size_t(NC + 1) * 4);
+    const size_t scan_bytes = hashed ? al256(size_t(N) * 16) : al256(scan_temp_bytes(NC + 1));
+    const size_t radix_bytes = hashed ? al256(radix_temp_bytes_wide(N, key_bits)) : al256(radix_temp_bytes(N, NC));
+    const size_t table_bytes = hashed ? al256(cone_table_temp_bytes(N)) : 0;
+    const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes + table_bytes;
     char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
     if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->rowstat || !ix->status ||
-        !ix->diag || !ix->tcs || (tc_possible && (!ix->x16[1] || !ix->xe16[1])) || !temp) {
+        !ix->diag || !ix->tcs || (tc_possible && (!ix->x16[1] || !ix->xe16[1])) ||
+        (hashed && (!ix->ukeys || !ix->htab)) || !temp) {
         if (temp) dev_free(temp, temp_bytes, st);
         index_release(ix);
         set_error("osann_build: device allocation failed");
@@ -625,11 +717,13 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     uint32_t* counts = reinterpret_cast<uint32_t*>(temp);
     void* scan_temp = temp + counts_bytes;
     void* radix_temp = temp + counts_bytes + scan_bytes;
+    void* table_temp = temp + counts_bytes + scan_bytes + radix_bytes;
+    uint4* wkeys = hashed ? static_cast<uint4*>(scan_temp) : nullptr;  // 128-bit ids of the rows
 
     cudaMemsetAsync(ix->status, 0, 64 * 4, st);
     cudaMemsetAsync(ix->diag, 0, 8 * sizeof(unsigned long long), st);
     cudaMemsetAsync(ix->rowstat + N, 0, TC_N_ROWS * sizeof(float4), st);
-    cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
+    if (!hashed) cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
     {
         StageScope s(OSANN_STAGE_DATA_KEYS, st);
         // keys come from the rows' coordinates on the index's basis
@@ -652,7 +746,8 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
             }
         }
         if (!rc)
-            rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms);
+            rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms,
+                                  ds->binom_w, wkeys);
         // the fp16 scale and the norm bound need the original rows' norms, which
         // a projection or an offset does not keep
         if (!rc && d_rot && (m < d || d_off)) {
@@ -664,7 +759,12 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     }
     if (!rc) {
         StageScope s(OSANN_STAGE_BUCKETS, st);
-        if (radix_single_pass(NC)) {
+        if (hashed) {
+            rc = launch_stable_sort_wide(wkeys, N, key_bits, ix->perm, radix_temp, st);
+            if (!rc)
+                rc = launch_cone_table(wkeys, ix->perm, N, NC, ix->keys, ix->offsets, ix->ukeys, ix->status + 4,
+                                       ix->htab, ix->hmask, table_temp, st, ix->num_sms);
+        } else if (radix_single_pass(NC)) {
             rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, ix->offsets, radix_temp, st);
         } else {
             rc = launch_key_histogram(ix->keys, N, NC, counts, st, ix->num_sms);
@@ -677,7 +777,7 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->rowstat, ix->Bn,
                                 tc_possible ? ix->tcs + 4 : nullptr, ix->x16[1], ix->xe16[1], st, ix->num_sms);
     }
-    if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st);
+    if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st, ix->status + 3);
     dev_free(temp, temp_bytes, st);
     // the tensor maps need only addresses and sizes: encode them while the device works
     const bool maps_ok = !rc && tc_possible && tc_map_bytes() <= sizeof(ix->tmap[1]) &&
@@ -718,12 +818,24 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
 
 int osann_build(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, nullptr, nullptr, d, stream, false, out);
+    return build_impl(d_data, N, d, L, nullptr, nullptr, d, stream, false, OSANN_CONES_AUTO, out);
 }
 
 int osann_build_async(const float* d_data, int64_t N, int32_t d, int32_t L, void* stream, osann_index** out)
 {
-    return build_impl(d_data, N, d, L, nullptr, nullptr, d, stream, true, out);
+    return build_impl(d_data, N, d, L, nullptr, nullptr, d, stream, true, OSANN_CONES_AUTO, out);
+}
+
+int osann_build_ex(const float* d_data, int64_t N, int32_t d, int32_t L, const osann_build_opts* opts, void* stream,
+                   osann_index** out)
+{
+    if (!opts) return osann_build(d_data, N, d, L, stream, out);
+    if (!opts->d_basis && opts->d_offset) {
+        set_error("osann_build_ex: an offset needs a basis");
+        return OSANN_ERR_INVALID;
+    }
+    return build_impl(d_data, N, d, L, opts->d_basis, opts->d_offset, opts->d_basis ? opts->m : d, stream,
+                      opts->async != 0, opts->cone_table, out);
 }
 
 int osann_build_rot(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, int32_t async,
@@ -733,7 +845,7 @@ int osann_build_rot(const float* d_data, int64_t N, int32_t d, int32_t L, const 
         set_error("osann_build_rot: null basis");
         return OSANN_ERR_INVALID;
     }
-    return build_impl(d_data, N, d, L, d_rot, nullptr, d, stream, async != 0, out);
+    return build_impl(d_data, N, d, L, d_rot, nullptr, d, stream, async != 0, OSANN_CONES_AUTO, out);
 }
 
 int osann_build_proj(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_proj, const float* d_off,
@@ -743,7 +855,7 @@ int osann_build_proj(const float* d_data, int64_t N, int32_t d, int32_t L, const
         set_error("osann_build_proj: null projection");
         return OSANN_ERR_INVALID;
     }
-    return build_impl(d_data, N, d, L, d_proj, d_off, m, stream, async != 0, out);
+    return build_impl(d_data, N, d, L, d_proj, d_off, m, stream, async != 0, OSANN_CONES_AUTO, out);
 }
 
 int osann_free(osann_index* index)
@@ -784,6 +896,45 @@ int osann_export(const osann_index* ix, uint32_t* d_keys, uint32_t* d_offsets, u
     return e == cudaSuccess ? OSANN_OK : cuda_fail(e, "osann_export");
 }
 
+int osann_cones(const osann_index* ix, int32_t* hashed, uint64_t* n_cones, int64_t* table_cones, int64_t* occupied,
+                void* stream)
+{
+    if (!ix) {
+        set_error("osann_cones: null index");
+        return OSANN_ERR_INVALID;
+    }
+    if (hashed) *hashed = ix->hashed ? 1 : 0;
+    if (n_cones) {
+        n_cones[0] = uint64_t(ix->nc_true);
+        n_cones[1] = uint64_t(ix->nc_true >> 64);
+    }
+    if (table_cones) *table_cones = ix->NC;
+    if (occupied) {
+        cudaStream_t st = static_cast<cudaStream_t>(stream);
+        uint32_t h = 0;
+        cudaError_t e = cudaMemcpyAsync(&h, ix->status + 3, 4, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "osann_cones");
+        *occupied = h;
+    }
+    return OSANN_OK;
+}
+
+int osann_export_cones(const osann_index* ix, uint32_t* d_ids, void* stream)
+{
+    if (!ix || !d_ids) {
+        set_error("osann_export_cones: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    if (!ix->hashed) {
+        set_error("osann_export_cones: the index has a direct cone table");
+        return OSANN_ERR_INVALID;
+    }
+    cudaError_t e = cudaMemcpyAsync(d_ids, ix->ukeys, size_t(ix->NC) * 16, cudaMemcpyDeviceToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? OSANN_OK : cuda_fail(e, "osann_export_cones");
+}
+
 int osann_status(const osann_index* ix, void* stream, uint32_t* flags)
 {
     if (!ix || !flags) {
@@ -807,7 +958,7 @@ size_t osann_search_workspace_size_group(const osann_index* ix, int64_t Q, int32
 {
     if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K) return 0;
     if (path < 0 || path > OSANN_PATH_FP16 || group < 0) return 0;
-    const int64_t P_eff = P < ix->NC ? P : ix->NC;
+    const int64_t P_eff = p_eff(ix, P);
     return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path), group).total;
 }
 
@@ -835,10 +986,18 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
     }
     if (rc) return rc;
     StageScope s(OSANN_STAGE_PROBES, st);
+    WideTable wt{};
+    if (ix->hashed) {
+        wt.binom_w = ix->binom_w;
+        wt.ukeys = ix->ukeys;
+        wt.htab = ix->htab;
+        wt.hmask = ix->hmask;
+        wt.sentinel = uint32_t(ix->NC - 1);  // always empty
+    }
     return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Q, ix->dk,
                          ix->L, P_eff, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
                          transposed ? reinterpret_cast<uint32_t*>(w + L.probesT) : nullptr,
-                         init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st);
+                         init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st, wt);
 }
 
 int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32_t P, uint32_t* d_probes, void* d_ws,
@@ -850,7 +1009,7 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
     }
     if (Q == 0) return OSANN_OK;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int64_t P_eff = P < ix->NC ? P : ix->NC;
+    const int64_t P_eff = p_eff(ix, P);
     const WsLayout L = ws_layout(ix, Q, P_eff, 1, MODE_PLAIN);
     void* owned = nullptr;
     if (!d_ws) {
@@ -887,7 +1046,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_INVALID;
     }
     if (Q == 0) return OSANN_OK;
-    const int64_t P_eff = P < ix->NC ? P : ix->NC;
+    const int64_t P_eff = p_eff(ix, P);
     if (Q * P_eff >= (int64_t(1) << 32)) {
         set_error("osann_search: Q * min(P, N_C) must stay below 2^32");
         return OSANN_ERR_UNSUPPORTED;

@@ -25,6 +25,59 @@ constexpr int MAX_D = 256;
 constexpr int MAX_L = 16;
 constexpr int MAX_K = 32;
 
+// ---------------------------------------------------------------- wide cone ids
+// When N_C reaches 2^31 (the second-level table of Sec. 4) a cone id is the
+// same number rank(S) * 2^L + sign code, held in 128 bits (N_C < 2^127 for
+// every d <= MAX_D, L <= MAX_L) and stored as four 32-bit words, low first.
+typedef unsigned __int128 u128;
+
+// C(n, k) in 128 bits from a table of (low, high) words, n <= MAX_D, k <= MAX_L.
+__device__ __forceinline__ u128 binom_wide(const ulonglong2* __restrict__ t, int n, int k)
+{
+    const ulonglong2 v = __ldg(t + n * (MAX_L + 1) + k);
+    return (u128(v.y) << 64) | u128(v.x);
+}
+__device__ __forceinline__ uint4 wide_words(u128 k)
+{
+    return make_uint4(uint32_t(k), uint32_t(k >> 32), uint32_t(k >> 64), uint32_t(k >> 96));
+}
+__device__ __forceinline__ u128 wide_value(uint4 w)
+{
+    return (u128(w.w) << 96) | (u128(w.z) << 64) | (u128(w.y) << 32) | u128(w.x);
+}
+__device__ __forceinline__ bool wide_eq(uint4 a, uint4 b) { return a.x == b.x && a.y == b.y && a.z == b.z && a.w == b.w; }
+
+// Slot of a cone id in the open-addressing table: the 64-bit finaliser of
+// SplitMix64 (Steele, Lea and Flood, 2014) over the folded words.
+__device__ __forceinline__ uint32_t cone_hash(uint4 w)
+{
+    uint64_t h = (uint64_t(w.y) << 32 | w.x) ^ ((uint64_t(w.w) << 32 | w.z) * 0x9E3779B97F4A7C15ull);
+    h ^= h >> 30;
+    h *= 0xBF58476D1CE4E5B9ull;
+    h ^= h >> 27;
+    h *= 0x94D049BB133111EBull;
+    h ^= h >> 31;
+    return uint32_t(h);
+}
+constexpr uint32_t HASH_EMPTY = 0xFFFFFFFFu;
+
+// Compact cone of a 128-bit id: the table (capacity hmask + 1, a power of
+// two at least twice the occupied cones, linear probing) holds the compact
+// index of each occupied cone; an id that no point carries maps to
+// `sentinel`, a compact cone with no rows.
+__device__ __forceinline__ uint32_t cone_lookup(uint4 key, const uint4* __restrict__ ukeys,
+                                                const uint32_t* __restrict__ htab, uint32_t hmask, uint32_t sentinel)
+{
+    uint32_t h = cone_hash(key) & hmask;
+    for (uint32_t it = 0; it <= hmask; ++it) {
+        const uint32_t v = __ldg(htab + h);
+        if (v == HASH_EMPTY) break;
+        if (wide_eq(__ldg(ukeys + v), key)) return v;
+        h = (h + 1) & hmask;
+    }
+    return sentinel;
+}
+
 // Squared distances are >= 0, so their IEEE bit patterns order like the
 // values; packing (dist bits, id) into a u64 makes u64 order the
 // lexicographic (distance, id) order used for every top-k in this library.

@@ -20,8 +20,11 @@ void add_launches(int64_t n);
 int64_t launch_total();
 
 // keys.cu
+// maxn2 may be null; wkeys non-null: 128-bit ids (four words per row) from
+// the 128-bit binomial table binom_w instead of keys
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
-                     uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms);  // maxn2 may be null
+                     uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms,
+                     const ulonglong2* binom_w = nullptr, uint4* wkeys = nullptr);
 // out (n x m) = rows of X on the m basis rows of Pm (m x d) minus off (null:
 // none), fp32 in-order FMAs then one subtraction; d <= 128, m <= d (else -2)
 int launch_rotate_rows(const float* Pm, const float* off, const float* X, int64_t n, int d, int m, float* out,
@@ -42,16 +45,39 @@ size_t radix_temp_bytes(int64_t N, int64_t NC);
 bool radix_single_pass(int64_t NC);
 int launch_stable_sort_ids(const uint32_t* keys, int64_t N, int64_t NC, uint32_t* perm, uint32_t* offsets, void* temp,
                            cudaStream_t st);
+// LSD radix sort of the ids 0..N-1 by 128-bit key (key_bits significant
+// bits), stable: perm[i] = the id at sorted position i
+size_t radix_temp_bytes_wide(int64_t N, int key_bits);
+int launch_stable_sort_wide(const uint4* wkeys, int64_t N, int key_bits, uint32_t* perm, void* temp, cudaStream_t st);
 int launch_gather_rows(const float* X, int64_t N, int d, int d_pad, const uint32_t* perm, float* xs, float4* rowstat,
                        float Bn, const float* tcs, uint16_t* x16, uint16_t* xe16, cudaStream_t st,
                        int num_sms);  // tcs, x16, xe16 null: no fp16 operands
 int launch_tc_scale(int prec, const uint32_t* maxn2_bits, float* tcs, cudaStream_t st);
-int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st);
+// out_max: largest cone size (atomicMax); out_occ (nullable): occupied cones (atomicAdd)
+int launch_max_bucket(const uint32_t* offsets, int64_t NC, uint32_t* out_max, cudaStream_t st,
+                      uint32_t* out_occ = nullptr);
+
+// cone_table.cu: the second-level table of occupied cones.  From perm
+// (sorted by 128-bit id) and the ids: keys[row] = compact cone, offsets over
+// the NCt compact cones (cones past the occupied ones are empty), ukeys[c] =
+// the 128-bit id of compact cone c, the occupied count in *n_occ, and the
+// hash table (hmask + 1 slots) from ids to compact cones.
+size_t cone_table_temp_bytes(int64_t N);
+int launch_cone_table(const uint4* wkeys, const uint32_t* perm, int64_t N, int64_t NCt, uint32_t* keys,
+                      uint32_t* offsets, uint4* ukeys, uint32_t* n_occ, uint32_t* htab, uint32_t hmask, void* temp,
+                      cudaStream_t st, int num_sms);
 
 // probes.cu
+// Lookup of 128-bit probe ids in a second-level table (null htab: a direct table).
+struct WideTable {
+    const ulonglong2* binom_w = nullptr;
+    const uint4* ukeys = nullptr;
+    const uint32_t* htab = nullptr;
+    uint32_t hmask = 0, sentinel = 0;
+};
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
                   const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
-                  cudaStream_t st);  // probesT (p-major copy) may be null
+                  cudaStream_t st, const WideTable& wt = WideTable{});  // probesT (p-major copy) may be null
 
 // scan_plain.cu
 int launch_plain_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad,

@@ -47,12 +47,15 @@ __device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, u
 }
 
 // LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
-template <int LC>
+// WIDE: 128-bit cone ids looked up in the second-level table (wt); the
+// unranking above still uses the saturated 64-bit binomials, which is exact
+// for positions below 2^32 (a saturated count only exceeds the position).
+template <int LC, bool WIDE>
 __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
                                                      const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
                                                      int64_t P_eff, const uint64_t* __restrict__ binom,
                                                      uint32_t* __restrict__ probes, uint32_t* __restrict__ probesT,
-                                                     uint64_t* __restrict__ partial, int k)
+                                                     uint64_t* __restrict__ partial, int k, const WideTable wt)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
     if (LC > 0) L = LC;
@@ -111,6 +114,7 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
     }
     // cone id of the profile with the query's signs (and the chosen flips)
     uint64_t rank = 0;
+    u128 rank_w = 0;
     uint32_t code = 0;
 #pragma unroll
     for (int j = 0; j < LM; ++j) {
@@ -125,11 +129,14 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
             }
             uint32_t bit = (sg[cm[j] >> 5] >> (cm[j] & 31)) & 1u;
             bit ^= (flip >> asc) & 1u;
-            rank += C(binom, cm[j], pos + 1);
+            if (WIDE) rank_w += binom_wide(wt.binom_w, cm[j], pos + 1);
+            else rank += C(binom, cm[j], pos + 1);
             code |= bit << (L - 1 - pos);
         }
     }
-    const uint32_t cone = uint32_t((rank << L) | code);
+    const uint32_t cone = WIDE ? cone_lookup(wide_words((rank_w << L) | u128(code)), wt.ukeys, wt.htab, wt.hmask,
+                                             wt.sentinel)
+                               : uint32_t((rank << L) | code);
     probes[t] = cone;
     if (probesT) probesT[int64_t(t - q * P_eff) * Q + q] = cone;  // probe-position-major copy
     if (partial)
@@ -137,18 +144,26 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
 }
 
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k, cudaStream_t st)
+                  const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k, cudaStream_t st,
+                  const WideTable& wt)
 {
     const int64_t n = Q * P_eff;
     if (n == 0) return 0;
     const unsigned g = unsigned((n + 255) / 256);
-    switch (L) {
-    case 1: probes_kernel<1><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
-    case 2: probes_kernel<2><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
-    case 3: probes_kernel<3><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
-    case 4: probes_kernel<4><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
-    default: probes_kernel<0><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k); break;
+#define OSANN_PROBES(LC, W) \
+    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k, wt)
+    if (wt.htab) {
+        OSANN_PROBES(0, true);
+        return count_launch();
     }
+    switch (L) {
+    case 1: OSANN_PROBES(1, false); break;
+    case 2: OSANN_PROBES(2, false); break;
+    case 3: OSANN_PROBES(3, false); break;
+    case 4: OSANN_PROBES(4, false); break;
+    default: OSANN_PROBES(0, false); break;
+    }
+#undef OSANN_PROBES
     return count_launch();
 }
 

@@ -101,8 +101,11 @@ def test_errors_are_loud(osann):
         osann.Index(to_dev(X), 9)                  # L > d
     assert e.value.code == -1
     with pytest.raises(OsannError) as e:
-        osann.Index(to_dev(np.zeros((10, 64), np.float32)), 16)   # N_C >= 2^31
+        osann.Index(to_dev(np.zeros((10, 64), np.float32)), 16, cone_table="dense")   # N_C >= 2^31
     assert e.value.code == -2
+    with pytest.raises(OsannError) as e:
+        osann.Index(to_dev(np.zeros((10, 64), np.float32)), 17)   # L > 16
+    assert e.value.code == -1
     idx = osann.Index(to_dev(X), 2)
     with pytest.raises(OsannError):
         idx.search(to_dev(X[:3]), 4, 33)          # k > 32
