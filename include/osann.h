@@ -122,8 +122,8 @@ int osann_build(const float *d_data, int64_t N, int32_t d, int32_t L, void *stre
 int osann_build_rot(const float *d_data, int64_t N, int32_t d, int32_t L, const float *d_rot, int32_t async,
                     void *stream, osann_index **out);
 
-/* The PCA front-end of Sec. 4-B ("classify on the first PCA components,
- * search on all"): as osann_build_rot with a projection on m <= d
+/* The PCA front-end of Sec. 4-B (cone keys from the leading principal
+ * components, distances on all of them): as osann_build_rot with a projection on m <= d
  * components, d_proj (m x d fp32, row r = axis r) and optional offsets d_off
  * (m fp32, the projected mean; NULL: none): keys and query orders come from
  * y_r = (sum_j d_proj[r][j] x_j) - d_off[r] (fp32 in-order fused
@@ -142,8 +142,8 @@ int osann_build_async(const float *d_data, int64_t N, int32_t d, int32_t L, void
 
 /* Cone table kinds for osann_build_ex.  A direct table holds all N_C cones
  * (CSR offsets over the cone ids) and needs N_C < 2^31.  The second-level
- * table (Sec. 4: "a second-level hash table is used ... when the number of
- * cones grows very large") keeps only the occupied cones: the point ids
+ * table (Sec. 4: an extra hash level for cone counts too large for a
+ * direct table) keeps only the occupied cones: the point ids
  * are sorted by 128-bit cone id (osann_keys_wide), the occupied cones are
  * numbered 0..n_occ-1 in ascending id order ("compact" cones), offsets span
  * NC_t = min(N, N_C) + 1 compact cones (those from n_occ on are empty), and

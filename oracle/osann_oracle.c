@@ -209,9 +209,8 @@ void oracle_buckets(const uint32_t *keys, int64_t N, int64_t NC,
     free(cursor);
 }
 
-/* Second-level table for large N_C (Sec. 4: "a second-level hash table is
- * used ... when the number of cones grows very large"): only occupied cones
- * are kept.  perm[N] lists the point ids sorted by (128-bit cone id, id);
+/* Second-level table for large N_C (Sec. 4 keeps a further hash level for
+ * cone counts too large for a direct table): only occupied cones are kept.  perm[N] lists the point ids sorted by (128-bit cone id, id);
  * uniq[2 * n_occ] holds the distinct ids in ascending order (low, high
  * words) and offsets[n_occ + 1] the start of each one's points in perm.
  * Returns n_occ.  The sort is the C library's qsort on (cone id, point id)

@@ -1,5 +1,5 @@
-// Second-level cone table (Sec. 4: when the number of cones grows very large,
-// a second-level hash table manages the per-basis tables).
+// Second-level cone table (Sec. 4: an extra hash level over the per-basis
+// tables once the cone count is too large for a direct table).
 //
 // With N_C >= 2^31 the direct CSR over all N_C cones cannot be allocated, but
 // at most min(N, N_C) cones hold a point.  The build sorts the point ids by
