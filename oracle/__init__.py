@@ -36,7 +36,8 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared",
+    # no contraction of a*b+c into fused multiply-adds: the same roundings on x86 and Arm
+    subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-ffp-contract=off", "-fPIC", "-shared",
                            "-o", tmp, _SRC, "-lm"])
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -95,6 +96,16 @@ def lib():
         L.oracle_search_wide.argtypes = [
             _f32p, c.c_int64, c.c_int, c.c_int, c.c_int64, _u64p, _u32p, _u32p, _f32p, c.c_int64,
             c.c_int64, c.c_int, c.c_void_p, c.c_int64, c.c_int64, _i64p, _f64p, c.c_void_p]
+        L.oracle_sqdist_f32.restype = c.c_float
+        L.oracle_sqdist_f32.argtypes = [_f32p, _f32p, c.c_int]
+        L.oracle_nearest_centroids.restype = None
+        L.oracle_nearest_centroids.argtypes = [_f32p, c.c_int64, c.c_int, _f32p, c.c_int, c.c_int, _i32p]
+        L.oracle_keys_clustered.restype = c.c_int
+        L.oracle_keys_clustered.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _f32p, c.c_int, _u64p, _i32p]
+        L.oracle_search_clustered.restype = None
+        L.oracle_search_clustered.argtypes = [
+            _f32p, c.c_int64, c.c_int, c.c_int, _f32p, c.c_int, c.c_int, c.c_int64, _u64p, _u32p, _u32p,
+            _f32p, c.c_int64, c.c_int64, c.c_int, _i64p, _f64p, c.c_void_p]
         L.oracle_pair_dists.restype = None
         L.oracle_pair_dists.argtypes = [_f32p, c.c_int, _f32p, c.c_int64,
                                         c.c_int, _i64p, _f64p]
@@ -250,6 +261,59 @@ class WideIndex:
             src, grid_w, radius, ids, dists,
             counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
         del keep
+        ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
+        return (ids, dists, counts) if want_counts else (ids, dists)
+
+
+def sqdist_f32(x, y) -> float:
+    """The kernels' fp32 squared distance (padded float4 pieces, pairwise tree)."""
+    x, y = _f32(x), _f32(y)
+    return float(lib().oracle_sqdist_f32(x, y, x.shape[-1]))
+
+
+def nearest_centroids(X, C, M: int) -> np.ndarray:
+    """[n, M] indices of the M nearest centroids (fp32 distance, then index)."""
+    X, C = _f32(np.atleast_2d(X)), _f32(C)
+    out = np.empty((X.shape[0], M), np.int32)
+    lib().oracle_nearest_centroids(X, X.shape[0], X.shape[1], C, C.shape[0], M, out)
+    return out
+
+
+class ClusteredIndex:
+    """ROSANNA+ oracle (Sec. 4-B): points assigned to their nearest of K
+    given centroids, hashed by their residual, stored under the composite
+    id cluster * N_C + cone; the search visits the query's M nearest
+    clusters."""
+
+    def __init__(self, X, L: int, centroids):
+        self.X = _f32(X)
+        self.N, self.d = self.X.shape
+        self.L = L
+        self.C = _f32(centroids)
+        self.K = self.C.shape[0]
+        self.NC = num_cones_wide(self.d, L)
+        kw = np.empty(2 * self.N, np.uint64)
+        self.asg = np.empty(self.N, np.int32)
+        if lib().oracle_keys_clustered(self.X, self.N, self.d, L, self.C, self.K, kw, self.asg) != 0:
+            raise ValueError("K * N_C does not fit in 127 bits")
+        self.keys = _wide_ints(kw)
+        self.perm = np.empty(self.N, np.uint32)
+        uniq = np.empty(2 * max(self.N, 1), np.uint64)
+        offs = np.empty(self.N + 1, np.uint32)
+        self.n_occ = int(lib().oracle_buckets_wide(kw, self.N, self.perm, uniq, offs))
+        self._uniq = np.ascontiguousarray(uniq[:2 * max(self.n_occ, 1)])
+        self.uniq = _wide_ints(uniq[:2 * self.n_occ])
+        self.offsets = offs[:self.n_occ + 1].copy()
+
+    def search(self, Y, M: int, P: int, k: int, want_counts: bool = False):
+        Y = _f32(Y)
+        Q = Y.shape[0]
+        ids = np.empty(Q * k, np.int64)
+        dists = np.empty(Q * k, np.float64)
+        counts = np.empty(Q, np.int64) if want_counts else None
+        lib().oracle_search_clustered(
+            self.X, self.N, self.d, self.L, self.C, self.K, M, self.n_occ, self._uniq, self.offsets, self.perm,
+            Y, Q, P, k, ids, dists, counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
         ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
         return (ids, dists, counts) if want_counts else (ids, dists)
 

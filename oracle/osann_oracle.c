@@ -41,6 +41,15 @@
  *     sign code held in 128 bits; only the occupied cones are stored, in
  *     ascending id order, and a probed cone that holds no point is skipped
  *     (it still counts against the budget C).
+ *   - ROSANNA+ (Sec. 4-B): the k-means centroids are an input (clustered
+ *     off line); a point belongs to its nearest centroid and is hashed by
+ *     its residual x - c (fp32 subtraction); the cone id inside the
+ *     composite table is cluster * N_C + cone id of the residual; a query
+ *     visits its M nearest clusters (nearest first), in each the first
+ *     min(C, N_C) cones of its residual y - c.  "Nearest" is decided in fp32
+ *     by the canonical expression of the GPU kernels (oracle_sqdist_f32),
+ *     ties to the lower centroid index, so both sides take the same integer
+ *     decisions; candidate distances stay in double precision.
  * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
  * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
  * The intra-class probe order and the sign-flip extension are this
@@ -507,6 +516,131 @@ void oracle_search_wide(const float *X, int64_t N, int d, int L, int64_t n_occ,
         if (cand_count) cand_count[q] = cands;
     }
     free(probes);
+}
+
+/* ---------------------------------------------------------------- ROSANNA+ */
+
+/* Squared distance in fp32 in the order every GPU kernel evaluates it: the
+ * vectors zero padded to d_pad = max(16, next power of two >= d), cut into
+ * float4 pieces j, piece j giving fma(t3,t3, fma(t2,t2, fma(t1,t1, t0*t0)))
+ * with t = x - y, and the pieces summed by a perfect binary tree that pairs
+ * adjacent pieces first.  Used only where a float decides an integer (the
+ * nearest centroid), so that the oracle takes the kernels' decision. */
+float oracle_sqdist_f32(const float *x, const float *y, int d)
+{
+    int dp = 16;
+    while (dp < d) dp <<= 1;
+    int n = dp / 4;
+    float c[ORACLE_MAX_D / 4];
+    for (int j = 0; j < n; ++j) {
+        float t[4];
+        for (int e = 0; e < 4; ++e) {
+            int i = 4 * j + e;
+            t[e] = i < d ? x[i] - y[i] : 0.0f;
+        }
+        c[j] = fmaf(t[3], t[3], fmaf(t[2], t[2], fmaf(t[1], t[1], t[0] * t[0])));
+    }
+    for (int w = 1; w < n; w <<= 1)
+        for (int j = 0; j < n; j += 2 * w) c[j] = c[j] + c[j + w];
+    return c[0];
+}
+
+/* The M nearest of K centroids (K x d) of each of n vectors, nearest first,
+ * by (oracle_sqdist_f32, centroid index): out[i * M + j]. */
+void oracle_nearest_centroids(const float *X, int64_t n, int d, const float *C, int K, int M, int32_t *out)
+{
+    float *bd = (float *)malloc(sizeof(float) * (size_t)M);
+    for (int64_t i = 0; i < n; ++i) {
+        int32_t *bi = out + i * M;
+        for (int j = 0; j < M; ++j) { bd[j] = INFINITY; bi[j] = -1; }
+        for (int c = 0; c < K; ++c) {
+            float dist = oracle_sqdist_f32(X + i * d, C + (int64_t)c * d, d);
+            /* insertion by (distance, index); c ascending, so a tie never moves in front */
+            if (bi[M - 1] >= 0 && !(dist < bd[M - 1])) continue;
+            int j = M - 1;
+            while (j > 0 && (bi[j - 1] < 0 || bd[j - 1] > dist)) {
+                bd[j] = bd[j - 1];
+                bi[j] = bi[j - 1];
+                --j;
+            }
+            bd[j] = dist;
+            bi[j] = c;
+        }
+    }
+    free(bd);
+}
+
+/* Composite 128-bit cone ids of ROSANNA+ (two words per point) and the
+ * cluster of each point: asg[n] = nearest centroid, residual r = x - c in
+ * fp32, id = asg * N_C + cone id of r.  Returns -1 if K * N_C >= 2^127. */
+int oracle_keys_clustered(const float *X, int64_t N, int d, int L, const float *C, int K, uint64_t *keys,
+                          int32_t *asg)
+{
+    uint64_t nc[2];
+    if (oracle_num_cones_wide(d, L, nc) != 0) return -1;
+    u128 NC = ((u128)nc[1] << 64) | nc[0];
+    if ((u128)K > (((u128)1 << 127) - 1) / NC) return -1;
+    float *r = (float *)malloc(sizeof(float) * (size_t)d);
+    int32_t order[ORACLE_MAX_D];
+    oracle_nearest_centroids(X, N, d, C, K, 1, asg);
+    for (int64_t n = 0; n < N; ++n) {
+        const float *c = C + (int64_t)asg[n] * d;
+        for (int i = 0; i < d; ++i) r[i] = X[n * d + i] - c[i];
+        oracle_magnitude_order(r, d, order);
+        u128 k = (u128)asg[n] * NC + cone_of_profile_wide(order, L, r, NULL, 0);
+        keys[2 * n] = (uint64_t)k;
+        keys[2 * n + 1] = (uint64_t)(k >> 64);
+    }
+    free(r);
+    return 0;
+}
+
+/* ROSANNA+ search over the composite table of oracle_buckets_wide (keys of
+ * oracle_keys_clustered): for each of the query's M nearest clusters,
+ * nearest first, the first min(P, N_C) cones of the residual y - c,
+ * looked up among the occupied composite ids; exact top-k over the
+ * candidates (the clusters are disjoint, so no point is seen twice). */
+void oracle_search_clustered(const float *X, int64_t N, int d, int L, const float *C, int K, int M,
+                             int64_t n_occ, const uint64_t *uniq, const uint32_t *offsets, const uint32_t *perm,
+                             const float *Y, int64_t Q, int64_t P, int k, int64_t *ids, double *dists,
+                             int64_t *cand_count)
+{
+    (void)N;
+    (void)K;
+    uint64_t nc[2];
+    if (oracle_num_cones_wide(d, L, nc) != 0) return;
+    u128 NC = ((u128)nc[1] << 64) | nc[0];
+    if ((u128)P > NC) P = (int64_t)NC;
+    uint64_t *probes = (uint64_t *)malloc(sizeof(uint64_t) * 2 * (size_t)(P > 0 ? P : 1));
+    int32_t *near = (int32_t *)malloc(sizeof(int32_t) * (size_t)M);
+    float *r = (float *)malloc(sizeof(float) * (size_t)d);
+    for (int64_t q = 0; q < Q; ++q) {
+        const float *y = Y + q * d;
+        double *bd = dists + q * k;
+        int64_t *bi = ids + q * k;
+        topk_init(bd, bi, k);
+        oracle_nearest_centroids(y, 1, d, C, K, M, near);
+        int64_t cands = 0;
+        for (int j = 0; j < M; ++j) {
+            if (near[j] < 0) continue;
+            const float *c = C + (int64_t)near[j] * d;
+            for (int i = 0; i < d; ++i) r[i] = y[i] - c[i];
+            int64_t np = oracle_probes_wide(r, d, L, P, probes);
+            for (int64_t l = 0; l < np; ++l) {
+                int64_t cc = find_cone(uniq, n_occ, (u128)near[j] * NC + wide_at(probes, l));
+                if (cc < 0) continue;
+                for (uint32_t row = offsets[cc]; row < offsets[cc + 1]; ++row) {
+                    int64_t n = perm[row];
+                    ++cands;
+                    topk_insert(bd, bi, k, sqdist(X + n * d, y, d), n);
+                }
+            }
+        }
+        if (cand_count) cand_count[q] = cands;
+    }
+    free(probes);
+    free(near);
+    free(r);
 }
 
 /* Coordinates on a rotated basis (Sec. 3-D, "projection of y on the r-th
