@@ -160,13 +160,25 @@ typedef struct {
     int32_t m;             /* rows of d_basis (ignored without one) */
     int32_t async;         /* nonzero: no final synchronisation (as osann_build_async) */
     int32_t cone_table;    /* OSANN_CONES_* */
+    const float *d_centroids; /* ROSANNA+: K x d k-means centroids (see below), NULL: none */
+    int32_t n_clusters;       /* K (0: none) */
 } osann_build_opts;
 
 /* Build with explicit options (opts NULL: as osann_build).  Every other
  * build entry point is this one with the matching options and
- * OSANN_CONES_AUTO.  Errors as osann_build, plus: UNSUPPORTED for
- * OSANN_CONES_DENSE with N_C >= 2^31, and for a second-level table of more
- * than 2^30 cones. */
+ * OSANN_CONES_AUTO.
+ * ROSANNA+ (Sec. 4-B: data clustered off line by k-means, a query searching
+ * only its nearest clusters): with d_centroids (K x d fp32, read during the
+ * build; the index keeps a copy) every point belongs to its nearest centroid
+ * c -- by the library's fp32 squared distance (float4 pieces, adjacent-
+ * pairwise tree), ties to the lower index -- and is hashed by its residual
+ * x - c (fp32); its cone id is cluster * N_C + cone id of the residual, so
+ * the table holds K * N_C cones (a second-level table from 2^31 on).
+ * Search with osann_search_clusters; osann_search visits the nearest
+ * cluster only.  Needs d <= 128, 1 <= K <= 2^24, no key basis.
+ * Errors as osann_build, plus: INVALID for a bad cluster set-up,
+ * UNSUPPORTED for OSANN_CONES_DENSE with N_C >= 2^31, and for a
+ * second-level table of more than 2^30 cones. */
 int osann_build_ex(const float *d_data, int64_t N, int32_t d, int32_t L, const osann_build_opts *opts, void *stream,
                    osann_index **out);
 
@@ -216,6 +228,18 @@ int osann_probes(const osann_index *index, const float *d_queries, int64_t Q, in
 /* Workspace bytes that osann_search / osann_search_excl need for (Q, P, k)
  * on `path`. */
 size_t osann_search_workspace_size(const osann_index *index, int64_t Q, int32_t P, int32_t k, int32_t path);
+
+/* ROSANNA+ search (Sec. 4-B) on an index built with centroids: each query
+ * visits its M nearest clusters (1 <= M <= 32, clamped to K; nearest first, as in the
+ * build), in each the first min(P, N_C) cones of its residual y - c in the
+ * order of osann_probes; exact top-k over all their points, as osann_search
+ * (same paths, same bits on every path).  Workspace:
+ * osann_search_clusters_workspace_size(index, Q, M, P, k, path). */
+size_t osann_search_clusters_workspace_size(const osann_index *index, int64_t Q, int32_t M, int32_t P, int32_t k,
+                                            int32_t path);
+int osann_search_clusters(const osann_index *index, const float *d_queries, int64_t Q, int32_t M, int32_t P,
+                          int32_t k, int32_t path, void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists,
+                          void *stream);
 
 /* ROSANNA search with one basis (Algorithm 1, R = 1): hash each query,
  * visit its first P_eff = min(P, N_C) cones in the order of osann_probes and

@@ -122,14 +122,17 @@ class Index:
     """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
 
     def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None, rot_offset=None,
-                 cone_table: str = "auto"):
+                 cone_table: str = "auto", centroids=None):
         """sync=False: no final synchronisation (call status() before
         trusting results).  rot: d x d (a rotated basis) or m x d (a
         projection on m components, e.g. PCA axes) float32 CUDA tensor, the
         basis of the keys and query orders; rot_offset: m offsets subtracted
         after projecting.  cone_table: "auto" (a direct table when
         N_C < 2^31), "dense" or "hashed" (the second-level table of occupied
-        cones); the results are the same."""
+        cones); the results are the same.  centroids: K x d float32 CUDA
+        tensor (ROSANNA+, e.g. from kmeans.kmeans): points hashed by their
+        residual on their nearest centroid; search(..., clusters=M) visits
+        a query's M nearest clusters."""
         torch = _torch()
         x = _dev_f32(data, "data")
         self.N, self.d = x.shape
@@ -153,6 +156,15 @@ class Index:
                 opts.d_basis = r.data_ptr()
                 opts.d_offset = off.data_ptr() if off is not None else None
                 opts.m = r.shape[0]
+            self.K = 0
+            if centroids is not None:
+                cc = _dev_f32(centroids, "centroids")
+                if cc.shape[1] != self.d:
+                    raise ValueError("centroids must be K x d")
+                self._cent = cc  # read by the build in stream order
+                opts.d_centroids = cc.data_ptr()
+                opts.n_clusters = cc.shape[0]
+                self.K = cc.shape[0]
             _lib.check(load().osann_build_ex(_ptr(x), self.N, self.d, L, ctypes.byref(opts), _stream_ptr(stream),
                                              ctypes.byref(h)))
         self._h = h
@@ -203,12 +215,17 @@ class Index:
         return int(load().osann_search_workspace_size_group(self._h, Q, P, k, PATHS[path], group))
 
     def search(self, queries, P: int, k: int, path: str = "auto", query_src=None, grid_w: int = 0,
-               radius: int = 0, stream=None, out=None, workspace=None, group: int = 0):
+               radius: int = 0, stream=None, out=None, workspace=None, group: int = 0, clusters: int = 1):
         """Top-k by exact squared distance over the first min(P, N_C)
         probed cones.  Returns (ids int64 [Q,k], sqdists float32 [Q,k]).
         ``group``: queries per work-list item on the batched paths (0 =
-        default); it changes the speed, not the result."""
+        default); it changes the speed, not the result.  ``clusters``
+        (ROSANNA+ index): nearest clusters visited, P cones in each."""
         torch = _torch()
+        if clusters != 1:
+            if query_src is not None or group:
+                raise ValueError("clusters > 1 takes no exclusion and no group size")
+            return self._search_clusters(queries, clusters, P, k, path, stream, out, workspace)
         q = _dev_f32(queries, "queries")
         Q = q.shape[0]
         if q.shape[1] != self.d:
@@ -229,6 +246,24 @@ class Index:
             rc = L.osann_search_excl(self._h, _ptr(q), _ptr(src), Q, P, k, grid_w, radius, PATHS[path],
                                      _ptr(ws), ws.numel(), _ptr(ids), _ptr(d2), _stream_ptr(stream))
         _lib.check(rc)
+        return ids, d2
+
+    def _search_clusters(self, queries, M, P, k, path, stream, out, workspace):
+        torch = _torch()
+        q = _dev_f32(queries, "queries")
+        Q = q.shape[0]
+        if q.shape[1] != self.d:
+            raise ValueError("query dimension differs from the index's")
+        if out is None:
+            ids = torch.empty((Q, k), dtype=torch.int64, device=q.device)
+            d2 = torch.empty((Q, k), dtype=torch.float32, device=q.device)
+        else:
+            ids, d2 = out
+        L = load()
+        ws_bytes = int(L.osann_search_clusters_workspace_size(self._h, Q, M, P, k, PATHS[path]))
+        ws = workspace if workspace is not None else torch.empty(ws_bytes, dtype=torch.uint8, device=q.device)
+        _lib.check(L.osann_search_clusters(self._h, _ptr(q), Q, M, P, k, PATHS[path], _ptr(ws), ws.numel(),
+                                           _ptr(ids), _ptr(d2), _stream_ptr(stream)))
         return ids, d2
 
     def bruteforce(self, queries, k: int, query_src=None, grid_w: int = 0, radius: int = 0, stream=None):

@@ -29,7 +29,7 @@ CONE_TABLES = {"auto": 0, "dense": 1, "hashed": 2}
 class BuildOpts(c.Structure):
     """osann_build_opts."""
     _fields_ = [("d_basis", c.c_void_p), ("d_offset", c.c_void_p), ("m", c.c_int32), ("async_", c.c_int32),
-                ("cone_table", c.c_int32)]
+                ("cone_table", c.c_int32), ("d_centroids", c.c_void_p), ("n_clusters", c.c_int32)]
 STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
           "plain_scan", "bruteforce", "tc_prep", "tc_scan", "tc_rerank"]
 STATUS_NONFINITE_DATA = 1
@@ -57,6 +57,10 @@ SIGNATURES = {
                               c.POINTER(c.c_int64), c.c_void_p]),
     "osann_export_cones": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
     "osann_keys_wide": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p]),
+    "osann_search_clusters": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
+                                        c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_search_clusters_workspace_size": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
+                                                          c.c_int32]),
     "osann_free": (c.c_int, [c.c_void_p]),
     "osann_info": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
                              c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),

@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libosann.so")
 SOURCES = ["osann.cu", "keys.cu", "buckets.cu", "probes.cu", "scan_plain.cu", "scan_batched.cu",
            "static_search.cu", "tc_scan.cu", "server.cu",
-           "shard_merge.cu", "cone_table.cu"]
+           "shard_merge.cu", "cone_table.cu", "clusters.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

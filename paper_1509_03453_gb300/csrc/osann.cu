@@ -238,6 +238,12 @@ struct osann_index {
     uint32_t* htab = nullptr;     // open-addressing table: id -> compact cone
     uint32_t hmask = 0;
     const ulonglong2* binom_w = nullptr;
+    // ROSANNA+: K centroids (K x d_pad, zero padded); cone ids are
+    // cluster * ncc + cone of the residual (ncc = N_C of one cluster), and
+    // nc_clamp bounds the budget per cluster
+    int K = 0;
+    float* cent = nullptr;
+    unsigned __int128 ncc = 0;
     int d = 0, d_pad = 0, L = 0, device = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
     uint32_t* keys = nullptr;
@@ -344,6 +350,8 @@ static int64_t cones_or_error(int d, int L)
 }
 
 static int64_t p_eff(const osann_index* ix, int64_t P) { return P < ix->nc_clamp ? P : ix->nc_clamp; }
+// clusters visited per query: M, at most K (1 without clusters)
+static int clusters_of(const osann_index* ix, int32_t M) { return ix->K ? (M < ix->K ? M : ix->K) : 1; }
 
 static int pad_dim(int d)
 {
@@ -361,7 +369,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, yrot;
+    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, yrot, vcl;
     size_t total;
     int64_t max_items;
 };
@@ -448,7 +456,9 @@ static int item_group(const osann_index* ix, int mode, int group)
     return group >= 1 && group <= gmax ? group : gmax;
 }
 
-static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, int mode, int group = 0)
+// P_eff: probe slots per query (Mv lists of P_eff / Mv positions with
+// clusters); Mv: key rows per query (the residuals on its Mv clusters)
+static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, int mode, int group = 0, int Mv = 1)
 {
     WsLayout w{};
     size_t off = 0;
@@ -457,9 +467,11 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         off = al256(off + bytes);
         return o;
     };
-    w.qorder = take(size_t(Q) * ix->dk);
-    if (ix->rot) w.yrot = take(size_t(Q) * ix->dk * 4);
-    w.qsign = take(size_t(Q) * (MAX_D / 32) * 4);
+    const int64_t Qv = Q * Mv;
+    w.qorder = take(size_t(Qv) * ix->dk);
+    if (ix->rot || ix->K) w.yrot = take(size_t(Qv) * ix->dk * 4);
+    if (ix->K) w.vcl = take(size_t(Qv) * 4);
+    w.qsign = take(size_t(Qv) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
     if (mode != MODE_PLAIN) {
         const int G = item_group(ix, mode, group);
@@ -614,7 +626,8 @@ int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_o
 }
 
 static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, const float* d_off,
-                      int32_t m, void* stream, bool async, int32_t cone_table, osann_index** out)
+                      int32_t m, void* stream, bool async, int32_t cone_table, osann_index** out,
+                      const float* d_cent = nullptr, int32_t K = 0)
 {
     if (!d_rot) m = d;
     if (d_rot && (m < 1 || m > d || d > 128)) {
@@ -636,6 +649,12 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         set_error("osann_build: unsupported (d=%d, L=%d): need 1<=d<=%d, 1<=L<=min(d,%d)", m, L, MAX_D, MAX_L);
         return OSANN_ERR_INVALID;
     }
+    const unsigned __int128 ncc = nc_true;  // cones of one cluster
+    if (K < 0 || (K > 0 && (!d_cent || d_rot || d > 128 || K > (1 << 24)))) {
+        set_error("osann_build: clusters need 1 <= K <= 2^24 centroids, d <= 128 and no key basis (K=%d d=%d)", K, d);
+        return OSANN_ERR_INVALID;
+    }
+    if (K > 0) nc_true *= (unsigned __int128)K;  // composite ids cluster * N_C + cone
     if (N >= (int64_t(1) << 31)) {
         set_error("osann_build: N=%lld exceeds 2^31-1", (long long)N);
         return OSANN_ERR_UNSUPPORTED;
@@ -665,7 +684,9 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     ix->N = N;
     ix->NC = NC;
     ix->nc_true = nc_true;
-    ix->nc_clamp = nc_true < ((unsigned __int128)1 << 62) ? int64_t(nc_true) : (int64_t(1) << 62);
+    ix->nc_clamp = ncc < ((unsigned __int128)1 << 62) ? int64_t(ncc) : (int64_t(1) << 62);
+    ix->K = K;
+    ix->ncc = ncc;
     ix->hashed = hashed;
     ix->key_bits = key_bits;
     ix->hmask = hcap - 1;
@@ -698,6 +719,7 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         ix->ukeys = index_alloc<uint4>(ix, size_t(NC));
         ix->htab = index_alloc<uint32_t>(ix, size_t(hcap));
     }
+    if (K > 0) ix->cent = index_alloc<float>(ix, size_t(K) * ix->d_pad);
     // temporaries: direct table (counts, scan, radix) or second-level table
     // (128-bit ids, wide radix sort, run heads and their scan)
     const size_t counts_bytes = hashed ? 0 : al256(size_t(NC + 1) * 4);
@@ -708,7 +730,7 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
     if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->rowstat || !ix->status ||
         !ix->diag || !ix->tcs || (tc_possible && (!ix->x16[1] || !ix->xe16[1])) ||
-        (hashed && (!ix->ukeys || !ix->htab)) || !temp) {
+        (hashed && (!ix->ukeys || !ix->htab)) || (K > 0 && !ix->cent) || !temp) {
         if (temp) dev_free(temp, temp_bytes, st);
         index_release(ix);
         set_error("osann_build: device allocation failed");
@@ -729,7 +751,26 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         // keys come from the rows' coordinates on the index's basis
         const float* key_src = d_data;
         float* xr = nullptr;
-        if (d_rot) {
+        uint32_t* asg = nullptr;
+        if (K > 0) {
+            // ROSANNA+: each point's nearest centroid, then its residual
+            cudaError_t e = cudaMemsetAsync(ix->cent, 0, size_t(K) * ix->d_pad * 4, st);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DAsync(ix->cent, size_t(ix->d_pad) * 4, d_cent, size_t(d) * 4, size_t(d) * 4, size_t(K),
+                                      cudaMemcpyDeviceToDevice, st);
+            xr = static_cast<float*>(dev_alloc(size_t(N) * d * 4, st));
+            asg = static_cast<uint32_t*>(dev_alloc(size_t(N) * 4, st));
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "osann_build: centroids");
+            } else if (!xr || !asg) {
+                set_error("osann_build: device allocation failed");
+                rc = OSANN_ERR_OOM;
+            } else {
+                rc = launch_nearest_centroids(d_data, N, d, ix->d_pad, ix->cent, K, 1, asg, st);
+                if (!rc) rc = launch_residual_rows(d_data, N, d, ix->cent, ix->d_pad, asg, 1, xr, st, ix->num_sms);
+                key_src = xr;
+            }
+        } else if (d_rot) {
             ix->rot = index_alloc<float>(ix, size_t(m) * d);
             if (d_off) ix->rot_off = index_alloc<float>(ix, size_t(m));
             xr = static_cast<float*>(dev_alloc(size_t(N) * m * 4, st));
@@ -748,13 +789,16 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         if (!rc)
             rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms,
                                   ds->binom_w, wkeys);
+        if (!rc && K > 0)
+            rc = launch_composite_keys(asg, N, uint64_t(ncc), uint64_t(ncc >> 64), ix->keys, wkeys, st, ix->num_sms);
         // the fp16 scale and the norm bound need the original rows' norms, which
-        // a projection or an offset does not keep
-        if (!rc && d_rot && (m < d || d_off)) {
+        // a projection, an offset or a residual does not keep
+        if (!rc && ((d_rot && (m < d || d_off)) || K > 0)) {
             cudaMemsetAsync(ix->status + 2, 0, 4, st);
             rc = launch_row_norm_max(d_data, N, d, ix->status + 2, st, ix->num_sms);
         }
         if (xr) dev_free(xr, size_t(N) * m * 4, st);
+        if (asg) dev_free(asg, size_t(N) * 4, st);
         if (!rc && tc_possible) rc = launch_tc_scale(1, ix->status + 2, ix->tcs + 4, st);
     }
     if (!rc) {
@@ -835,7 +879,7 @@ int osann_build_ex(const float* d_data, int64_t N, int32_t d, int32_t L, const o
         return OSANN_ERR_INVALID;
     }
     return build_impl(d_data, N, d, L, opts->d_basis, opts->d_offset, opts->d_basis ? opts->m : d, stream,
-                      opts->async != 0, opts->cone_table, out);
+                      opts->async != 0, opts->cone_table, out, opts->d_centroids, opts->n_clusters);
 }
 
 int osann_build_rot(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, int32_t async,
@@ -962,15 +1006,30 @@ size_t osann_search_workspace_size_group(const osann_index* ix, int64_t Q, int32
     return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path), group).total;
 }
 
+size_t osann_search_clusters_workspace_size(const osann_index* ix, int64_t Q, int32_t M, int32_t P, int32_t k,
+                                            int32_t path)
+{
+    if (!ix || Q < 0 || M < 1 || P < 1 || k < 1 || k > MAX_K) return 0;
+    if (path < 0 || path > OSANN_PATH_FP16) return 0;
+    const int Mv = clusters_of(ix, M);
+    const int64_t P_eff = Mv * p_eff(ix, P);
+    return ws_layout(ix, Q, P_eff, k, choose_mode(ix, Q, P_eff, path), 0, Mv).total;
+}
+
 size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, int32_t k, int32_t path)
 {
     return osann_search_workspace_size_group(ix, Q, P, k, path, 0);
 }
 
-static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_eff, const WsLayout& L, char* w,
-                       bool init_partial, bool transposed, int k, cudaStream_t st)
+// Query keys and probe lists.  P_per: positions per key row; Mv: key rows
+// per query (its Mv nearest clusters with ROSANNA+, else 1); the probe list
+// of query q is rows q * Mv .. q * Mv + Mv - 1 in turn (Mv * P_per slots).
+static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_per, int Mv, const WsLayout& L,
+                       char* w, bool init_partial, bool transposed, int k, cudaStream_t st)
 {
     int rc = 0;
+    const int64_t Qv = Q * Mv;
+    uint32_t* vcl = ix->K ? reinterpret_cast<uint32_t*>(w + L.vcl) : nullptr;
     {
         StageScope s(OSANN_STAGE_QUERY_ORDER, st);
         // on a rotated basis the magnitude order is that of the query's coordinates there
@@ -979,25 +1038,38 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
             rc = launch_rotate_rows(ix->rot, ix->rot_off, Y, Q, ix->d, ix->dk, reinterpret_cast<float*>(w + L.yrot), st,
                                     ix->num_sms);
             Yk = reinterpret_cast<const float*>(w + L.yrot);
+        } else if (ix->K) {
+            // ROSANNA+: the residuals on the query's Mv nearest clusters
+            rc = launch_nearest_centroids(Y, Q, ix->d, ix->d_pad, ix->cent, ix->K, Mv, vcl, st);
+            if (!rc)
+                rc = launch_residual_rows(Y, Q, ix->d, ix->cent, ix->d_pad, vcl, Mv,
+                                          reinterpret_cast<float*>(w + L.yrot), st, ix->num_sms);
+            Yk = reinterpret_cast<const float*>(w + L.yrot);
         }
         if (!rc)
-            rc = launch_query_order(Yk, Q, ix->dk, reinterpret_cast<uint8_t*>(w + L.qorder),
+            rc = launch_query_order(Yk, Qv, ix->dk, reinterpret_cast<uint8_t*>(w + L.qorder),
                                     reinterpret_cast<uint32_t*>(w + L.qsign), ix->status, st);
     }
     if (rc) return rc;
     StageScope s(OSANN_STAGE_PROBES, st);
-    WideTable wt{};
+    ProbeMap pm{};
     if (ix->hashed) {
-        wt.binom_w = ix->binom_w;
-        wt.ukeys = ix->ukeys;
-        wt.htab = ix->htab;
-        wt.hmask = ix->hmask;
-        wt.sentinel = uint32_t(ix->NC - 1);  // always empty
+        pm.binom_w = ix->binom_w;
+        pm.ukeys = ix->ukeys;
+        pm.htab = ix->htab;
+        pm.hmask = ix->hmask;
+        pm.sentinel = uint32_t(ix->NC - 1);  // always empty
     }
-    return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Q, ix->dk,
-                         ix->L, P_eff, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
+    if (ix->K) {
+        pm.M = Mv;
+        pm.vcl = vcl;
+        pm.ncc_lo = uint64_t(ix->ncc);
+        pm.ncc_hi = uint64_t(ix->ncc >> 64);
+    }
+    return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Qv, ix->dk,
+                         ix->L, P_per, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
                          transposed ? reinterpret_cast<uint32_t*>(w + L.probesT) : nullptr,
-                         init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st, wt);
+                         init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st, pm);
 }
 
 int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32_t P, uint32_t* d_probes, void* d_ws,
@@ -1023,7 +1095,7 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, d_queries, Q, P_eff, L, w, false, false, 1, st);
+    int rc = query_front(ix, d_queries, Q, P_eff, 1, L, w, false, false, 1, st);
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(d_probes, w + L.probes, size_t(Q) * P_eff * 4, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "osann_probes");
@@ -1034,9 +1106,9 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
 
 static int search_impl(const osann_index* ix, const float* Y, const int64_t* src, int64_t Q, int32_t P, int32_t k,
                        int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
-                       float* dists, void* stream, int32_t group = 0)
+                       float* dists, void* stream, int32_t group = 0, int32_t M = 1)
 {
-    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 || group < 0 ||
+    if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 || group < 0 || M < 1 ||
         (Q > 0 && (!Y || !ids || !dists))) {
         set_error("osann_search: invalid arguments (Q=%lld P=%d k=%d path=%d)", (long long)Q, P, k, path);
         return OSANN_ERR_INVALID;
@@ -1045,8 +1117,14 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         set_error("osann_search_excl: grid_w must be >= 1 and radius >= 0");
         return OSANN_ERR_INVALID;
     }
+    if (ix->K && M > 32) {
+        set_error("osann_search_clusters: at most 32 clusters per query (M=%d)", M);
+        return OSANN_ERR_INVALID;
+    }
     if (Q == 0) return OSANN_OK;
-    const int64_t P_eff = p_eff(ix, P);
+    const int Mv = clusters_of(ix, M);
+    const int64_t P_per = p_eff(ix, P);
+    const int64_t P_eff = Mv * P_per;  // probe slots per query
     if (Q * P_eff >= (int64_t(1) << 32)) {
         set_error("osann_search: Q * min(P, N_C) must stay below 2^32");
         return OSANN_ERR_UNSUPPORTED;
@@ -1059,7 +1137,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         if (trc) return trc;
     }
     const bool batched = mode != MODE_PLAIN;
-    const WsLayout L = ws_layout(ix, Q, P_eff, k, mode, group);
+    const WsLayout L = ws_layout(ix, Q, P_eff, k, mode, group, Mv);
     void* owned = nullptr;
     if (!d_ws) {
         owned = d_ws = dev_alloc(L.total, st);
@@ -1072,7 +1150,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, Y, Q, P_eff, L, w, mode == MODE_BATCHED, batched, k, st);
+    int rc = query_front(ix, Y, Q, P_per, Mv, L, w, mode == MODE_BATCHED, batched, k, st);
     if (!rc && batched) {
         BatchedBuffers b{};
         b.qcount = reinterpret_cast<uint32_t*>(w + L.qcount);
@@ -1173,6 +1251,13 @@ int osann_search_group(const osann_index* index, const float* d_queries, int64_t
                        void* stream)
 {
     return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, group);
+}
+
+int osann_search_clusters(const osann_index* index, const float* d_queries, int64_t Q, int32_t M, int32_t P,
+                          int32_t k, int32_t path, void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists,
+                          void* stream)
+{
+    return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, 0, M);
 }
 
 int osann_search_excl(const osann_index* index, const float* d_queries, const int64_t* d_query_src, int64_t Q,

@@ -68,16 +68,34 @@ int launch_cone_table(const uint4* wkeys, const uint32_t* perm, int64_t N, int64
                       cudaStream_t st, int num_sms);
 
 // probes.cu
-// Lookup of 128-bit probe ids in a second-level table (null htab: a direct table).
-struct WideTable {
+// How probed cone ids become table cones.  Second-level table (htab non-null):
+// 128-bit ids looked up, unoccupied ones to `sentinel`.  Clusters (vcl
+// non-null, ROSANNA+): the Q rows of qorder/qsign are M residuals per query
+// (row q * M + j on cluster vcl[q * M + j]), each with P_eff positions; the
+// id is vcl * ncc + cone, and query q's list is its M lists in turn.
+struct ProbeMap {
     const ulonglong2* binom_w = nullptr;
     const uint4* ukeys = nullptr;
     const uint32_t* htab = nullptr;
     uint32_t hmask = 0, sentinel = 0;
+    int M = 1;
+    const uint32_t* vcl = nullptr;
+    uint64_t ncc_lo = 0, ncc_hi = 0;
 };
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
                   const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
-                  cudaStream_t st, const WideTable& wt = WideTable{});  // probesT (p-major copy) may be null
+                  cudaStream_t st, const ProbeMap& pm = ProbeMap{});  // probesT (p-major copy) may be null
+
+// clusters.cu (ROSANNA+): nearest M of K centroids (K x d_pad, zero padded;
+// d_pad <= 128, M <= min(K, 32)) by the canonical fp32 distance, ties to the
+// lower index; residual rows X[v] - C[idx[v * M + j]]; composite ids
+// asg * ncc + key (keys, or the 128-bit wkeys)
+int launch_nearest_centroids(const float* X, int64_t n, int d, int d_pad, const float* C, int K, int M,
+                             uint32_t* out, cudaStream_t st);
+int launch_residual_rows(const float* X, int64_t n, int d, const float* C, int d_pad, const uint32_t* idx, int M,
+                         float* out, cudaStream_t st, int num_sms);
+int launch_composite_keys(const uint32_t* asg, int64_t N, uint64_t ncc_lo, uint64_t ncc_hi, uint32_t* keys,
+                          uint4* wkeys, cudaStream_t st, int num_sms);
 
 // scan_plain.cu
 int launch_plain_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad,

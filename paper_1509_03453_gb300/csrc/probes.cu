@@ -47,21 +47,22 @@ __device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, u
 }
 
 // LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
-// WIDE: 128-bit cone ids looked up in the second-level table (wt); the
+// WIDE: 128-bit cone ids looked up in the second-level table (pm); the
 // unranking above still uses the saturated 64-bit binomials, which is exact
 // for positions below 2^32 (a saturated count only exceeds the position).
+// Q counts the rows of qorder/qsign: pm.M per query with clusters.
 template <int LC, bool WIDE>
 __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
                                                      const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
                                                      int64_t P_eff, const uint64_t* __restrict__ binom,
                                                      uint32_t* __restrict__ probes, uint32_t* __restrict__ probesT,
-                                                     uint64_t* __restrict__ partial, int k, const WideTable wt)
+                                                     uint64_t* __restrict__ partial, int k, const ProbeMap pm)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
     if (LC > 0) L = LC;
     const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (t >= Q * P_eff) return;
-    const int64_t q = t / P_eff;
+    const int64_t q = t / P_eff;  // row of qorder/qsign
     uint64_t idx = uint64_t(t - q * P_eff);
     const uint8_t* ord = qorder + q * int64_t(d);
     const uint32_t* sg = qsign + q * (MAX_D / 32);
@@ -129,30 +130,41 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
             }
             uint32_t bit = (sg[cm[j] >> 5] >> (cm[j] & 31)) & 1u;
             bit ^= (flip >> asc) & 1u;
-            if (WIDE) rank_w += binom_wide(wt.binom_w, cm[j], pos + 1);
+            if (WIDE) rank_w += binom_wide(pm.binom_w, cm[j], pos + 1);
             else rank += C(binom, cm[j], pos + 1);
             code |= bit << (L - 1 - pos);
         }
     }
-    const uint32_t cone = WIDE ? cone_lookup(wide_words((rank_w << L) | u128(code)), wt.ukeys, wt.htab, wt.hmask,
-                                             wt.sentinel)
-                               : uint32_t((rank << L) | code);
+    const uint32_t cl = pm.vcl ? pm.vcl[q] : 0u;
+    uint32_t cone;
+    if (WIDE) {
+        u128 id = (rank_w << L) | u128(code);
+        if (pm.vcl) id += u128(cl) * ((u128(pm.ncc_hi) << 64) | u128(pm.ncc_lo));
+        cone = cone_lookup(wide_words(id), pm.ukeys, pm.htab, pm.hmask, pm.sentinel);
+    } else {
+        cone = uint32_t((rank << L) | code) + cl * uint32_t(pm.ncc_lo);
+    }
+    // slot of this position in its query's list: query q / M, position
+    // (q % M) * P_eff + p; its flat index is t either way
     probes[t] = cone;
-    if (probesT) probesT[int64_t(t - q * P_eff) * Q + q] = cone;  // probe-position-major copy
+    if (probesT) {
+        const int64_t qr = q / pm.M, Qr = Q / pm.M;
+        probesT[(t - qr * pm.M * P_eff) * Qr + qr] = cone;  // probe-position-major copy
+    }
     if (partial)
         for (int j = 0; j < k; ++j) partial[t * k + j] = EMPTY_DI;
 }
 
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
                   const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k, cudaStream_t st,
-                  const WideTable& wt)
+                  const ProbeMap& pm)
 {
     const int64_t n = Q * P_eff;
     if (n == 0) return 0;
     const unsigned g = unsigned((n + 255) / 256);
 #define OSANN_PROBES(LC, W) \
-    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k, wt)
-    if (wt.htab) {
+    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k, pm)
+    if (pm.htab) {
         OSANN_PROBES(0, true);
         return count_launch();
     }
