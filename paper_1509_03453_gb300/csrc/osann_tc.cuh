@@ -142,12 +142,11 @@ __device__ __forceinline__ void tmem_ld32x2(uint32_t taddr, float (&v)[64])
     for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// As tmem_ld32x2, with the minimum of each thread's 64 values computed by
-// the load itself (tcgen05.ld.red .min over the columns each thread loads).
-__device__ __forceinline__ void tmem_ld32x2_min(uint32_t taddr, float (&v)[64], float& vmin)
+// As tmem_ld32x2, with the minimum of each thread's first and last 32 values
+// (m0, m1) computed by the loads themselves (tcgen05.ld.red .min).
+__device__ __forceinline__ void tmem_ld32x2_min(uint32_t taddr, float (&v)[64], float& m0, float& m1)
 {
     uint32_t r[64];
-    float m0, m1;
     asm volatile(
         "tcgen05.ld.red.sync.aligned.32x32b.x32.min.f32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
@@ -171,7 +170,6 @@ __device__ __forceinline__ void tmem_ld32x2_min(uint32_t taddr, float (&v)[64], 
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
-    vmin = fminf(m0, m1);
 }
 
 // ---------------------------------------------------------------- TMA
