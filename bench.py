@@ -153,10 +153,10 @@ def run_profile(args):
     for i in range(args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        ix = osann.Index(Xd, L)
-        ix.search(Yd, P, K, path=args.path)
+        ix, _, _ = osann.build_search(Xd, L, Yd, P, K, path=args.path, sync=False)
         b.record()
         b.synchronize()
+        ix.status()
         ix.close()
         if i >= args.warmup:
             times.append(a.elapsed_time(b))
@@ -213,10 +213,9 @@ def run_gpu(args):
     out_d2 = torch.empty((Q_FULL, K), dtype=torch.float32, device=dev)
 
     def step(path="auto"):
-        # build without its synchronisation (osann_build_async): the search
-        # follows in stream order; the build's status is read after the step
-        ix = osann.Index(Xd, L, sync=False)
-        ix.search(Yd, P, K, path=path, out=(out_ids, out_d2), workspace=work)
+        # build and search in one call (osann_build_search): the query-side
+        # steps run beside the build; the build's status is read after the step
+        ix, _, _ = osann.build_search(Xd, L, Yd, P, K, path=path, sync=False, out=(out_ids, out_d2))
         return ix
 
     def check(ix):
@@ -336,8 +335,7 @@ def run_gpu(args):
         a.record(stream)
         xd = Xh.to(dev, non_blocking=True)
         yd = Yh.to(dev, non_blocking=True)
-        ix = osann.Index(xd, L, sync=False)
-        ix.search(yd, P, K, out=(out_ids, out_d2), workspace=work)
+        ix, _, _ = osann.build_search(xd, L, yd, P, K, sync=False, out=(out_ids, out_d2))
         ids_h.copy_(out_ids, non_blocking=True)
         d2_h.copy_(out_d2, non_blocking=True)
         b.record(stream)
@@ -419,7 +417,7 @@ def run_gpu(args):
         "data": "synthetic (seeded iid N(0,1), generated on the host)",
         "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P,
                    "path": f"auto -> {path_used}",
-                   "step": "index build (asynchronous; its status read after the step) + search of the Q queries",
+                   "step": "index build + search of the Q queries in one call (osann_build_search: the query-side steps beside the build; the build's status read after the step)",
                    "l2": "flushed before every step by a 256 MiB device write (untimed)",
                    "parallelism": f"replicas x{ws} (independent data per rank)"},
         "recall_at_1": round(rec, 4),

@@ -241,6 +241,22 @@ int osann_search_clusters(const osann_index *index, const float *d_queries, int6
                           int32_t k, int32_t path, void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists,
                           void *stream);
 
+/* Build an index and search it, in one call: the same as osann_build_ex
+ * (opts may be NULL) followed by osann_search on the same stream, same
+ * results, except that the query-side steps (magnitude orders and probe
+ * lists, which do not read the built index) run on a side stream beside the
+ * build instead of after it (for a plain direct table; with a basis,
+ * centroids or a second-level table they follow the build).  The queries
+ * must be ready when the call is made (in stream order).  d_ws may be NULL
+ * (allocated and released in stream order); a caller workspace must hold
+ * osann_search_workspace_size of the built index.  With opts->async == 0 the
+ * call synchronises once at the end and reports the build's status (as
+ * osann_build); otherwise the status is left for osann_status.  On success
+ * *out is the index (release with osann_free). */
+int osann_build_search(const float *d_data, int64_t N, int32_t d, int32_t L, const osann_build_opts *opts,
+                       const float *d_queries, int64_t Q, int32_t P, int32_t k, int32_t path, void *d_ws,
+                       size_t ws_bytes, int64_t *d_ids, float *d_sqdists, void *stream, osann_index **out);
+
 /* ROSANNA search with one basis (Algorithm 1, R = 1): hash each query,
  * visit its first P_eff = min(P, N_C) cones in the order of osann_probes and
  * return the k nearest candidates by exact squared Euclidean distance

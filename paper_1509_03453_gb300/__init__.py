@@ -15,8 +15,8 @@ import ctypes
 from . import _lib
 from ._lib import OsannError, PATHS, STAGES, load
 
-__all__ = ["Index", "MultiIndex", "Server", "OsannError", "merge_topk", "keys", "keys_wide", "query_order",
-           "num_cones", "stats", "launch_count", "load"]
+__all__ = ["Index", "MultiIndex", "Server", "OsannError", "build_search", "merge_topk", "keys", "keys_wide",
+           "query_order", "num_cones", "stats", "launch_count", "load"]
 
 
 def _torch():
@@ -167,7 +167,15 @@ class Index:
                 self.K = cc.shape[0]
             _lib.check(load().osann_build_ex(_ptr(x), self.N, self.d, L, ctypes.byref(opts), _stream_ptr(stream),
                                              ctypes.byref(h)))
+        self._adopt(h, x, L, sync)
+
+    def _adopt(self, h, x, L, sync):
         self._h = h
+        self.N, self.d = x.shape
+        self.L = L
+        self.device = x.device
+        if not hasattr(self, "K"):
+            self.K = 0
         # an asynchronous build may still be reading the input: keep it until status()
         self._src = None if sync else x
         NC, mb = ctypes.c_int64(), ctypes.c_int64()
@@ -320,6 +328,36 @@ class Index:
             _lib.check(load().osann_info(self._h, None, None, None, None, ctypes.byref(mb)))
             self.max_bucket = mb.value
         return f.value
+
+
+def build_search(data, L: int, queries, P: int, k: int, path: str = "auto", stream=None, sync: bool = True,
+                 out=None, cone_table: str = "auto"):
+    """Build an Index over ``data`` and search ``queries`` in one call
+    (osann_build_search): the same results as Index(...).search(...), with
+    the query-side steps running beside the build.  Returns (index, ids,
+    sqdists); sync=False leaves the build's status for index.status()."""
+    torch = _torch()
+    x = _dev_f32(data, "data")
+    q = _dev_f32(queries, "queries")
+    N, d = x.shape
+    Q = q.shape[0]
+    if q.shape[1] != d:
+        raise ValueError("query dimension differs from the data's")
+    if out is None:
+        ids = torch.empty((Q, k), dtype=torch.int64, device=q.device)
+        d2 = torch.empty((Q, k), dtype=torch.float32, device=q.device)
+    else:
+        ids, d2 = out
+    opts = _lib.BuildOpts()
+    opts.async_ = 0 if sync else 1
+    opts.cone_table = _lib.CONE_TABLES[cone_table]
+    h = ctypes.c_void_p()
+    with torch.cuda.device(x.device):
+        _lib.check(load().osann_build_search(_ptr(x), N, d, L, ctypes.byref(opts), _ptr(q), Q, P, k, PATHS[path],
+                                             None, 0, _ptr(ids), _ptr(d2), _stream_ptr(stream), ctypes.byref(h)))
+    ix = Index.__new__(Index)
+    ix._adopt(h, x, L, sync)
+    return ix, ids, d2
 
 
 class MultiIndex:

@@ -61,6 +61,9 @@ SIGNATURES = {
                                         c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
     "osann_search_clusters_workspace_size": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
                                                           c.c_int32]),
+    "osann_build_search": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p,
+                                     c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p,
+                                     c.c_void_p, c.c_void_p, c.POINTER(c.c_void_p)]),
     "osann_free": (c.c_int, [c.c_void_p]),
     "osann_info": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
                              c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),

@@ -1104,9 +1104,14 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
     return rc;
 }
 
+// overlap_from (nullable): an event recorded on `stream` before the index's
+// build was enqueued; the query-side steps (magnitude orders, probe lists),
+// which do not read the built index, then run on a side stream after that
+// event only, beside the build, and join before the rest of the search.
 static int search_impl(const osann_index* ix, const float* Y, const int64_t* src, int64_t Q, int32_t P, int32_t k,
                        int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
-                       float* dists, void* stream, int32_t group = 0, int32_t M = 1)
+                       float* dists, void* stream, int32_t group = 0, int32_t M = 1,
+                       cudaEvent_t overlap_from = nullptr)
 {
     if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 || group < 0 || M < 1 ||
         (Q > 0 && (!Y || !ids || !dists))) {
@@ -1138,9 +1143,19 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
     }
     const bool batched = mode != MODE_PLAIN;
     const WsLayout L = ws_layout(ix, Q, P_eff, k, mode, group, Mv);
+    // the query-side steps read neither the rows, nor a second-level table,
+    // nor a basis or centroids of the index only with a plain direct table
+    SideStream front{};
+    if (overlap_from && !ix->hashed && !ix->rot && !ix->K) {
+        int frc = side_stream(ix->device, st, &front);
+        if (frc) return frc;
+        if (cudaStreamWaitEvent(front.st, overlap_from, 0) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "osann_build_search: fork");
+    }
+    const cudaStream_t fst = front.st ? front.st : st;
     void* owned = nullptr;
     if (!d_ws) {
-        owned = d_ws = dev_alloc(L.total, st);
+        owned = d_ws = dev_alloc(L.total, fst);  // usable on st after the join below
         if (!d_ws) {
             set_error("osann_search: workspace allocation failed (%zu bytes)", L.total);
             return OSANN_ERR_OOM;
@@ -1150,7 +1165,12 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, Y, Q, P_per, Mv, L, w, mode == MODE_BATCHED, batched, k, st);
+    int rc = query_front(ix, Y, Q, P_per, Mv, L, w, mode == MODE_BATCHED, batched, k, fst);
+    if (front.st) {
+        // join (also after an error, so that the side stream's work stays ordered before the caller's)
+        if (cudaEventRecord(front.join, front.st) != cudaSuccess || cudaStreamWaitEvent(st, front.join, 0) != cudaSuccess)
+            if (!rc) rc = cuda_fail(cudaGetLastError(), "osann_build_search: join");
+    }
     if (!rc && batched) {
         BatchedBuffers b{};
         b.qcount = reinterpret_cast<uint32_t*>(w + L.qcount);
@@ -1258,6 +1278,61 @@ int osann_search_clusters(const osann_index* index, const float* d_queries, int6
                           void* stream)
 {
     return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, 0, M);
+}
+
+int osann_build_search(const float* d_data, int64_t N, int32_t d, int32_t L, const osann_build_opts* opts,
+                       const float* d_queries, int64_t Q, int32_t P, int32_t k, int32_t path, void* d_ws,
+                       size_t ws_bytes, int64_t* d_ids, float* d_sqdists, void* stream, osann_index** out)
+{
+    if (!out) {
+        set_error("osann_build_search: null output");
+        return OSANN_ERR_INVALID;
+    }
+    *out = nullptr;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // the fork point: everything enqueued before the build (the queries' producers)
+    thread_local cudaEvent_t fork[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return OSANN_ERR_UNSUPPORTED;
+    if (!fork[dev] && cudaEventCreateWithFlags(&fork[dev], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "osann_build_search: event");
+    if (cudaEventRecord(fork[dev], st) != cudaSuccess) return cuda_fail(cudaGetLastError(), "osann_build_search: fork");
+    osann_build_opts o{};
+    if (opts) o = *opts;
+    const bool wait = o.async == 0;
+    o.async = 1;  // the search is enqueued behind the build; its status is read at the end
+    osann_index* ix = nullptr;
+    int rc = osann_build_ex(d_data, N, d, L, &o, stream, &ix);
+    if (rc) return rc;
+    rc = search_impl(ix, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, 0, 1,
+                     fork[dev]);
+    if (!rc && wait) {
+        // the build's status, read without clearing (the search's own flags
+        // stay for osann_status)
+        uint32_t h[2] = {0, 0};
+        cudaError_t e = cudaMemcpyAsync(h, ix->status, 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "osann_build_search");
+        } else {
+            if (ix->max_bucket < 0) ix->max_bucket = h[1];
+            if (h[0] & ST_TIMEOUT) {
+                set_error("osann_build_search: a device wait timed out");
+                rc = OSANN_ERR_TIMEOUT;
+            } else if (h[0] & ST_NONFINITE_DATA) {
+                set_error("osann_build_search: data contains NaN or Inf");
+                rc = OSANN_ERR_NONFINITE;
+            }
+        }
+    }
+    if (rc) {
+        if (!wait) cudaStreamSynchronize(st);  // nothing of the failed call may still use the index
+        osann_free(ix);
+        return rc;
+    }
+    *out = ix;
+    return OSANN_OK;
 }
 
 int osann_search_excl(const osann_index* index, const float* d_queries, const int64_t* d_query_src, int64_t Q,
