@@ -194,6 +194,26 @@ int osann_cones(const osann_index *index, int32_t *hashed, uint64_t *n_cones, in
  * occupied cones are all ones.  INVALID for a direct table. */
 int osann_export_cones(const osann_index *index, uint32_t *d_ids, void *stream);
 
+/* Rebuild an index in place from new data of the same shape (N x d): the
+ * build's kernels again (keys, cone table, permuted rows and screening
+ * operands; the same basis, centroids and table kind), into the index's own
+ * buffers.  Asynchronous, like osann_build_async: the status bits and the
+ * largest cone are read by the next osann_status.  The first call allocates
+ * the build's temporaries and keeps them with the index; later calls
+ * allocate nothing, so a rebuild and searches with caller workspaces can be
+ * captured together in a CUDA graph and replayed (searches already in
+ * flight on other streams must be complete).  Errors: INVALID, OOM, CUDA. */
+int osann_rebuild(osann_index *index, const float *d_data, void *stream);
+
+/* osann_rebuild followed by osann_search on the same stream, with the
+ * query-side steps beside the rebuild (as osann_build_search).  With a
+ * caller workspace (osann_search_workspace_size of this index) and after one
+ * earlier call, it allocates nothing: the whole build-and-search step can be
+ * captured in one CUDA graph.  The status bits are left for osann_status. */
+int osann_rebuild_search(osann_index *index, const float *d_data, const float *d_queries, int64_t Q, int32_t P,
+                         int32_t k, int32_t path, void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists,
+                         void *stream);
+
 /* Release an index.  NULL is accepted.  The caller must ensure that no
  * work using the index is still pending on any stream. */
 int osann_free(osann_index *index);

@@ -186,6 +186,41 @@ class Index:
         self.hashed = bool(hashed.value)
         self.n_cones = int(ncw[0]) | (int(ncw[1]) << 64)  # N_C itself (NC: cones of the CSR table)
 
+    def rebuild(self, data, stream=None):
+        """Rebuild in place from new data of the same shape (osann_rebuild):
+        asynchronous, allocation-free after the first call (graph-capturable);
+        check status() before trusting results."""
+        x = _dev_f32(data, "data")
+        if tuple(x.shape) != (self.N, self.d):
+            raise ValueError("rebuild needs data of the index's shape")
+        _lib.check(load().osann_rebuild(self._h, _ptr(x), _stream_ptr(stream)))
+        self._src = x  # read in stream order until status()
+        self.max_bucket = -1
+
+    def rebuild_search(self, data, queries, P: int, k: int, path: str = "auto", stream=None, out=None,
+                       workspace=None):
+        """rebuild(data) then search(queries, ...) in one call
+        (osann_rebuild_search), the query-side steps beside the rebuild.
+        With ``out`` and ``workspace`` given (and after one earlier call) it
+        allocates nothing, so it can be captured in a CUDA graph."""
+        torch = _torch()
+        x = _dev_f32(data, "data")
+        q = _dev_f32(queries, "queries")
+        if tuple(x.shape) != (self.N, self.d) or q.shape[1] != self.d:
+            raise ValueError("rebuild_search needs data of the index's shape and queries of its dimension")
+        Q = q.shape[0]
+        if out is None:
+            ids = torch.empty((Q, k), dtype=torch.int64, device=q.device)
+            d2 = torch.empty((Q, k), dtype=torch.float32, device=q.device)
+        else:
+            ids, d2 = out
+        ws_ptr, ws_n = (None, 0) if workspace is None else (_ptr(workspace), workspace.numel())
+        _lib.check(load().osann_rebuild_search(self._h, _ptr(x), _ptr(q), Q, P, k, PATHS[path], ws_ptr, ws_n,
+                                               _ptr(ids), _ptr(d2), _stream_ptr(stream)))
+        self._src = x
+        self.max_bucket = -1
+        return ids, d2
+
     def occupied(self, stream=None) -> int:
         """Cones holding at least one point (synchronises)."""
         n = ctypes.c_int64()

@@ -64,6 +64,9 @@ SIGNATURES = {
     "osann_build_search": (c.c_int, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_void_p, c.c_void_p,
                                      c.c_int64, c.c_int32, c.c_int32, c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p,
                                      c.c_void_p, c.c_void_p, c.POINTER(c.c_void_p)]),
+    "osann_rebuild": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p]),
+    "osann_rebuild_search": (c.c_int, [c.c_void_p, c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32,
+                                       c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
     "osann_free": (c.c_int, [c.c_void_p]),
     "osann_info": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.POINTER(c.c_int32), c.POINTER(c.c_int32),
                              c.POINTER(c.c_int64), c.POINTER(c.c_int64)]),

@@ -244,6 +244,12 @@ struct osann_index {
     int K = 0;
     float* cent = nullptr;
     unsigned __int128 ncc = 0;
+    // temporaries kept by osann_rebuild after its first call (so that later
+    // calls allocate nothing and can be captured in a CUDA graph)
+    char* rb_temp = nullptr;
+    size_t rb_temp_bytes = 0;
+    float* rb_xr = nullptr;
+    uint32_t* rb_asg = nullptr;
     int d = 0, d_pad = 0, L = 0, device = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
     uint32_t* keys = nullptr;
@@ -625,6 +631,99 @@ int osann_query_order(const float* d_queries, int64_t Q, int32_t d, uint8_t* d_o
                               static_cast<cudaStream_t>(stream));
 }
 
+// Temporaries of one build: direct table (counts, scan, radix) or
+// second-level table (128-bit ids, wide radix sort, run heads and their
+// scan); plus the key-basis rows (a basis or centroids) and the points'
+// clusters.
+struct BuildTemps {
+    size_t counts_bytes = 0, scan_bytes = 0, radix_bytes = 0, table_bytes = 0, total = 0;
+    size_t xr_bytes = 0, asg_bytes = 0;
+};
+static BuildTemps build_temps(const osann_index* ix)
+{
+    BuildTemps t;
+    const int64_t N = ix->N, NC = ix->NC;
+    t.counts_bytes = ix->hashed ? 0 : al256(size_t(NC + 1) * 4);
+    t.scan_bytes = ix->hashed ? al256(size_t(N) * 16) : al256(scan_temp_bytes(NC + 1));
+    t.radix_bytes = ix->hashed ? al256(radix_temp_bytes_wide(N, ix->key_bits)) : al256(radix_temp_bytes(N, NC));
+    t.table_bytes = ix->hashed ? al256(cone_table_temp_bytes(N)) : 0;
+    t.total = t.counts_bytes + t.scan_bytes + t.radix_bytes + t.table_bytes;
+    if (ix->rot || ix->K) t.xr_bytes = size_t(N) * ix->dk * 4;
+    if (ix->K) t.asg_bytes = size_t(N) * 4;
+    return t;
+}
+
+// Every kernel of a build, in stream order, into the index's buffers (the
+// basis or centroids already in the index); temp, xr and asg as sized by
+// build_temps.  Allocates nothing.
+static int enqueue_build(osann_index* ix, const float* d_data, char* temp, float* xr, uint32_t* asg, cudaStream_t st)
+{
+    const BuildTemps t = build_temps(ix);
+    const int64_t N = ix->N, NC = ix->NC;
+    const int d = ix->d, m = ix->dk, L = ix->L, K = ix->K;
+    const bool hashed = ix->hashed;
+    const bool tc_possible = ix->d_pad <= 128;
+    uint32_t* counts = reinterpret_cast<uint32_t*>(temp);
+    void* scan_temp = temp + t.counts_bytes;
+    void* radix_temp = temp + t.counts_bytes + t.scan_bytes;
+    void* table_temp = temp + t.counts_bytes + t.scan_bytes + t.radix_bytes;
+    uint4* wkeys = hashed ? static_cast<uint4*>(scan_temp) : nullptr;  // 128-bit ids of the rows
+    int rc = 0;
+    cudaMemsetAsync(ix->status, 0, 64 * 4, st);
+    cudaMemsetAsync(ix->diag, 0, 8 * sizeof(unsigned long long), st);
+    cudaMemsetAsync(ix->rowstat + N, 0, TC_N_ROWS * sizeof(float4), st);
+    if (!hashed) cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
+    {
+        StageScope s(OSANN_STAGE_DATA_KEYS, st);
+        // keys come from the rows' coordinates on the index's basis
+        const float* key_src = d_data;
+        if (K > 0) {
+            // ROSANNA+: each point's nearest centroid, then its residual
+            rc = launch_nearest_centroids(d_data, N, d, ix->d_pad, ix->cent, K, 1, asg, st);
+            if (!rc) rc = launch_residual_rows(d_data, N, d, ix->cent, ix->d_pad, asg, 1, xr, st, ix->num_sms);
+            key_src = xr;
+        } else if (ix->rot) {
+            rc = launch_rotate_rows(ix->rot, ix->rot_off, d_data, N, d, m, xr, st, ix->num_sms);
+            key_src = xr;
+        }
+        if (!rc)
+            rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms,
+                                  ix->binom_w, wkeys);
+        if (!rc && K > 0)
+            rc = launch_composite_keys(asg, N, uint64_t(ix->ncc), uint64_t(ix->ncc >> 64), ix->keys, wkeys, st,
+                                       ix->num_sms);
+        // the fp16 scale and the norm bound need the original rows' norms, which
+        // a projection, an offset or a residual does not keep
+        if (!rc && ((ix->rot && (m < d || ix->rot_off)) || K > 0)) {
+            cudaMemsetAsync(ix->status + 2, 0, 4, st);
+            rc = launch_row_norm_max(d_data, N, d, ix->status + 2, st, ix->num_sms);
+        }
+        if (!rc && tc_possible) rc = launch_tc_scale(1, ix->status + 2, ix->tcs + 4, st);
+    }
+    if (!rc) {
+        StageScope s(OSANN_STAGE_BUCKETS, st);
+        if (hashed) {
+            rc = launch_stable_sort_wide(wkeys, N, ix->key_bits, ix->perm, radix_temp, st);
+            if (!rc)
+                rc = launch_cone_table(wkeys, ix->perm, N, NC, ix->keys, ix->offsets, ix->ukeys, ix->status + 4,
+                                       ix->htab, ix->hmask, table_temp, st, ix->num_sms);
+        } else if (radix_single_pass(NC)) {
+            rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, ix->offsets, radix_temp, st);
+        } else {
+            rc = launch_key_histogram(ix->keys, N, NC, counts, st, ix->num_sms);
+            if (!rc) rc = launch_exclusive_scan(counts, ix->offsets, NC + 1, scan_temp, st);
+            if (!rc) rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, nullptr, radix_temp, st);
+        }
+    }
+    if (!rc) {
+        StageScope s(OSANN_STAGE_GATHER, st);
+        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->rowstat, ix->Bn,
+                                tc_possible ? ix->tcs + 4 : nullptr, ix->x16[1], ix->xe16[1], st, ix->num_sms);
+    }
+    if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st, ix->status + 3);
+    return rc;
+}
+
 static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, const float* d_off,
                       int32_t m, void* stream, bool async, int32_t cone_table, osann_index** out,
                       const float* d_cent = nullptr, int32_t K = 0)
@@ -720,109 +819,42 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         ix->htab = index_alloc<uint32_t>(ix, size_t(hcap));
     }
     if (K > 0) ix->cent = index_alloc<float>(ix, size_t(K) * ix->d_pad);
-    // temporaries: direct table (counts, scan, radix) or second-level table
-    // (128-bit ids, wide radix sort, run heads and their scan)
-    const size_t counts_bytes = hashed ? 0 : al256(size_t(NC + 1) * 4);
-    const size_t scan_bytes = hashed ? al256(size_t(N) * 16) : al256(scan_temp_bytes(NC + 1));
-    const size_t radix_bytes = hashed ? al256(radix_temp_bytes_wide(N, key_bits)) : al256(radix_temp_bytes(N, NC));
-    const size_t table_bytes = hashed ? al256(cone_table_temp_bytes(N)) : 0;
-    const size_t temp_bytes = counts_bytes + scan_bytes + radix_bytes + table_bytes;
-    char* temp = static_cast<char*>(dev_alloc(temp_bytes, st));
+    if (d_rot) {
+        ix->rot = index_alloc<float>(ix, size_t(m) * d);
+        if (d_off) ix->rot_off = index_alloc<float>(ix, size_t(m));
+    }
+    const BuildTemps bt = build_temps(ix);
+    char* temp = static_cast<char*>(dev_alloc(bt.total, st));
+    float* xr = bt.xr_bytes ? static_cast<float*>(dev_alloc(bt.xr_bytes, st)) : nullptr;
+    uint32_t* asg = bt.asg_bytes ? static_cast<uint32_t*>(dev_alloc(bt.asg_bytes, st)) : nullptr;
+    auto free_temps = [&]() {
+        if (temp) dev_free(temp, bt.total, st);
+        if (xr) dev_free(xr, bt.xr_bytes, st);
+        if (asg) dev_free(asg, bt.asg_bytes, st);
+    };
     if (!ix->keys || !ix->offsets || !ix->perm || !ix->xs || !ix->rowstat || !ix->status ||
         !ix->diag || !ix->tcs || (tc_possible && (!ix->x16[1] || !ix->xe16[1])) ||
-        (hashed && (!ix->ukeys || !ix->htab)) || (K > 0 && !ix->cent) || !temp) {
-        if (temp) dev_free(temp, temp_bytes, st);
+        (hashed && (!ix->ukeys || !ix->htab)) || (K > 0 && !ix->cent) || (d_rot && !ix->rot) ||
+        (d_off && !ix->rot_off) || !temp || (bt.xr_bytes && !xr) || (bt.asg_bytes && !asg)) {
+        free_temps();
         index_release(ix);
         set_error("osann_build: device allocation failed");
         return OSANN_ERR_OOM;
     }
-    uint32_t* counts = reinterpret_cast<uint32_t*>(temp);
-    void* scan_temp = temp + counts_bytes;
-    void* radix_temp = temp + counts_bytes + scan_bytes;
-    void* table_temp = temp + counts_bytes + scan_bytes + radix_bytes;
-    uint4* wkeys = hashed ? static_cast<uint4*>(scan_temp) : nullptr;  // 128-bit ids of the rows
-
-    cudaMemsetAsync(ix->status, 0, 64 * 4, st);
-    cudaMemsetAsync(ix->diag, 0, 8 * sizeof(unsigned long long), st);
-    cudaMemsetAsync(ix->rowstat + N, 0, TC_N_ROWS * sizeof(float4), st);
-    if (!hashed) cudaMemsetAsync(counts, 0, size_t(NC + 1) * 4, st);
-    {
-        StageScope s(OSANN_STAGE_DATA_KEYS, st);
-        // keys come from the rows' coordinates on the index's basis
-        const float* key_src = d_data;
-        float* xr = nullptr;
-        uint32_t* asg = nullptr;
-        if (K > 0) {
-            // ROSANNA+: each point's nearest centroid, then its residual
-            cudaError_t e = cudaMemsetAsync(ix->cent, 0, size_t(K) * ix->d_pad * 4, st);
-            if (e == cudaSuccess)
-                e = cudaMemcpy2DAsync(ix->cent, size_t(ix->d_pad) * 4, d_cent, size_t(d) * 4, size_t(d) * 4, size_t(K),
-                                      cudaMemcpyDeviceToDevice, st);
-            xr = static_cast<float*>(dev_alloc(size_t(N) * d * 4, st));
-            asg = static_cast<uint32_t*>(dev_alloc(size_t(N) * 4, st));
-            if (e != cudaSuccess) {
-                rc = cuda_fail(e, "osann_build: centroids");
-            } else if (!xr || !asg) {
-                set_error("osann_build: device allocation failed");
-                rc = OSANN_ERR_OOM;
-            } else {
-                rc = launch_nearest_centroids(d_data, N, d, ix->d_pad, ix->cent, K, 1, asg, st);
-                if (!rc) rc = launch_residual_rows(d_data, N, d, ix->cent, ix->d_pad, asg, 1, xr, st, ix->num_sms);
-                key_src = xr;
-            }
-        } else if (d_rot) {
-            ix->rot = index_alloc<float>(ix, size_t(m) * d);
-            if (d_off) ix->rot_off = index_alloc<float>(ix, size_t(m));
-            xr = static_cast<float*>(dev_alloc(size_t(N) * m * 4, st));
-            if (!ix->rot || (d_off && !ix->rot_off) || !xr) {
-                set_error("osann_build_proj: device allocation failed");
-                rc = OSANN_ERR_OOM;
-            } else {
-                cudaError_t e = cudaMemcpyAsync(ix->rot, d_rot, size_t(m) * d * 4, cudaMemcpyDeviceToDevice, st);
-                if (e == cudaSuccess && d_off)
-                    e = cudaMemcpyAsync(ix->rot_off, d_off, size_t(m) * 4, cudaMemcpyDeviceToDevice, st);
-                rc = e != cudaSuccess ? cuda_fail(e, "osann_build_proj")
-                                      : launch_rotate_rows(ix->rot, ix->rot_off, d_data, N, d, m, xr, st, ix->num_sms);
-                key_src = xr;
-            }
-        }
-        if (!rc)
-            rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms,
-                                  ds->binom_w, wkeys);
-        if (!rc && K > 0)
-            rc = launch_composite_keys(asg, N, uint64_t(ncc), uint64_t(ncc >> 64), ix->keys, wkeys, st, ix->num_sms);
-        // the fp16 scale and the norm bound need the original rows' norms, which
-        // a projection, an offset or a residual does not keep
-        if (!rc && ((d_rot && (m < d || d_off)) || K > 0)) {
-            cudaMemsetAsync(ix->status + 2, 0, 4, st);
-            rc = launch_row_norm_max(d_data, N, d, ix->status + 2, st, ix->num_sms);
-        }
-        if (xr) dev_free(xr, size_t(N) * m * 4, st);
-        if (asg) dev_free(asg, size_t(N) * 4, st);
-        if (!rc && tc_possible) rc = launch_tc_scale(1, ix->status + 2, ix->tcs + 4, st);
+    // the key basis or the centroids: the index keeps its own copy
+    cudaError_t e = cudaSuccess;
+    if (K > 0) {
+        e = cudaMemsetAsync(ix->cent, 0, size_t(K) * ix->d_pad * 4, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpy2DAsync(ix->cent, size_t(ix->d_pad) * 4, d_cent, size_t(d) * 4, size_t(d) * 4, size_t(K),
+                                  cudaMemcpyDeviceToDevice, st);
+    } else if (d_rot) {
+        e = cudaMemcpyAsync(ix->rot, d_rot, size_t(m) * d * 4, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess && d_off)
+            e = cudaMemcpyAsync(ix->rot_off, d_off, size_t(m) * 4, cudaMemcpyDeviceToDevice, st);
     }
-    if (!rc) {
-        StageScope s(OSANN_STAGE_BUCKETS, st);
-        if (hashed) {
-            rc = launch_stable_sort_wide(wkeys, N, key_bits, ix->perm, radix_temp, st);
-            if (!rc)
-                rc = launch_cone_table(wkeys, ix->perm, N, NC, ix->keys, ix->offsets, ix->ukeys, ix->status + 4,
-                                       ix->htab, ix->hmask, table_temp, st, ix->num_sms);
-        } else if (radix_single_pass(NC)) {
-            rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, ix->offsets, radix_temp, st);
-        } else {
-            rc = launch_key_histogram(ix->keys, N, NC, counts, st, ix->num_sms);
-            if (!rc) rc = launch_exclusive_scan(counts, ix->offsets, NC + 1, scan_temp, st);
-            if (!rc) rc = launch_stable_sort_ids(ix->keys, N, NC, ix->perm, nullptr, radix_temp, st);
-        }
-    }
-    if (!rc) {
-        StageScope s(OSANN_STAGE_GATHER, st);
-        rc = launch_gather_rows(d_data, N, d, ix->d_pad, ix->perm, ix->xs, ix->rowstat, ix->Bn,
-                                tc_possible ? ix->tcs + 4 : nullptr, ix->x16[1], ix->xe16[1], st, ix->num_sms);
-    }
-    if (!rc) rc = launch_max_bucket(ix->offsets, NC, ix->status + 1, st, ix->status + 3);
-    dev_free(temp, temp_bytes, st);
+    rc = e != cudaSuccess ? cuda_fail(e, "osann_build: basis") : enqueue_build(ix, d_data, temp, xr, asg, st);
+    free_temps();
     // the tensor maps need only addresses and sizes: encode them while the device works
     const bool maps_ok = !rc && tc_possible && tc_map_bytes() <= sizeof(ix->tmap[1]) &&
                          tc_encode_rows_map(ix->tmap[1], ix->x16[1], N, ix->d_pad, 1) == 0 &&
@@ -900,6 +932,39 @@ int osann_build_proj(const float* d_data, int64_t N, int32_t d, int32_t L, const
         return OSANN_ERR_INVALID;
     }
     return build_impl(d_data, N, d, L, d_proj, d_off, m, stream, async != 0, OSANN_CONES_AUTO, out);
+}
+
+int osann_rebuild(osann_index* ix, const float* d_data, void* stream)
+{
+    if (!ix || !d_data) {
+        set_error("osann_rebuild: invalid arguments");
+        return OSANN_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!ix->rb_temp) {
+        // first call: the build's temporaries become the index's own
+        const BuildTemps bt = build_temps(ix);
+        auto keep = [&](size_t bytes) -> void* {
+            void* p = dev_alloc(bytes, st);
+            if (p) ix->allocs.push_back({p, bytes});
+            return p;
+        };
+        ix->rb_temp = static_cast<char*>(keep(bt.total));
+        if (bt.xr_bytes) ix->rb_xr = static_cast<float*>(keep(bt.xr_bytes));
+        if (bt.asg_bytes) ix->rb_asg = static_cast<uint32_t*>(keep(bt.asg_bytes));
+        if (!ix->rb_temp || (bt.xr_bytes && !ix->rb_xr) || (bt.asg_bytes && !ix->rb_asg)) {
+            set_error("osann_rebuild: device allocation failed");
+            return OSANN_ERR_OOM;
+        }
+        ix->rb_temp_bytes = bt.total;
+    }
+    int rc = enqueue_build(ix, d_data, ix->rb_temp, ix->rb_xr, ix->rb_asg, st);
+    // bf16 operands made by an earlier bf16 search follow the new rows
+    if (!rc && ix->tc_ready[0])
+        rc = launch_tc_rows(0, ix->xs, ix->rowstat, ix->N, ix->d_pad, ix->status + 2, ix->tcs, ix->x16[0],
+                            ix->xe16[0], st, ix->num_sms);
+    ix->max_bucket = -1;
+    return rc;
 }
 
 int osann_free(osann_index* index)
@@ -1333,6 +1398,28 @@ int osann_build_search(const float* d_data, int64_t N, int32_t d, int32_t L, con
     }
     *out = ix;
     return OSANN_OK;
+}
+
+int osann_rebuild_search(osann_index* ix, const float* d_data, const float* d_queries, int64_t Q, int32_t P,
+                         int32_t k, int32_t path, void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists,
+                         void* stream)
+{
+    if (!ix) {
+        set_error("osann_rebuild_search: null index");
+        return OSANN_ERR_INVALID;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    thread_local cudaEvent_t fork[64] = {};
+    if (ix->device < 0 || ix->device >= 64) return OSANN_ERR_UNSUPPORTED;
+    if (!fork[ix->device] && cudaEventCreateWithFlags(&fork[ix->device], cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "osann_rebuild_search: event");
+    // the fork point: everything enqueued before the rebuild (the queries' producers)
+    if (cudaEventRecord(fork[ix->device], st) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "osann_rebuild_search: fork");
+    int rc = osann_rebuild(ix, d_data, stream);
+    if (rc) return rc;
+    return search_impl(ix, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, 0, 1,
+                       fork[ix->device]);
 }
 
 int osann_search_excl(const osann_index* index, const float* d_queries, const int64_t* d_query_src, int64_t Q,
