@@ -145,7 +145,14 @@ def run_profile(args):
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     osann.load()
-    X, Y = gen(0)
+    if args.workload == "desc128":
+        # the descriptor recipe (N = 2*10^6, d = 128, 1.02 GB of rows), L = 3, k = 10
+        from paper_1509_03453_gb300 import datagen
+        w = datagen.workload("desc128")
+        X, Y, Lw, Kw = w["X"], w["Y"], w["L"], w["k"]
+    else:
+        X, Y = gen(0)
+        Lw, Kw = L, K
     Xd = torch.from_numpy(X).to(dev)
     Yd = torch.from_numpy(Y).to(dev)
     P = args.P or 224
@@ -153,14 +160,15 @@ def run_profile(args):
     for i in range(args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        ix, _, _ = osann.build_search(Xd, L, Yd, P, K, path=args.path, sync=False)
+        ix, _, _ = osann.build_search(Xd, Lw, Yd, P, Kw, path=args.path, sync=False)
         b.record()
         b.synchronize()
         ix.status()
         ix.close()
         if i >= args.warmup:
             times.append(a.elapsed_time(b))
-    print(json.dumps({"profile_run": True, "P": P, "path": args.path, "ms_per_step": float(np.mean(times))}))
+    print(json.dumps({"profile_run": True, "workload": args.workload, "P": P, "path": args.path,
+                      "ms_per_step": float(np.mean(times))}))
 
 
 def run_gpu(args):
@@ -796,6 +804,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16", "fp16"])
+    ap.add_argument("--workload", default="gauss32", choices=["gauss32", "desc128"],
+                    help="workload of --profile runs")
     ap.add_argument("--serving", action="store_true", help="the request-server workload (three resident indexes)")
     ap.add_argument("--no-multi", action="store_true", help="skip the multi-basis (R > 1) measurement")
     ap.add_argument("--rosanna-plus", action="store_true",
