@@ -1349,8 +1349,9 @@ int osann_build_search(const float* d_data, int64_t N, int32_t d, int32_t L, con
                        const float* d_queries, int64_t Q, int32_t P, int32_t k, int32_t path, void* d_ws,
                        size_t ws_bytes, int64_t* d_ids, float* d_sqdists, void* stream, osann_index** out)
 {
-    if (!out) {
-        set_error("osann_build_search: null output");
+    if (!out || !d_data || N < 1 || Q < 0 || (Q > 0 && (!d_queries || !d_ids || !d_sqdists))) {
+        set_error("osann_build_search: invalid arguments");
+        if (out) *out = nullptr;
         return OSANN_ERR_INVALID;
     }
     *out = nullptr;
@@ -1404,8 +1405,8 @@ int osann_rebuild_search(osann_index* ix, const float* d_data, const float* d_qu
                          int32_t k, int32_t path, void* d_ws, size_t ws_bytes, int64_t* d_ids, float* d_sqdists,
                          void* stream)
 {
-    if (!ix) {
-        set_error("osann_rebuild_search: null index");
+    if (!ix || !d_data || Q < 0 || (Q > 0 && (!d_queries || !d_ids || !d_sqdists))) {
+        set_error("osann_rebuild_search: invalid arguments");
         return OSANN_ERR_INVALID;
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -68,3 +68,24 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(build, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not found"):
         _lib.load()
+
+
+def test_host_only_argument_checks_of_the_newer_entry_points(L):
+    h = ctypes.c_void_p()
+    c = ctypes
+    # build with options: no data
+    assert L.osann_build_ex(None, 10, 4, 2, None, None, c.byref(h)) == -1
+    # build and search in one call: no output handle / no data
+    assert L.osann_build_search(None, 10, 4, 2, None, None, 1, 1, 1, 0, None, 0, None, None, None, None) == -1
+    assert L.osann_build_search(None, 10, 4, 2, None, None, 1, 1, 1, 0, None, 0, None, None, None, c.byref(h)) == -1
+    # in-place rebuild and rebuild-and-search: no index
+    assert L.osann_rebuild(None, None, None) == -1
+    assert L.osann_rebuild_search(None, None, None, 1, 1, 1, 0, None, 0, None, None, None) == -1
+    # ROSANNA+ search, cone table queries: no index
+    assert L.osann_search_clusters(None, None, 1, 2, 1, 1, 0, None, 0, None, None, None) == -1
+    assert L.osann_search_clusters_workspace_size(None, 1, 2, 1, 1, 0) == 0
+    assert L.osann_cones(None, None, None, None, None, None) == -1
+    assert L.osann_export_cones(None, None, None) == -1
+    # 128-bit keys: bad sizes are rejected before any device work
+    assert L.osann_keys_wide(None, 1, 0, 2, None, None) == -1
+    assert L.osann_keys_wide(None, 1, 300, 2, None, None) == -1
