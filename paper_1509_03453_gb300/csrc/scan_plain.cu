@@ -5,13 +5,9 @@
 //
 // One CTA per query (or, with a device query list, a grid-stride loop over
 // the listed queries with the stage ring's phases carried across them).
-// Warp 0 streams the rows of the visited cones from the permuted vector
-// array into a ring of shared-memory stages with 1-D bulk copies (TMA
-// engine), each stage guarded by an mbarrier: its lanes fetch the row ranges
-// of the next 32 probed cones at once, and a stage is filled with as many
-// consecutive ranges as fit (one copy per range, a table of the stage rows'
-// indices), so that small cones share a stage instead of each costing a
-// round trip.  The CTA
+// Thread 0 streams the rows of the visited cones from
+// the permuted vector array into a ring of shared-memory stages with 1-D
+// bulk copies (TMA engine), each stage guarded by an mbarrier.  The CTA
 // consumes a stage with TPR = min(32, d_pad/4) adjacent threads per row,
 // each holding one or two float4 pieces of the query: a quarter-warp reads
 // 128 contiguous bytes (no bank conflicts) and the row's distance is the
@@ -26,8 +22,6 @@ namespace osann {
 constexpr int PLAIN_THREADS = 128;
 constexpr int PLAIN_STAGES = 4;
 constexpr int PLAIN_STAGE_FLOATS = 4096;  // 16 KB per stage
-constexpr int PLAIN_RPC_MAX = PLAIN_STAGE_FLOATS / 16;  // rows per stage at the smallest d_pad
-constexpr int PLAIN_SEGQ = 64;  // row ranges of upcoming non-empty cones
 
 __device__ __forceinline__ bool excluded_pair(uint32_t id, int64_t src, int64_t grid_w, int radius)
 {
@@ -72,14 +66,11 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* stage_buf = reinterpret_cast<float*>(smem_raw);
     __shared__ __align__(8) uint64_t bars[PLAIN_STAGES];
-    __shared__ int stage_rows[PLAIN_STAGES];               // rows in the stage, -1 = none
-    __shared__ uint32_t rowid[PLAIN_STAGES][PLAIN_RPC_MAX];  // index into xs / perm of each stage row
-    __shared__ uint2 segq[PLAIN_SEGQ];                      // (first row, end row), probe order
-    __shared__ uint4 plan[PLAIN_RPC_MAX];                   // copies of a stage: (first row, rows, stage row)
+    __shared__ int2 meta[PLAIN_STAGES];  // (first row, row count or -1 = no chunk)
     __shared__ uint64_t red[PLAIN_THREADS / 32];
     __shared__ int abort_flag;
 
-    const int tid = threadIdx.x, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int n4 = d_pad >> 2;               // float4 pieces per row
     const int TPR = n4 / F;                  // threads per row (<= 32)
     const int RPP = PLAIN_THREADS / TPR;     // rows per pass
@@ -117,76 +108,39 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
         uint64_t list[KMAX];
         topk_init<KMAX>(list, k);
 
-        // producer state (warp 0, the same in all its lanes)
+        // producer state (thread 0 only)
         int64_t pi = 0;
         uint32_t cur = 0, cur_end = 0;
-        int qh = 0, qt = 0;
         const uint32_t* qprobes = probes + q * P_eff;
-        // the row ranges of the next 32 probed cones, the non-empty ones queued in probe order
-        auto refill = [&]() {
-            const int64_t j = pi + lane;
-            uint32_t r0 = 0, r1 = 0;
-            if (j < P_eff) {
-                const uint32_t b = qprobes[j];
-                if (b < NC) {  // never otherwise; guards the offsets read
-                    r0 = offsets[b];
-                    r1 = offsets[b + 1];
-                }
-            }
-            const bool ne = r1 > r0;
-            const unsigned mk = __ballot_sync(0xffffffffu, ne);
-            if (ne) segq[(qt + __popc(mk & ((1u << lane) - 1u))) % PLAIN_SEGQ] = make_uint2(r0, r1);
-            qt += __popc(mk);
-            pi += 32;
-            __syncwarp();
-        };
         auto issue = [&](int s) {
-            int rows = 0, nseg = 0;
-            while (rows < RPC) {
-                if (cur >= cur_end) {
-                    if (qh == qt) {
-                        if (pi >= P_eff) break;
-                        refill();
-                        continue;
-                    }
-                    const uint2 sg = segq[qh % PLAIN_SEGQ];
-                    ++qh;
-                    cur = sg.x;
-                    cur_end = sg.y;
-                    continue;
-                }
-                const uint32_t n = cur_end - cur < uint32_t(RPC - rows) ? cur_end - cur : uint32_t(RPC - rows);
-                for (uint32_t i = lane; i < n; i += 32) rowid[s][rows + i] = cur + i;
-                if (lane == 0) plan[nseg] = make_uint4(cur, n, uint32_t(rows), 0u);
-                ++nseg;
-                rows += int(n);
-                cur += n;
+            while (cur >= cur_end && pi < P_eff) {
+                const uint32_t b = qprobes[pi++];
+                if (b >= NC) continue;  // never produced by the probe kernel; guards the offsets read
+                cur = offsets[b];
+                cur_end = offsets[b + 1];
             }
-            __syncwarp();
-            if (lane == 0) {
-                stage_rows[s] = rows > 0 ? rows : -1;
-                if (rows > 0) {
-                    fence_proxy_async_smem();
-                    mbar_arrive_expect_tx(&bars[s], uint32_t(rows) * uint32_t(d_pad) * 4u);
-                    float* dst = stage_buf + size_t(s) * PLAIN_STAGE_FLOATS;
-                    for (int j = 0; j < nseg; ++j) {
-                        const uint4 pl = plan[j];
-                        bulk_g2s(dst + size_t(pl.z) * d_pad, xs + size_t(pl.x) * d_pad, pl.y * uint32_t(d_pad) * 4u,
-                                 &bars[s]);
-                    }
-                }
+            if (cur >= cur_end) {
+                meta[s] = make_int2(0, -1);
+                return;
             }
+            const uint32_t n = cur_end - cur < uint32_t(RPC) ? cur_end - cur : uint32_t(RPC);
+            meta[s] = make_int2(int(cur), int(n));
+            const uint32_t bytes = n * uint32_t(d_pad) * 4u;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(&bars[s], bytes);
+            bulk_g2s(stage_buf + size_t(s) * PLAIN_STAGE_FLOATS, xs + size_t(cur) * d_pad, bytes, &bars[s]);
+            cur += n;
         };
 
         // no copy is in flight here: the previous query ended on S empty stages
-        if (tid < 32)
+        if (tid == 0)
             for (int i = 0; i < PLAIN_STAGES; ++i) issue((c + i) % PLAIN_STAGES);
         __syncthreads();
 
         for (;; ++c) {
             const int s = c % PLAIN_STAGES;
-            const int nrows = stage_rows[s];
-            if (nrows < 0) break;
+            const int2 m = meta[s];
+            if (m.y < 0) break;
             const bool ok = mbar_wait_bounded(&bars[s], uint32_t((c / PLAIN_STAGES) & 1));
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
@@ -196,7 +150,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
                 break;
             }
             const float* stage = stage_buf + size_t(s) * PLAIN_STAGE_FLOATS;
-            for (int r0 = 0; r0 < nrows; r0 += RPP) {
+            for (int r0 = 0; r0 < m.y; r0 += RPP) {
                 // rows past the chunk's end (still inside the stage) read stale
                 // memory; their result is discarded
                 const int r = r0 + r_in;
@@ -205,29 +159,29 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
 #pragma unroll
                 for (int f = 0; f < F; ++f) cpart[f] = sq4(row[f], qv[f]);
                 const float dist = lane_tree(pair_tree<F>(cpart), TPR);
-                if (sub == 0 && r < nrows) {
-                    const uint32_t ri = rowid[s][r];
+                if (sub == 0 && r < m.y) {
+                    const uint32_t rowid = uint32_t(m.x + r);
                     if (EXCL) {
-                        const uint32_t id = __ldg(perm + ri);
+                        const uint32_t id = __ldg(perm + rowid);
                         if (!excluded_pair(id, src, grid_w, radius)) {
                             const uint64_t v = pack_di(dist, id);
                             if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
                         }
                     } else if (dist <= di_dist(list[KMAX - 1])) {
-                        const uint64_t v = pack_di(dist, __ldg(perm + ri));
+                        const uint64_t v = pack_di(dist, __ldg(perm + rowid));
                         if (v < list[KMAX - 1]) topk_insert<KMAX>(list, v);
                     }
                 }
             }
             __syncthreads();
-            if (tid < 32) issue(s);
+            if (tid == 0) issue(s);
         }
         if (abort_flag) {
             // let copies still in flight land before the CTA's shared memory goes away
             if (tid == 0)
                 for (int i = 0; i < PLAIN_STAGES; ++i) {
                     const int cc = c + i, ss = cc % PLAIN_STAGES;
-                    if (stage_rows[ss] >= 0) mbar_wait_bounded(&bars[ss], uint32_t((cc / PLAIN_STAGES) & 1));
+                    if (meta[ss].y >= 0) mbar_wait_bounded(&bars[ss], uint32_t((cc / PLAIN_STAGES) & 1));
                 }
             __syncthreads();
             block_merge_write<KMAX>(list, k, out_ids + q * k, out_d + q * k, red);
