@@ -537,7 +537,7 @@ def run_reference(args):
         return
     import oracle
     oracle.build()
-    P = args.P or 256
+    P = args.P or 224  # the GPU arm's recall@1 >= 0.9 budget on this workload (its P ladder)
     X, Y = gen(0)
     sample = 40
     times = []
