@@ -55,3 +55,32 @@ def test_classification_and_sign_agreement():
     f1 = [np.mean([q_order[i, 0] in n_order[i, :G] for i in range(len(Y))])
           for G in (1, 2, 3, 4)]
     assert all(a < b for a, b in zip(f1, f1[1:]))
+
+
+def test_crossing_probability_bounds_k2_g1():
+    """Appendix, 2-d case (K = 2, G = 1, iid standard Gaussian X, Y uniform on
+    the circle of radius r around X): the probability that Y lies in another
+    cone than X is at least the mean of theta(r, Delta)/pi over Delta < r
+    (Delta the distance of X to its nearest cone boundary, theta =
+    arccos(Delta/r)), at most the mean of min(2 theta/pi, (N_C-1)/N_C), close
+    to the lower bound for small r and tends to 3/4 as r grows (N_C = 4)."""
+    rng = np.random.default_rng(21)
+    n = 200_000
+    X = rng.standard_normal((n, 2))
+    phi = rng.uniform(0.0, 2.0 * np.pi, n)
+    a = np.abs(X)
+    delta = (a.max(1) - a.min(1)) / np.sqrt(2.0)
+    kx = oracle.keys(X.astype(np.float32), 1)
+    assert oracle.num_cones(2, 1) == 4 and set(np.unique(kx)) == {0, 1, 2, 3}
+    se = lambda p: np.sqrt(p * (1 - p) / n)
+    for r in (0.05, 0.3, 1.0, 3.0, 100.0):
+        Y = X + r * np.stack([np.cos(phi), np.sin(phi)], 1)
+        p = np.mean(oracle.keys(Y.astype(np.float32), 1) != kx)
+        theta = np.where(delta < r, np.arccos(np.minimum(delta / r, 1.0)), 0.0)
+        lower = np.mean(theta / np.pi)
+        upper = np.mean(np.minimum(2.0 * theta / np.pi, 3.0 / 4.0))
+        tol = 5 * se(max(p, 1e-4)) + 1e-4
+        assert lower - tol <= p <= upper + tol, (r, lower, p, upper)
+        if r <= 0.05:
+            assert p - lower <= 0.1 * lower + tol  # the nearest boundary dominates
+    assert abs(p - 0.75) <= 5 * se(0.75) + 0.005  # r = 100: any cone alike
