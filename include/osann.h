@@ -326,7 +326,9 @@ int osann_search_excl(const osann_index *index, const float *d_queries, const in
  * Inputs and outputs are as for osann_search; nothing is allocated, freed
  * or returned to an allocator.  The scratch needed is
  * osann_search_workspace_size(index, Q, P, k, OSANN_PATH_PLAIN); calls that
- * need more than 32 MiB fail with OSANN_ERR_INVALID (split the batch).
+ * need more than 32 MiB fail with OSANN_ERR_INVALID (split the batch), and
+ * so do calls made while the current device is not the index's (each device
+ * has its own array).
  * The first call on a device looks up the array's device address and the
  * library's per-device tables; make it before any stream capture.  All
  * calls share the one array, which keeps the last call's contents (every

@@ -96,16 +96,15 @@ def lib():
         L.oracle_search_wide.argtypes = [
             _f32p, c.c_int64, c.c_int, c.c_int, c.c_int64, _u64p, _u32p, _u32p, _f32p, c.c_int64,
             c.c_int64, c.c_int, c.c_void_p, c.c_int64, c.c_int64, _i64p, _f64p, c.c_void_p]
-        L.oracle_sqdist_f32.restype = c.c_float
-        L.oracle_sqdist_f32.argtypes = [_f32p, _f32p, c.c_int]
         L.oracle_nearest_centroids.restype = None
         L.oracle_nearest_centroids.argtypes = [_f32p, c.c_int64, c.c_int, _f32p, c.c_int, c.c_int, _i32p]
         L.oracle_keys_clustered.restype = c.c_int
-        L.oracle_keys_clustered.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _f32p, c.c_int, _u64p, _i32p]
+        L.oracle_keys_clustered.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _f32p, c.c_int, _u64p, _i32p,
+                                            c.c_void_p]
         L.oracle_search_clustered.restype = None
         L.oracle_search_clustered.argtypes = [
             _f32p, c.c_int64, c.c_int, c.c_int, _f32p, c.c_int, c.c_int, c.c_int64, _u64p, _u32p, _u32p,
-            _f32p, c.c_int64, c.c_int64, c.c_int, _i64p, _f64p, c.c_void_p]
+            _f32p, c.c_int64, c.c_int64, c.c_int, _i64p, _f64p, c.c_void_p, c.c_void_p]
         L.oracle_pair_dists.restype = None
         L.oracle_pair_dists.argtypes = [_f32p, c.c_int, _f32p, c.c_int64,
                                         c.c_int, _i64p, _f64p]
@@ -265,14 +264,9 @@ class WideIndex:
         return (ids, dists, counts) if want_counts else (ids, dists)
 
 
-def sqdist_f32(x, y) -> float:
-    """The kernels' fp32 squared distance (padded float4 pieces, pairwise tree)."""
-    x, y = _f32(x), _f32(y)
-    return float(lib().oracle_sqdist_f32(x, y, x.shape[-1]))
-
-
 def nearest_centroids(X, C, M: int) -> np.ndarray:
-    """[n, M] indices of the M nearest centroids (fp32 distance, then index)."""
+    """[n, M] indices of the M nearest centroids (fp64 squared distance, then
+    index; -1 pads when M > K)."""
     X, C = _f32(np.atleast_2d(X)), _f32(C)
     out = np.empty((X.shape[0], M), np.int32)
     lib().oracle_nearest_centroids(X, X.shape[0], X.shape[1], C, C.shape[0], M, out)
@@ -285,7 +279,9 @@ class ClusteredIndex:
     id cluster * N_C + cone; the search visits the query's M nearest
     clusters."""
 
-    def __init__(self, X, L: int, centroids):
+    def __init__(self, X, L: int, centroids, asg=None):
+        """asg: optional cluster of every point (int, [N]) used instead of
+        the nearest centroid."""
         self.X = _f32(X)
         self.N, self.d = self.X.shape
         self.L = L
@@ -294,8 +290,12 @@ class ClusteredIndex:
         self.NC = num_cones_wide(self.d, L)
         kw = np.empty(2 * self.N, np.uint64)
         self.asg = np.empty(self.N, np.int32)
-        if lib().oracle_keys_clustered(self.X, self.N, self.d, L, self.C, self.K, kw, self.asg) != 0:
-            raise ValueError("K * N_C does not fit in 127 bits")
+        a_in = None if asg is None else np.ascontiguousarray(asg, dtype=np.int32)
+        if a_in is not None and a_in.shape != (self.N,):
+            raise ValueError("asg must hold one cluster per point")
+        if lib().oracle_keys_clustered(self.X, self.N, self.d, L, self.C, self.K, kw, self.asg,
+                                       None if a_in is None else a_in.ctypes.data_as(ctypes.c_void_p)) != 0:
+            raise ValueError("K * N_C does not fit in 127 bits, or a given cluster is out of range")
         self.keys = _wide_ints(kw)
         self.perm = np.empty(self.N, np.uint32)
         uniq = np.empty(2 * max(self.N, 1), np.uint64)
@@ -305,15 +305,21 @@ class ClusteredIndex:
         self.uniq = _wide_ints(uniq[:2 * self.n_occ])
         self.offsets = offs[:self.n_occ + 1].copy()
 
-    def search(self, Y, M: int, P: int, k: int, want_counts: bool = False):
+    def search(self, Y, M: int, P: int, k: int, want_counts: bool = False, near=None):
+        """near: optional [Q, M] clusters of each query (-1: none) used
+        instead of its M nearest."""
         Y = _f32(Y)
         Q = Y.shape[0]
         ids = np.empty(Q * k, np.int64)
         dists = np.empty(Q * k, np.float64)
         counts = np.empty(Q, np.int64) if want_counts else None
+        n_in = None if near is None else np.ascontiguousarray(near, dtype=np.int32)
+        if n_in is not None and n_in.shape != (Q, M):
+            raise ValueError("near must be [Q, M]")
         lib().oracle_search_clustered(
             self.X, self.N, self.d, self.L, self.C, self.K, M, self.n_occ, self._uniq, self.offsets, self.perm,
-            Y, Q, P, k, ids, dists, counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+            Y, Q, P, k, ids, dists, counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None,
+            None if n_in is None else n_in.ctypes.data_as(ctypes.c_void_p))
         ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
         return (ids, dists, counts) if want_counts else (ids, dists)
 
@@ -342,8 +348,8 @@ def project(Pm, X, off=None) -> np.ndarray:
 class MultiIndex:
     """Oracle index over R bases: per basis, keys of the rows' coordinates on
     the basis (R x m x d, m <= d: a projection, with optional offsets R x m)
-    and a stable counting sort; the search visits the bases' cones in
-    Algorithm 1's order with the "analyzed" flag."""
+    and a stable counting sort; the search is the exact top-k over the union
+    of the points of the bases' probed cones (Sec. 3-D)."""
 
     def __init__(self, X, L: int, rots, offsets=None):
         self.X = _f32(X)

@@ -3,7 +3,7 @@
  * order-statistics cone-hash ANN search of Verdoliva, Cozzolino and Poggi,
  * "A reliable order-statistics-based approximate nearest neighbor search
  * algorithm" (ROSANNA): one basis (R = 1), and R bases (Algorithm 1 with
- * its "analyzed" flag) for the multi-basis search of Sec. 3-D.
+ * the union of its bases' cones) for the multi-basis search of Sec. 3-D.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
  * CPU-baseline leg of the benchmark may load this library.  The product path
@@ -46,10 +46,11 @@
  *     its residual x - c (fp32 subtraction); the cone id inside the
  *     composite table is cluster * N_C + cone id of the residual; a query
  *     visits its M nearest clusters (nearest first), in each the first
- *     min(C, N_C) cones of its residual y - c.  "Nearest" is decided in fp32
- *     by the canonical expression of the GPU kernels (oracle_sqdist_f32),
- *     ties to the lower centroid index, so both sides take the same integer
- *     decisions; candidate distances stay in double precision.
+ *     min(C, N_C) cones of its residual y - c.  "Nearest" is the plain
+ *     definition: the smallest squared distance (Eq. 1) in double precision,
+ *     ties to the lower centroid index.  A caller that holds another
+ *     program's assignment (a GPU that decided a near-tie in fp32 the other
+ *     way) may pass it in, and the keys and the search then follow it.
  * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
  * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
  * The intra-class probe order and the sign-flip extension are this
@@ -520,61 +521,29 @@ void oracle_search_wide(const float *X, int64_t N, int d, int L, int64_t n_occ,
 
 /* ---------------------------------------------------------------- ROSANNA+ */
 
-/* Squared distance in fp32 in the order every GPU kernel evaluates it: the
- * vectors zero padded to d_pad = max(16, next power of two >= d), cut into
- * float4 pieces j, piece j giving fma(t3,t3, fma(t2,t2, fma(t1,t1, t0*t0)))
- * with t = x - y, and the pieces summed by a perfect binary tree that pairs
- * adjacent pieces first.  Used only where a float decides an integer (the
- * nearest centroid), so that the oracle takes the kernels' decision. */
-float oracle_sqdist_f32(const float *x, const float *y, int d)
-{
-    int dp = 16;
-    while (dp < d) dp <<= 1;
-    int n = dp / 4;
-    float c[ORACLE_MAX_D / 4];
-    for (int j = 0; j < n; ++j) {
-        float t[4];
-        for (int e = 0; e < 4; ++e) {
-            int i = 4 * j + e;
-            t[e] = i < d ? x[i] - y[i] : 0.0f;
-        }
-        c[j] = fmaf(t[3], t[3], fmaf(t[2], t[2], fmaf(t[1], t[1], t[0] * t[0])));
-    }
-    for (int w = 1; w < n; w <<= 1)
-        for (int j = 0; j < n; j += 2 * w) c[j] = c[j] + c[j + w];
-    return c[0];
-}
-
 /* The M nearest of K centroids (K x d) of each of n vectors, nearest first,
- * by (oracle_sqdist_f32, centroid index): out[i * M + j]. */
+ * by (squared distance in double precision, centroid index): out[i * M + j];
+ * -1 pads when M > K. */
 void oracle_nearest_centroids(const float *X, int64_t n, int d, const float *C, int K, int M, int32_t *out)
 {
-    float *bd = (float *)malloc(sizeof(float) * (size_t)M);
+    double *bd = (double *)malloc(sizeof(double) * (size_t)M);
+    int64_t *bi = (int64_t *)malloc(sizeof(int64_t) * (size_t)M);
     for (int64_t i = 0; i < n; ++i) {
-        int32_t *bi = out + i * M;
-        for (int j = 0; j < M; ++j) { bd[j] = INFINITY; bi[j] = -1; }
-        for (int c = 0; c < K; ++c) {
-            float dist = oracle_sqdist_f32(X + i * d, C + (int64_t)c * d, d);
-            /* insertion by (distance, index); c ascending, so a tie never moves in front */
-            if (bi[M - 1] >= 0 && !(dist < bd[M - 1])) continue;
-            int j = M - 1;
-            while (j > 0 && (bi[j - 1] < 0 || bd[j - 1] > dist)) {
-                bd[j] = bd[j - 1];
-                bi[j] = bi[j - 1];
-                --j;
-            }
-            bd[j] = dist;
-            bi[j] = c;
-        }
+        topk_init(bd, bi, M);
+        for (int c = 0; c < K; ++c) topk_insert(bd, bi, M, sqdist(X + i * d, C + (int64_t)c * d, d), c);
+        for (int j = 0; j < M; ++j) out[i * M + j] = (int32_t)bi[j];
     }
     free(bd);
+    free(bi);
 }
 
 /* Composite 128-bit cone ids of ROSANNA+ (two words per point) and the
  * cluster of each point: asg[n] = nearest centroid, residual r = x - c in
- * fp32, id = asg * N_C + cone id of r.  Returns -1 if K * N_C >= 2^127. */
+ * fp32, id = asg * N_C + cone id of r.  asg_in (may be NULL) gives the
+ * assignment instead of the nearest centroid (copied to asg).  Returns -1 if
+ * K * N_C >= 2^127 or an entry of asg_in is not a centroid. */
 int oracle_keys_clustered(const float *X, int64_t N, int d, int L, const float *C, int K, uint64_t *keys,
-                          int32_t *asg)
+                          int32_t *asg, const int32_t *asg_in)
 {
     uint64_t nc[2];
     if (oracle_num_cones_wide(d, L, nc) != 0) return -1;
@@ -582,7 +551,14 @@ int oracle_keys_clustered(const float *X, int64_t N, int d, int L, const float *
     if ((u128)K > (((u128)1 << 127) - 1) / NC) return -1;
     float *r = (float *)malloc(sizeof(float) * (size_t)d);
     int32_t order[ORACLE_MAX_D];
-    oracle_nearest_centroids(X, N, d, C, K, 1, asg);
+    if (asg_in) {
+        for (int64_t n = 0; n < N; ++n) {
+            if (asg_in[n] < 0 || asg_in[n] >= K) { free(r); return -1; }
+            asg[n] = asg_in[n];
+        }
+    } else {
+        oracle_nearest_centroids(X, N, d, C, K, 1, asg);
+    }
     for (int64_t n = 0; n < N; ++n) {
         const float *c = C + (int64_t)asg[n] * d;
         for (int i = 0; i < d; ++i) r[i] = X[n * d + i] - c[i];
@@ -599,11 +575,13 @@ int oracle_keys_clustered(const float *X, int64_t N, int d, int L, const float *
  * oracle_keys_clustered): for each of the query's M nearest clusters,
  * nearest first, the first min(P, N_C) cones of the residual y - c,
  * looked up among the occupied composite ids; exact top-k over the
- * candidates (the clusters are disjoint, so no point is seen twice). */
+ * candidates (the clusters are disjoint, so no point is seen twice).
+ * near_in (may be NULL) gives each query's M clusters (Q x M, -1 entries
+ * skipped) instead of its M nearest. */
 void oracle_search_clustered(const float *X, int64_t N, int d, int L, const float *C, int K, int M,
                              int64_t n_occ, const uint64_t *uniq, const uint32_t *offsets, const uint32_t *perm,
                              const float *Y, int64_t Q, int64_t P, int k, int64_t *ids, double *dists,
-                             int64_t *cand_count)
+                             int64_t *cand_count, const int32_t *near_in)
 {
     (void)N;
     (void)K;
@@ -619,7 +597,8 @@ void oracle_search_clustered(const float *X, int64_t N, int d, int L, const floa
         double *bd = dists + q * k;
         int64_t *bi = ids + q * k;
         topk_init(bd, bi, k);
-        oracle_nearest_centroids(y, 1, d, C, K, M, near);
+        if (near_in) memcpy(near, near_in + q * M, sizeof(int32_t) * (size_t)M);
+        else oracle_nearest_centroids(y, 1, d, C, K, M, near);
         int64_t cands = 0;
         for (int j = 0; j < M; ++j) {
             if (near[j] < 0) continue;
@@ -675,13 +654,21 @@ void oracle_search_multi_proj(const float *X, int64_t N, int d, int L, int R, in
                               const float *Y, int64_t Q, int64_t P, int k, int64_t *ids, double *dists,
                               int64_t *cand_count);
 
-/* Search over R bases (Algorithm 1): basis r has its own cone index
- * (offsets_r, perm_r, built from the rotated data) and its own probe list,
- * made from the query's coordinates on that basis.  Cones are visited in
- * the algorithm's order -- for l = 1..C, for r = 1..R, cone c_l^(r) -- and a
- * point is analysed once (the "analyzed" flag); distances are exact (Eq. 1)
- * on the original vectors.  rots: R x d x d; offsets: R x (N_C + 1);
- * perms: R x N.  Outputs as oracle_search. */
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+/* Search over R bases (Sec. 3-D): basis r has its own cone index
+ * (offsets_r, perm_r, built from the data's coordinates on that basis) and
+ * its own list of the query's first min(P, N_C) cones, made from the query's
+ * coordinates on that basis.  The candidates are the union of the points of
+ * all R lists' cones -- a point that falls in probed cones of several bases
+ * is one candidate, its distance computed once -- and the answer is the
+ * exact top-k (Eq. 1, original vectors) over that union.  rots: R x d x d;
+ * offsets: R x (N_C + 1); perms: R x N.  Outputs as oracle_search
+ * (cand_count: size of the union). */
 void oracle_search_multi(const float *X, int64_t N, int d, int L, int R, const float *rots,
                          const uint32_t *offsets, const uint32_t *perms, const float *Y, int64_t Q,
                          int64_t P, int k, int64_t *ids, double *dists, int64_t *cand_count)
@@ -699,43 +686,37 @@ void oracle_search_multi_proj(const float *X, int64_t N, int d, int L, int R, in
 {
     int64_t NC = oracle_num_cones(m, L);
     if (P > NC) P = NC;
-    uint32_t *probes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(R * (P > 0 ? P : 1)));
-    int64_t *np = (int64_t *)malloc(sizeof(int64_t) * (size_t)R);
-    float *yr = (float *)malloc(sizeof(float) * (size_t)d);
-    unsigned char *analyzed = (unsigned char *)calloc((size_t)(N > 0 ? N : 1), 1);
-    int64_t *touched = (int64_t *)malloc(sizeof(int64_t) * (size_t)(N > 0 ? N : 1));
+    uint32_t *probes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(P > 0 ? P : 1));
+    float *yr = (float *)malloc(sizeof(float) * (size_t)m);
+    /* a point can be listed once per basis */
+    int64_t *cand = (int64_t *)malloc(sizeof(int64_t) * (size_t)(R * N > 0 ? R * N : 1));
     for (int64_t q = 0; q < Q; ++q) {
         const float *y = Y + q * d;
         double *bd = dists + q * k;
         int64_t *bi = ids + q * k;
-        topk_init(bd, bi, k);
+        /* 1. the points of every basis's probed cones */
+        int64_t nc = 0;
         for (int r = 0; r < R; ++r) {
             oracle_project(projs + (int64_t)r * m * d, projoff ? projoff + (int64_t)r * m : NULL, y, 1, d, m, yr);
-            np[r] = oracle_probes(yr, m, L, P, probes + (int64_t)r * P);
+            int64_t np = oracle_probes(yr, m, L, P, probes);
+            const uint32_t *off = offsets + (int64_t)r * (NC + 1);
+            const uint32_t *perm = perms + (int64_t)r * N;
+            for (int64_t l = 0; l < np; ++l)
+                for (uint32_t row = off[probes[l]]; row < off[probes[l] + 1]; ++row) cand[nc++] = perm[row];
         }
-        int64_t nt = 0;
-        for (int64_t l = 0; l < P; ++l)
-            for (int r = 0; r < R; ++r) {
-                if (l >= np[r]) continue;
-                const uint32_t c = probes[(int64_t)r * P + l];
-                const uint32_t *off = offsets + (int64_t)r * (NC + 1);
-                const uint32_t *perm = perms + (int64_t)r * N;
-                for (uint32_t row = off[c]; row < off[c + 1]; ++row) {
-                    const int64_t n = perm[row];
-                    if (analyzed[n]) continue;
-                    analyzed[n] = 1;
-                    touched[nt++] = n;
-                    topk_insert(bd, bi, k, sqdist(X + n * d, y, d), n);
-                }
-            }
-        if (cand_count) cand_count[q] = nt;
-        for (int64_t t = 0; t < nt; ++t) analyzed[touched[t]] = 0;
+        /* 2. their union: sorted, repeated ids dropped */
+        qsort(cand, (size_t)nc, sizeof(int64_t), cmp_i64);
+        int64_t nu = 0;
+        for (int64_t i = 0; i < nc; ++i)
+            if (nu == 0 || cand[nu - 1] != cand[i]) cand[nu++] = cand[i];
+        /* 3. exact top-k over the union */
+        topk_init(bd, bi, k);
+        for (int64_t i = 0; i < nu; ++i) topk_insert(bd, bi, k, sqdist(X + cand[i] * d, y, d), cand[i]);
+        if (cand_count) cand_count[q] = nu;
     }
     free(probes);
-    free(np);
     free(yr);
-    free(analyzed);
-    free(touched);
+    free(cand);
 }
 
 /* Exact linear search (Eq. 1): the k nearest of all N points. */

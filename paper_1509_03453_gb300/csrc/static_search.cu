@@ -12,6 +12,10 @@
 #include "osann.h"
 #include "osann_launch.h"
 
+namespace osann {
+int index_device(const osann_index* ix);
+}
+
 namespace {
 
 constexpr size_t NOALLOC_SCRATCH_BYTES = size_t(32) << 20;  // 32 MiB
@@ -21,13 +25,20 @@ __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES]
 std::mutex g_mu;
 void* g_scratch_addr[64];
 
-int scratch_address(void** out)
+// The scratch array of the current device, which must be the index's: the
+// array of another device would put the kernels' scratch on that device.
+int scratch_address(int index_dev, void** out)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) {
         osann::set_error("osann_search_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
         return OSANN_ERR_CUDA;
+    }
+    if (dev != index_dev) {
+        osann::set_error("osann_search_noalloc: the current device (%d) is not the index's device (%d)", dev,
+                         index_dev);
+        return OSANN_ERR_INVALID;
     }
     if (dev < 0 || dev >= 64) {
         osann::set_error("osann_search_noalloc: device ordinal %d out of range", dev);
@@ -64,7 +75,7 @@ extern "C" int osann_search_noalloc(const osann_index* index, const float* d_que
         return OSANN_ERR_INVALID;
     }
     void* scratch = nullptr;
-    int rc = scratch_address(&scratch);
+    int rc = scratch_address(osann::index_device(index), &scratch);
     if (rc) return rc;
     // every scratch byte the plain path reads is written earlier in the same
     // call, so nothing needs clearing between calls

@@ -1,9 +1,10 @@
 """Oracle pins for ROSANNA+ (Sec. 4-B: k-means clusters, each searched with
 the cone hash of its residuals; a query visits its nearest clusters).
 
-The fp32 distance that decides the nearest centroid is pinned to exact
-integer arithmetic and to its rounding bound; the nearest centroids to a
-numpy fp64 ranking (up to near-ties); one centroid at the origin reduces the
+The nearest centroid is the plain definition (fp64 squared distance, ties to
+the lower index), pinned to a numpy fp64 ranking, to exact ties on a bisecting
+hyperplane and to a difference below fp32 resolution; a given assignment and
+given query clusters are followed; one centroid at the origin reduces the
 method to the one-basis search, bit for bit; the search equals the exact
 top-k (numpy fp64) over the points of the selected clusters whose residual
 cone is in the residual's probed list; all clusters at the full budget is
@@ -15,52 +16,89 @@ import oracle
 from paper_1509_03453_gb300.kmeans import kmeans
 
 
-def _d_pad(d):
-    p = 16
-    while p < d:
-        p *= 2
-    return p
+def _fp64_sqdists(X, C):
+    return ((np.asarray(X, np.float64)[:, None, :] - np.asarray(C, np.float64)[None]) ** 2).sum(-1)
 
 
-@pytest.mark.parametrize("d", [3, 16, 30, 64, 128])
-def test_sqdist_f32_exact_on_small_integers(d):
-    rng = np.random.default_rng(d)
-    for _ in range(20):
-        x = rng.integers(-40, 41, size=d).astype(np.float32)
-        y = rng.integers(-40, 41, size=d).astype(np.float32)
-        assert oracle.sqdist_f32(x, y) == float(((x.astype(np.int64) - y.astype(np.int64)) ** 2).sum())
-
-
-@pytest.mark.parametrize("d", [5, 32, 100, 256])
-def test_sqdist_f32_within_rounding_bound(d):
-    rng = np.random.default_rng(10 + d)
-    bound = (5 + np.log2(_d_pad(d) / 4)) * 2.0 ** -24
-    worst = 0.0
-    for _ in range(200):
-        x = rng.standard_normal(d).astype(np.float32)
-        y = rng.standard_normal(d).astype(np.float32)
-        ref = ((x.astype(np.float64) - y.astype(np.float64)) ** 2).sum()
-        worst = max(worst, abs(oracle.sqdist_f32(x, y) - ref) / ref)
-    assert worst <= bound
-    assert worst > 0  # it is an fp32 evaluation, not the fp64 one
-
-
-def test_nearest_centroids_match_fp64_ranking():
+def test_nearest_centroids_are_the_fp64_ranking():
     rng = np.random.default_rng(3)
     X = rng.standard_normal((500, 24)).astype(np.float32)
     C = rng.standard_normal((40, 24)).astype(np.float32)
     C[7] = C[3]  # duplicate centroid: the lower index first
     near = oracle.nearest_centroids(X, C, 5)
-    D = ((X.astype(np.float64)[:, None, :] - C.astype(np.float64)[None]) ** 2).sum(-1)
+    D = _fp64_sqdists(X, C)
     for i in range(X.shape[0]):
         exp = np.lexsort((np.arange(40), D[i]))[:5]
         got = near[i]
-        assert np.allclose(D[i, got], D[i, exp], rtol=1e-6, atol=0)
+        # numpy sums in another order: identical up to a last-bit near-tie
+        same = got == exp
+        assert np.all(same | (np.abs(D[i, got] - D[i, exp]) <= 1e-12 * D[i, exp]))
         assert len(set(got.tolist())) == 5
         if 3 in got and 7 in got:
             assert list(got).index(3) < list(got).index(7)
     # M > K pads with -1
     assert (oracle.nearest_centroids(X[:3], C[:2], 4)[:, 2:] == -1).all()
+
+
+@pytest.mark.parametrize("d", [2, 16, 33])
+def test_nearest_centroid_exact_ties_go_to_the_lower_index(d):
+    # x on the bisecting hyperplane of two centroids mirrored through it: the
+    # fp64 distances are equal exactly, so the lower index wins whatever the
+    # order the centroids are listed in
+    rng = np.random.default_rng(40 + d)
+    c = np.zeros(d, np.float32)
+    c[0] = 1.5
+    X = rng.integers(-8, 9, size=(20, d)).astype(np.float32)
+    X[:, 0] = 0.0
+    far = np.full((3, d), 50.0, np.float32)
+    for order in ([0, 1], [1, 0]):
+        C = np.concatenate([far, np.stack([c, -c])[order]])
+        near = oracle.nearest_centroids(X, C, 2)
+        assert (near == [[3, 4]]).all()
+    # one step off the hyperplane decides it
+    X[:, 0] = 0.25
+    C = np.concatenate([far, np.stack([-c, c])])
+    assert (oracle.nearest_centroids(X, C, 1)[:, 0] == 4).all()
+
+
+def test_nearest_centroid_is_not_an_fp32_decision():
+    # two centroids whose fp64 distances differ by far less than an fp32 ulp
+    # of the distance: fp64 decides it (an fp32 evaluation would call it a tie)
+    x = np.zeros((1, 4), np.float32)
+    c0 = np.array([4096.0, 0.0, 0.0, 0.0], np.float32)
+    c1 = np.array([4096.0, 2.0 ** -12, 0.0, 0.0], np.float32)
+    assert np.float32(4096.0) ** 2 == np.float32(4096.0) ** 2 + np.float32(2.0 ** -24)
+    assert oracle.nearest_centroids(x, np.stack([c1, c0]), 1)[0, 0] == 1
+
+
+def test_given_assignment_and_query_clusters_are_followed():
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((2000, 16)).astype(np.float32)
+    Y = rng.standard_normal((30, 16)).astype(np.float32)
+    C = kmeans(X, 6, iters=4, seed=2)
+    ci = oracle.ClusteredIndex(X, 2, C)
+    same = oracle.ClusteredIndex(X, 2, C, asg=ci.asg)
+    assert same.keys == ci.keys and np.array_equal(same.perm, ci.perm)
+    # another assignment: each point keyed by its residual on the given cluster
+    alt = (ci.asg + 1) % 6
+    ca = oracle.ClusteredIndex(X, 2, C, asg=alt)
+    assert np.array_equal(ca.asg, alt)
+    nc = oracle.num_cones_wide(16, 2)
+    rk = oracle.keys_wide(X - C[alt], 2)
+    assert ca.keys == [int(a) * nc + r for a, r in zip(alt, rk)]
+    with pytest.raises(ValueError):
+        oracle.ClusteredIndex(X, 2, C, asg=np.full(2000, 6))
+    # the query's own nearest clusters given explicitly: the default search
+    near = oracle.nearest_centroids(Y, C, 3)
+    a = ci.search(Y, 3, 8, 2)
+    b = ci.search(Y, 3, 8, 2, near=near)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # other clusters given: the search over those
+    other = near[:, ::-1].copy()
+    other[:, 0] = -1  # skipped
+    ids, dd, cnt = ci.search(Y, 3, 8, 2, near=other, want_counts=True)
+    ref_ids, _, ref_cnt = ci.search(Y, 2, 8, 2, near=near[:, :2][:, ::-1].copy(), want_counts=True)
+    assert np.array_equal(cnt, ref_cnt) and np.array_equal(ids, ref_ids)
 
 
 def test_one_centroid_at_origin_is_the_one_basis_search():
