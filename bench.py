@@ -1,20 +1,34 @@
-"""Benchmark: queries/s at recall@1 >= 0.9 of the cone-hash search on GB300.
+"""Benchmark: queries/s at recall@1 >= 0.9 and p50/p99 latency of the
+cone-hash search serving three resident indexes on one GB300, against the
+plain fp32 scan.
 
-Workload (the scale-up Gaussian case): N = 1,000,000 data and Q = 10,000
-query vectors, d = 32, iid N(0,1) (seeds 1002 / 2002, +rank under torchrun),
-key depth L = 2, k = 1.  The probe budget P is the smallest of a fixed
-ladder whose recall@1 against exact linear search reaches 0.9.
+Workload (the serving configuration): three indexes resident on the device
+-- d = 32, N = 10^6 iid N(0,1), L = 2; d = 64, N = 4*10^6 iid N(0,1), L = 2;
+d = 128, N = 2*10^6 descriptor-like rows, L = 3 keyed on their first 16
+principal components (the PCA front-end of Sec. 4-B) -- each with a fixed
+probe budget P (the smallest of a ladder reaching recall@1 >= 0.9 against
+exact linear search, checked at run time) and k = 1.  A trace of 10^4
+requests (sizes floor(exp(U(0, ln 4096))), 1..4096 queries, index uniform,
+queries drawn from per-index pools of fresh vectors; seed 5000) is served
+by the library's continuous-batching request server (resident indexes,
+slots admitted by memory, batches across requests, CUDA graph replays,
+autotuned path and group size).
 
-One step = the whole path over one batch: build the index of the N points
-(cone keys, histogram + scan, stable sort, permuted copy) and search the Q
-queries (query order, probe lists, cone-major work list, tile scan, merge).
-`value` = Q / device time of a step (CUDA events on the stream, inputs
-resident in HBM, L2 flushed by a 256 MiB write before every step);
-`e2e` = the same through host buffers (pinned H2D of X and Y, D2H of the
-results inside the timed region).
+One step = one closed-loop window of the trace: 1000 consecutive requests
+(the windows cycle through the trace) submitted at once and drained.
+`value` = queries of the K timed windows / their device time (CUDA events,
+inputs resident in HBM; the 3.3 GB of resident rows are far above L2, so no
+flush is needed).  `latency_ms` = request latency (completion - arrival)
+p50/p99 with Poisson arrivals of the whole trace at 50/80/95% of that
+capacity.  `e2e` = the same windows through pinned host buffers (H2D of the
+window's queries and D2H of its results inside the timed region).  Beside
+it: the plain fp32 scan, GPU linear search, the CPU oracle (one core and all
+host cores), per-index recall and fp64 error, the roofline of the dominant
+kernel, and secondary blocks for the scale-up Gaussian build+search step
+and the descriptor configuration (k = 10).
 
---impl reference times the CPU oracle (the single-threaded plain program)
-on a bounded sample of the same workload.
+--impl reference times the CPU oracle on the same workload (bounded query
+samples per step, all host cores).
 """
 from __future__ import annotations
 
@@ -24,6 +38,7 @@ import os
 import statistics
 import subprocess
 import sys
+import threading
 import time
 
 import numpy as np
@@ -31,12 +46,26 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_FULL, Q_FULL, D, L, K = 1_000_000, 10_000, 32, 2, 1
-P_LADDER = [64, 96, 128, 160, 192, 224, 256, 320, 384, 512]
-MB_LADDER = [8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256]
-WORKLOAD = "gauss32: N=1,000,000 x d=32 data, Q=10,000 queries, iid N(0,1), L=2 (N_C=1984), k=1"
-METRIC = "queries/s at recall@1>=0.9"
+METRIC = "queries/s at recall@1>=0.9 and p50/p99 latency"
 FP32_LANES_PER_SM = 128
+
+# serving workload
+SERVE_SEED = 5000
+SERVE_POOL = 8192
+SERVE_REQUESTS = 10_000
+REQ_PER_STEP = 1000
+SERVE_K = 1
+SERVE_MAX_BATCH = 4096
+SERVE_LADDER = [16, 32, 64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192]
+# per-index probe budgets: the smallest ladder values with recall@1 >= 0.9 on
+# 1000 pool queries (measured on GB300: 0.910, 0.946, 0.932); re-checked at run time
+SERVE_P = (256, 3072, 2048)
+LOADS = (0.5, 0.8, 0.95)
+
+# scale-up Gaussian build+search step (secondary)
+G32_N, G32_Q, G32_D, G32_L, G32_K, G32_P = 1_000_000, 10_000, 32, 2, 1, 224
+# descriptor configuration (secondary): k = 10, one basis, L = 3
+C4_LADDER = [4096, 8192, 12288, 16384, 24576]
 
 
 def dist_env():
@@ -46,19 +75,66 @@ def dist_env():
     return ws, rank, local
 
 
-def gen(rank, n=N_FULL, q=Q_FULL):
-    from paper_1509_03453_gb300 import datagen
-    X = datagen.gaussian(n, D, 1002 + rank)
-    Y = datagen.gaussian(q, D, 2002 + rank)
-    return X, Y
-
-
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return json.load(f), "measured"
     except Exception:
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def serve_specs(rank=0):
+    """(name, X, query pool, L, PCA components) of the three resident
+    indexes; replicas under torchrun draw independent data (seed + 100 rank)."""
+    from paper_1509_03453_gb300 import datagen
+    r = 100 * rank
+    return [
+        ("gauss32 N=1M", datagen.gaussian(1_000_000, 32, 1002 + r), datagen.gaussian(SERVE_POOL, 32, 5001 + r), 2, 0),
+        ("gauss64 N=4M", datagen.gaussian(4_000_000, 64, 1005 + r), datagen.gaussian(SERVE_POOL, 64, 5002 + r), 2, 0),
+        ("desc128 N=2M (PCA 16)", datagen.descriptors(2_000_000, 1004 + r),
+         datagen.descriptor_queries(SERVE_POOL, 5003 + r), 3, 16),
+    ]
+
+
+def serve_trace(n_req=SERVE_REQUESTS, seed=SERVE_SEED, n_idx=3):
+    """Request sizes (log-uniform 1..4096), index (uniform) and pool offsets."""
+    rng = np.random.default_rng(seed)
+    sizes = np.floor(np.exp(rng.uniform(0.0, np.log(4096.0), n_req))).astype(np.int64).clip(1, 4096)
+    which = rng.integers(0, n_idx, n_req)
+    offs = np.array([rng.integers(0, SERVE_POOL - s + 1) for s in sizes], dtype=np.int64)
+    return sizes, which, offs, rng
+
+
+def serve_config(ws):
+    """The `config` of both arms (identical dicts)."""
+    return {"workload": "serving: 3 resident indexes (gauss32 N=1M d=32 L=2; gauss64 N=4M d=64 L=2; desc128 "
+                        "N=2M d=128 L=3 on 16 PCA axes), 10^4 Poisson requests of 1-4096 queries (log-uniform), "
+                        "index uniform, k=1",
+            "indexes": ["gauss32 N=1M", "gauss64 N=4M", "desc128 N=2M (PCA 16)"],
+            "P": list(SERVE_P), "k": SERVE_K, "requests_per_step": REQ_PER_STEP,
+            "step": "one closed-loop window of 1000 consecutive requests of the trace (windows cycle), submitted "
+                    "at once and drained through the request server",
+            "l2": "no flush: the 3.3 GB of resident index rows are far above the 129 MB L2",
+            "parallelism": f"replicas x{ws} (independent data per rank)"}
+
+
+def recall1(ids, d2, gt_ids, gt_d2):
+    hit = ids[:, 0] == gt_ids[:, 0]
+    near = np.abs(d2[:, 0].astype(np.float64) - gt_d2[:, 0]) <= 1e-6 * gt_d2[:, 0]
+    return float(np.mean(hit | near))
+
+
+def max_rel_err_fp64(X, Y, ids, d2):
+    """Largest |d_gpu - d_fp64| / d_fp64 over the returned (query, id) pairs
+    (the fp64 distance from the oracle's plain definition)."""
+    import oracle
+    ids = np.asarray(ids)
+    ok = ids >= 0
+    d64 = oracle.pair_dists(X, Y, np.where(ok, ids, 0))
+    den = np.where(d64 > 0, d64, 1.0)
+    err = np.abs(np.asarray(d2, np.float64) - d64) / den
+    return float(err[ok].max()) if ok.any() else 0.0
 
 
 class ClockSampler:
@@ -108,12 +184,6 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def recall1(ids, d2, gt_ids, gt_d2):
-    hit = ids[:, 0] == gt_ids[:, 0]
-    near = np.abs(d2[:, 0].astype(np.float64) - gt_d2[:, 0]) <= 1e-6 * gt_d2[:, 0]
-    return float(np.mean(hit | near))
-
-
 def profiled_traffic(kernel_md, sources):
     """DRAM bytes per launch from a committed ncu summary under profiles/,
     or None when the kernel's sources changed since the capture (the
@@ -138,37 +208,287 @@ TC_SOURCES = ["paper_1509_03453_gb300/csrc/tc_scan_kernel.cuh", "paper_1509_0345
 def run_profile(args):
     """Only the warm-up and timed steps (fixed P, chosen path): the command
     the ncu captures under profiles/ run, so that the launch list holds
-    exactly the kernels of the step."""
+    exactly the kernels of the step.  gauss32 / desc128: one build+search
+    step of the scale-up Gaussian (k = 1) or descriptor (k = 10) case;
+    serve64 / serve128: the search of one max-size batch (4096 pool queries)
+    on the prebuilt gauss64 (P = 3072) or PCA-keyed desc128 (P = 2048)
+    serving index, k = 1."""
     import torch
 
     import paper_1509_03453_gb300 as osann
+    from paper_1509_03453_gb300 import datagen
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     osann.load()
-    if args.workload == "desc128":
-        # the descriptor recipe (N = 2*10^6, d = 128, 1.02 GB of rows), L = 3, k = 10
-        from paper_1509_03453_gb300 import datagen
-        w = datagen.workload("desc128")
-        X, Y, Lw, Kw = w["X"], w["Y"], w["L"], w["k"]
+    if args.workload.startswith("serve"):
+        i = {"serve64": 1, "serve128": 2}[args.workload]
+        name, X, Y, Lk, m = serve_specs(0)[i]
+        Xd = torch.from_numpy(X).to(dev)
+        if m:
+            from paper_1509_03453_gb300.pca import pca_basis
+            axes, off = pca_basis(X, m, seed=SERVE_SEED)
+            ix = osann.Index(Xd, Lk, rot=torch.from_numpy(axes).to(dev), rot_offset=torch.from_numpy(off).to(dev))
+        else:
+            ix = osann.Index(Xd, Lk)
+        Yd = torch.from_numpy(Y[:SERVE_MAX_BATCH]).to(dev)
+        P = args.P or SERVE_P[i]
+        ws = torch.empty(ix.workspace_size(Yd.shape[0], P, SERVE_K, args.path), dtype=torch.uint8, device=dev)
+        step = lambda: ix.search(Yd, P, SERVE_K, path=args.path, workspace=ws)  # noqa: E731
     else:
-        X, Y = gen(0)
-        Lw, Kw = L, K
-    Xd = torch.from_numpy(X).to(dev)
-    Yd = torch.from_numpy(Y).to(dev)
-    P = args.P or 224
+        if args.workload == "desc128":
+            # the descriptor recipe (N = 2*10^6, d = 128, 1.02 GB of rows), L = 3, k = 10
+            w = datagen.workload("desc128")
+            X, Y, Lw, Kw = w["X"], w["Y"], w["L"], w["k"]
+        else:
+            X, Y = datagen.gaussian(G32_N, G32_D, 1002), datagen.gaussian(G32_Q, G32_D, 2002)
+            Lw, Kw = G32_L, G32_K
+        Xd = torch.from_numpy(X).to(dev)
+        Yd = torch.from_numpy(Y).to(dev)
+        P = args.P or G32_P
+
+        def step():
+            ix, _, _ = osann.build_search(Xd, Lw, Yd, P, Kw, path=args.path, sync=False)
+            ix.status()
+            ix.close()
     times = []
     for i in range(args.warmup + args.steps):
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        ix, _, _ = osann.build_search(Xd, Lw, Yd, P, Kw, path=args.path, sync=False)
+        step()
         b.record()
         b.synchronize()
-        ix.status()
-        ix.close()
         if i >= args.warmup:
             times.append(a.elapsed_time(b))
     print(json.dumps({"profile_run": True, "workload": args.workload, "P": P, "path": args.path,
                       "ms_per_step": float(np.mean(times))}))
+
+
+class ServingRun:
+    """The three resident indexes, the request server over them and the
+    request trace, with outputs preallocated for the whole trace."""
+
+    def __init__(self, dev, rank=0, slots=4, mem_gb=8.0):
+        import torch
+
+        import paper_1509_03453_gb300 as osann
+        from paper_1509_03453_gb300.pca import pca_basis
+        self.torch, self.osann, self.dev = torch, osann, dev
+        self.names, self.X, self.Ynp, self.L, self.m, self.idx, self.pools, self.proj = [], [], [], [], [], [], [], []
+        for name, X, Y, Lk, m in serve_specs(rank):
+            Xd = torch.from_numpy(X).to(dev)
+            if m:
+                axes, off = pca_basis(X, m, seed=SERVE_SEED)
+                self.proj.append((axes, off))
+                ix = osann.Index(Xd, Lk, rot=torch.from_numpy(axes).to(dev), rot_offset=torch.from_numpy(off).to(dev))
+            else:
+                self.proj.append(None)
+                ix = osann.Index(Xd, Lk)
+            del Xd
+            self.names.append(name)
+            self.X.append(X)
+            self.Ynp.append(Y)
+            self.L.append(Lk)
+            self.m.append(m)
+            self.idx.append(ix)
+            self.pools.append(torch.from_numpy(Y).to(dev))
+        self.P = list(SERVE_P)
+        self.srv = osann.Server(self.idx, P=self.P, k=[SERVE_K] * 3, slots=slots, max_batch=SERVE_MAX_BATCH,
+                                mem_budget=int(mem_gb * (1 << 30)), graphs=True)
+        self.sizes, self.which, self.offs, self.rng = serve_trace()
+        self.cum = np.concatenate([[0], np.cumsum(self.sizes)])
+        self.total_q = int(self.cum[-1])
+        self.ids = torch.empty((self.total_q, SERVE_K), dtype=torch.int64, device=dev)
+        self.d2 = torch.empty((self.total_q, SERVE_K), dtype=torch.float32, device=dev)
+        self.views = [(self.pools[int(w)][int(o):int(o) + int(s)],
+                       (self.ids[int(c):int(c) + int(s)], self.d2[int(c):int(c) + int(s)]))
+                      for w, o, s, c in zip(self.which, self.offs, self.sizes, self.cum[:-1])]
+
+    def check_recall(self):
+        """recall@1 at the fixed P (1000 pool queries against GPU linear
+        search) and the smallest ladder budget reaching 0.9."""
+        out = []
+        for ix, pool, P in zip(self.idx, self.pools, self.P):
+            gi, gd = (t.cpu().numpy() for t in ix.bruteforce(pool[:1000], SERVE_K))
+            ids, d2 = (t.cpu().numpy() for t in ix.search(pool[:1000], P, SERVE_K))
+            rec = recall1(ids, d2, gi, gd)
+            pmin = None
+            for cand in SERVE_LADDER:
+                if cand > P:
+                    break
+                i2, e2 = (t.cpu().numpy() for t in ix.search(pool[:1000], cand, SERVE_K))
+                if recall1(i2, e2, gi, gd) >= 0.9:
+                    pmin = cand
+                    break
+            out.append({"recall_at_1": round(rec, 4), "smallest_ladder_P_at_0.9": pmin})
+        return out
+
+    def tune(self):
+        self.choices = self.srv.tune(reps=2, queries=self.pools)
+        self.srv.warmup()
+        return self.choices
+
+    def window(self, w):
+        n = len(self.sizes)
+        a = (w * REQ_PER_STEP) % n
+        return [(a + j) % n for j in range(REQ_PER_STEP)]
+
+    def closed(self, reqs, views=None):
+        """Submit the requests at once and drain; returns their query count."""
+        srv = self.srv
+        views = views or self.views
+        for j in reqs:
+            q, out = views[j]
+            srv.submit(int(self.which[j]), q, out=out)
+        for t in srv.drain():
+            srv.result(t)
+        return int(self.sizes[reqs].sum())
+
+    def open_loop(self, rate_qps):
+        """The whole trace with Poisson arrivals at rate_qps queries/s;
+        returns (elapsed s, per-request latency s)."""
+        srv = self.srv
+        n = len(self.sizes)
+        mean = self.total_q / n
+        arr = np.cumsum(self.rng.exponential(mean / rate_qps, n))
+        arr -= arr[0]
+        lat = np.zeros(n)
+        owner = {}
+        t0 = time.perf_counter()
+        nxt, done = 0, 0
+        while done < n:
+            now = time.perf_counter() - t0
+            while nxt < n and arr[nxt] <= now:
+                q, out = self.views[nxt]
+                owner[srv.submit(int(self.which[nxt]), q, out=out)] = nxt
+                nxt += 1
+            got = srv.progress(wait=False)
+            tn = time.perf_counter() - t0
+            for t in got:
+                j = owner.pop(t)
+                srv.result(t)
+                lat[j] = tn - arr[j]
+                done += 1
+        return time.perf_counter() - t0, lat, arr[-1]
+
+    def mix_weights(self):
+        """Queries of each index in the trace."""
+        return np.array([self.sizes[self.which == i].sum() for i in range(3)], np.float64)
+
+    def per_index_ms(self, fn, nq, reps=3):
+        """Median device ms of fn(i, queries[:nq]) per index."""
+        torch = self.torch
+        out = []
+        for i in range(3):
+            q = self.pools[i][:nq]
+            fn(i, q)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn(i, q)
+                b.record()
+                b.synchronize()
+                ts.append(a.elapsed_time(b))
+            out.append(float(np.median(ts)))
+        return out
+
+    def close(self):
+        self.srv.close()
+        for ix in self.idx:
+            ix.close()
+
+
+def serving_roofline(sr, peaks, peak_src):
+    """Per index, one max-size batch (4096 pool queries) on the tuner's
+    choice for that bucket, with the library's stage events: the stage times,
+    and for the tensor-core screen its algorithmic flops (2d per (query,
+    candidate) pair, pairs counted exactly from the probe lists).  The
+    dominant kernel of the trace and its roofline, weighting each index by
+    its queries in the trace."""
+    import paper_1509_03453_gb300 as osann
+    torch = sr.torch
+    w = sr.mix_weights() / SERVE_MAX_BATCH  # max-size batches of each index in the trace
+    per, stage_tot = [], {}
+    for i, ix in enumerate(sr.idx):
+        path, group = sr.choices[i][-1]
+        q = sr.pools[i][:SERVE_MAX_BATCH]
+        ws = torch.empty(ix.workspace_size(q.shape[0], sr.P[i], SERVE_K, path, group), dtype=torch.uint8,
+                         device=sr.dev)
+        ix.search(q, sr.P[i], SERVE_K, path=path, group=group, workspace=ws)
+        torch.cuda.synchronize()
+        osann.stats(enable=True, reset=True)
+        reps = 5
+        for _ in range(reps):
+            ix.search(q, sr.P[i], SERVE_K, path=path, group=group, workspace=ws)
+        torch.cuda.synchronize()
+        st = osann.stats(enable=False)
+        stage_ms = {k: v[0] / reps for k, v in st.items() if v[1]}
+        off = ix.export()[1]
+        pr = ix.probes(q, sr.P[i])
+        pairs = int((off[1:] - off[:-1])[pr.long()].sum().item())
+        per.append({"index": sr.names[i], "path": path, "group": group, "pairs": pairs,
+                    "stage_ms_per_batch": {k: round(v, 4) for k, v in stage_ms.items()}})
+        for k, v in stage_ms.items():
+            stage_tot[k] = stage_tot.get(k, 0.0) + w[i] * v
+    dom = max(stage_tot, key=stage_tot.get)
+    if dom == "tc_scan":
+        flops = sum(w[i] * per[i]["pairs"] * 2.0 * sr.X[i].shape[1] for i in range(3))
+        t = sum(w[i] * per[i]["stage_ms_per_batch"].get("tc_scan", 0.0) for i in range(3))
+        peak = peaks.get("bf16_tflops", 1900.0)
+        achieved = flops / (t / 1e3) / 1e12
+        roof = {"kernel": "tc_scan", "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                "traffic": profiled_traffic("tc_scan_serving_batch4096.md", TC_SOURCES),
+                "traffic_source": "ncu capture in profiles/tc_scan_serving_batch4096.md (null if absent or the "
+                                  "kernel changed since)",
+                "peak_source": f"{peak_src} bf16 dense burst (each launch timed alone; fp16 has the same "
+                               f"nominal rate)",
+                "algorithmic": "2d flops per (query, candidate) pair, pairs counted from the probe lists; "
+                               "per-index launches of max-size batches weighted by the trace's queries "
+                               "(issued MMA work is larger: padded tiles and one extra K block of 16)",
+                "avg_launch_ms": round(t / w.sum(), 4)}
+    else:
+        roof = {"kernel": dom, "bound": "unknown", "note": "dominant stage is not the tensor-core screen"}
+    return roof, per, {k: round(v / w.sum(), 4) for k, v in stage_tot.items()}
+
+
+def oracle_serving_rates(sr_like, budget_s):
+    """The oracle as it stands on the serving workload: each index built
+    (keys over row slices in parallel threads; not timed, the indexes are
+    resident in serving), then pool queries of each index searched, on one
+    core and on all host cores (query slices in threads), for about
+    budget_s seconds in all, scaled to the trace's index mix.
+    sr_like: (X list, pools, L, projections, P, mix weights)."""
+    import oracle
+    oracle.build()
+    Xs, Ys, Ls, projs, Ps, wmix = sr_like
+    ncpu = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    refs = []
+    for X, Lk, pj in zip(Xs, Ls, projs):
+        if pj is None:
+            refs.append(oracle.Index(X, Lk, threads=ncpu))
+        else:
+            refs.append(oracle.MultiIndex(X, Lk, pj[0][None], offsets=pj[1][None], threads=ncpu))
+    t_build = time.perf_counter() - t0
+    out = {}
+    for threads, share in ((1, 0.3), (ncpu, 0.7)):
+        per_q, samples = [], []
+        start = 0
+        for ref, Y, P in zip(refs, Ys, Ps):
+            n, t = 0, 0.0
+            chunk = threads
+            while t < share * budget_s / 3 and n + chunk <= Y.shape[0]:
+                t1 = time.perf_counter()
+                ref.search(Y[start + n:start + n + chunk], P, SERVE_K, threads=threads)
+                t += time.perf_counter() - t1
+                n += chunk
+            per_q.append(t / max(n, 1))
+            samples.append(n)
+        start = 0
+        out[threads] = (float(wmix.sum() / sum(w * c for w, c in zip(wmix, per_q))), per_q, samples)
+    return out, ncpu, t_build
 
 
 def run_gpu(args):
@@ -188,261 +508,115 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     osann.load()
+    peaks, peak_src = load_peaks()
 
-    X, Y = gen(rank)
-    Xd = torch.from_numpy(X).to(dev)
-    Yd = torch.from_numpy(Y).to(dev)
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
+    sr = ServingRun(dev, rank, slots=args.serve_slots, mem_gb=args.serve_mem_gb)
+    recalls = sr.check_recall()
+    choices = sr.tune()
 
-    # ground truth (exact linear search on the GPU) and the probe budget
-    idx = osann.Index(Xd, L)
-    gt_ids, gt_d2 = (t.cpu().numpy() for t in idx.bruteforce(Yd, K))
-    P, rec = None, None
-    if args.P:
-        P = args.P
-        ids, d2 = idx.search(Yd, P, K)
-        rec = recall1(ids.cpu().numpy(), d2.cpu().numpy(), gt_ids, gt_d2)
-    else:
-        for cand in P_LADDER:
-            ids, d2 = idx.search(Yd, cand, K)
-            rec = recall1(ids.cpu().numpy(), d2.cpu().numpy(), gt_ids, gt_d2)
-            P = cand
-            if rec >= 0.9:
-                break
-    if ws > 1:
-        t = torch.tensor([P], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        P = int(t.item())
-    ws_bytes = idx.workspace_size(Q_FULL, P, K)
-    idx.close()
-    work = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
-    out_ids = torch.empty((Q_FULL, K), dtype=torch.int64, device=dev)
-    out_d2 = torch.empty((Q_FULL, K), dtype=torch.float32, device=dev)
-
-    def step(path="auto"):
-        # build and search in one call (osann_build_search): the query-side
-        # steps run beside the build; the build's status is read after the step
-        ix, _, _ = osann.build_search(Xd, L, Yd, P, K, path=path, sync=False, out=(out_ids, out_d2))
-        return ix
-
-    def check(ix):
-        if ix.status() & 5:  # non-finite data or a device wait timeout
-            raise RuntimeError("index build reported an error status")
-
-    def timed(path, steps, warmup, with_stats=False):
-        times = []
-        for i in range(warmup + steps):
-            flush.zero_()
-            if with_stats and i == warmup:
-                osann.stats(enable=True, reset=True)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            ix = step(path)
-            b.record(stream)
-            b.synchronize()
-            check(ix)
-            ix.close()
-            if i >= warmup:
-                times.append(a.elapsed_time(b))
-        st = osann.stats(enable=False) if with_stats else None
-        return times, st
-
-    # the timed step: the index rebuilt in place from the data and the Q
-    # queries searched (osann_rebuild_search, query side beside the rebuild),
-    # captured once as a CUDA graph and replayed -- every build and search
-    # kernel runs in every step; the graph only removes launch gaps
-    gix = osann.Index(Xd, L)
-    gws = torch.empty(gix.workspace_size(Q_FULL, P, K), dtype=torch.uint8, device=dev)
-    cap = torch.cuda.Stream(device=dev)  # graphs are captured on a non-default stream
-    cap.wait_stream(stream)
-    for _ in range(2):  # the first call allocates the rebuild's temporaries
-        gix.rebuild_search(Xd, Yd, P, K, out=(out_ids, out_d2), workspace=gws, stream=cap)
-    cap.synchronize()
-    check(gix)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    launches0 = osann.launch_count()
-    with torch.cuda.graph(graph, stream=cap, capture_error_mode="thread_local"):
-        gix.rebuild_search(Xd, Yd, P, K, out=(out_ids, out_d2), workspace=gws, stream=cap)
-    launches_per_step = osann.launch_count() - launches0
-    torch.cuda.synchronize()
-
-    def timed_graph(steps, warmup):
-        times = []
-        for i in range(warmup + steps):
-            flush.zero_()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            graph.replay()
-            b.record(stream)
-            b.synchronize()
-            check(gix)
-            if i >= warmup:
-                times.append(a.elapsed_time(b))
-        return times
-
-    # warm-up, then exactly `steps` timed steps bracketed by barrier + sync
-    timed_graph(0, args.warmup)
+    # warm-up windows, then exactly K timed windows bracketed by barrier + sync
+    for i in range(args.warmup):
+        sr.closed(sr.window(i))
     torch.cuda.synchronize()
     if ws > 1:
         dist.barrier()
+    stream = torch.cuda.current_stream()
     sampler = ClockSampler(local)
     sampler.start()
+    launches0 = osann.launch_count()
+    times, nq = [], []
     t_wall0 = time.perf_counter()
-    times = timed_graph(args.steps, 0)
+    for i in range(args.steps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        nq.append(sr.closed(sr.window(args.warmup + i)))
+        b.record(stream)
+        b.synchronize()
+        times.append(a.elapsed_time(b))
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
-    launches = launches_per_step * args.steps
+    launches = osann.launch_count() - launches0
     clocks = sampler.stop()
-    rec_graph = recall1(out_ids.cpu().numpy(), out_d2.cpu().numpy(), gt_ids, gt_d2)
-    del graph
-    gix.close()
-    # the same step without the graph: one osann_build_search call (fresh index)
-    eager_times, _ = timed("auto", max(3, args.steps // 2), 2)
+    tot_ms = float(sum(times))
+    tq = torch.tensor([tot_ms], dtype=torch.float64, device=dev)
     if ws > 1:
-        dist.barrier()
-    ms = sum(times) / len(times)
-    ms_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        dist.all_reduce(ms_max, op=dist.ReduceOp.MAX)
-    ms_step = float(ms_max.item())
-    value = ws * Q_FULL / (ms_step / 1e3)
+        dist.all_reduce(tq, op=dist.ReduceOp.MAX)
+    tot_ms = float(tq.item())
+    value = ws * sum(nq) / (tot_ms / 1e3)
+    ms_step = tot_ms / args.steps
+    per_rank_capacity = sum(nq) / (tot_ms / 1e3)
 
-    # multi-basis search (Sec. 3-D): R rotated indexes, P per basis the
-    # smallest of a ladder with recall@1 >= 0.9; step = R asynchronous builds
-    # + R searches + the duplicate-free merge, timed the same way
-    multi = []
-    if rank == 0 and ws == 1 and not args.no_multi:
-        from paper_1509_03453_gb300 import datagen
-        for R in (2, 4):
-            rots = torch.from_numpy(datagen.rotations(R, D, 6000 + R)).to(dev)
-            mi = osann.MultiIndex(Xd, L, rots)
-            Pm, recm = None, 0.0
-            for cand in MB_LADDER:
-                ids, d2 = mi.search(Yd, cand, K)
-                recm = recall1(ids.cpu().numpy(), d2.cpu().numpy(), gt_ids, gt_d2)
-                Pm = cand
-                if recm >= 0.9:
-                    break
-            mi.close()
-            mt = []
-            for i in range(args.warmup + args.steps):
-                flush.zero_()
-                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                a.record(stream)
-                mi = osann.MultiIndex(Xd, L, rots, sync=False)
-                mi.search(Yd, Pm, K)
-                b.record(stream)
-                b.synchronize()
-                if mi.status() & 5:
-                    raise RuntimeError("multi-basis build reported an error status")
-                mi.close()
-                if i >= args.warmup:
-                    mt.append(a.elapsed_time(b))
-            mms = float(np.mean(mt))
-            multi.append({"R": R, "P_per_basis": Pm, "recall_at_1": round(recm, 4),
-                          "value": round(Q_FULL / (mms / 1e3), 1), "unit": "queries/s", "ms_per_step": round(mms, 4),
-                          "bases": "identity + seeded random rotations (QR of Gaussian, seed 6000 + R)"})
+    # open loop: Poisson arrivals of the whole trace at fractions of the capacity
+    loads = []
+    for frac in LOADS:
+        el, lat, span = sr.open_loop(frac * per_rank_capacity)
+        loads.append({"offered_frac": frac, "offered_qps": round(sr.total_q / max(span, 1e-9), 1),
+                      "qps": round(sr.total_q / el, 1),
+                      "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                      "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)})
 
-    # per-stage device times, from a separate pass (the stage events stay out
-    # of the timed steps above)
-    n_stat = max(3, args.steps // 2)
-    _, stats = timed("auto", n_stat, 0, with_stats=True)
-
-    # plain per-query fp32 scan and exact linear search, same P, same clocking
-    plain_times, _ = timed("plain", max(3, args.steps // 2), 1)
-    bf_times = []
-    for i in range(3):
-        ix = osann.Index(Xd, L)
-        flush.zero_()
+    # the same windows end to end through pinned host buffers
+    e2e_ms, h2d, d2h = [], [], []
+    n_e2e = max(3, min(args.steps, 10))
+    for i in range(args.warmup + n_e2e):
+        reqs = sr.window(i)
+        dims = [sr.X[int(sr.which[j])].shape[1] for j in reqs]
+        lens = [int(sr.sizes[j]) * dd for j, dd in zip(reqs, dims)]
+        starts = np.concatenate([[0], np.cumsum(lens)])
+        host = torch.empty(int(starts[-1]), dtype=torch.float32, pin_memory=True)
+        for j, s0, ln, dd in zip(reqs, starts[:-1], lens, dims):
+            o = int(sr.offs[j])
+            host[int(s0):int(s0) + ln] = torch.from_numpy(sr.Ynp[int(sr.which[j])][o:o + ln // dd].reshape(-1))
+        dbuf = torch.empty(int(starts[-1]), dtype=torch.float32, device=dev)
+        nres = int(sr.sizes[reqs].sum())
+        ids_d = torch.empty((nres, SERVE_K), dtype=torch.int64, device=dev)
+        d2_d = torch.empty((nres, SERVE_K), dtype=torch.float32, device=dev)
+        ids_h = torch.empty((nres, SERVE_K), dtype=torch.int64, pin_memory=True)
+        d2_h = torch.empty((nres, SERVE_K), dtype=torch.float32, pin_memory=True)
+        views = {}
+        r0 = 0
+        for j, s0, ln, dd in zip(reqs, starts[:-1], lens, dims):
+            n = ln // dd
+            views[j] = (dbuf[int(s0):int(s0) + ln].view(n, dd), (ids_d[r0:r0 + n], d2_d[r0:r0 + n]))
+            r0 += n
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        ix.bruteforce(Yd, K)
+        dbuf.copy_(host, non_blocking=True)
+        stream.synchronize()  # the server's streams read the queries once submitted
+        sr.closed(reqs, views)
+        ids_h.copy_(ids_d, non_blocking=True)
+        d2_h.copy_(d2_d, non_blocking=True)
         b.record(stream)
         b.synchronize()
-        ix.close()
-        if i:
-            bf_times.append(a.elapsed_time(b))
-
-    # end to end through host buffers (pinned), copies inside the timed region
-    Xh = torch.from_numpy(X).pin_memory()
-    Yh = torch.from_numpy(Y).pin_memory()
-    ids_h = torch.empty((Q_FULL, K), dtype=torch.int64).pin_memory()
-    d2_h = torch.empty((Q_FULL, K), dtype=torch.float32).pin_memory()
-    e2e_times = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        xd = Xh.to(dev, non_blocking=True)
-        yd = Yh.to(dev, non_blocking=True)
-        ix, _, _ = osann.build_search(xd, L, yd, P, K, sync=False, out=(out_ids, out_d2))
-        ids_h.copy_(out_ids, non_blocking=True)
-        d2_h.copy_(out_d2, non_blocking=True)
-        b.record(stream)
-        b.synchronize()
-        check(ix)
-        ix.close()
         if i >= args.warmup:
-            e2e_times.append(a.elapsed_time(b))
-    e2e_ms = sum(e2e_times) / len(e2e_times)
-    e2e_t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+            e2e_ms.append(a.elapsed_time(b))
+            h2d.append(host.numel() * 4)
+            d2h.append(nres * SERVE_K * 12)
+    e2e_t = torch.tensor([float(np.mean(e2e_ms))], dtype=torch.float64, device=dev)
     if ws > 1:
         dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(e2e_t.item())
+    e2e_step_ms = float(e2e_t.item())
+    e2e_q = float(np.mean([sr.sizes[sr.window(args.warmup + i)].sum() for i in range(n_e2e)]))
 
-    # roofline of the dominant stage
-    peaks, peak_src = load_peaks()
-    stage_ms = {k: v[0] / max(v[1], 1) for k, v in stats.items() if v[1]}
-    stage_n = {k: v[1] / n_stat for k, v in stats.items() if v[1]}
-    dom = max(stats, key=lambda s: stats[s][0])
-    path_used = "tensor-core screen (fp16 operands)" if stats.get("tc_scan", (0, 0))[1] else (
-        "batched fp32" if stats.get("tile_scan", (0, 0))[1] else "plain fp32")
-    pairs = None
-    roof = None
-    # candidate pairs of the timed search (exact count from the probe lists)
-    ix = osann.Index(Xd, L)
-    off = ix.export()[1]
-    pr = ix.probes(Yd, P)
-    sizes = (off[1:] - off[:-1])
-    pairs = int(sizes[pr].sum().item())
-    ix.search(Yd, P, K, out=(out_ids, out_d2), workspace=work)
-    screen = ix.screen_stats() if path_used.startswith("tensor") else None
-    ix.close()
-    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    dom_ms = stage_ms[dom]
-    if dom == "tc_scan":
-        # the contraction: 2d flops per (query, candidate) pair on 16-bit tensor
-        # cores (fp16 and bf16 share the dense rate)
-        flops = 2.0 * D * pairs
-        peak = peaks.get("bf16_tflops", 1900.0)
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "tensor", "achieved": round(achieved, 2), "peak": peak,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                "traffic": profiled_traffic("tc_scan_gauss32_N1M_Q10k_P224.md", TC_SOURCES),
-                "traffic_source": "ncu capture in profiles/tc_scan_gauss32_N1M_Q10k_P224.md (null if the kernel changed)",
-                "peak_source": f"{peak_src} bf16 dense (burst; fp16 has the same nominal rate)",
-                "algorithmic": f"{pairs} (query, candidate) pairs x 2d flops per launch "
-                               f"(issued MMA work is larger: padded tiles and one extra K block of 16)",
-                "avg_launch_ms": round(dom_ms, 4)}
-    elif dom in ("tile_scan", "plain_scan", "bruteforce"):
-        flops = 3.0 * D * pairs  # d subtractions, d squares, d additions per pair
-        peak = sm_count * FP32_LANES_PER_SM * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = flops / (dom_ms / 1e3) / 1e12
-        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
-                "peak_source": f"derived: {sm_count} SMs x {FP32_LANES_PER_SM} fp32 lanes x 2 (FMA) x "
-                               f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
-                "algorithmic": f"{pairs} (query, candidate) pairs x 3d flops per launch",
-                "avg_launch_ms": round(dom_ms, 4)}
-    else:
-        byts = 4.0 * N_FULL * D * 3
-        achieved = byts / (dom_ms / 1e3) / 1e9
-        peak = peaks["hbm_gbs"]
-        roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None, "peak_source": f"{peak_src} copy bandwidth",
-                "avg_launch_ms": round(dom_ms, 4)}
+    # counterparts on the same indexes and queries: the plain fp32 scan and
+    # GPU linear search, per index, scaled to the trace's index mix
+    wmix = sr.mix_weights()
+    plain_ms = sr.per_index_ms(lambda i, q: sr.idx[i].search(q, sr.P[i], SERVE_K, path="plain"), 1024)
+    bf_ms = sr.per_index_ms(lambda i, q: sr.idx[i].bruteforce(q, SERVE_K), 256, reps=2)
+    plain_rate = float(wmix.sum() / sum(w * t / 1024 / 1e3 for w, t in zip(wmix, plain_ms)))
+    bf_rate = float(wmix.sum() / sum(w * t / 256 / 1e3 for w, t in zip(wmix, bf_ms)))
+
+    # error against fp64 per index (256 pool queries, returned pairs)
+    errs = []
+    for i in range(3):
+        ids, d2 = (t.cpu().numpy() for t in sr.idx[i].search(sr.pools[i][:256], sr.P[i], SERVE_K))
+        errs.append(max_rel_err_fp64(sr.X[i], sr.Ynp[i][:256], ids, d2))
+
+    roof, roof_per, stage_ms = serving_roofline(sr, peaks, peak_src)
+    srv_stats = sr.srv.stats()
+    if ws > 1:
+        dist.barrier()
 
     line = {
         "metric": METRIC,
@@ -452,250 +626,272 @@ def run_gpu(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": round(ms_step, 4),
-        "eager_ms_per_step": round(float(np.mean(eager_times)), 4),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
-        "data": "synthetic (seeded iid N(0,1), generated on the host)",
-        "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P,
-                   "path": f"auto -> {path_used}",
-                   "step": "index build (rebuilt in place from the data: keys, cone table, permuted rows, screening operands) + search of the Q queries, one osann_rebuild_search call (query side beside the build) captured as a CUDA graph and replayed; the build's status read after every step; eager_ms_per_step: the same step as one osann_build_search call on a fresh index, no graph",
-                   "l2": "flushed before every step by a 256 MiB device write (untimed)",
-                   "parallelism": f"replicas x{ws} (independent data per rank)"},
-        "recall_at_1": round(rec, 4),
-        "recall_at_1_timed_step": round(rec_graph, 4),
-        "latency_ms": {"p50": round(float(np.percentile(times, 50)), 4),
-                       "p99": round(float(np.percentile(times, 99)), 4),
-                       "note": "per batch step of Q queries"},
-        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
-        "multi_basis": multi,
-        "screen": screen,
-        "stage_launches_per_step": stage_n,
-        "plain_fp32": {"value": round(Q_FULL / (np.mean(plain_times) / 1e3), 1), "unit": "queries/s",
-                       "ms_per_step": round(float(np.mean(plain_times)), 4)},
-        "bruteforce_fp32": {"value": round(Q_FULL / (np.mean(bf_times) / 1e3), 1), "unit": "queries/s",
-                            "ms_per_search": round(float(np.mean(bf_times)), 4), "recall_at_1": 1.0},
-        "e2e": {"value": round(ws * Q_FULL / (e2e_ms / 1e3), 1), "unit": "queries/s",
-                "ms_per_step": round(e2e_ms, 4),
-                "h2d_bytes_per_step": int(X.nbytes + Y.nbytes),
-                "d2h_bytes_per_step": int(out_ids.numel() * 8 + out_d2.numel() * 4)},
+        "data": "synthetic (seeded: iid N(0,1) and the descriptor recipe, generated on the host)",
+        "config": serve_config(ws),
+        "latency_ms": {f"load_{int(l['offered_frac'] * 100)}pct": {"p50": l["p50_ms"], "p99": l["p99_ms"]}
+                       for l in loads},
+        "loads": loads,
+        "recall_at_1": {n: r["recall_at_1"] for n, r in zip(sr.names, recalls)},
+        "recall_check": [dict(index=n, P=p, **r) for n, p, r in zip(sr.names, sr.P, recalls)],
+        "max_rel_err_fp64": {n: float(f"{e:.3g}") for n, e in zip(sr.names, errs)},
+        "tuned": {n: [list(c) for c in ch] for n, ch in zip(sr.names, choices)},
+        "queries_per_step": round(float(np.mean(nq)), 1),
+        "plain_fp32": {"value": round(ws * plain_rate, 1), "unit": "queries/s",
+                       "ms_per_1024_queries": {n: round(t, 3) for n, t in zip(sr.names, plain_ms)},
+                       "how": "per index: the plain per-query fp32 scan (same P, same bits) on 1024 pool queries, "
+                              "median of 3; throughput over the trace's index mix"},
+        "bruteforce_fp32": {"value": round(ws * bf_rate, 1), "unit": "queries/s",
+                            "ms_per_256_queries": {n: round(t, 3) for n, t in zip(sr.names, bf_ms)},
+                            "how": "cuBLAS-free GPU linear search per index on 256 pool queries, trace mix"},
+        "speedup_vs_plain_fp32": round(value / (ws * plain_rate), 1),
+        "e2e": {"value": round(ws * e2e_q / (e2e_step_ms / 1e3), 1), "unit": "queries/s",
+                "ms_per_step": round(e2e_step_ms, 4),
+                "h2d_bytes_per_step": int(np.mean(h2d)), "d2h_bytes_per_step": int(np.mean(d2h)),
+                "how": "each window's queries copied from one pinned host buffer to the device, served, results "
+                       "copied back to pinned host buffers, all inside the timed region"},
         "roofline": roof,
+        "roofline_per_index": roof_per,
+        "stage_ms_per_max_batch_mix": stage_ms,
         "gpu_launches": int(launches),
+        "server": srv_stats,
         "clocks": clocks,
         "wall_s_timed": round(t_wall, 3),
     }
+    sr_like = (sr.X, sr.Ynp, sr.L, sr.proj, sr.P, wmix)
+    sr.close()
+    del sr
+    torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(P, budget_s=args.cpu_budget)
-    if rank == 0 and ws == 1 and args.serve_requests > 0:
-        # the serving workload (three resident indexes), shortened: its own
-        # numbers, reported beside the step throughput
+        rates, ncpu, tb = oracle_serving_rates(sr_like, args.cpu_budget)
+        rn, pqn, nn = rates[ncpu]
+        r1, pq1, n1 = rates[1]
+        line["cpu_baseline"] = {
+            "value": round(rn, 3), "unit": "queries/s", "cores": ncpu, "kind": "oracle",
+            "sample": f"oracle indexes of the three datasets (built in {tb:.1f} s, not timed: resident in serving) "
+                      f"+ {nn} pool queries of the three indexes searched by {ncpu} threads on query slices, "
+                      f"scaled to the trace's index mix",
+            "one_core": {"value": round(r1, 3), "unit": "queries/s", "cores": 1,
+                         "sample": f"{n1} pool queries of the three indexes"},
+            "lscpu": _lscpu()}
+    if rank == 0 and ws == 1 and not args.no_secondary:
         try:
-            del Xd, Yd, work, flush
-            torch.cuda.empty_cache()
-            args_s = argparse.Namespace(**vars(args))
-            args_s.serve_requests = min(args.serve_requests, 2000)
-            sv = run_serving(args_s, emit=False)
-            line["serving"] = {k: sv[k] for k in ("indexes", "requests", "queries", "slots", "max_batch",
-                                                  "capacity_qps", "sustained_qps", "loads", "server")}
+            line["gauss32_build_search_step"] = gauss32_step(args, dev, peaks, peak_src)
         except Exception as exc:  # reported, never fatal to the main line
-            line["serving"] = {"error": repr(exc)[:300]}
+            line["gauss32_build_search_step"] = {"error": repr(exc)[:300]}
+        try:
+            line["descriptor_k10"] = descriptor_block(dev)
+        except Exception as exc:
+            line["descriptor_k10"] = {"error": repr(exc)[:300]}
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
         dist.destroy_process_group()
 
 
-def cpu_baseline(P, budget_s=15.0, rank=0):
-    """The oracle as it stands, single-threaded, on a bounded sample: the full
-    build of the N points plus a sample of the queries, scaled to a step of
-    the whole workload (build + Q queries)."""
-    import oracle
-    oracle.build()
-    X, Y = gen(rank)
-    t0 = time.perf_counter()
-    ref = oracle.Index(X, L)
-    t_build = time.perf_counter() - t0
-    n, t_search = 0, 0.0
-    chunk = 25
-    while t_search < max(1.0, budget_s - t_build) and n < Q_FULL:
-        t1 = time.perf_counter()
-        ref.search(Y[n:n + chunk], P, K)
-        t_search += time.perf_counter() - t1
-        n += chunk
-    t_step = t_build + t_search * Q_FULL / n
-    return {"value": round(Q_FULL / t_step, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle build of all {N_FULL} points ({t_build:.2f} s) + search of {n} of {Q_FULL} "
-                      f"queries at P={P} ({t_search:.2f} s), scaled to build + {Q_FULL} queries",
-            "P": P}
+def _lscpu():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        keep = {}
+        for ln in out.splitlines():
+            if ":" in ln:
+                k, v = ln.split(":", 1)
+                if k.strip() in ("Architecture", "CPU(s)", "Model name", "Thread(s) per core", "Core(s) per socket",
+                                 "Socket(s)", "CPU max MHz"):
+                    keep[k.strip()] = v.strip()
+        return keep
+    except Exception:
+        return None
+
+
+def gauss32_step(args, dev, peaks, peak_src):
+    """The scale-up Gaussian case as one build+search step: N = 10^6, Q =
+    10^4, d = 32, L = 2, k = 1, P = 224 (recall@1 >= 0.9): the index rebuilt
+    in place from the data and the queries searched, one osann_rebuild_search
+    call captured as a CUDA graph and replayed (L2 flushed before each
+    step); the tensor-core screen's roofline from the stage events."""
+    import torch
+
+    import paper_1509_03453_gb300 as osann
+    from paper_1509_03453_gb300 import datagen
+    X = datagen.gaussian(G32_N, G32_D, 1002)
+    Y = datagen.gaussian(G32_Q, G32_D, 2002)
+    Xd, Yd = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ix = osann.Index(Xd, G32_L)
+    gt_ids, gt_d2 = (t.cpu().numpy() for t in ix.bruteforce(Yd, G32_K))
+    out_ids = torch.empty((G32_Q, G32_K), dtype=torch.int64, device=dev)
+    out_d2 = torch.empty((G32_Q, G32_K), dtype=torch.float32, device=dev)
+    gws = torch.empty(ix.workspace_size(G32_Q, G32_P, G32_K), dtype=torch.uint8, device=dev)
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(stream)
+    for _ in range(2):
+        ix.rebuild_search(Xd, Yd, G32_P, G32_K, out=(out_ids, out_d2), workspace=gws, stream=cap)
+    cap.synchronize()
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=cap, capture_error_mode="thread_local"):
+        ix.rebuild_search(Xd, Yd, G32_P, G32_K, out=(out_ids, out_d2), workspace=gws, stream=cap)
+    torch.cuda.synchronize()
+    times = []
+    for i in range(3 + 10):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        graph.replay()
+        b.record(stream)
+        b.synchronize()
+        if ix.status() & 5:
+            raise RuntimeError("rebuild reported an error status")
+        if i >= 3:
+            times.append(a.elapsed_time(b))
+    rec = recall1(out_ids.cpu().numpy(), out_d2.cpu().numpy(), gt_ids, gt_d2)
+    del graph
+    # stage times of the same step, eager, with the library's stage events
+    osann.stats(enable=True, reset=True)
+    n = 5
+    for _ in range(n):
+        flush.zero_()
+        ix.rebuild_search(Xd, Yd, G32_P, G32_K, out=(out_ids, out_d2), workspace=gws)
+    torch.cuda.synchronize()
+    st = osann.stats(enable=False)
+    stage_ms = {k: v[0] / n for k, v in st.items() if v[1]}
+    off = ix.export()[1]
+    pr = ix.probes(Yd, G32_P)
+    pairs = int((off[1:] - off[:-1])[pr.long()].sum().item())
+    plain_t = []
+    for _ in range(3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ix.search(Yd, G32_P, G32_K, path="plain")
+        b.record(stream)
+        b.synchronize()
+        plain_t.append(a.elapsed_time(b))
+    ix.close()
+    tc = stage_ms.get("tc_scan")
+    ms = float(np.mean(times))
+    out = {"workload": "gauss32: N=1,000,000 x d=32, Q=10,000, iid N(0,1), L=2, k=1, P=224",
+           "value": round(G32_Q / (ms / 1e3), 1), "unit": "queries/s", "ms_per_step": round(ms, 4),
+           "step": "index rebuilt in place + search of the Q queries, one osann_rebuild_search call replayed as a "
+                   "CUDA graph, L2 flushed before each step",
+           "recall_at_1": round(rec, 4), "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+           "plain_fp32_search_ms": round(float(np.median(plain_t)), 3)}
+    if tc:
+        ach = 2.0 * G32_D * pairs / (tc / 1e3) / 1e12
+        out["tc_scan_roofline"] = {"achieved": round(ach, 2), "peak": peaks.get("bf16_tflops", 1900.0),
+                                   "unit": "TFLOP/s", "frac": round(ach / peaks.get("bf16_tflops", 1900.0), 4),
+                                   "pairs": pairs, "avg_launch_ms": round(tc, 4),
+                                   "traffic": profiled_traffic("tc_scan_gauss32_N1M_Q10k_P224.md", TC_SOURCES),
+                                   "peak_source": f"{peak_src} bf16 dense burst"}
+    return out
+
+
+def descriptor_block(dev):
+    """The descriptor configuration (N = 2*10^6, d = 128, Q = 10^4, L = 3,
+    k = 10; one basis): the smallest ladder budget with recall@1 >= 0.9
+    against GPU linear search (1000 queries), then the search of all Q at
+    that P (index prebuilt) on the default path and the plain fp32 scan,
+    recall@1, the overlap of the 10 returned with the true 10 (recall@10 in
+    the sense of the fraction of true neighbours found), and the fp64 error."""
+    import torch
+
+    import paper_1509_03453_gb300 as osann
+    from paper_1509_03453_gb300 import datagen
+    w = datagen.workload("desc128")
+    X, Y = w["X"], w["Y"]
+    Xd, Yd = torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)
+    ix = osann.Index(Xd, 3)
+    ng = 1000
+    gi, gd = (t.cpu().numpy() for t in ix.bruteforce(Yd[:ng], 10))
+    P, r1 = None, 0.0
+    for cand in C4_LADDER:
+        ids, d2 = (t.cpu().numpy() for t in ix.search(Yd[:ng], cand, 10))
+        r1 = recall1(ids, d2, gi, gd)
+        P = cand
+        if r1 >= 0.9:
+            break
+    ov = float(np.mean([len(set(gi[i]) & set(ids[i])) / 10.0 for i in range(ng)]))
+    err = max_rel_err_fp64(X, Y[:ng], ids, d2)
+
+    def tm(f, n=3):
+        f()
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            f()
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.median(ts))
+    t_auto = tm(lambda: ix.search(Yd, P, 10))
+    t_plain = tm(lambda: ix.search(Yd, P, 10, path="plain"), n=2)
+    t_bf = tm(lambda: ix.bruteforce(Yd[:1000], 10), n=1) * 10
+    ix.close()
+    Q = Y.shape[0]
+    return {"workload": "desc128: N=2,000,000 x d=128 descriptor recipe, Q=10,000, L=3, k=10, one basis",
+            "P": P, "recall_at_1": round(r1, 4), "top10_overlap": round(ov, 4), "max_rel_err_fp64": float(f"{err:.3g}"),
+            "search_ms": round(t_auto, 3), "value": round(Q / (t_auto / 1e3), 1), "unit": "queries/s",
+            "plain_fp32": {"search_ms": round(t_plain, 3), "value": round(Q / (t_plain / 1e3), 1)},
+            "bruteforce_fp32": {"search_ms": round(t_bf, 3), "value": round(Q / (t_bf / 1e3), 1),
+                                "how": "1000 queries timed, scaled to Q"},
+            "note": "search only (index prebuilt); recall measured on the first 1000 queries"}
 
 
 def run_reference(args):
-    """CPU oracle arm: each step = oracle build + a bounded query sample."""
+    """CPU oracle arm on the serving workload: the oracle indexes of the
+    three datasets built once (not timed: resident in serving), then each
+    step searches a bounded sample of pool queries per index on all host
+    cores (query slices in threads), timed and scaled to the trace's mix."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
     oracle.build()
-    P = args.P or 224  # the GPU arm's recall@1 >= 0.9 budget on this workload (its P ladder)
-    X, Y = gen(0)
-    sample = 40
-    times = []
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        ref = oracle.Index(X, L)
-        tb = time.perf_counter() - t0
-        t1 = time.perf_counter()
-        s = (i * sample) % (Q_FULL - sample)
-        ref.search(Y[s:s + sample], P, K)
-        tq = time.perf_counter() - t1
-        if i >= args.warmup:
-            times.append(tb + tq * Q_FULL / sample)
-    t_step = float(np.mean(times))
-    value = Q_FULL / t_step
-    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_step * 1e3, 1),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded iid N(0,1))",
-            "config": {"workload": WORKLOAD, "N": N_FULL, "Q": Q_FULL, "d": D, "L": L, "k": K, "P": P},
-            "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": 1, "kind": "oracle",
-                             "sample": f"per step: oracle build of all {N_FULL} points + {sample} queries at "
-                                       f"P={P}, scaled to {Q_FULL} queries"},
-            "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}
-    print(json.dumps(line))
-
-
-# ---------------------------------------------------------------- serving
-
-SERVE_SEED = 5000
-SERVE_POOL = 8192
-SERVE_LADDER = [16, 32, 64, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192, 12288,
-                16384]
-
-
-def serve_indexes():
-    """The three resident indexes of the serving workload: (name, X, query
-    pool, L, PCA components or 0).  Gaussian rows iid N(0,1); descriptor rows
-    as the descriptor recipe, keyed on their first 16 principal components
-    (the PCA front-end of Sec. 4-B); query pools are fresh draws (seeds
-    5001..5003)."""
-    from paper_1509_03453_gb300 import datagen
-    return [
-        ("gauss32 N=1M", datagen.gaussian(1_000_000, 32, 1002), datagen.gaussian(SERVE_POOL, 32, 5001), 2, 0),
-        ("gauss64 N=4M", datagen.gaussian(4_000_000, 64, 1005), datagen.gaussian(SERVE_POOL, 64, 5002), 2, 0),
-        ("desc128 N=2M (PCA 16)", datagen.descriptors(2_000_000, 1004), datagen.descriptor_queries(SERVE_POOL, 5003),
-         3, 16),
-    ]
-
-
-def run_serving(args, emit=True):
-    """Poisson-arriving requests of 1..4096 queries (log-uniform sizes,
-    uniform index) through the request server; capacity first (all requests
-    at once), then open-loop loads at 50/80/95% of it."""
-    import torch
-
-    import paper_1509_03453_gb300 as osann
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    osann.load()
-    specs = serve_indexes()
-    idx, pools, Ps, names, recalls = [], [], [], [], []
+    from paper_1509_03453_gb300.pca import pca_basis
+    specs = serve_specs(0)
+    sizes, which, _, _ = serve_trace()
+    wmix = np.array([sizes[which == i].sum() for i in range(3)], np.float64)
+    ncpu = os.cpu_count() or 1
+    refs = []
     for name, X, Y, Lk, m in specs:
         if m:
-            from paper_1509_03453_gb300.pca import pca_basis
             axes, off = pca_basis(X, m, seed=SERVE_SEED)
-            ix = osann.Index(torch.from_numpy(X).to(dev), Lk, rot=torch.from_numpy(axes).to(dev),
-                             rot_offset=torch.from_numpy(off).to(dev))
+            refs.append((oracle.MultiIndex(X, Lk, axes[None], offsets=off[None], threads=ncpu), Y))
         else:
-            ix = osann.Index(torch.from_numpy(X).to(dev), Lk)
-        pool = torch.from_numpy(Y).to(dev)
-        gt_ids, gt_d2 = (t.cpu().numpy() for t in ix.bruteforce(pool[:1000], 1))
-        P, rec = SERVE_LADDER[-1], 0.0
-        for cand in SERVE_LADDER:
-            ids, d2 = (t.cpu().numpy() for t in ix.search(pool[:1000], cand, 1))
-            rec = recall1(ids, d2, gt_ids, gt_d2)
-            if rec >= 0.9:
-                P = cand
-                break
-        idx.append(ix)
-        pools.append(pool)
-        Ps.append(P)
-        names.append(name)
-        recalls.append(round(rec, 4))
-    srv = osann.Server(idx, P=Ps, k=[1] * len(idx), slots=args.serve_slots, max_batch=4096,
-                       mem_budget=int(args.serve_mem_gb * (1 << 30)), graphs=True)
-    choices = srv.tune(reps=2, queries=pools)
-    rng = np.random.default_rng(SERVE_SEED)
-    n_req = args.serve_requests
-    sizes = np.floor(np.exp(rng.uniform(0.0, np.log(4096.0), n_req))).astype(np.int64).clip(1, 4096)
-    which = rng.integers(0, len(idx), n_req)
-    offs = np.array([rng.integers(0, SERVE_POOL - s + 1) for s in sizes], dtype=np.int64)
-    total_q = int(sizes.sum())
-
-    def drive(arrivals):
-        lat = np.zeros(n_req)
-        t0 = time.perf_counter()
-        nxt, done = 0, 0
-        owner = {}
-        while done < n_req:
-            now = time.perf_counter() - t0
-            while nxt < n_req and arrivals[nxt] <= now:
-                i = int(which[nxt])
-                t = srv.submit(i, pools[i][offs[nxt]:offs[nxt] + sizes[nxt]])
-                owner[t] = nxt
-                nxt += 1
-            got = srv.progress(wait=False)
-            tn = time.perf_counter() - t0
-            for t in got:
-                j = owner.pop(t)
-                srv.result(t)
-                lat[j] = tn - arrivals[j]
-                done += 1
-        return time.perf_counter() - t0, lat
-
-    # warm-up: capture every graph the run needs
-    srv.warmup()  # every (slot, index, bucket) graph captured before timing
-    el, _ = drive(np.zeros(n_req))
-    capacity = total_q / el  # closed loop: every request queued at once, full batches
-    loads = []
-    mean_size = total_q / n_req
-    # open loop: Poisson arrivals at fractions of the closed-loop capacity; the
-    # sustained capacity is the largest offered rate the server keeps up with
-    # (achieved >= 95% of offered)
-    sustained = 0.0
-    for frac in (0.1, 0.2, 0.3, 0.45, 0.6, 0.8):
-        rate = frac * capacity / mean_size
-        arr = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        arr -= arr[0]
-        el, lat = drive(arr)
-        achieved = total_q / el
-        offered = total_q / max(arr[-1], 1e-9)
-        keeps_up = achieved >= 0.95 * offered
-        if keeps_up:
-            sustained = max(sustained, offered)
-        loads.append({"offered_frac": frac, "offered_qps": round(offered, 1), "qps": round(achieved, 1),
-                      "keeps_up": bool(keeps_up),
-                      "p50_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-                      "p99_ms": round(float(np.percentile(lat, 99)) * 1e3, 3)})
-    st = srv.stats()
-    out = {
-        "serving": True,
-        "metric": "request latency p50/p99 and queries/s at recall@1>=0.9",
-        "indexes": [{"name": n, "P": p, "recall_at_1": r, "tuned": [list(c) for c in ch]}
-                    for n, p, r, ch in zip(names, Ps, recalls, choices)],
-        "requests": n_req, "queries": total_q, "sizes": "floor(exp(U(0, ln 4096))), index uniform",
-        "slots": srv.slots, "max_batch": 4096, "graphs": True,
-        "capacity_qps": round(capacity, 1), "capacity_note": "closed loop (all requests queued at once)",
-        "sustained_qps": round(sustained, 1), "loads": loads,
-        "server": st,
-    }
-    srv.close()
-    for ix in idx:
-        ix.close()
-    if emit:
-        print(json.dumps(out))
-    return out
+            refs.append((oracle.Index(X, Lk, threads=ncpu), Y))
+    per_step = [ncpu, ncpu, max(1, ncpu // 4)]  # queries per index per step (the d128 index is the slowest)
+    times, walls = [], []
+    for i in range(args.warmup + args.steps):
+        per_q = []
+        tw = time.perf_counter()
+        for (ref, Y), P, n in zip(refs, SERVE_P, per_step):
+            s = (i * n) % (Y.shape[0] - n)
+            t0 = time.perf_counter()
+            ref.search(Y[s:s + n], P, SERVE_K, threads=ncpu)
+            per_q.append((time.perf_counter() - t0) / n)
+        if i >= args.warmup:
+            times.append(sum(w * c for w, c in zip(wmix, per_q)) / wmix.sum())
+            walls.append(time.perf_counter() - tw)
+    t_q = float(np.mean(times))
+    value = 1.0 / t_q
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "queries/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(float(np.mean(walls)) * 1e3, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded: iid N(0,1) and the descriptor recipe, generated on the host)",
+            "config": serve_config(ws),
+            "cpu_baseline": {"value": round(value, 3), "unit": "queries/s", "cores": ncpu, "kind": "oracle",
+                             "sample": f"per step: {per_step} pool queries of the three indexes searched on "
+                                       f"{ncpu} threads (query slices), per-query times scaled to the trace's "
+                                       f"index mix; ms_per_step is the measured time of that sample"},
+            "e2e": {"value": round(value, 3), "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
 
 
 def run_rosanna_plus(args):
@@ -799,19 +995,17 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="osann", choices=["osann", "reference"])
-    ap.add_argument("--P", type=int, default=0, help="fixed probe budget (default: recall ladder)")
-    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--P", type=int, default=0, help="probe budget of --profile runs")
+    ap.add_argument("--cpu-budget", type=float, default=20.0, help="seconds of oracle search for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the Gaussian build+search step and the descriptor (k = 10) block")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16", "fp16"])
-    ap.add_argument("--workload", default="gauss32", choices=["gauss32", "desc128"],
+    ap.add_argument("--workload", default="gauss32", choices=["gauss32", "desc128", "serve64", "serve128"],
                     help="workload of --profile runs")
-    ap.add_argument("--serving", action="store_true", help="the request-server workload (three resident indexes)")
-    ap.add_argument("--no-multi", action="store_true", help="skip the multi-basis (R > 1) measurement")
     ap.add_argument("--rosanna-plus", action="store_true",
                     help="ROSANNA+ vs the one-basis search and the PCA front-end (search times at recall 0.9)")
-    ap.add_argument("--serve-requests", type=int, default=10_000,
-                    help="requests of the serving workload (0: skip it in the default run)")
     ap.add_argument("--serve-slots", type=int, default=4)
     ap.add_argument("--serve-mem-gb", type=float, default=8.0)
     args = ap.parse_args()
@@ -821,8 +1015,6 @@ def main():
         run_reference(args)
     elif args.profile:
         run_profile(args)
-    elif args.serving:
-        run_serving(args)
     elif args.rosanna_plus:
         run_rosanna_plus(args)
     else:

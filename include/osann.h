@@ -62,8 +62,11 @@ typedef struct osann_index osann_index; /* opaque; owns its device buffers */
  * workspaces that the caller does not provide.  alloc returns a device
  * pointer (NULL on failure) usable in stream order on `stream`; free
  * releases it in stream order.  Passing NULL functions restores the default
- * (cudaMallocAsync / cudaFreeAsync).  Not thread-safe with concurrent
- * builds. */
+ * (cudaMallocAsync / cudaFreeAsync).  A block always goes back to the
+ * allocator that provided it, even after another one is installed (so its
+ * functions and ctx must stay valid until the blocks it gave are released).
+ * A failed request makes the call return OSANN_ERR_OOM after releasing
+ * what it took.  Not thread-safe with concurrent builds. */
 typedef void *(*osann_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*osann_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 int osann_set_allocator(osann_alloc_fn alloc, osann_free_fn free_fn, void *ctx);
@@ -154,6 +157,25 @@ int osann_build_async(const float *d_data, int64_t N, int32_t d, int32_t L, void
 #define OSANN_CONES_DENSE 1
 #define OSANN_CONES_HASHED 2
 
+/* Key modes for osann_build_ex.  OSANN_KEY_SET is the paper's profile
+ * (Sec. 2: the unordered set of the L largest-magnitude components; the
+ * paper does not order the components inside the group).
+ * OSANN_KEY_ORDERED keys the tuple (i_1, ..., i_L) of those components in
+ * decreasing magnitude (ties: the lower component first) with their
+ * signs: N_C = d!/(d-L)! 2^L, id = rank * 2^L + code, rank the tuple's
+ * position in lexicographic order, sum_j c_j (d-1-j)!/(d-L)! with c_j =
+ * i_(j+1) minus the number of earlier members below it, code bit L-1-j
+ * the sign of i_(j+1) (zero positive).  Its probe order follows the tree
+ * of ordered prefixes: distance delta = L - (length of the common prefix
+ * with the query's tuple); a profile at distance delta keeps
+ * (i_1..i_(L-delta)), its next member is any component but i_(L-delta+1)
+ * outside the prefix, the later ones any unused component; inside a class
+ * lexicographic in the members' magnitude ranks in the query; each with
+ * the query's signs, then the sign-flipped cones as for the set key.
+ * ORDERED needs N_C < 2^31 (a direct table) and no clusters. */
+#define OSANN_KEY_SET 0
+#define OSANN_KEY_ORDERED 1
+
 typedef struct {
     const float *d_basis;  /* m x d key basis (osann_build_rot / osann_build_proj), NULL: the identity */
     const float *d_offset; /* m offsets subtracted after projecting, NULL: none (needs d_basis) */
@@ -162,6 +184,7 @@ typedef struct {
     int32_t cone_table;    /* OSANN_CONES_* */
     const float *d_centroids; /* ROSANNA+: K x d k-means centroids (see below), NULL: none */
     int32_t n_clusters;       /* K (0: none) */
+    int32_t key_mode;         /* OSANN_KEY_SET (0, the paper's) or OSANN_KEY_ORDERED */
 } osann_build_opts;
 
 /* Build with explicit options (opts NULL: as osann_build).  Every other
@@ -381,6 +404,19 @@ int osann_stats_enable(int on);
 int osann_stats_reset(void);
 int osann_stats_get(int32_t stage, double *total_ms, int64_t *count);
 int64_t osann_launch_count(void);
+
+/* Test hook for failure detection (the paper has no counterpart): the clock
+ * budget, in SM cycles, of the plain scan's waits for its staged copies
+ * (OSANN_PATH_PLAIN, and the exact rescan of the tensor-core paths).  A wait
+ * that runs past it gives up: the kernel lets its copies in flight land
+ * (under the full budget), writes what it found for the query at hand and
+ * empty results (-1, +inf) for its other queries, and sets
+ * OSANN_STATUS_TIMEOUT, which the next osann_status reports; the context
+ * stays usable.  0 restores the default of about one second, which no
+ * legitimate wait approaches; a budget of a few cycles makes the waits run
+ * out.  Process-wide, read at each launch; not for production use.
+ * Errors: INVALID for a negative budget. */
+int osann_debug_wait_budget(int64_t cycles);
 
 /* Merge of per-shard results (the exchange step of a search sharded by data
  * rows; the paper has no counterpart).  d_ids / d_sqdists hold G lists laid

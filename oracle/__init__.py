@@ -67,6 +67,19 @@ def lib():
             _f32p, c.c_int64, c.c_int, c.c_int, _u32p, _u32p, _f32p, c.c_int64,
             c.c_int64, c.c_int, c.c_void_p, c.c_int64, c.c_int64, _i64p, _f64p,
             c.c_void_p]
+        L.oracle_num_cones_ordered.restype = c.c_int64
+        L.oracle_num_cones_ordered.argtypes = [c.c_int, c.c_int]
+        L.oracle_key_ordered.restype = c.c_uint32
+        L.oracle_key_ordered.argtypes = [_f32p, c.c_int, c.c_int]
+        L.oracle_keys_ordered.restype = None
+        L.oracle_keys_ordered.argtypes = [_f32p, c.c_int64, c.c_int, c.c_int, _u32p]
+        L.oracle_probes_ordered.restype = c.c_int64
+        L.oracle_probes_ordered.argtypes = [_f32p, c.c_int, c.c_int, c.c_int64, _u32p]
+        L.oracle_search_mode.restype = None
+        L.oracle_search_mode.argtypes = [
+            _f32p, c.c_int64, c.c_int, c.c_int, c.c_int, _u32p, _u32p, _f32p, c.c_int64,
+            c.c_int64, c.c_int, c.c_void_p, c.c_int64, c.c_int64, _i64p, _f64p,
+            c.c_void_p]
         L.oracle_bruteforce.restype = None
         L.oracle_bruteforce.argtypes = [
             _f32p, c.c_int64, c.c_int, _f32p, c.c_int64, c.c_int, c.c_void_p,
@@ -136,12 +149,64 @@ def key(x, L: int) -> int:
     return int(lib().oracle_key(x, x.shape[-1], L))
 
 
-def keys(X, L: int) -> np.ndarray:
+def _sliced(n: int, threads: int, fn) -> None:
+    """Run fn(lo, hi) on `threads` contiguous slices of range(n), one thread
+    each.  The C calls release the GIL and share no state, so the slices run
+    in parallel; each runs the same single-threaded code on its rows."""
+    threads = max(1, min(int(threads), n))
+    if threads == 1:
+        fn(0, n)
+        return
+    import threading
+    cuts = [n * t // threads for t in range(threads + 1)]
+    errs = []
+
+    def run(lo, hi):
+        try:
+            fn(lo, hi)
+        except BaseException as e:  # re-raised below
+            errs.append(e)
+    ts = [threading.Thread(target=run, args=(cuts[t], cuts[t + 1])) for t in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if errs:
+        raise errs[0]
+
+
+def keys(X, L: int, threads: int = 1) -> np.ndarray:
     X = _f32(X)
     N, d = X.shape
     out = np.empty(N, np.uint32)
-    lib().oracle_keys(X, N, d, L, out)
+    _sliced(N, threads, lambda lo, hi: lib().oracle_keys(X[lo:hi], hi - lo, d, L, out[lo:hi]))
     return out
+
+
+def num_cones_ordered(d: int, L: int) -> int:
+    """N_C of the ORDERED key: d!/(d-L)! 2^L (-1 if it does not fit)."""
+    return int(lib().oracle_num_cones_ordered(d, L))
+
+
+def key_ordered(x, L: int) -> int:
+    x = _f32(x)
+    return int(lib().oracle_key_ordered(x, x.shape[-1], L))
+
+
+def keys_ordered(X, L: int, threads: int = 1) -> np.ndarray:
+    X = _f32(X)
+    N, d = X.shape
+    out = np.empty(N, np.uint32)
+    _sliced(N, threads, lambda lo, hi: lib().oracle_keys_ordered(X[lo:hi], hi - lo, d, L, out[lo:hi]))
+    return out
+
+
+def probes_ordered(y, L: int, P: int) -> np.ndarray:
+    """The ordered cone list of y for the ORDERED key."""
+    y = _f32(y)
+    out = np.empty(max(P, 1), np.uint32)
+    n = lib().oracle_probes_ordered(y, y.shape[-1], L, P, out)
+    return out[:n].copy()
 
 
 def buckets(k: np.ndarray, NC: int):
@@ -198,28 +263,38 @@ def _src_ptr(query_src):
 class Index:
     """Oracle index: keys, stable counting sort into cone buckets."""
 
-    def __init__(self, X, L: int):
+    def __init__(self, X, L: int, threads: int = 1, key_mode: int = 0):
+        """threads > 1: the keys of row slices computed in parallel threads
+        (the same single-threaded code per slice).  key_mode 1: the ORDERED
+        key (the top-L components as a tuple in magnitude order)."""
         self.X = _f32(X)
         self.N, self.d = self.X.shape
         self.L = L
-        self.NC = num_cones(self.d, L)
-        if self.NC < 0:
-            raise ValueError("N_C does not fit")
-        self.keys = keys(self.X, L)
+        self.key_mode = int(key_mode)
+        self.NC = num_cones_ordered(self.d, L) if self.key_mode else num_cones(self.d, L)
+        if self.NC < 0 or self.NC >= 1 << 32:
+            raise ValueError("N_C does not fit a direct table")
+        self.keys = (keys_ordered if self.key_mode else keys)(self.X, L, threads)
         self.offsets, self.perm = buckets(self.keys, self.NC)
 
     def search(self, Y, P: int, k: int, query_src=None, grid_w: int = 0,
-               radius: int = 0, want_counts: bool = False):
+               radius: int = 0, want_counts: bool = False, threads: int = 1):
+        """threads > 1: query slices searched in parallel threads."""
         Y = _f32(Y)
         Q = Y.shape[0]
         ids = np.empty(Q * k, np.int64)
         dists = np.empty(Q * k, np.float64)
         counts = np.empty(Q, np.int64) if want_counts else None
         keep, src = _src_ptr(query_src)
-        lib().oracle_search(
-            self.X, self.N, self.d, self.L, self.offsets, self.perm, Y, Q, P, k,
-            src, grid_w, radius, ids, dists,
-            counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+        step = np.dtype(np.int64).itemsize
+
+        def part(lo, hi):
+            lib().oracle_search_mode(
+                self.X, self.N, self.d, self.L, self.key_mode, self.offsets, self.perm, Y[lo:hi], hi - lo, P, k,
+                None if src is None else src.value + lo * step, grid_w, radius, ids[lo * k:hi * k],
+                dists[lo * k:hi * k],
+                counts[lo:hi].ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+        _sliced(Q, threads, part)
         del keep
         ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
         return (ids, dists, counts) if want_counts else (ids, dists)
@@ -333,7 +408,7 @@ def rotate(Rm, X) -> np.ndarray:
     return out
 
 
-def project(Pm, X, off=None) -> np.ndarray:
+def project(Pm, X, off=None, threads: int = 1) -> np.ndarray:
     """Rows of X projected on the m rows of Pm minus off (fp32, in-order FMAs,
     one final subtraction)."""
     Pm, X = _f32(Pm), _f32(X)
@@ -341,7 +416,8 @@ def project(Pm, X, off=None) -> np.ndarray:
     n, d = X.shape
     out = np.empty((n, m), np.float32)
     o = None if off is None else _f32(off)
-    lib().oracle_project(Pm, None if o is None else o.ctypes.data_as(ctypes.c_void_p), X, n, d, m, out)
+    _sliced(n, threads, lambda lo, hi: lib().oracle_project(
+        Pm, None if o is None else o.ctypes.data_as(ctypes.c_void_p), X[lo:hi], hi - lo, d, m, out[lo:hi]))
     return out
 
 
@@ -351,7 +427,7 @@ class MultiIndex:
     and a stable counting sort; the search is the exact top-k over the union
     of the points of the bases' probed cones (Sec. 3-D)."""
 
-    def __init__(self, X, L: int, rots, offsets=None):
+    def __init__(self, X, L: int, rots, offsets=None, threads: int = 1):
         self.X = _f32(X)
         self.N, self.d = self.X.shape
         self.L = L
@@ -363,22 +439,26 @@ class MultiIndex:
         offs, perms = [], []
         for b in range(self.R):
             ob = None if self.off is None else self.off[b]
-            o, p = buckets(keys(project(self.rots[b], self.X, ob), L), self.NC)
+            o, p = buckets(keys(project(self.rots[b], self.X, ob, threads), L, threads), self.NC)
             offs.append(o)
             perms.append(p)
         self.offsets = np.ascontiguousarray(np.stack(offs), np.uint32)
         self.perms = np.ascontiguousarray(np.stack(perms), np.uint32)
 
-    def search(self, Y, P: int, k: int, want_counts: bool = False):
+    def search(self, Y, P: int, k: int, want_counts: bool = False, threads: int = 1):
         Y = _f32(Y)
         Q = Y.shape[0]
         ids = np.empty(Q * k, np.int64)
         dists = np.empty(Q * k, np.float64)
         counts = np.empty(Q, np.int64) if want_counts else None
-        lib().oracle_search_multi_proj(
-            self.X, self.N, self.d, self.L, self.R, self.m, self.rots,
-            None if self.off is None else self.off.ctypes.data_as(ctypes.c_void_p), self.offsets, self.perms,
-            Y, Q, P, k, ids, dists, counts.ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+
+        def part(lo, hi):
+            lib().oracle_search_multi_proj(
+                self.X, self.N, self.d, self.L, self.R, self.m, self.rots,
+                None if self.off is None else self.off.ctypes.data_as(ctypes.c_void_p), self.offsets, self.perms,
+                Y[lo:hi], hi - lo, P, k, ids[lo * k:hi * k], dists[lo * k:hi * k],
+                counts[lo:hi].ctypes.data_as(ctypes.c_void_p) if want_counts else None)
+        _sliced(Q, threads, part)
         ids, dists = ids.reshape(Q, k), dists.reshape(Q, k)
         return (ids, dists, counts) if want_counts else (ids, dists)
 

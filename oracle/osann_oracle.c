@@ -51,6 +51,19 @@
  *     ties to the lower centroid index.  A caller that holds another
  *     program's assignment (a GPU that decided a near-tie in fp32 the other
  *     way) may pass it in, and the keys and the search then follow it.
+ *   - the ORDERED key (an option beside the paper's set key): the profile is
+ *     the tuple (i_1, ..., i_G) of the G largest-magnitude components in
+ *     decreasing magnitude (ties to the lower index), numbered in
+ *     lexicographic order of the tuples, rank = sum_j c_j (K-1-j)!/(K-G)!
+ *     with c_j = i_(j+1) minus the number of earlier members below it; the
+ *     sign code puts the largest member (position 1) in the most
+ *     significant bit; N_C = K!/(K-G)! 2^G.  Its probe order uses the tree
+ *     of ordered prefixes: distance delta = G - (length of the common
+ *     ordered prefix with the query's tuple); a profile at distance delta
+ *     keeps (i_1..i_(G-delta)), its next member is any component but
+ *     i_(G-delta+1) outside the prefix, the later ones any unused component;
+ *     inside a class, lexicographic in the members' magnitude ranks; then
+ *     the sign-flipped cones as for the set key.
  * Parity pinned by: Fig. 2 worked example, N_C closed forms of Sec. 2,
  * class sizes of Sec. 3-B, invariants and brute-force identities (tests).
  * The intra-class probe order and the sign-flip extension are this
@@ -201,6 +214,71 @@ void oracle_keys_wide(const float *X, int64_t N, int d, int L, uint64_t *keys)
         keys[2 * n] = (uint64_t)k;
         keys[2 * n + 1] = (uint64_t)(k >> 64);
     }
+}
+
+/* ---------------------------------------------------------------- ORDERED key */
+
+/* (K - 1 - j)! / (K - G)!: the number of ways to fill the tuple positions
+ * after position j (0-based) with distinct unused components. */
+static uint64_t falling_after(int d, int L, int j)
+{
+    uint64_t f = 1;
+    for (int m = j + 1; m < L; ++m) {
+        uint64_t v = (uint64_t)(d - m);
+        if (f > UINT64_MAX / v) return UINT64_MAX;
+        f *= v;
+    }
+    return f;
+}
+
+/* N_C of the ORDERED key: K!/(K-G)! * 2^G; -1 if it does not fit in 63 bits. */
+int64_t oracle_num_cones_ordered(int d, int L)
+{
+    if (d < 1 || L < 1 || L > d || L > 62) return -1;
+    uint64_t f = falling_after(d, L, -1);
+    if (f == UINT64_MAX || f > ((uint64_t)INT64_MAX >> L)) return -1;
+    return (int64_t)(f << L);
+}
+
+/* Cone id of the ordered profile T (G distinct components in tuple order)
+ * with the signs of y on its members, the members whose position in the
+ * ascending-|y| ordering of T is set in flip_mask sign-inverted. */
+static uint32_t ordered_cone(const int32_t *T, int d, int L, const float *y, const int32_t *rank_of,
+                             uint32_t flip_mask)
+{
+    uint64_t rank = 0;
+    for (int j = 0; j < L; ++j) {
+        int below = 0;
+        for (int t = 0; t < j; ++t)
+            if (T[t] < T[j]) ++below;
+        rank += (uint64_t)(T[j] - below) * falling_after(d, L, j);
+    }
+    uint32_t code = 0;
+    for (int j = 0; j < L; ++j) {
+        uint32_t bit = (y[T[j]] >= 0.0f) ? 1u : 0u;
+        if (flip_mask) {
+            int pos = 0;
+            for (int t = 0; t < L; ++t)
+                if (rank_of[T[t]] > rank_of[T[j]]) ++pos;
+            if ((flip_mask >> pos) & 1u) bit ^= 1u;
+        }
+        code |= bit << (L - 1 - j);
+    }
+    return (uint32_t)((rank << L) | code);
+}
+
+/* ORDERED cone id of one vector: its G largest-magnitude components in
+ * decreasing magnitude, with their signs. */
+uint32_t oracle_key_ordered(const float *x, int d, int L)
+{
+    int32_t order[ORACLE_MAX_D];
+    oracle_magnitude_order(x, d, order);
+    return ordered_cone(order, d, L, x, NULL, 0);
+}
+
+void oracle_keys_ordered(const float *X, int64_t N, int d, int L, uint32_t *keys)
+{
+    for (int64_t n = 0; n < N; ++n) keys[n] = oracle_key_ordered(X + n * d, d, L);
 }
 
 /* Bucket index: offsets[N_C + 1] (exclusive prefix sum of the cone counts)
@@ -397,6 +475,100 @@ int64_t oracle_probes_wide(const float *y, int d, int L, int64_t P, uint64_t *ou
     return probes_into(y, d, L, P, NULL, out);
 }
 
+/* The ordered profiles in their probe order (see the header): class delta
+ * = 0..G; in class delta the prefix (i_1..i_(G-delta)) and delta more
+ * members at magnitude ranks (0-based positions into order[]) p_1 ..
+ * p_delta, p_1 in keep+1 .. K-1, the later ones in keep .. K-1, all
+ * distinct, the rank tuple in lexicographic order (nested ascending loops,
+ * written as an odometer).  Calls emit(T) until it returns nonzero. */
+static void enumerate_ordered_profiles(const int32_t *order, int d, int L, profile_cb emit, void *ctx)
+{
+    int32_t T[ORACLE_MAX_L], p[ORACLE_MAX_L];
+    for (int delta = 0; delta <= L; ++delta) {
+        const int keep = L - delta;
+        for (int j = 0; j < keep; ++j) T[j] = order[j];
+        if (delta == 0) {
+            if (emit(T, ctx)) return;
+            continue;
+        }
+        if (keep + 1 > d - 1) continue;
+        /* odometer over (p_1, ..., p_delta): position m takes the smallest
+         * admissible value above its current one, unused by positions < m */
+        int m = 0;
+        p[0] = keep;  /* incremented to keep + 1 below */
+        for (;;) {
+            /* advance position m */
+            int v = p[m] + 1;
+            for (;; ++v) {
+                int used = 0;
+                for (int t = 0; t < m; ++t)
+                    if (p[t] == v) used = 1;
+                if (!used) break;
+            }
+            if (v > d - 1) {
+                if (m == 0) break;
+                --m;
+                continue;
+            }
+            p[m] = v;
+            if (m + 1 < delta) {
+                ++m;
+                p[m] = keep - 1;  /* the smallest value of a later position is keep */
+                continue;
+            }
+            for (int j = 0; j < delta; ++j) T[keep + j] = order[p[j]];
+            if (emit(T, ctx)) return;
+        }
+    }
+}
+
+struct oprobe_ctx {
+    const float *y;
+    const int32_t *rank_of;
+    int d, L, h;
+    int64_t P, count;
+    uint32_t *out;
+};
+
+static int emit_ordered_unflipped(const int32_t *T, void *vctx)
+{
+    struct oprobe_ctx *c = (struct oprobe_ctx *)vctx;
+    if (c->count >= c->P) return 1;
+    c->out[c->count++] = ordered_cone(T, c->d, c->L, c->y, c->rank_of, 0);
+    return c->count >= c->P;
+}
+
+static int emit_ordered_flipped(const int32_t *T, void *vctx)
+{
+    struct oprobe_ctx *c = (struct oprobe_ctx *)vctx;
+    int32_t F[ORACLE_MAX_L];
+    for (int j = 0; j < c->h; ++j) F[j] = j;
+    do {
+        if (c->count >= c->P) return 1;
+        uint32_t mask = 0;
+        for (int j = 0; j < c->h; ++j) mask |= 1u << F[j];
+        c->out[c->count++] = ordered_cone(T, c->d, c->L, c->y, c->rank_of, mask);
+    } while (next_combination(F, c->h, 0, c->L - 1));
+    return c->count >= c->P;
+}
+
+/* The ordered cone list of the ORDERED key, truncated at P entries; returns
+ * min(P, N_C). */
+int64_t oracle_probes_ordered(const float *y, int d, int L, int64_t P, uint32_t *out)
+{
+    int32_t order[ORACLE_MAX_D], rank_of[ORACLE_MAX_D];
+    oracle_magnitude_order(y, d, order);
+    for (int r = 0; r < d; ++r) rank_of[order[r]] = r;
+    struct oprobe_ctx c;
+    c.y = y; c.rank_of = rank_of; c.d = d; c.L = L; c.h = 0; c.P = P; c.count = 0; c.out = out;
+    enumerate_ordered_profiles(order, d, L, emit_ordered_unflipped, &c);
+    for (int h = 1; h <= L && c.count < P; ++h) {
+        c.h = h;
+        enumerate_ordered_profiles(order, d, L, emit_ordered_flipped, &c);
+    }
+    return c.count;
+}
+
 /* Candidate exclusion used by the patch workload: data id n sits at grid
  * position (n / grid_w, n % grid_w); it is skipped for a query taken from
  * grid id src when the Chebyshev distance is <= radius. */
@@ -449,14 +621,31 @@ static void topk_init(double *bd, int64_t *bi, int k)
  * and dists[Q*k] (+inf pad), squared distances.  probe_buf must hold P
  * entries.  cand_count (may be NULL) receives the number of candidates
  * scanned per query. */
+void oracle_search_mode(const float *X, int64_t N, int d, int L, int key_mode,
+                        const uint32_t *offsets, const uint32_t *perm,
+                        const float *Y, int64_t Q, int64_t P, int k,
+                        const int64_t *query_src, int64_t grid_w, int64_t radius,
+                        int64_t *ids, double *dists, int64_t *cand_count);
+
 void oracle_search(const float *X, int64_t N, int d, int L,
                    const uint32_t *offsets, const uint32_t *perm,
                    const float *Y, int64_t Q, int64_t P, int k,
                    const int64_t *query_src, int64_t grid_w, int64_t radius,
                    int64_t *ids, double *dists, int64_t *cand_count)
 {
+    oracle_search_mode(X, N, d, L, 0, offsets, perm, Y, Q, P, k, query_src, grid_w, radius, ids, dists,
+                       cand_count);
+}
+
+/* As oracle_search, for the set key (key_mode 0) or the ORDERED key (1). */
+void oracle_search_mode(const float *X, int64_t N, int d, int L, int key_mode,
+                        const uint32_t *offsets, const uint32_t *perm,
+                        const float *Y, int64_t Q, int64_t P, int k,
+                        const int64_t *query_src, int64_t grid_w, int64_t radius,
+                        int64_t *ids, double *dists, int64_t *cand_count)
+{
     (void)N;
-    int64_t NC = oracle_num_cones(d, L);
+    int64_t NC = key_mode ? oracle_num_cones_ordered(d, L) : oracle_num_cones(d, L);
     if (P > NC) P = NC;
     uint32_t *probes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(P > 0 ? P : 1));
     for (int64_t q = 0; q < Q; ++q) {
@@ -464,7 +653,7 @@ void oracle_search(const float *X, int64_t N, int d, int L,
         double *bd = dists + q * k;
         int64_t *bi = ids + q * k;
         topk_init(bd, bi, k);
-        int64_t np = oracle_probes(y, d, L, P, probes);
+        int64_t np = key_mode ? oracle_probes_ordered(y, d, L, P, probes) : oracle_probes(y, d, L, P, probes);
         int64_t cands = 0;
         int64_t src = query_src ? query_src[q] : -1;
         for (int64_t l = 0; l < np; ++l) {

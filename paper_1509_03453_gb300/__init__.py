@@ -122,7 +122,7 @@ class Index:
     """A one-basis cone index over ``data`` (N x d float32 CUDA tensor)."""
 
     def __init__(self, data, L: int, stream=None, sync: bool = True, rot=None, rot_offset=None,
-                 cone_table: str = "auto", centroids=None):
+                 cone_table: str = "auto", centroids=None, key_mode: str = "set"):
         """sync=False: no final synchronisation (call status() before
         trusting results).  rot: d x d (a rotated basis) or m x d (a
         projection on m components, e.g. PCA axes) float32 CUDA tensor, the
@@ -132,7 +132,9 @@ class Index:
         cones); the results are the same.  centroids: K x d float32 CUDA
         tensor (ROSANNA+, e.g. from kmeans.kmeans): points hashed by their
         residual on their nearest centroid; search(..., clusters=M) visits
-        a query's M nearest clusters."""
+        a query's M nearest clusters.  key_mode: "set" (the paper's
+        unordered profile) or "ordered" (the top-L components as a tuple in
+        magnitude order; N_C = d!/(d-L)! 2^L, direct table only)."""
         torch = _torch()
         x = _dev_f32(data, "data")
         self.N, self.d = x.shape
@@ -142,6 +144,8 @@ class Index:
         opts = _lib.BuildOpts()
         opts.async_ = 0 if sync else 1
         opts.cone_table = _lib.CONE_TABLES[cone_table]
+        opts.key_mode = _lib.KEY_MODES[key_mode]
+        self.key_mode = key_mode
         with torch.cuda.device(x.device):
             if rot is not None:
                 r = _dev_f32(rot, "rot")

@@ -29,7 +29,9 @@ CONE_TABLES = {"auto": 0, "dense": 1, "hashed": 2}
 class BuildOpts(c.Structure):
     """osann_build_opts."""
     _fields_ = [("d_basis", c.c_void_p), ("d_offset", c.c_void_p), ("m", c.c_int32), ("async_", c.c_int32),
-                ("cone_table", c.c_int32), ("d_centroids", c.c_void_p), ("n_clusters", c.c_int32)]
+                ("cone_table", c.c_int32), ("d_centroids", c.c_void_p), ("n_clusters", c.c_int32),
+                ("key_mode", c.c_int32)]
+KEY_MODES = {"set": 0, "ordered": 1}
 STAGES = ["data_keys", "buckets", "gather", "query_order", "probes", "worklist", "tile_scan", "merge",
           "plain_scan", "bruteforce", "tc_prep", "tc_scan", "tc_rerank"]
 STATUS_NONFINITE_DATA = 1
@@ -91,6 +93,7 @@ SIGNATURES = {
     "osann_stats_reset": (c.c_int, []),
     "osann_stats_get": (c.c_int, [c.c_int32, c.POINTER(c.c_double), c.POINTER(c.c_int64)]),
     "osann_launch_count": (c.c_int64, []),
+    "osann_debug_wait_budget": (c.c_int, [c.c_int64]),
     "osann_search_group": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
                                      c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
     "osann_search_workspace_size_group": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,

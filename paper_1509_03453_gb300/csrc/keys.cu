@@ -75,13 +75,47 @@ __device__ __forceinline__ uint4 cone_wide_from_members(const int (&comp)[MAX_L]
     return wide_words((rank << L) | u128(code));
 }
 
-// Store the key of one row: a direct-table id, or (WIDE) a 128-bit id.
-template <int LC, bool WIDE>
-__device__ __forceinline__ void store_key(int64_t row, const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L], int L,
-                                          const uint64_t* __restrict__ binom, const ulonglong2* __restrict__ binom_w,
-                                          uint32_t* __restrict__ keys, uint4* __restrict__ wkeys)
+// ORDERED key: the members as a tuple in decreasing magnitude (comp[0] the
+// largest), numbered lexicographically among the L-permutations of the d
+// components, rank = sum_j c_j (d-1-j)!/(d-L)! with c_j = comp[j] minus the
+// number of earlier members below it; the sign of member j at bit L-1-j.
+// N_C = d!/(d-L)! 2^L < 2^31 (checked on the host), so rank fits 64 bits.
+template <int LC>
+__device__ __forceinline__ uint32_t ordered_from_members(const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L],
+                                                         int L, int d)
 {
-    if (WIDE) wkeys[row] = cone_wide_from_members<LC>(comp, sgn, L, binom_w);
+    constexpr int LM = LC > 0 ? LC : MAX_L;
+    uint64_t rank = 0;
+    uint32_t code = 0;
+#pragma unroll
+    for (int j = 0; j < LM; ++j) {
+        if (LC > 0 || j < L) {
+            int below = 0;
+#pragma unroll
+            for (int t = 0; t < LM; ++t)
+                if (t < j && comp[t] < comp[j]) ++below;
+            uint64_t after = 1;  // (d-1-j)!/(d-L)!: ways to fill the later positions
+#pragma unroll
+            for (int m = 0; m < LM; ++m)
+                if (m > j && (LC > 0 || m < L)) after *= uint64_t(d - m);
+            rank += uint64_t(comp[j] - below) * after;
+            code |= sgn[j] << (L - 1 - j);
+        }
+    }
+    return uint32_t((rank << L) | code);
+}
+
+// Store the key of one row: a direct-table id, or (WIDE) a 128-bit id; ORD:
+// the ORDERED key (direct table only).  comp[] lists the members by
+// decreasing magnitude (ties: the lower component first).
+template <int LC, bool WIDE, bool ORD>
+__device__ __forceinline__ void store_key(int64_t row, const int (&comp)[MAX_L], const uint32_t (&sgn)[MAX_L], int L,
+                                          int d, const uint64_t* __restrict__ binom,
+                                          const ulonglong2* __restrict__ binom_w, uint32_t* __restrict__ keys,
+                                          uint4* __restrict__ wkeys)
+{
+    if (ORD) keys[row] = ordered_from_members<LC>(comp, sgn, L, d);
+    else if (WIDE) wkeys[row] = cone_wide_from_members<LC>(comp, sgn, L, binom_w);
     else keys[row] = cone_from_members<LC>(comp, sgn, L, binom);
 }
 
@@ -91,7 +125,7 @@ __device__ __forceinline__ void store_key(int64_t row, const int (&comp)[MAX_L],
 // and keeps the L largest selection keys in a sorted register list: one
 // 32-bit magnitude compare per component, the 64-bit key and an insertion
 // only when the component can enter the list.
-template <int LC, bool WIDE>
+template <int LC, bool WIDE, bool ORD>
 __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                            const uint64_t* __restrict__ binom,
                                                            const ulonglong2* __restrict__ binom_w,
@@ -174,7 +208,7 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
                 comp[r] = sel_comp(top[r]);
                 sgn[r] = sel_sign(top[r]);
             }
-        store_key<LC, WIDE>(row, comp, sgn, L, binom, binom_w, keys, wkeys);
+        store_key<LC, WIDE, ORD>(row, comp, sgn, L, d, binom, binom_w, keys, wkeys);
         nmax = fmaxf(nmax, nsq);  // non-finite rows are reported separately
     }
     if (maxn2_bits) {
@@ -189,7 +223,7 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
 // One group of LPV lanes per row.  VEC: d % 4 == 0 and 16-byte aligned rows,
 // lane l holds float4 number l, l+LPV (128-bit loads); else lane l holds the
 // scalars l, l+32, ... (LPV = 32).  At most 8 values per lane (d <= 256).
-template <int LPV, bool VEC, int LC, bool WIDE>
+template <int LPV, bool VEC, int LC, bool WIDE, bool ORD>
 __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                        const uint64_t* __restrict__ binom,
                                                        const ulonglong2* __restrict__ binom_w,
@@ -276,7 +310,8 @@ __global__ void __launch_bounds__(256) data_keys_kernel(const float* __restrict_
                     sgn[r] = sel_sign(best);
                 }
             }
-            if (rows[h] < N && glane == 0) store_key<LC, WIDE>(rows[h], comp, sgn, L, binom, binom_w, keys, wkeys);
+            if (rows[h] < N && glane == 0)
+                store_key<LC, WIDE, ORD>(rows[h], comp, sgn, L, d, binom, binom_w, keys, wkeys);
 #pragma unroll
             for (int m = LPV / 2; m > 0; m >>= 1) nsq[h] += __shfl_xor_sync(0xffffffffu, nsq[h], m);
             nmax = fmaxf(nmax, nsq[h]);  // non-finite rows are reported separately
@@ -405,18 +440,21 @@ int launch_row_norm_max(const float* X, int64_t n, int d, uint32_t* maxn2_bits, 
     return count_launch();
 }
 
-template <int LC, bool WIDE = false>
+template <int LC, bool WIDE = false, bool ORD = false>
 static void launch_keys_lc(bool vec, dim3 g, dim3 b, cudaStream_t st, const float* X, int64_t N, int d, int L,
                            const uint64_t* binom, const ulonglong2* binom_w, uint32_t* keys, uint4* wkeys,
                            uint32_t* status, uint32_t* maxn2)
 {
-    if (vec) data_keys_row_kernel<LC, WIDE><<<g, b, 0, st>>>(X, N, d, L, binom, binom_w, keys, wkeys, status, maxn2);
-    else data_keys_kernel<32, false, LC, WIDE><<<g, b, 0, st>>>(X, N, d, L, binom, binom_w, keys, wkeys, status, maxn2);
+    if (vec)
+        data_keys_row_kernel<LC, WIDE, ORD><<<g, b, 0, st>>>(X, N, d, L, binom, binom_w, keys, wkeys, status, maxn2);
+    else
+        data_keys_kernel<32, false, LC, WIDE, ORD><<<g, b, 0, st>>>(X, N, d, L, binom, binom_w, keys, wkeys, status,
+                                                                     maxn2);
 }
 
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
                      uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms,
-                     const ulonglong2* binom_w, uint4* wkeys)
+                     const ulonglong2* binom_w, uint4* wkeys, bool ordered)
 {
     if (N == 0) return 0;
     const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(X) & 15) == 0);
@@ -429,6 +467,15 @@ int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* bi
     if (wkeys) {
         // 128-bit ids: one instantiation with a runtime L
         launch_keys_lc<0, true>(vec, g, b, st, X, N, d, L, binom, binom_w, nullptr, wkeys, status, maxn2_bits);
+        return count_launch();
+    }
+    if (ordered) {
+        switch (L) {
+        case 1: launch_keys_lc<1, false, true>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+        case 2: launch_keys_lc<2, false, true>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+        case 3: launch_keys_lc<3, false, true>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+        default: launch_keys_lc<0, false, true>(vec, g, b, st, X, N, d, L, binom, nullptr, keys, nullptr, status, maxn2_bits); break;
+        }
         return count_launch();
     }
     switch (L) {

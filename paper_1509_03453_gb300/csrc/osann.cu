@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <vector>
 
 #include "osann.h"
@@ -70,10 +71,28 @@ static osann_alloc_fn g_alloc = nullptr;
 static osann_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
 
+// A block goes back to the allocator that gave it, even when the caller
+// installs another allocator in between (an index built under one and
+// freed under another): blocks of a caller's allocator are recorded with
+// its release function.
+struct CallerBlock {
+    osann_free_fn fn;
+    void* ctx;
+};
+static std::mutex g_blocks_mu;
+static std::unordered_map<void*, CallerBlock> g_caller_blocks;
+
 static void* dev_alloc(size_t bytes, cudaStream_t st)
 {
     if (bytes == 0) bytes = 256;
-    if (g_alloc) return g_alloc(bytes, st, g_alloc_ctx);
+    if (g_alloc) {
+        void* p = g_alloc(bytes, st, g_alloc_ctx);
+        if (p) {
+            std::lock_guard<std::mutex> lk(g_blocks_mu);
+            g_caller_blocks[p] = CallerBlock{g_free, g_alloc_ctx};
+        }
+        return p;
+    }
     void* p = nullptr;
     if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
         cudaGetLastError();
@@ -85,8 +104,22 @@ static void* dev_alloc(size_t bytes, cudaStream_t st)
 static void dev_free(void* p, size_t bytes, cudaStream_t st)
 {
     if (!p) return;
-    if (g_free) g_free(p, bytes, st, g_alloc_ctx);
-    else cudaFreeAsync(p, st);
+    CallerBlock b{nullptr, nullptr};
+    bool caller = false;
+    {
+        std::lock_guard<std::mutex> lk(g_blocks_mu);
+        auto it = g_caller_blocks.find(p);
+        if (it != g_caller_blocks.end()) {
+            b = it->second;
+            caller = true;
+            g_caller_blocks.erase(it);
+        }
+    }
+    if (caller) {
+        if (b.fn) b.fn(p, bytes, st, b.ctx);  // an allocator installed without a release function keeps its blocks
+    } else {
+        cudaFreeAsync(p, st);
+    }
 }
 
 // ---------------------------------------------------------------- per device
@@ -251,6 +284,7 @@ struct osann_index {
     float* rb_xr = nullptr;
     uint32_t* rb_asg = nullptr;
     int d = 0, d_pad = 0, L = 0, device = 0, num_sms = 0;
+    int key_mode = OSANN_KEY_SET;  // OSANN_KEY_ORDERED: the members as a tuple in magnitude order
     cudaStream_t stream = nullptr;
     uint32_t* keys = nullptr;
     uint32_t* offsets = nullptr;
@@ -557,6 +591,16 @@ const char* osann_last_error(void) { return g_err; }
 
 int64_t osann_launch_count(void) { return g_launches.load(); }
 
+int osann_debug_wait_budget(int64_t cycles)
+{
+    if (cycles < 0) {
+        set_error("osann_debug_wait_budget: negative budget %lld", (long long)cycles);
+        return OSANN_ERR_INVALID;
+    }
+    set_plain_wait_budget(cycles);
+    return OSANN_OK;
+}
+
 int osann_stats_enable(int on)
 {
     std::lock_guard<std::mutex> lk(g_stats_mu);
@@ -688,7 +732,7 @@ static int enqueue_build(osann_index* ix, const float* d_data, char* temp, float
         }
         if (!rc)
             rc = launch_data_keys(key_src, N, m, L, ix->binom, ix->keys, ix->status, ix->status + 2, st, ix->num_sms,
-                                  ix->binom_w, wkeys);
+                                  ix->binom_w, wkeys, ix->key_mode == OSANN_KEY_ORDERED);
         if (!rc && K > 0)
             rc = launch_composite_keys(asg, N, uint64_t(ix->ncc), uint64_t(ix->ncc >> 64), ix->keys, wkeys, st,
                                        ix->num_sms);
@@ -726,7 +770,7 @@ static int enqueue_build(osann_index* ix, const float* d_data, char* temp, float
 
 static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, const float* d_off,
                       int32_t m, void* stream, bool async, int32_t cone_table, osann_index** out,
-                      const float* d_cent = nullptr, int32_t K = 0)
+                      const float* d_cent = nullptr, int32_t K = 0, int32_t key_mode = OSANN_KEY_SET)
 {
     if (!d_rot) m = d;
     if (d_rot && (m < 1 || m > d || d > 128)) {
@@ -747,6 +791,21 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     if (cone_count(m, L, &nc_true) != OSANN_OK) {
         set_error("osann_build: unsupported (d=%d, L=%d): need 1<=d<=%d, 1<=L<=min(d,%d)", m, L, MAX_D, MAX_L);
         return OSANN_ERR_INVALID;
+    }
+    if (key_mode != OSANN_KEY_SET && key_mode != OSANN_KEY_ORDERED) {
+        set_error("osann_build: unknown key mode %d", key_mode);
+        return OSANN_ERR_INVALID;
+    }
+    if (key_mode == OSANN_KEY_ORDERED) {
+        // d!/(d-L)! 2^L in a direct table only, and no clusters
+        unsigned __int128 f = 1;
+        for (int i = 0; i < L && f < ((unsigned __int128)1 << 31); ++i) f *= (unsigned __int128)(m - i);
+        nc_true = f << L;
+        if (nc_true >= ((unsigned __int128)1 << 31) || cone_table == OSANN_CONES_HASHED || K > 0) {
+            set_error("osann_build: the ORDERED key needs N_C = d!/(d-L)! 2^L < 2^31, a direct table and no "
+                      "clusters (d=%d L=%d)", m, L);
+            return OSANN_ERR_UNSUPPORTED;
+        }
     }
     const unsigned __int128 ncc = nc_true;  // cones of one cluster
     if (K < 0 || (K > 0 && (!d_cent || d_rot || d > 128 || K > (1 << 24)))) {
@@ -794,6 +853,7 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     ix->dk = m;
     ix->d_pad = pad_dim(d);
     ix->L = L;
+    ix->key_mode = key_mode;
     ix->stream = st;
     ix->num_sms = ds->num_sms;
     ix->binom = ds->binom;
@@ -911,7 +971,7 @@ int osann_build_ex(const float* d_data, int64_t N, int32_t d, int32_t L, const o
         return OSANN_ERR_INVALID;
     }
     return build_impl(d_data, N, d, L, opts->d_basis, opts->d_offset, opts->d_basis ? opts->m : d, stream,
-                      opts->async != 0, opts->cone_table, out, opts->d_centroids, opts->n_clusters);
+                      opts->async != 0, opts->cone_table, out, opts->d_centroids, opts->n_clusters, opts->key_mode);
 }
 
 int osann_build_rot(const float* d_data, int64_t N, int32_t d, int32_t L, const float* d_rot, int32_t async,
@@ -1118,6 +1178,7 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
     if (rc) return rc;
     StageScope s(OSANN_STAGE_PROBES, st);
     ProbeMap pm{};
+    pm.ordered = ix->key_mode == OSANN_KEY_ORDERED;
     if (ix->hashed) {
         pm.binom_w = ix->binom_w;
         pm.ukeys = ix->ukeys;

@@ -227,15 +227,41 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
     return ok != 0;
 }
 
+// Non-blocking probe of the phase (mbarrier.test_wait returns at once).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 // About one second at GB300 clocks: no legitimate wait here comes close.
 constexpr long long WAIT_BUDGET_CYCLES = 2000000000LL;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// Wait for the phase with the given parity to complete, for at most `budget`
+// SM clock cycles; false when the budget ran out.  try_wait may suspend the
+// thread inside the hardware until the phase completes, so a budget shorter
+// than the default (a test making the wait run out) polls with test_wait,
+// which never blocks.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long budget = WAIT_BUDGET_CYCLES)
 {
+    if (budget < WAIT_BUDGET_CYCLES) {
+        const long long t0 = clock64();
+        while (!mbar_test_wait(bar, parity))
+            if (clock64() - t0 > budget) return false;
+        return true;
+    }
     if (mbar_try_wait(bar, parity)) return true;
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > WAIT_BUDGET_CYCLES) return false;
+        if (clock64() - t0 > budget) return false;
     }
     return true;
 }

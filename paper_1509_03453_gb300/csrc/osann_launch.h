@@ -22,9 +22,10 @@ int64_t launch_total();
 // keys.cu
 // maxn2 may be null; wkeys non-null: 128-bit ids (four words per row) from
 // the 128-bit binomial table binom_w instead of keys
+// ordered: the ORDERED key (members as a tuple in magnitude order), direct table only
 int launch_data_keys(const float* X, int64_t N, int d, int L, const uint64_t* binom, uint32_t* keys,
                      uint32_t* status, uint32_t* maxn2_bits, cudaStream_t st, int num_sms,
-                     const ulonglong2* binom_w = nullptr, uint4* wkeys = nullptr);
+                     const ulonglong2* binom_w = nullptr, uint4* wkeys = nullptr, bool ordered = false);
 // out (n x m) = rows of X on the m basis rows of Pm (m x d) minus off (null:
 // none), fp32 in-order FMAs then one subtraction; d <= 128, m <= d (else -2)
 int launch_rotate_rows(const float* Pm, const float* off, const float* X, int64_t n, int d, int m, float* out,
@@ -74,6 +75,7 @@ int launch_cone_table(const uint4* wkeys, const uint32_t* perm, int64_t N, int64
 // (row q * M + j on cluster vcl[q * M + j]), each with P_eff positions; the
 // id is vcl * ncc + cone, and query q's list is its M lists in turn.
 struct ProbeMap {
+    bool ordered = false;  // the ORDERED key's profiles and ids (direct table only)
     const ulonglong2* binom_w = nullptr;
     const uint4* ukeys = nullptr;
     const uint32_t* htab = nullptr;
@@ -98,6 +100,8 @@ int launch_composite_keys(const uint32_t* asg, int64_t N, uint64_t ncc_lo, uint6
                           uint4* wkeys, cudaStream_t st, int num_sms);
 
 // scan_plain.cu
+// clock budget of the plain scan's stage waits (0: the default, about a second)
+void set_plain_wait_budget(long long cycles);
 int launch_plain_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad,
                       const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, uint32_t NC, int k,
                       const int64_t* query_src, int64_t grid_w, int radius, const uint32_t* qlist, int num_sms,

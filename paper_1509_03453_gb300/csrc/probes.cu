@@ -46,6 +46,60 @@ __device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, u
     return r;
 }
 
+// n (n-1) ... (n-k+1), the ordered selections of k of n (0 for k > n).
+__device__ __forceinline__ uint64_t falling(int n, int k)
+{
+    if (k > n) return 0;
+    uint64_t f = 1;
+    for (int i = 0; i < k; ++i) f *= uint64_t(n - i);
+    return f;
+}
+
+// ORDERED key (the members as a tuple in decreasing magnitude): the
+// profile tree is the tree of ordered prefixes, so a tuple is at distance
+// delta = L - (length of its common prefix with the query's tuple
+// (i_1..i_L)).  Class delta keeps (i_1..i_(L-delta)); its next member has
+// rank (0-based position in the query's order) in keep+1 .. d-1 (any but
+// i_(keep+1)), each later one any unused rank in keep .. d-1; there are
+// (n0-1) (n0-1)!/(n0-delta)! such tuples, n0 = d - keep.  Inside a class the
+// rank tuple is lexicographic: position idx is unranked as a mixed-radix
+// number whose m-th digit picks the digit-th unused rank.  Writes the
+// members' ranks rk[0..L-1]; idx < nprof = d!/(d-L)! on entry.
+template <int LM>
+__device__ __forceinline__ void unrank_ordered(uint64_t idx, int d, int L, int (&rk)[LM])
+{
+    int delta = 0;
+    for (; delta < L; ++delta) {
+        const int n0 = d - L + delta;
+        const uint64_t cnt = delta == 0 ? 1 : uint64_t(n0 - 1) * falling(n0 - 1, delta - 1);
+        if (idx < cnt) break;
+        idx -= cnt;
+    }
+    const int keep = L - delta;
+    const int n0 = d - keep;
+#pragma unroll
+    for (int j = 0; j < LM; ++j)
+        if (j < keep) rk[j] = j;
+    for (int m = 0; m < delta; ++m) {
+        // completions of the later positions, each choosing among the unused ranks
+        const uint64_t f = falling(n0 - 1 - m, delta - 1 - m);
+        const uint64_t digit = idx / f;
+        idx -= digit * f;
+        // the digit-th rank in keep (keep + 1 for the first member) .. d-1 not used yet
+        int v = (m == 0 ? keep + 1 : keep) + int(digit);
+        for (;;) {
+            int below = 0;  // earlier members at ranks <= v, past the start of the range
+#pragma unroll
+            for (int t = 0; t < LM; ++t)
+                if (t >= keep && t < keep + m && rk[t] <= v) ++below;
+            const int target = (m == 0 ? keep + 1 : keep) + int(digit) + below;
+            if (target == v) break;
+            v = target;
+        }
+        rk[keep + m] = v;
+    }
+}
+
 // LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
 // WIDE: 128-bit cone ids looked up in the second-level table (pm); the
 // unranking above still uses the saturated 64-bit binomials, which is exact
@@ -67,7 +121,7 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
     const uint8_t* ord = qorder + q * int64_t(d);
     const uint32_t* sg = qsign + q * (MAX_D / 32);
 
-    const uint64_t nprof = C(binom, d, L);
+    const uint64_t nprof = pm.ordered ? falling(d, L) : C(binom, d, L);
     uint32_t flip = 0;  // bit m: flip the member at position m of the ascending-|y| member list
     if (idx >= nprof) {
         idx -= nprof;
@@ -88,29 +142,36 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
             idx -= blk;
         }
     }
-    // profile class delta, then the idx-th delta-subset of the ranks after keep
-    int delta = 0;
-    for (; delta < L; ++delta) {
-        const uint64_t cnt = delta == 0 ? 1 : C(binom, d - L + delta - 1, delta);
-        if (idx < cnt) break;
-        idx -= cnt;
-    }
-    const int keep = L - delta;
-    const int n = d - keep - 1;  // candidate ranks keep+1 .. d-1
-    int rk[LM];                  // member ranks (0-based positions into the query's order)
-    int cm[LM];                  // member components
-    int r = 0;
+    int rk[LM];  // member ranks (0-based positions into the query's order)
+    int cm[LM];  // member components
+    if (pm.ordered) {
+        unrank_ordered<LM>(idx, d, L, rk);
 #pragma unroll
-    for (int j = 0; j < LM; ++j) {
-        if (LC > 0 || j < L) {
-            if (j < keep) {
-                rk[j] = j;
-            } else {
-                r = next_member(binom, idx, r, n, L - j);
-                rk[j] = keep + 1 + r;
-                ++r;
+        for (int j = 0; j < LM; ++j)
+            if (LC > 0 || j < L) cm[j] = ord[rk[j]];
+    } else {
+        // profile class delta, then the idx-th delta-subset of the ranks after keep
+        int delta = 0;
+        for (; delta < L; ++delta) {
+            const uint64_t cnt = delta == 0 ? 1 : C(binom, d - L + delta - 1, delta);
+            if (idx < cnt) break;
+            idx -= cnt;
+        }
+        const int keep = L - delta;
+        const int n = d - keep - 1;  // candidate ranks keep+1 .. d-1
+        int r = 0;
+#pragma unroll
+        for (int j = 0; j < LM; ++j) {
+            if (LC > 0 || j < L) {
+                if (j < keep) {
+                    rk[j] = j;
+                } else {
+                    r = next_member(binom, idx, r, n, L - j);
+                    rk[j] = keep + 1 + r;
+                    ++r;
+                }
+                cm[j] = ord[rk[j]];
             }
-            cm[j] = ord[rk[j]];
         }
     }
     // cone id of the profile with the query's signs (and the chosen flips)
@@ -130,9 +191,22 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
             }
             uint32_t bit = (sg[cm[j] >> 5] >> (cm[j] & 31)) & 1u;
             bit ^= (flip >> asc) & 1u;
-            if (WIDE) rank_w += binom_wide(pm.binom_w, cm[j], pos + 1);
-            else rank += C(binom, cm[j], pos + 1);
-            code |= bit << (L - 1 - pos);
+            if (pm.ordered) {
+                // tuple position j: c_j = cm[j] minus the earlier members below it
+                int below = 0;
+                uint64_t after = 1;
+#pragma unroll
+                for (int u = 0; u < LM; ++u) {
+                    if (u < j && cm[u] < cm[j]) ++below;
+                    if (u > j && (LC > 0 || u < L)) after *= uint64_t(d - u);
+                }
+                rank += uint64_t(cm[j] - below) * after;
+                code |= bit << (L - 1 - j);
+            } else {
+                if (WIDE) rank_w += binom_wide(pm.binom_w, cm[j], pos + 1);
+                else rank += C(binom, cm[j], pos + 1);
+                code |= bit << (L - 1 - pos);
+            }
         }
     }
     const uint32_t cl = pm.vcl ? pm.vcl[q] : 0u;
