@@ -101,6 +101,27 @@ def rotations(R: int, d: int, seed: int) -> np.ndarray:
     return out
 
 
+def hadamard_rotations(R: int, d: int, seed: int) -> np.ndarray:
+    """R structured orthonormal d x d bases (float32, row i = basis vector
+    i) for the multi-basis search: basis 0 is the identity, basis r > 0 is
+    H D_r / sqrt(d) with H the Sylvester-Hadamard matrix (entry (i, j) =
+    (-1)^popcount(i & j)) and D_r a diagonal of random signs -- the cheap
+    structured rotation (Walsh-Hadamard) the paper suggests instead of a
+    dense random one.  d must be a power of two."""
+    if d < 1 or d & (d - 1):
+        raise ValueError("a Walsh-Hadamard basis needs d a power of two")
+    rng = np.random.default_rng(seed)
+    i = np.arange(d)
+    pc = np.vectorize(lambda v: bin(int(v)).count("1"))(i[:, None] & i[None, :])
+    H = np.where(pc % 2 == 0, 1.0, -1.0)
+    out = np.empty((R, d, d), np.float32)
+    out[0] = np.eye(d, dtype=np.float32)
+    for r in range(1, R):
+        s = rng.choice(np.array([-1.0, 1.0]), size=d)
+        out[r] = (H * s[None, :] / np.sqrt(d)).astype(np.float32)
+    return out
+
+
 def workload(name: str, n: int | None = None, q: int | None = None) -> dict:
     """Named workload.  ``n``/``q`` shrink it (same recipe, prefix of the
     draws for Gaussian data) for tests that need a smaller case."""

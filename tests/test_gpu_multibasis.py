@@ -2,7 +2,8 @@
 the oracle: per-basis keys and buckets bit-exact (the rotated coordinates
 are computed in the same fp32 order on both sides), results within the
 distance contract of the exact top-k over the union of the bases' probed
-cones, and R = 1 on the identity basis equal to the single-basis index."""
+cones, and R = 1 on the identity basis equal to the single-basis index;
+with random (QR) and structured Walsh-Hadamard bases."""
 import numpy as np
 import pytest
 
@@ -21,13 +22,16 @@ def osann():
     yield m
 
 
-@pytest.mark.parametrize("d,L,R,P,k", [(16, 2, 3, 8, 1), (32, 2, 4, 16, 4), (64, 3, 2, 32, 10), (13, 2, 3, 6, 2)])
-def test_multibasis_matches_oracle(osann, d, L, R, P, k):
+@pytest.mark.parametrize("d,L,R,P,k,kind", [(16, 2, 3, 8, 1, "qr"), (32, 2, 4, 16, 4, "qr"), (64, 3, 2, 32, 10, "qr"),
+                                             (13, 2, 3, 6, 2, "qr"), (32, 2, 3, 16, 1, "wht"),
+                                             (128, 3, 2, 24, 4, "wht")])
+def test_multibasis_matches_oracle(osann, d, L, R, P, k, kind):
+    """Random (QR) and structured Walsh-Hadamard ("wht") bases."""
     from paper_1509_03453_gb300 import datagen
     rng = np.random.default_rng(100 + d)
     X = rng.standard_normal((20_000, d)).astype(np.float32)
     Y = rng.standard_normal((400, d)).astype(np.float32)
-    rots = datagen.rotations(R, d, 7 + d)
+    rots = datagen.rotations(R, d, 7 + d) if kind == "qr" else datagen.hadamard_rotations(R, d, 7 + d)
     mi = osann.MultiIndex(to_dev(X), L, rots)
     om = oracle.MultiIndex(X, L, rots)
     for r, ix in enumerate(mi.bases):

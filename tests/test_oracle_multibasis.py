@@ -130,3 +130,31 @@ def test_projected_multibasis_is_exact_topk_over_union():
         dd = ((X[u].astype(np.float64) - Y[q].astype(np.float64)) ** 2).sum(1)
         order = np.lexsort((u, dd))[:k]
         assert np.array_equal(ids[q, :len(order)], u[order])
+
+
+@pytest.mark.parametrize("d", [16, 32, 128])
+def test_walsh_hadamard_bases(d):
+    """The structured bases: basis 0 the identity; the others orthonormal,
+    every entry +-1/sqrt(d), entry (i, j) = s_j (-1)^popcount(i & j) / sqrt(d)
+    (checked against the Sylvester recursion H_2n = [[H, H], [H, -H]]), with
+    signs that differ between bases; the oracle's rotated coordinates match
+    an fp64 product within the fp32 in-order FMA bound."""
+    B = datagen.hadamard_rotations(3, d, 17)
+    assert np.array_equal(B[0], np.eye(d, dtype=np.float32))
+    H = np.array([[1.0]])
+    while H.shape[0] < d:
+        H = np.block([[H, H], [H, -H]])
+    inv = np.float32(1.0 / np.sqrt(d))
+    for r in (1, 2):
+        Rm = B[r].astype(np.float64)
+        assert np.allclose(Rm @ Rm.T, np.eye(d), atol=1e-6)
+        assert np.all(np.abs(np.abs(B[r]) - inv) == 0)
+        s = np.sign(Rm[0])  # row 0 of H is all ones: it carries the signs
+        assert np.array_equal(np.sign(Rm), H * s[None, :])
+    assert not np.array_equal(np.sign(B[1][0]), np.sign(B[2][0]))
+    X = np.random.default_rng(d).standard_normal((200, d)).astype(np.float32)
+    got = oracle.rotate(B[1], X).astype(np.float64)
+    ref = X.astype(np.float64) @ B[1].astype(np.float64).T
+    assert np.all(np.abs(got - ref) <= d * 2.0 ** -23 * (np.abs(X) @ np.abs(B[1]).T.astype(np.float64)))
+    with pytest.raises(ValueError):
+        datagen.hadamard_rotations(2, 24, 0)

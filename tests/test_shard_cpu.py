@@ -93,3 +93,44 @@ def test_two_rank_sharded_search_equals_unsharded(k):
     full_ids, full_d = oracle.Index(X, L).search(Y, P, k)
     assert np.array_equal(ids, full_ids)
     assert np.array_equal(d, full_d)
+
+
+def _worker_drop(rank, world, port, X, Y, L, P, k, out):
+    """Rank 1 leaves before the exchange (between steps, nothing of its own in
+    flight); rank 0's all-gather must end with an error, not wait forever."""
+    import datetime
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=datetime.timedelta(seconds=10))
+    from paper_1509_03453_gb300.shard import ShardedIndex, shard_rows
+    lo, hi = shard_rows(X.shape[0], rank, world)
+    sh = ShardedIndex(X[lo:hi], L, lo, index_factory=_OracleIndex, merge=_merge_lexsort)
+    dist.barrier()
+    if rank == 1:
+        os._exit(0)  # the rank is gone: no search, no collective
+    try:
+        sh.search(Y, P, k)
+        out.put("no error")
+    except Exception as exc:  # the peer's loss surfaces as an error on the collective
+        out.put("error: " + type(exc).__name__)
+    os._exit(0)
+
+
+def test_dropped_rank_fails_the_exchange_instead_of_hanging():
+    import multiprocessing as mp
+    import time
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((2001, 16)).astype(np.float32)
+    Y = rng.standard_normal((20, 16)).astype(np.float32)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_drop, args=(r, 2, port, X, Y, 2, 8, 1, q)) for r in range(2)]
+    t0 = time.time()
+    for p in procs:
+        p.start()
+    res = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert res.startswith("error"), res
+    assert time.time() - t0 < 100
