@@ -40,7 +40,9 @@ extern "C" {
 #define OSANN_ERR_TIMEOUT (-6)     /* a bounded device wait gave up */
 
 /* Search paths (same results, different schedules). */
-#define OSANN_PATH_AUTO 0    /* batched when enough queries share a cone */
+#define OSANN_PATH_AUTO 0    /* the 16-bit screen when enough queries share a cone (per
+                                occupied cone, as counted by a synchronous build), the
+                                fp32 tile scan for d > 128, else plain */
 #define OSANN_PATH_PLAIN 1   /* one CTA per query scanning its cones */
 #define OSANN_PATH_BATCHED 2 /* cone-major work list, persistent fp32 tile scan */
 #define OSANN_PATH_BF16 3    /* cone-major work list, bf16 tensor-core screening with a

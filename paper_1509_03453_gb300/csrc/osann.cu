@@ -264,6 +264,10 @@ struct osann_index {
     // compact cones for the second-level table); nc_clamp: N_C itself,
     // clamped to 2^62 (it bounds the probe budget)
     int64_t N = 0, NC = 0, max_bucket = 0, nc_clamp = 0;
+    // occupied cones as counted by a synchronous build (0: unknown, e.g. an
+    // asynchronous build); kept for the index's life, so the automatic path
+    // choice -- and with it the workspace size -- never changes
+    int64_t occupied = 0;
     unsigned __int128 nc_true = 0;
     bool hashed = false;          // second-level table (128-bit cone ids)
     int key_bits = 0;             // significant bits of the 128-bit ids
@@ -409,7 +413,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, yrot, vcl;
+    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, yrot, vcl, ptab;
     size_t total;
     int64_t max_items;
 };
@@ -513,6 +517,7 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
     if (ix->K) w.vcl = take(size_t(Qv) * 4);
     w.qsign = take(size_t(Qv) * (MAX_D / 32) * 4);
     w.probes = take(size_t(Q) * P_eff * 4);
+    w.ptab = take(probe_table_bytes(P_eff));
     if (mode != MODE_PLAIN) {
         const int G = item_group(ix, mode, group);
         const int64_t n = Q * P_eff;
@@ -550,13 +555,18 @@ static int choose_mode(const osann_index* ix, int64_t Q, int64_t P_eff, int path
     if (path == OSANN_PATH_BATCHED) return MODE_BATCHED;
     if (path == OSANN_PATH_BF16) return MODE_BF16;
     if (path == OSANN_PATH_FP16) return MODE_FP16;
-    // queries per probed cone decide whether cone-major batching pays; the
-    // candidates per query decide whether one CTA per query (plain) finishes
-    // soon enough: a small batch with a large budget goes cone-major too
-    const double per_cone = double(Q) * double(P_eff) / double(ix->NC);
+    // queries per probed cone decide whether cone-major batching pays (over
+    // the occupied cones when the build counted them: thin or skewed data
+    // leaves most cones empty); the candidates per query decide whether one
+    // CTA per query (plain) finishes soon enough: a small batch with a large
+    // budget goes cone-major too.  The 16-bit screen beats the fp32 tile scan
+    // wherever cone-major pays (measured on Gaussian and descriptor data,
+    // thin cones included); the fp32 tile scan serves d_pad > 128
+    const double cones = ix->occupied > 0 ? double(ix->occupied) : double(ix->NC);
+    const double per_cone = double(Q) * double(P_eff) / cones;
     const double per_query = double(P_eff) * double(ix->N) / double(ix->NC);
     const bool big_queries = per_query >= 16384.0;
-    if (ix->tc_ready[1] && (per_cone >= 64.0 || big_queries)) return MODE_FP16;
+    if (ix->tc_ready[1] && (per_cone >= 8.0 || big_queries)) return MODE_FP16;
     return per_cone >= 16.0 || big_queries ? MODE_BATCHED : MODE_PLAIN;
 }
 
@@ -927,9 +937,9 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
         *out = ix;
         return OSANN_OK;
     }
-    uint32_t host_status[2] = {0, 0};
+    uint32_t host_status[4] = {0, 0, 0, 0};  // flags, largest cone, largest |x|^2, occupied cones
     if (!rc) {
-        cudaError_t e = cudaMemcpyAsync(host_status, ix->status, 8, cudaMemcpyDeviceToHost, st);
+        cudaError_t e = cudaMemcpyAsync(host_status, ix->status, 16, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) rc = cuda_fail(e, "osann_build");
     }
@@ -947,6 +957,7 @@ static int build_impl(const float* d_data, int64_t N, int32_t d, int32_t L, cons
     }
     cudaMemsetAsync(ix->status, 0, 4, st);
     ix->max_bucket = host_status[1];
+    ix->occupied = host_status[3];
     ix->tc_ready[1] = maps_ok;
     *out = ix;
     return OSANN_OK;
@@ -1193,7 +1204,8 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
         pm.ncc_hi = uint64_t(ix->ncc >> 64);
     }
     return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Qv, ix->dk,
-                         ix->L, P_per, ix->binom, reinterpret_cast<uint32_t*>(w + L.probes),
+                         ix->L, P_per, ix->binom, reinterpret_cast<uint32_t*>(w + L.ptab),
+                         reinterpret_cast<uint32_t*>(w + L.probes),
                          transposed ? reinterpret_cast<uint32_t*>(w + L.probesT) : nullptr,
                          init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st, pm);
 }

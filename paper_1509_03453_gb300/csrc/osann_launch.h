@@ -84,8 +84,10 @@ struct ProbeMap {
     const uint32_t* vcl = nullptr;
     uint64_t ncc_lo = 0, ncc_hi = 0;
 };
+// tab: scratch of probe_table_bytes(P_eff) for the per-position ranks and flips
+size_t probe_table_bytes(int64_t P_eff);
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
+                  const uint64_t* binom, uint32_t* tab, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
                   cudaStream_t st, const ProbeMap& pm = ProbeMap{});  // probesT (p-major copy) may be null
 
 // clusters.cu (ROSANNA+): nearest M of K centroids (K x d_pad, zero padded;

@@ -74,6 +74,17 @@ __device__ __forceinline__ uint32_t swz_offset(int r, int c, int row_bytes)
     return logical ^ (((logical >> 7) & mask) << 4);
 }
 
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only), and the
+// wait for all of this thread's copies; both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // ---------------------------------------------------------------- MMA
 
 // D[tmem] (+)= A[smem] * B[smem]^T, issued by one thread.

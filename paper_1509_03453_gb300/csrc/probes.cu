@@ -100,28 +100,25 @@ __device__ __forceinline__ void unrank_ordered(uint64_t idx, int d, int L, int (
     }
 }
 
-// LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
-// WIDE: 128-bit cone ids looked up in the second-level table (pm); the
-// unranking above still uses the saturated 64-bit binomials, which is exact
-// for positions below 2^32 (a saturated count only exceeds the position).
-// Q counts the rows of qorder/qsign: pm.M per query with clusters.
-template <int LC, bool WIDE>
-__global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
-                                                     const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
-                                                     int64_t P_eff, const uint64_t* __restrict__ binom,
-                                                     uint32_t* __restrict__ probes, uint32_t* __restrict__ probesT,
-                                                     uint64_t* __restrict__ partial, int k, const ProbeMap pm)
+// Words per entry of the position table: the members' magnitude ranks as
+// bytes (MAX_L of them), then the flip mask.
+constexpr int PROBE_TAB_WORDS = MAX_L / 4 + 1;
+
+// Which magnitude ranks the profile at list position p takes, and which of
+// its members are sign-flipped, depend only on (d, L, p), not on the query:
+// unrank every position once per search.  Table entry p: PROBE_TAB_WORDS
+// words (ranks, flip mask).
+template <int LC, bool ORD>
+__global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, int L,
+                                                          const uint64_t* __restrict__ binom,
+                                                          uint32_t* __restrict__ tab)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
     if (LC > 0) L = LC;
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= Q * P_eff) return;
-    const int64_t q = t / P_eff;  // row of qorder/qsign
-    uint64_t idx = uint64_t(t - q * P_eff);
-    const uint8_t* ord = qorder + q * int64_t(d);
-    const uint32_t* sg = qsign + q * (MAX_D / 32);
-
-    const uint64_t nprof = pm.ordered ? falling(d, L) : C(binom, d, L);
+    const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (p >= P_eff) return;
+    uint64_t idx = uint64_t(p);
+    const uint64_t nprof = ORD ? falling(d, L) : C(binom, d, L);
     uint32_t flip = 0;  // bit m: flip the member at position m of the ascending-|y| member list
     if (idx >= nprof) {
         idx -= nprof;
@@ -142,13 +139,9 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
             idx -= blk;
         }
     }
-    int rk[LM];  // member ranks (0-based positions into the query's order)
-    int cm[LM];  // member components
-    if (pm.ordered) {
+    int rk[LM];  // member ranks (0-based positions into a query's order)
+    if (ORD) {
         unrank_ordered<LM>(idx, d, L, rk);
-#pragma unroll
-        for (int j = 0; j < LM; ++j)
-            if (LC > 0 || j < L) cm[j] = ord[rk[j]];
     } else {
         // profile class delta, then the idx-th delta-subset of the ranks after keep
         int delta = 0;
@@ -170,10 +163,54 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
                     rk[j] = keep + 1 + r;
                     ++r;
                 }
-                cm[j] = ord[rk[j]];
             }
         }
     }
+    uint32_t w[PROBE_TAB_WORDS];
+#pragma unroll
+    for (int i = 0; i < PROBE_TAB_WORDS; ++i) w[i] = 0;
+#pragma unroll
+    for (int j = 0; j < LM; ++j)
+        if (LC > 0 || j < L) w[j >> 2] |= uint32_t(rk[j]) << (8 * (j & 3));
+    w[PROBE_TAB_WORDS - 1] = flip;
+#pragma unroll
+    for (int i = 0; i < PROBE_TAB_WORDS; ++i) tab[p * PROBE_TAB_WORDS + i] = w[i];
+}
+
+// LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
+// WIDE: 128-bit cone ids looked up in the second-level table (pm).
+// Q counts the rows of qorder/qsign: pm.M per query with clusters.  One
+// thread per (row, position): the position's ranks and flips from the
+// table, mapped through the row's magnitude order.
+template <int LC, bool WIDE>
+__global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
+                                                     const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
+                                                     int64_t P_eff, const uint64_t* __restrict__ binom,
+                                                     const uint32_t* __restrict__ tab,
+                                                     uint32_t* __restrict__ probes, uint32_t* __restrict__ probesT,
+                                                     uint64_t* __restrict__ partial, int k, const ProbeMap pm)
+{
+    constexpr int LM = LC > 0 ? LC : MAX_L;
+    if (LC > 0) L = LC;
+    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= Q * P_eff) return;
+    const int64_t q = t / P_eff;  // row of qorder/qsign
+    const int64_t posn = t - q * P_eff;  // list position
+    const uint8_t* ord = qorder + q * int64_t(d);
+    const uint32_t* sg = qsign + q * (MAX_D / 32);
+    uint32_t w[PROBE_TAB_WORDS];
+#pragma unroll
+    for (int i = 0; i < PROBE_TAB_WORDS; ++i)
+        if (i < (LM + 3) / 4 || i == PROBE_TAB_WORDS - 1) w[i] = __ldg(tab + posn * PROBE_TAB_WORDS + i);
+    const uint32_t flip = w[PROBE_TAB_WORDS - 1];
+    int rk[LM];  // member ranks (0-based positions into the query's order)
+    int cm[LM];  // member components
+#pragma unroll
+    for (int j = 0; j < LM; ++j)
+        if (LC > 0 || j < L) {
+            rk[j] = int((w[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+            cm[j] = ord[rk[j]];
+        }
     // cone id of the profile with the query's signs (and the chosen flips)
     uint64_t rank = 0;
     u128 rank_w = 0;
@@ -229,15 +266,40 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
         for (int j = 0; j < k; ++j) partial[t * k + j] = EMPTY_DI;
 }
 
+size_t probe_table_bytes(int64_t P_eff) { return size_t(P_eff > 0 ? P_eff : 1) * PROBE_TAB_WORDS * 4; }
+
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k, cudaStream_t st,
-                  const ProbeMap& pm)
+                  const uint64_t* binom, uint32_t* tab, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
+                  cudaStream_t st, const ProbeMap& pm)
 {
     const int64_t n = Q * P_eff;
     if (n == 0) return 0;
+    {
+        const unsigned gt = unsigned((P_eff + 255) / 256);
+#define OSANN_RANKS(LC, O) probe_ranks_kernel<LC, O><<<gt, 256, 0, st>>>(P_eff, d, L, binom, tab)
+        if (pm.ordered) {
+            switch (L) {
+            case 1: OSANN_RANKS(1, true); break;
+            case 2: OSANN_RANKS(2, true); break;
+            case 3: OSANN_RANKS(3, true); break;
+            default: OSANN_RANKS(0, true); break;
+            }
+        } else {
+            switch (L) {
+            case 1: OSANN_RANKS(1, false); break;
+            case 2: OSANN_RANKS(2, false); break;
+            case 3: OSANN_RANKS(3, false); break;
+            case 4: OSANN_RANKS(4, false); break;
+            default: OSANN_RANKS(0, false); break;
+            }
+        }
+#undef OSANN_RANKS
+        const int rc = count_launch();
+        if (rc) return rc;
+    }
     const unsigned g = unsigned((n + 255) / 256);
 #define OSANN_PROBES(LC, W) \
-    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, probes, probesT, partial, k, pm)
+    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, tab, probes, probesT, partial, k, pm)
     if (pm.htab) {
         OSANN_PROBES(0, true);
         return count_launch();

@@ -19,8 +19,8 @@
 //     keeps a register top-k and maps a candidate's flat position back to
 //     its point id (binary search in the chunk's table, then perm) only when
 //     it enters the top-k (every row when an exclusion filter needs the id).
-// Hand-offs are mbarriers -- stage full (transaction bytes) / empty (one
-// arrival per consumer warp), cone table full / empty (two tables, so the
+// Hand-offs are mbarriers -- stage full (an arrival per producer lane, plus
+// the bulk copies' transaction bytes) / empty (one arrival per consumer warp), cone table full / empty (two tables, so the
 // next chunk's table is built while the current one is consumed) -- so no
 // block-wide barrier stands in the streaming loop; the consumers meet at a
 // named barrier only when a query ends, to merge their lists.  Every wait is
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
 
     if (tid == 0) {
         for (int s = 0; s < PLAIN_STAGES; ++s) {
-            mbar_init(&full[s], 1);
+            mbar_init(&full[s], 32);  // one arrival per producer lane
             mbar_init(&empty[s], PLAIN_CONSUMERS / 32);
         }
         for (int b = 0; b < 2; ++b) {
@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
                     }
                     const uint32_t a = i * RPC, e = a + (total - a < RPC ? total - a : RPC);
                     if (lane == 0) mbar_arrive_expect_tx(&full[s], (e - a) * row_bytes);
-                    __syncwarp();
+                    else mbar_arrive(&full[s]);
                     fence_proxy_async_smem();
                     float* dst = stage_buf + size_t(s) * PLAIN_STAGE_FLOATS;
                     for (int base = cc;; base += 32) {

@@ -111,9 +111,10 @@ struct TcItem {
 
 // Warp roles (256 threads): warp 0 lane 0 fetches items and streams the cone
 // tiles with TMA; warp 1 lane 0 issues the MMAs (warp 1 owns the TMEM
-// allocation); warps 2-3 ("loaders", 64 threads) write the query tile of each
-// item and the per-query constants into one of two shared buffers, up to two
-// items ahead; warps 4-7 (128 threads, one per query row and TMEM lane)
+// allocation); warps 2-3 ("loaders", 64 threads) gather the query tile of each
+// item (asynchronous 16-byte copies of the queries' 16-bit rows straight into
+// the swizzled tile) and write the per-query constants into one of the
+// shared query buffers, ahead of the MMAs; warps 4-7 (128 threads, one per query row and TMEM lane)
 // screen the accumulators.  Hand-offs are mbarriers: item queue (4 slots, the
 // producer one item ahead of its tiles), tile stages (full/empty), query
 // buffers (full/empty), accumulators (2 TMEM buffers of 128 columns,
@@ -336,8 +337,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             const uint32_t ab = it % NA;
             if (it >= NA && !wait(&aempty[ab], ((it / NA) - 1) & 1u)) break;
             unsigned char* dstA = sA + size_t(ab) * (mainA + extA);
-            // both rows' query indices, then both rows' constants, so that the
-            // dependent loads of the two rows overlap
+            // both rows' query indices; then their 16-bit rows as asynchronous
+            // 16-byte copies straight into the swizzled tile (every chunk in
+            // flight at once), and, while those land, both rows' constants
             uint32_t qr[2];
             float4 qs[2];
             float Ur[2];
@@ -345,6 +347,18 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             for (int h = 0; h < 2; ++h) {
                 const int r = lt + 64 * h;
                 qr[h] = uint32_t(r) < d.qn ? uint32_t(int64_t(a.qlist[d.qbeg + r]) / a.S) : 0xFFFFFFFFu;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int r = lt + 64 * h;
+                const bool active = qr[h] != 0xFFFFFFFFu;
+                const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(active ? qr[h] : 0u) * a.d_pad);
+                for (int kb = 0; kb < kblocks; ++kb)
+                    for (int c = 0; c < chunks; ++c) {
+                        unsigned char* dst = dstA + size_t(kb) * TC_M * row_bytes + swz_offset(r, c, row_bytes);
+                        if (active) cp_async16(dst, src + kb * chunks + c);
+                        else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+                    }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -359,12 +373,6 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             for (int h = 0; h < 2; ++h) {
                 const int r = lt + 64 * h;
                 const bool active = qr[h] != 0xFFFFFFFFu;
-                const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(active ? qr[h] : 0u) * a.d_pad);
-                for (int kb = 0; kb < kblocks; ++kb)
-                    for (int c = 0; c < chunks; ++c) {
-                        const uint4 v = active ? src[kb * chunks + c] : make_uint4(0, 0, 0, 0);
-                        *reinterpret_cast<uint4*>(dstA + size_t(kb) * TC_M * row_bytes + swz_offset(r, c, row_bytes)) = v;
-                    }
                 // extra block: (1, 1, -A', -A', 0, ...) against (|x|^2 hi, lo, |x| hi, lo, 0, ...)
                 uint4 e0 = make_uint4(0, 0, 0, 0);
                 if (active) {
@@ -384,6 +392,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 qc[ab][r] = c;
                 qidx[ab][r] = qr[h];
             }
+            // this thread's copies have landed; make them and the stores above
+            // visible to the tensor core (async proxy)
+            cp_async_wait_all();
             fence_proxy_async_smem();
             mbar_arrive(&afull[ab]);
             mbar_arrive(&iq_empty[slot]);
