@@ -243,7 +243,7 @@ def run_profile(args):
         print(json.dumps({"profile_run": True, "workload": "serving", "ms_per_step": float(np.mean(times))}))
         return
     if args.workload.startswith("serve"):
-        i = {"serve64": 1, "serve128": 2}[args.workload]
+        i = {"serve32": 0, "serve64": 1, "serve128": 2}[args.workload]
         name, X, Y, Lk, m = serve_specs(0)[i]
         Xd = torch.from_numpy(X).to(dev)
         if m:
@@ -1057,7 +1057,7 @@ def main():
                     help="skip the Gaussian build+search step and the descriptor (k = 10) block")
     ap.add_argument("--profile", action="store_true", help="only warm-up + timed steps (for ncu captures)")
     ap.add_argument("--path", default="auto", choices=["auto", "plain", "batched", "bf16", "fp16"])
-    ap.add_argument("--workload", default="gauss32", choices=["gauss32", "desc128", "serve64", "serve128", "serving"],
+    ap.add_argument("--workload", default="gauss32", choices=["gauss32", "desc128", "serve32", "serve64", "serve128", "serving"],
                     help="workload of --profile runs")
     ap.add_argument("--rosanna-plus", action="store_true",
                     help="ROSANNA+ vs the one-basis search and the PCA front-end (search times at recall 0.9)")

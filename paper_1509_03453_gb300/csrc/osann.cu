@@ -413,7 +413,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
-    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, probesT, yrot, vcl, ptab;
+    size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, yrot, vcl, ptab;
     size_t total;
     int64_t max_items;
 };
@@ -534,7 +534,6 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         w.items = take(size_t(mi > 0 ? mi : 1) * 16);
         w.counters = take(256);
         w.hbuf = take(size_t(wl_hist_entries(ix->NC, n, ix->num_sms)) * 4 + 4);
-        w.probesT = take(size_t(n) * 4);
         w.scan_temp = take(batched_scan_temp_bytes(ix->NC, n, ix->num_sms));
     }
     if (tc_mode(mode)) {
@@ -1161,7 +1160,7 @@ size_t osann_search_workspace_size(const osann_index* ix, int64_t Q, int32_t P, 
 // per query (its Mv nearest clusters with ROSANNA+, else 1); the probe list
 // of query q is rows q * Mv .. q * Mv + Mv - 1 in turn (Mv * P_per slots).
 static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t P_per, int Mv, const WsLayout& L,
-                       char* w, bool init_partial, bool transposed, int k, cudaStream_t st)
+                       char* w, bool init_partial, int k, cudaStream_t st)
 {
     int rc = 0;
     const int64_t Qv = Q * Mv;
@@ -1206,7 +1205,6 @@ static int query_front(const osann_index* ix, const float* Y, int64_t Q, int64_t
     return launch_probes(reinterpret_cast<uint8_t*>(w + L.qorder), reinterpret_cast<uint32_t*>(w + L.qsign), Qv, ix->dk,
                          ix->L, P_per, ix->binom, reinterpret_cast<uint32_t*>(w + L.ptab),
                          reinterpret_cast<uint32_t*>(w + L.probes),
-                         transposed ? reinterpret_cast<uint32_t*>(w + L.probesT) : nullptr,
                          init_partial ? reinterpret_cast<uint64_t*>(w + L.partial) : nullptr, k, st, pm);
 }
 
@@ -1233,7 +1231,7 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, d_queries, Q, P_eff, 1, L, w, false, false, 1, st);
+    int rc = query_front(ix, d_queries, Q, P_eff, 1, L, w, false, 1, st);
     if (!rc) {
         cudaError_t e = cudaMemcpyAsync(d_probes, w + L.probes, size_t(Q) * P_eff * 4, cudaMemcpyDeviceToDevice, st);
         if (e != cudaSuccess) rc = cuda_fail(e, "osann_probes");
@@ -1303,7 +1301,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         return OSANN_ERR_INVALID;
     }
     char* w = static_cast<char*>(d_ws);
-    int rc = query_front(ix, Y, Q, P_per, Mv, L, w, mode == MODE_BATCHED, batched, k, fst);
+    int rc = query_front(ix, Y, Q, P_per, Mv, L, w, mode == MODE_BATCHED, k, fst);
     if (front.st) {
         // join (also after an error, so that the side stream's work stays ordered before the caller's)
         if (cudaEventRecord(front.join, front.st) != cudaSuccess || cudaStreamWaitEvent(st, front.join, 0) != cudaSuccess)
@@ -1346,7 +1344,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         }
         if (!rc) {
             StageScope s(OSANN_STAGE_WORKLIST, st);
-            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probesT), Q, P_eff, ix->offsets, ix->NC, G, b, st,
+            rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probes), Q, P_eff, ix->offsets, ix->NC, G, b, st,
                                  ix->num_sms);
         }
         if (side.st) {

@@ -87,8 +87,8 @@ struct ProbeMap {
 // tab: scratch of probe_table_bytes(P_eff) for the per-position ranks and flips
 size_t probe_table_bytes(int64_t P_eff);
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* tab, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
-                  cudaStream_t st, const ProbeMap& pm = ProbeMap{});  // probesT (p-major copy) may be null
+                  const uint64_t* binom, uint32_t* tab, uint32_t* probes, uint64_t* partial, int k, cudaStream_t st,
+                  const ProbeMap& pm = ProbeMap{});
 
 // clusters.cu (ROSANNA+): nearest M of K centroids (K x d_pad, zero padded;
 // d_pad <= 128, M <= min(K, 32)) by the canonical fp32 distance, ties to the
@@ -127,10 +127,10 @@ struct BatchedBuffers {
 };
 size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms);
 int wl_hist_entries(int64_t NC, int64_t n, int num_sms);
-// probesT: probe lists in probe-position-major order (probesT[p * Q + q]);
-// slots are still numbered q * P_eff + p, and each cone's slot list is in
-// probe-position order.  Items are in cone order.
-int launch_worklist(const uint32_t* probesT, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
+// probes: the query-major probe lists (slot q * P_eff + p = flat index);
+// each cone's slots are grouped (ascending per chunk of the list).  Items are
+// in cone order.
+int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
                     int group, BatchedBuffers& b, cudaStream_t st, int num_sms);
 int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y,
                      int d, int64_t slots_per_query, int k, const int64_t* query_src, int64_t grid_w, int radius,

@@ -187,8 +187,8 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
                                                      const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
                                                      int64_t P_eff, const uint64_t* __restrict__ binom,
                                                      const uint32_t* __restrict__ tab,
-                                                     uint32_t* __restrict__ probes, uint32_t* __restrict__ probesT,
-                                                     uint64_t* __restrict__ partial, int k, const ProbeMap pm)
+                                                     uint32_t* __restrict__ probes, uint64_t* __restrict__ partial,
+                                                     int k, const ProbeMap pm)
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
     if (LC > 0) L = LC;
@@ -258,10 +258,6 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
     // slot of this position in its query's list: query q / M, position
     // (q % M) * P_eff + p; its flat index is t either way
     probes[t] = cone;
-    if (probesT) {
-        const int64_t qr = q / pm.M, Qr = Q / pm.M;
-        probesT[(t - qr * pm.M * P_eff) * Qr + qr] = cone;  // probe-position-major copy
-    }
     if (partial)
         for (int j = 0; j < k; ++j) partial[t * k + j] = EMPTY_DI;
 }
@@ -269,8 +265,8 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
 size_t probe_table_bytes(int64_t P_eff) { return size_t(P_eff > 0 ? P_eff : 1) * PROBE_TAB_WORDS * 4; }
 
 int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d, int L, int64_t P_eff,
-                  const uint64_t* binom, uint32_t* tab, uint32_t* probes, uint32_t* probesT, uint64_t* partial, int k,
-                  cudaStream_t st, const ProbeMap& pm)
+                  const uint64_t* binom, uint32_t* tab, uint32_t* probes, uint64_t* partial, int k, cudaStream_t st,
+                  const ProbeMap& pm)
 {
     const int64_t n = Q * P_eff;
     if (n == 0) return 0;
@@ -299,7 +295,7 @@ int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d
     }
     const unsigned g = unsigned((n + 255) / 256);
 #define OSANN_PROBES(LC, W) \
-    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, tab, probes, probesT, partial, k, pm)
+    probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, tab, probes, partial, k, pm)
     if (pm.htab) {
         OSANN_PROBES(0, true);
         return count_launch();

@@ -7,7 +7,8 @@
 //   work list  (all on device, no host round trip, graph-capturable):
 //     qcount[c]  = number of queries that probe non-empty cone c
 //     qoff       = exclusive scan of qcount
-//     qlist      = the (query, probe position) slots grouped by cone
+//     qlist      = the (query, probe position) slots q * P + p grouped by cone
+//                  (ascending inside a cone's run of each block's chunk)
 //     items      = (cone, group) pairs, group = up to G consecutive slots of
 //                  the cone's list; G = 128 / TPR queries per CTA
 //   tile scan  (persistent CTAs, atomic work counter):
@@ -49,20 +50,13 @@ __global__ void wl_count_global_kernel(const uint32_t* __restrict__ probes, int6
     }
 }
 
-// slot number q * P + p of position t = p * Q + q of the probe-major array
-__device__ __forceinline__ uint32_t slot_of(uint32_t t, uint32_t Q, uint32_t P)
-{
-    const uint32_t p = t / Q;
-    return (t - p * Q) * P + p;
-}
-
 __global__ void wl_fill_kernel(const uint32_t* __restrict__ probes, int64_t n, const uint32_t* __restrict__ offsets,
                                uint32_t NC, const uint32_t* __restrict__ qoff, uint32_t* __restrict__ fill,
-                               uint32_t* __restrict__ qlist, uint32_t Q, uint32_t P)
+                               uint32_t* __restrict__ qlist)
 {
     for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < n; t += int64_t(gridDim.x) * blockDim.x) {
         const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, NC)) qlist[qoff[b] + atomicAdd(&fill[b], 1u)] = slot_of(uint32_t(t), Q, P);
+        if (cone_nonempty(offsets, b, NC)) qlist[qoff[b] + atomicAdd(&fill[b], 1u)] = uint32_t(t);
     }
 }
 
@@ -85,18 +79,35 @@ __global__ void __launch_bounds__(512) wl_block_hist_kernel(const uint32_t* __re
     for (int c = threadIdx.x; c < NC; c += blockDim.x) H[int64_t(c) * gridDim.x + blockIdx.x] = h[c];
 }
 
+// Also writes the item descriptors (first row, end row, first slot, slot
+// count) of the cones c = blockIdx.x + j * gridDim.x, from the per-cone
+// counts, first slots and item offsets of wl_cones_kernel.
 __global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __restrict__ probes, int64_t n,
                                                             int64_t chunk, const uint32_t* __restrict__ offsets,
                                                             int NC, const uint32_t* __restrict__ Hs,
-                                                            uint32_t* __restrict__ qlist, uint32_t Q, uint32_t P)
+                                                            uint32_t* __restrict__ qlist,
+                                                            const uint32_t* __restrict__ qcount,
+                                                            const uint32_t* __restrict__ qoff,
+                                                            const uint32_t* __restrict__ item_off, int G,
+                                                            uint4* __restrict__ items)
 {
     extern __shared__ uint32_t cur[];
     for (int c = threadIdx.x; c < NC; c += blockDim.x) cur[c] = Hs[int64_t(c) * gridDim.x + blockIdx.x];
+    // this block's share of the item descriptors: one warp per cone
+    for (int c = int(blockIdx.x) + int(gridDim.x) * int(threadIdx.x >> 5); c < NC;
+         c += int(gridDim.x) * int(blockDim.x >> 5)) {
+        const uint32_t cnt = qcount[c], o = item_off[c], ni = (cnt + uint32_t(G) - 1) / uint32_t(G);
+        const uint32_t r0 = offsets[c], r1 = offsets[c + 1], q0 = qoff[c];
+        for (uint32_t g = threadIdx.x & 31; g < ni; g += 32) {
+            const uint32_t rest = cnt - g * uint32_t(G);
+            items[o + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
+        }
+    }
     __syncthreads();
     const int64_t t0 = int64_t(blockIdx.x) * chunk, t1 = t0 + chunk < n ? t0 + chunk : n;
     for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
         const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = slot_of(uint32_t(t), Q, P);
+        if (cone_nonempty(offsets, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = uint32_t(t);
     }
 }
 
@@ -128,14 +139,14 @@ __global__ void wl_items_kernel(const uint32_t* __restrict__ nitems, const uint3
 
 // One CTA over all cones (N_C <= 12288, at most 12 per thread): per-cone
 // counts and first slots from the scanned per-block histograms, the number of
-// items of each cone, their exclusive scan and the item descriptors, in one
-// launch.  item_off[N_C] receives the total.
+// items of each cone and their exclusive scan, in one launch (the many-block
+// fill kernel then writes the item descriptors).  item_off[N_C] receives the
+// total.
 constexpr int WL_CONES_THREADS = 1024;
 
 __global__ void __launch_bounds__(WL_CONES_THREADS) wl_cones_kernel(
-    const uint32_t* __restrict__ Hs, int NC, int64_t nb, const uint32_t* __restrict__ offsets, int G,
-    uint32_t* __restrict__ qcount, uint32_t* __restrict__ qoff, uint32_t* __restrict__ item_off,
-    uint4* __restrict__ items, uint32_t* __restrict__ counters)
+    const uint32_t* __restrict__ Hs, int NC, int64_t nb, int G, uint32_t* __restrict__ qcount,
+    uint32_t* __restrict__ qoff, uint32_t* __restrict__ item_off, uint32_t* __restrict__ counters)
 {
     __shared__ uint32_t wsum[WL_CONES_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -169,14 +180,8 @@ __global__ void __launch_bounds__(WL_CONES_THREADS) wl_cones_kernel(
     __syncthreads();
     uint32_t off = wsum[warp] + incl - mine;
     for (int c = c0; c < c1; ++c) {
-        const uint32_t cnt = qcount[c], n = (cnt + uint32_t(G) - 1) / uint32_t(G);
         item_off[c] = off;
-        const uint32_t r0 = offsets[c], r1 = offsets[c + 1], q0 = qoff[c];
-        for (uint32_t g = 0; g < n; ++g) {
-            const uint32_t rest = cnt - g * uint32_t(G);
-            items[off + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
-        }
-        off += n;
+        off += (qcount[c] + uint32_t(G) - 1) / uint32_t(G);
     }
     if (tid == WL_CONES_THREADS - 1) item_off[NC] = off;
     if (tid == 0) counters[0] = 0;  // work counter of the scan that follows
@@ -219,11 +224,12 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         wl_block_hist_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf);
         if ((rc = count_launch())) return rc;
         if ((rc = launch_exclusive_scan(b.hbuf, b.hbuf, hn, b.scan_temp, st))) return rc;
-        wl_cones_kernel<<<1, WL_CONES_THREADS, 0, st>>>(b.hbuf, int(NC), nb, offsets, group, b.qcount, b.qoff,
-                                                          b.item_off, b.items, b.counters);
+        wl_cones_kernel<<<1, WL_CONES_THREADS, 0, st>>>(b.hbuf, int(NC), nb, group, b.qcount, b.qoff, b.item_off,
+                                                          b.counters);
         if ((rc = count_launch())) return rc;
         wl_block_fill_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf,
-                                                                         b.qlist, uint32_t(Q), uint32_t(P_eff));
+                                                                         b.qlist, b.qcount, b.qoff, b.item_off,
+                                                                         group, b.items);
         return count_launch();
     } else {
         cudaMemsetAsync(b.qcount, 0, size_t(NC + 1) * 4, st);
@@ -234,8 +240,7 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         wl_count_global_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qcount);
         if ((rc = count_launch())) return rc;
         if ((rc = launch_exclusive_scan(b.qcount, b.qoff, NC + 1, b.scan_temp, st))) return rc;
-        wl_fill_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qoff, b.fill, b.qlist,
-                                                      uint32_t(Q), uint32_t(P_eff));
+        wl_fill_kernel<<<unsigned(bl), 256, 0, st>>>(probes, n, offsets, uint32_t(NC), b.qoff, b.fill, b.qlist);
         if ((rc = count_launch())) return rc;
     }
     wl_nitems_kernel<<<unsigned(cb), 256, 0, st>>>(b.qcount, NC, group, b.nitems);

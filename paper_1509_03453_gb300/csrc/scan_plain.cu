@@ -159,9 +159,11 @@ __global__ void __launch_bounds__(PLAIN_THREADS) plain_scan_kernel(
     int64_t nq = Q;
     if (qlist) nq = qlist[0] < uint64_t(Q) ? int64_t(qlist[0]) : Q;
     auto query_of = [=](int64_t qi) -> int64_t { return qlist ? int64_t(qlist[1 + qi]) : qi; };
-    // a wait that gives up when another role has dropped out, or its budget runs out
+    // a wait that gives up when another role has dropped out, or its budget
+    // runs out (a shortened budget skips the first try_wait, which may suspend
+    // the thread until the phase completes)
     auto wait = [&](uint64_t* bar, uint32_t parity) -> bool {
-        if (mbar_try_wait(bar, parity)) return true;
+        if (wait_budget >= WAIT_BUDGET_CYCLES && mbar_try_wait(bar, parity)) return true;
         if (abort_sh) return false;
         if (mbar_wait_bounded(bar, parity, wait_budget)) return true;
         atomicOr(status, ST_TIMEOUT);

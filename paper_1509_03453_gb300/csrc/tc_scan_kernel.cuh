@@ -126,6 +126,9 @@ constexpr int TC_IQ = 4;
 constexpr int TC_SBUF = 8;  // survivors buffered per thread before a flush
 constexpr int TC_NA_MAX = 4;
 constexpr int TC_STAGES_MAX = 8;
+// TMEM accumulators of TC_N columns per CTA (two CTAs share an SM's 512
+// columns; a CTA alone on its SM with four was measured slower)
+constexpr uint32_t TC_NACC = 2;
 
 // per-query constants of a query tile, written by the loaders
 struct TcQConst {
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t iq_full[TC_IQ], iq_empty[TC_IQ];
     __shared__ __align__(8) uint64_t bfull[TC_STAGES_MAX], bempty[TC_STAGES_MAX];
-    __shared__ __align__(8) uint64_t afull[TC_NA_MAX], aempty[TC_NA_MAX], accfull[2], accempty[2];
+    __shared__ __align__(8) uint64_t afull[TC_NA_MAX], aempty[TC_NA_MAX], accfull[TC_NACC], accempty[TC_NACC];
     __shared__ TcItem iq[TC_IQ];
     __shared__ TcQConst qc[TC_NA_MAX][TC_M];
     __shared__ uint32_t qidx[TC_NA_MAX][TC_M];  // query index, 0xFFFFFFFF for an unused row
@@ -167,6 +170,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     const int extA = TC_M * 32, extB = TC_N * 32;  // extra K block: 16 bf16 per row
     const int S = a.stages;
     const uint32_t NA = uint32_t(a.abufs);
+    constexpr uint32_t NACC = TC_NACC;
     unsigned char* sA = base;                              // NA x (mainA + extA)
     unsigned char* sB = base + NA * size_t(mainA + extA);  // S x (mainB + extB)
     const uint32_t idesc = idesc_f16_f32(TC_M, TC_N, PREC == 0 ? 1u : 0u);
@@ -177,7 +181,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     constexpr bool FAST = KMAX == 1 && !EXCL;
 
     if (warp == 1) {
-        tmem_alloc(&tmem_base_sh, 2 * TC_N);
+        tmem_alloc(&tmem_base_sh, uint32_t(NACC) * TC_N);
         tmem_relinquish();
     }
     if (tid == 0) {
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             mbar_init(&afull[b], 64);
             mbar_init(&aempty[b], 4);  // one arrival per screening warp
         }
-        for (int b = 0; b < 2; ++b) {
+        for (uint32_t b = 0; b < NACC; ++b) {
             mbar_init(&accfull[b], 1);
             mbar_init(&accempty[b], 4);
         }
@@ -297,9 +301,9 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 const uint64_t da = da0 + ab * a_step, dax = dax0 + ab * a_step;
                 bool ok = true;
                 for (int t = 0; t < ntiles; ++t, ++tc) {
-                    const uint32_t acc = tc & 1u;
+                    const uint32_t acc = tc % NACC;
                     if (!wait(&bfull[s], s_ph)) { ok = false; break; }
-                    if (tc >= 2 && !wait(&accempty[acc], ((tc >> 1) - 1) & 1u)) { ok = false; break; }
+                    if (tc >= NACC && !wait(&accempty[acc], ((tc / NACC) - 1) & 1u)) { ok = false; break; }
                     tc_fence_after();
                     const uint64_t db = db0 + s * b_step, dbx = dbx0 + s * b_step;
                     const uint32_t dt = tmem + acc * TC_N;
@@ -323,7 +327,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                     ab_ph ^= 1u;
                 }
             }
-            if (abort_sh && tc > 0) mbar_wait_bounded(&accfull[(tc - 1) & 1u], ((tc - 1) >> 1) & 1u);
+            if (abort_sh && tc > 0) mbar_wait_bounded(&accfull[(tc - 1) % NACC], ((tc - 1) / NACC) & 1u);
         }
     } else if (warp < 4) {
         // ------------------------------------------------ query tile loaders
@@ -483,8 +487,8 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             };
             bool ok = true;
             for (int t = 0; t < ntiles; ++t, ++tc) {
-                const int acc = int(tc & 1u);
-                if (!wait(&accfull[acc], (tc >> 1) & 1u)) { ok = false; break; }
+                const int acc = int(tc % NACC);
+                if (!wait(&accfull[acc], (tc / NACC) & 1u)) { ok = false; break; }
                 tc_fence_after();
                 const int y0 = int(dc.r0) + t * TC_N;
                 const int nvalid = min(TC_N, int(dc.r1) - y0);
@@ -574,7 +578,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, 2 * TC_N);
+    if (warp == 1) tmem_dealloc(tmem, uint32_t(NACC) * TC_N);
 }
 
 inline size_t tc_smem_bytes(int d_pad)
