@@ -113,6 +113,9 @@ def _worker_drop(rank, world, port, X, Y, L, P, k, out):
         out.put("no error")
     except Exception as exc:  # the peer's loss surfaces as an error on the collective
         out.put("error: " + type(exc).__name__)
+    # flush the queue's feeder thread before leaving without the group's teardown
+    out.close()
+    out.join_thread()
     os._exit(0)
 
 
