@@ -772,6 +772,7 @@ def gauss32_step(args, dev, peaks, peak_src):
         if i >= 3:
             times.append(a.elapsed_time(b))
     rec = recall1(out_ids.cpu().numpy(), out_d2.cpu().numpy(), gt_ids, gt_d2)
+    err = max_rel_err_fp64(X, Y[:1000], out_ids[:1000].cpu().numpy(), out_d2[:1000].cpu().numpy())
     del graph
     # stage times of the same step, eager, with the library's stage events
     osann.stats(enable=True, reset=True)
@@ -832,7 +833,8 @@ def gauss32_step(args, dev, peaks, peak_src):
            "value": round(G32_Q / (ms / 1e3), 1), "unit": "queries/s", "ms_per_step": round(ms, 4),
            "step": "index rebuilt in place + search of the Q queries, one osann_rebuild_search call replayed as a "
                    "CUDA graph, L2 flushed before each step",
-           "recall_at_1": round(rec, 4), "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+           "recall_at_1": round(rec, 4), "max_rel_err_fp64": float(f"{err:.3g}"),
+           "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
            "plain_fp32_search_ms": round(float(np.median(plain_t)), 3),
            "multi_basis": multi}
     if tc:
