@@ -17,12 +17,14 @@ constexpr int TC_SEED_ILP = 8;  // row groups loaded per iteration
 
 // Rows scanned exactly for a query's initial bound.  A large batch keeps
 // tightening its bounds as items finish, so a short seed suffices (64 rows
-// at 10^4 queries); in a small batch every item runs at once on the first
-// bound, which must then be tighter (up to 1024 rows, a few cones): about
-// 2^16 * 10 / Q rows, clamped.
+// from 4096 queries up; measured on 4096-query batches of d = 64 and 128,
+// 64 rows halve this kernel's time and cost the screen and rerank less than
+// that); in a small batch every item runs at once on the first bound, which
+// must then be tighter (up to 1024 rows, a few cones): about 2^18 / Q rows,
+// clamped.
 static int tc_seed_rows(int64_t Q)
 {
-    const int64_t r = Q > 0 ? (int64_t(655360) + Q - 1) / Q : 1024;
+    const int64_t r = Q > 0 ? (int64_t(262144) + Q - 1) / Q : 1024;
     return int(r < 64 ? 64 : (r > 1024 ? 1024 : r));
 }
 

@@ -69,9 +69,12 @@ __device__ __forceinline__ uint32_t pack16(uint16_t lo, uint16_t hi) { return ui
 __host__ __device__ inline int tc_row_bytes(int d_pad) { return d_pad >= 64 ? 128 : d_pad * 2; }
 __host__ __device__ inline int tc_kblocks(int d_pad) { return d_pad >= 64 ? d_pad / 64 : 1; }
 // tile stages and query buffers per CTA: two CTAs per SM (each with its own
-// MMA issuer) while the shared memory allows, else one
-__host__ inline int tc_stages(int d_pad) { return d_pad <= 16 ? 6 : (d_pad == 32 ? 4 : (d_pad == 64 ? 2 : 3)); }
-__host__ inline int tc_abufs(int d_pad) { return d_pad <= 16 ? 4 : (d_pad == 32 ? 3 : 2); }
+// MMA issuer) while the shared memory allows, else one.  Two query buffers
+// suffice (a third measured no faster at d = 32); the shared memory they
+// leave buys a third cone-tile stage at d = 64 (6% faster on 4096-query
+// batches), the stage ring being what the producer waits on.
+__host__ inline int tc_stages(int d_pad) { return d_pad <= 16 ? 6 : (d_pad == 32 ? 4 : 3); }
+__host__ inline int tc_abufs(int) { return 2; }
 // (both within TC_STAGES_MAX and TC_NA_MAX, the sizes of the kernel's barrier arrays)
 
 struct TcArgs {
@@ -124,7 +127,7 @@ struct TcItem {
 constexpr int TC_ROLE_THREADS = 256;
 constexpr int TC_IQ = 4;
 constexpr int TC_SBUF = 8;  // survivors buffered per thread before a flush
-constexpr int TC_NA_MAX = 4;
+constexpr int TC_NA_MAX = 2;
 constexpr int TC_STAGES_MAX = 8;
 // TMEM accumulators of TC_N columns per CTA (two CTAs share an SM's 512
 // columns; a CTA alone on its SM with four was measured slower)
@@ -331,8 +334,12 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         }
     } else if (warp < 4) {
         // ------------------------------------------------ query tile loaders
-        const int lt = tid - 64;  // 0..63, rows lt and lt + 64
-        const int chunks = row_bytes / 16;
+        // warp 2 gathers query rows 0..63 of the tile, warp 3 rows 64..127;
+        // lane l holds the indices and constants of rows rb + l and rb + 32 + l
+        const int rb = 64 * (warp - 2);
+        const int cpr = a.d_pad / 8;  // 16-byte chunks per 16-bit query row (2, 4, 8 or 16)
+        const int cpr_sh = __ffs(cpr) - 1;
+        const int chunks_sh = __ffs(row_bytes / 16) - 1;  // chunks per row of one K block of the tile
         for (uint32_t it = 0;; ++it) {
             const int slot = int(it % TC_IQ);
             if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
@@ -341,28 +348,30 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             const uint32_t ab = it % NA;
             if (it >= NA && !wait(&aempty[ab], ((it / NA) - 1) & 1u)) break;
             unsigned char* dstA = sA + size_t(ab) * (mainA + extA);
-            // both rows' query indices; then their 16-bit rows as asynchronous
-            // 16-byte copies straight into the swizzled tile (every chunk in
-            // flight at once), and, while those land, both rows' constants
+            // both rows' query indices; then the warp's 64 16-bit rows as
+            // asynchronous 16-byte copies straight into the swizzled tile, every
+            // chunk in flight at once, consecutive lanes on consecutive chunks of
+            // one row (each instruction reads whole 32-byte sectors); while those
+            // land, both rows' constants
             uint32_t qr[2];
             float4 qs[2];
             float Ur[2];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int r = lt + 64 * h;
-                qr[h] = uint32_t(r) < d.qn ? uint32_t(int64_t(a.qlist[d.qbeg + r]) / a.S) : 0xFFFFFFFFu;
+                const int r = rb + lane + 32 * h;
+                qr[h] = uint32_t(r) < d.qn ? a.qlist[d.qbeg + r] / uint32_t(a.S) : 0xFFFFFFFFu;
             }
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int r = lt + 64 * h;
-                const bool active = qr[h] != 0xFFFFFFFFu;
-                const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(active ? qr[h] : 0u) * a.d_pad);
-                for (int kb = 0; kb < kblocks; ++kb)
-                    for (int c = 0; c < chunks; ++c) {
-                        unsigned char* dst = dstA + size_t(kb) * TC_M * row_bytes + swz_offset(r, c, row_bytes);
-                        if (active) cp_async16(dst, src + kb * chunks + c);
-                        else *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
-                    }
+            for (int j = 0; j < 2 * cpr; ++j) {
+                const int i = lane + 32 * j;  // chunk of the warp's rows
+                const int rl = i >> cpr_sh, ch = i & (cpr - 1);
+                // rl < 32 for all lanes or for none: the source register is uniform
+                const uint32_t qs_src = __shfl_sync(0xffffffffu, j < cpr ? qr[0] : qr[1], rl & 31);
+                unsigned char* dst = dstA + size_t(ch >> chunks_sh) * TC_M * row_bytes +
+                                     swz_offset(rb + rl, ch & ((1 << chunks_sh) - 1), row_bytes);
+                if (qs_src != 0xFFFFFFFFu)
+                    cp_async16(dst, reinterpret_cast<const uint4*>(a.Y16 + int64_t(qs_src) * a.d_pad) + ch);
+                else
+                    *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -375,7 +384,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int r = lt + 64 * h;
+                const int r = rb + lane + 32 * h;
                 const bool active = qr[h] != 0xFFFFFFFFu;
                 // extra block: (1, 1, -A', -A', 0, ...) against (|x|^2 hi, lo, |x| hi, lo, 0, ...)
                 uint4 e0 = make_uint4(0, 0, 0, 0);
