@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(OUT_DIR, "libosann.so")
 SOURCES = ["osann.cu", "keys.cu", "buckets.cu", "probes.cu", "scan_plain.cu", "scan_batched.cu",
-           "static_search.cu", "tc_scan.cu", "tc_scan_debug.cu", "server.cu",
+           "static_search.cu", "tc_scan.cu", "tc_scan_debug.cu", "tc_scan_tmem.cu", "server.cu",
            "shard_merge.cu", "cone_table.cu", "clusters.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 

@@ -99,6 +99,20 @@ __device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t adesc, uin
         : "memory");
 }
 
+// D[tmem] (+)= A[tmem] * B[smem]^T, issued by one thread.  A occupies M = 128
+// lanes (row m in lane m) and K / 2 consecutive 32-bit columns from `a_tmem`,
+// elements 2j and 2j + 1 of a row packed (low, high) in column j.
+__device__ __forceinline__ void mma_f16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 // Arrive once on `bar` when all previously issued MMAs of this thread finish.
 __device__ __forceinline__ void mma_commit(uint64_t* bar)
 {
@@ -182,6 +196,36 @@ __device__ __forceinline__ void tmem_ld32x2_min(uint32_t taddr, float (&v)[64], 
 #pragma unroll
     for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+// Warp-collective stores to this warp's 32 TMEM lanes (thread i writes lane
+// 32 * (warp % 4) + i): 64 or 8 consecutive 32-bit columns from `taddr`.
+// tmem_wait_st() waits for this thread's stores.
+__device__ __forceinline__ void tmem_st64(uint32_t taddr, const uint4 (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x64.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32, "
+        "%33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47, %48, "
+        "%49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63, %64};"
+        ::"r"(taddr),
+          "r"(v[0].x), "r"(v[0].y), "r"(v[0].z), "r"(v[0].w), "r"(v[1].x), "r"(v[1].y), "r"(v[1].z), "r"(v[1].w),
+          "r"(v[2].x), "r"(v[2].y), "r"(v[2].z), "r"(v[2].w), "r"(v[3].x), "r"(v[3].y), "r"(v[3].z), "r"(v[3].w),
+          "r"(v[4].x), "r"(v[4].y), "r"(v[4].z), "r"(v[4].w), "r"(v[5].x), "r"(v[5].y), "r"(v[5].z), "r"(v[5].w),
+          "r"(v[6].x), "r"(v[6].y), "r"(v[6].z), "r"(v[6].w), "r"(v[7].x), "r"(v[7].y), "r"(v[7].z), "r"(v[7].w),
+          "r"(v[8].x), "r"(v[8].y), "r"(v[8].z), "r"(v[8].w), "r"(v[9].x), "r"(v[9].y), "r"(v[9].z), "r"(v[9].w),
+          "r"(v[10].x), "r"(v[10].y), "r"(v[10].z), "r"(v[10].w), "r"(v[11].x), "r"(v[11].y), "r"(v[11].z), "r"(v[11].w),
+          "r"(v[12].x), "r"(v[12].y), "r"(v[12].z), "r"(v[12].w), "r"(v[13].x), "r"(v[13].y), "r"(v[13].z), "r"(v[13].w),
+          "r"(v[14].x), "r"(v[14].y), "r"(v[14].z), "r"(v[14].w), "r"(v[15].x), "r"(v[15].y), "r"(v[15].z), "r"(v[15].w)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint4& a, const uint4& b)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+                 "r"(a.x), "r"(a.y), "r"(a.z), "r"(a.w), "r"(b.x), "r"(b.y), "r"(b.z), "r"(b.w)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // ---------------------------------------------------------------- TMA
 

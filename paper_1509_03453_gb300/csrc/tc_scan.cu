@@ -435,6 +435,11 @@ int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float
     a.Bn = Bn;
     a.cabs = cabs;
     const bool excl = query_src != nullptr;
+    if (d_pad == 128 && !excl) {
+        // one CTA per SM with the query tiles in TMEM and five cone-tile stages
+        a.stages = tc_stages_at(d_pad);
+        return launch_tc_scan_tmem(maps, a, k, prec, debug != 0, st, num_sms);
+    }
     if (debug) return launch_tc_scan_debug(maps, a, k, prec, excl, st, num_sms);
 #define OSANN_TC(KM)                                                                                 \
     do {                                                                                             \

@@ -124,7 +124,15 @@ struct TcItem {
 // full/empty), so the MMA of one tile overlaps the screening of the previous
 // one and the query loads overlap both.  Every wait is bounded; a timeout
 // sets ST_TIMEOUT and makes all roles drop out.
+//
+// AT (query tiles in tensor memory; one CTA per SM, 384 threads): the query
+// tile of an item is written into TMEM next to the two accumulators (lane m =
+// query row m, 16-bit elements packed two per column) by warps 8-11, one
+// thread per query row, and every MMA takes A from there.  The MMAs then read
+// only the cone tiles from shared memory, and the shared memory of the query
+// tiles holds more cone-tile stages.  Warps 2-3 idle.
 constexpr int TC_ROLE_THREADS = 256;
+constexpr int TC_AT_THREADS = 384;
 constexpr int TC_IQ = 4;
 constexpr int TC_SBUF = 8;  // survivors buffered per thread before a flush
 constexpr int TC_NA_MAX = 2;
@@ -145,8 +153,8 @@ struct TcQConst {
 
 // DEBUG: check every screened value against an fp32 evaluation of the
 // folded product (a separate instantiation, so the check costs nothing when off)
-template <int KMAX, bool EXCL, int PREC, bool DEBUG>
-__global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
+template <int KMAX, bool EXCL, int PREC, bool DEBUG, bool AT>
+__global__ void __launch_bounds__(AT ? TC_AT_THREADS : TC_ROLE_THREADS, AT ? 1 : 2)
     tc_scan_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_x,
                    const TcArgs a)
 {
@@ -174,8 +182,11 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     const int S = a.stages;
     const uint32_t NA = uint32_t(a.abufs);
     constexpr uint32_t NACC = TC_NACC;
-    unsigned char* sA = base;                              // NA x (mainA + extA)
-    unsigned char* sB = base + NA * size_t(mainA + extA);  // S x (mainB + extB)
+    unsigned char* sA = base;                                       // NA x (mainA + extA); none with AT
+    unsigned char* sB = AT ? base : base + NA * size_t(mainA + extA);  // S x (mainB + extB)
+    // AT: TMEM columns of a query tile (d_pad / 2 packed pairs, then the 8 of the extra block)
+    const uint32_t acols = uint32_t(a.d_pad / 2 + 8);
+    constexpr uint32_t TMEM_COLS = AT ? 512u : NACC * TC_N;
     const uint32_t idesc = idesc_f16_f32(TC_M, TC_N, PREC == 0 ? 1u : 0u);
     const uint32_t tx_bytes = uint32_t(mainB + extB);
     const float sc = a.tcs[0], sc2 = a.tcs[1], inv_sc2 = a.tcs[2], xmax = a.tcs[3];
@@ -184,20 +195,21 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
     constexpr bool FAST = KMAX == 1 && !EXCL;
 
     if (warp == 1) {
-        tmem_alloc(&tmem_base_sh, uint32_t(NACC) * TC_N);
+        tmem_alloc(&tmem_base_sh, TMEM_COLS);
         tmem_relinquish();
     }
     if (tid == 0) {
         for (int i = 0; i < TC_IQ; ++i) {
             mbar_init(&iq_full[i], 1);
-            mbar_init(&iq_empty[i], 1 + 64 + 4);  // MMA issuer, 64 loader threads, 4 screening warps
+            // MMA issuer, 64 loader threads (4 loader warps with AT), 4 screening warps
+            mbar_init(&iq_empty[i], AT ? 1 + 4 + 4 : 1 + 64 + 4);
         }
         for (int s = 0; s < S; ++s) {
             mbar_init(&bfull[s], 1);
             mbar_init(&bempty[s], 1);
         }
         for (uint32_t b = 0; b < NA; ++b) {
-            mbar_init(&afull[b], 64);
+            mbar_init(&afull[b], AT ? 4 : 64);
             mbar_init(&aempty[b], 4);  // one arrival per screening warp
         }
         for (uint32_t b = 0; b < NACC; ++b) {
@@ -219,6 +231,17 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
         if (!abort_sh) atomicOr(a.status, ST_TIMEOUT);
         abort_sh = 1;
         return false;
+    };
+    // per-query constants of a query row from its statistics and bound
+    auto make_qc = [&](const float4& qsv, float Uv) -> TcQConst {
+        TcQConst c;
+        c.qn2 = qsv.x;
+        c.U = Uv;
+        c.Cq = qsv.w;
+        c.Uthr = sc2 * Uv - (1.0f - a.Bn) * qsv.x + qsv.w;
+        c.Aq1 = -qsv.z;
+        c.Uoff = (1.0f + a.Bn) * qsv.x + 2.0f * a.Bn * sc2 * xmax * xmax + 2.0f * c.Aq1 * sc * xmax + qsv.w;
+        return c;
     };
 
     if (warp == 0) {
@@ -302,6 +325,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 if (!wait(&afull[ab], ab_ph)) break;
                 const int ntiles = int((d.r1 - d.r0 + TC_N - 1) / TC_N);
                 const uint64_t da = da0 + ab * a_step, dax = dax0 + ab * a_step;
+                const uint32_t ta = tmem + NACC * TC_N + ab * acols;  // AT: the query tile's columns
                 bool ok = true;
                 for (int t = 0; t < ntiles; ++t, ++tc) {
                     const uint32_t acc = tc % NACC;
@@ -310,11 +334,18 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                     tc_fence_after();
                     const uint64_t db = db0 + s * b_step, dbx = dbx0 + s * b_step;
                     const uint32_t dt = tmem + acc * TC_N;
+                    if (AT) {
 #pragma unroll
-                    for (int kk = 0; kk < 8; ++kk)
-                        if (kk < ksteps) mma_bf16_ss(dt, da + koff[kk], db + koff[kk], idesc, kk > 0 ? 1u : 0u);
-                    // extra K block: |x|^2 and |x| terms folded into the product
-                    mma_bf16_ss(dt, dax, dbx, idesc, 1u);
+                        for (int kk = 0; kk < 8; ++kk)
+                            if (kk < ksteps) mma_f16_ts(dt, ta + uint32_t(kk) * 8u, db + koff[kk], idesc, kk > 0 ? 1u : 0u);
+                        mma_f16_ts(dt, ta + uint32_t(a.d_pad / 2), dbx, idesc, 1u);
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk)
+                            if (kk < ksteps) mma_bf16_ss(dt, da + koff[kk], db + koff[kk], idesc, kk > 0 ? 1u : 0u);
+                        // extra K block: |x|^2 and |x| terms folded into the product
+                        mma_bf16_ss(dt, dax, dbx, idesc, 1u);
+                    }
                     mma_commit(&bempty[s]);
                     mma_commit(&accfull[acc]);
                     if (++s == uint32_t(S)) {
@@ -332,7 +363,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             }
             if (abort_sh && tc > 0) mbar_wait_bounded(&accfull[(tc - 1) % NACC], ((tc - 1) / NACC) & 1u);
         }
-    } else if (warp < 4) {
+    } else if (!AT && warp < 4) {
         // ------------------------------------------------ query tile loaders
         // warp 2 gathers query rows 0..63 of the tile, warp 3 rows 64..127;
         // lane l holds the indices and constants of rows rb + l and rb + 32 + l
@@ -395,14 +426,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 }
                 *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 0, 32)) = e0;
                 *reinterpret_cast<uint4*>(dstA + mainA + swz_offset(r, 1, 32)) = make_uint4(0, 0, 0, 0);
-                TcQConst c;
-                c.qn2 = qs[h].x;
-                c.U = Ur[h];
-                c.Cq = qs[h].w;
-                c.Uthr = sc2 * Ur[h] - (1.0f - a.Bn) * qs[h].x + qs[h].w;
-                c.Aq1 = -qs[h].z;
-                c.Uoff = (1.0f + a.Bn) * qs[h].x + 2.0f * a.Bn * sc2 * xmax * xmax + 2.0f * c.Aq1 * sc * xmax + qs[h].w;
-                qc[ab][r] = c;
+                qc[ab][r] = make_qc(qs[h], Ur[h]);
                 qidx[ab][r] = qr[h];
             }
             // this thread's copies have landed; make them and the stores above
@@ -412,7 +436,7 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
             mbar_arrive(&afull[ab]);
             mbar_arrive(&iq_empty[slot]);
         }
-    } else {
+    } else if (warp >= 4 && warp < 8) {
         // ------------------------------------------------ screening
         const int er = 32 * (warp & 3) + lane;  // query row of the group = TMEM lane
         const uint32_t tl = tmem + (uint32_t(32 * (warp & 3)) << 16);
@@ -584,41 +608,96 @@ __global__ void __launch_bounds__(TC_ROLE_THREADS, 2)
                 mbar_arrive(&iq_empty[slot]);
             }
         }
+    } else if (AT && warp >= 8) {
+        // ------------------------------------------------ query tiles into TMEM (AT, d_pad = 128)
+        const int r = 32 * (warp & 3) + lane;  // query row of the tile = TMEM lane
+        const uint32_t tl = tmem + (uint32_t(32 * (warp & 3)) << 16);
+        const int cpr = a.d_pad / 8;  // 16-byte chunks of a 16-bit query row (16)
+        for (uint32_t it = 0;; ++it) {
+            const int slot = int(it % TC_IQ);
+            if (!wait(&iq_full[slot], (it / TC_IQ) & 1u)) break;
+            const TcItem d = iq[slot];
+            if (d.r0 == 0xFFFFFFFFu) break;
+            const uint32_t ab = it % NA;
+            if (it >= NA && !wait(&aempty[ab], ((it / NA) - 1) & 1u)) break;
+            // the MMAs that read this buffer's columns have completed
+            tc_fence_after();
+            const uint32_t qr = uint32_t(r) < d.qn ? a.qlist[d.qbeg + r] / uint32_t(a.S) : 0xFFFFFFFFu;
+            const bool active = qr != 0xFFFFFFFFu;
+            const uint4* src = reinterpret_cast<const uint4*>(a.Y16 + int64_t(active ? qr : 0u) * a.d_pad);
+            uint4 row[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) row[c] = active && c < cpr ? __ldg(src + c) : make_uint4(0, 0, 0, 0);
+            float4 qs = make_float4(0.f, 0.f, 0.f, 0.f);
+            float Ur = INFINITY;
+            uint4 e0 = make_uint4(0, 0, 0, 0);
+            if (active) {
+                qs = a.qstat[qr];
+                Ur = __uint_as_float(a.Ubits[qr]);
+                // extra block: (1, 1, -A', -A', 0, ...) against (|x|^2 hi, lo, |x| hi, lo, 0, ...)
+                const uint16_t one = to16_rn<PREC>(1.0f), na = to16_rn<PREC>(qs.z);  // exact
+                e0.x = pack16(one, one);
+                e0.y = pack16(na, na);
+            }
+            qc[ab][r] = make_qc(qs, Ur);
+            qidx[ab][r] = qr;
+            const uint32_t tcol = tl + NACC * TC_N + ab * acols;
+            tmem_st64(tcol, row);
+            tmem_st8(tcol + uint32_t(a.d_pad / 2), e0, make_uint4(0, 0, 0, 0));
+            // the tile's columns are written; order them before the MMAs
+            tmem_wait_st();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&afull[ab]);
+                mbar_arrive(&iq_empty[slot]);
+            }
+        }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, uint32_t(NACC) * TC_N);
+    if (warp == 1) tmem_dealloc(tmem, TMEM_COLS);
 }
 
-inline size_t tc_smem_bytes(int d_pad)
+// AT: cone-tile stages in the shared memory the query tiles leave (d_pad = 128:
+// five of 36 KB)
+__host__ inline int tc_stages_at(int d_pad) { return d_pad == 128 ? 5 : tc_stages(d_pad); }
+
+inline size_t tc_smem_bytes(int d_pad, bool at)
 {
     const size_t tileA = size_t(TC_M) * d_pad * 2 + TC_M * 32, tileB = size_t(TC_N) * d_pad * 2 + TC_N * 32;
+    if (at) return 1024 + size_t(tc_stages_at(d_pad)) * tileB;
     const size_t need = 1024 + size_t(tc_abufs(d_pad)) * tileA + size_t(tc_stages(d_pad)) * tileB;
     // at least 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM
     return need < 80u * 1024u ? 80u * 1024u : need;
 }
 
-template <int KMAX, bool EXCL, int PREC, bool DEBUG>
+template <int KMAX, bool EXCL, int PREC, bool DEBUG, bool AT = false>
 static int launch_tc_t(const void* maps, const TcArgs& a, cudaStream_t st, int num_sms)
 {
-    const size_t smem = tc_smem_bytes(a.d_pad);
-    auto kern = tc_scan_kernel<KMAX, EXCL, PREC, DEBUG>;
+    const size_t smem = tc_smem_bytes(a.d_pad, AT);
+    auto kern = tc_scan_kernel<KMAX, EXCL, PREC, DEBUG, AT>;
+    constexpr int threads = AT ? TC_AT_THREADS : TC_ROLE_THREADS;
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     // resident CTAs per SM: registers, shared memory (228 KB per SM, 1 KB
-    // reserved per CTA) and TMEM (512 columns, 256 per CTA)
+    // reserved per CTA) and TMEM (512 columns: 256 per CTA, all of them with AT)
     cudaFuncAttributes fa{};
     cudaFuncGetAttributes(&fa, kern);
     const int regs = fa.numRegs > 0 ? fa.numRegs : 255;
-    const int by_regs = 65536 / (regs * TC_ROLE_THREADS);
+    const int by_regs = 65536 / (regs * threads);
     const int by_smem = int((228u * 1024u) / (smem + 1024u + size_t(fa.sharedSizeBytes)));
     int occ = by_regs < by_smem ? by_regs : by_smem;
-    if (occ > 2) occ = 2;
+    if (occ > (AT ? 1 : 2)) occ = AT ? 1 : 2;
     if (occ < 1) occ = 1;
     cudaGetLastError();
     const CUtensorMap* m = static_cast<const CUtensorMap*>(maps);
-    kern<<<unsigned(num_sms * occ), TC_ROLE_THREADS, smem, st>>>(m[0], m[1], a);
+    kern<<<unsigned(num_sms * occ), threads, smem, st>>>(m[0], m[1], a);
     return count_launch();
 }
+
+// tc_scan_tmem.cu: the launches with the query tiles in TMEM (d_pad = 128,
+// no exclusion), bound check on or off
+int launch_tc_scan_tmem(const void* maps, const TcArgs& a, int k, int prec, bool debug, cudaStream_t st, int num_sms);
 
 // tc_scan_debug.cu: the same launch with the bound check compiled in
 int launch_tc_scan_debug(const void* maps, const TcArgs& a, int k, int prec, bool excl, cudaStream_t st, int num_sms);
