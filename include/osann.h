@@ -310,8 +310,10 @@ int osann_build_search(const float *d_data, int64_t N, int32_t d, int32_t L, con
  * proven error bound before the same fp32 evaluation.
  * d_queries: Q x d fp32.  d_ids: Q x k int64 (point ids, -1 pad).
  * d_sqdists: Q x k fp32 (+inf pad).  d_ws/ws_bytes: workspace of at least
- * osann_search_workspace_size(...) bytes, 256-byte aligned (NULL: allocated
- * and released in stream order).  1 <= k <= 32, P >= 1, Q >= 0.
+ * osann_search_workspace_size(...) bytes, 256-byte aligned (else
+ * OSANN_ERR_INVALID, before anything runs; NULL: allocated and released in
+ * stream order).  The same holds for every other call taking d_ws.
+ * 1 <= k <= 32, P >= 1, Q >= 0.
  * Asynchronous.  Non-finite queries set OSANN_STATUS_NONFINITE_QUERY (see
  * osann_status); their results are unspecified but in range. */
 int osann_search(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k, int32_t path,

@@ -1226,6 +1226,9 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
             set_error("osann_probes: workspace allocation failed");
             return OSANN_ERR_OOM;
         }
+    } else if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) {
+        set_error("osann_probes: workspace must be 256-byte aligned");
+        return OSANN_ERR_INVALID;
     } else if (ws_bytes < L.total) {
         set_error("osann_probes: workspace too small (%zu < %zu)", ws_bytes, L.total);
         return OSANN_ERR_INVALID;
@@ -1296,6 +1299,9 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
             set_error("osann_search: workspace allocation failed (%zu bytes)", L.total);
             return OSANN_ERR_OOM;
         }
+    } else if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) {
+        set_error("osann_search: workspace must be 256-byte aligned");
+        return OSANN_ERR_INVALID;
     } else if (ws_bytes < L.total) {
         set_error("osann_search: workspace too small (%zu < %zu)", ws_bytes, L.total);
         return OSANN_ERR_INVALID;
@@ -1547,6 +1553,9 @@ int osann_bruteforce(const osann_index* ix, const float* d_queries, const int64_
             set_error("osann_bruteforce: workspace allocation failed");
             return OSANN_ERR_OOM;
         }
+    } else if (reinterpret_cast<uintptr_t>(d_ws) % 256 != 0) {
+        set_error("osann_bruteforce: workspace must be 256-byte aligned");
+        return OSANN_ERR_INVALID;
     } else if (ws_bytes < need) {
         set_error("osann_bruteforce: workspace too small (%zu < %zu)", ws_bytes, need);
         return OSANN_ERR_INVALID;

@@ -25,9 +25,27 @@ __device__ __forceinline__ uint64_t C(const uint64_t* __restrict__ binom, int n,
     return __ldg(binom + n * (MAX_L + 1) + k);
 }
 
+// C(n, k) for k <= KM: the product formula when KM <= 4 (exact in 64 bits for
+// n <= MAX_D; no table load), the table otherwise.
+template <int KM>
+__device__ __forceinline__ uint64_t Cs(const uint64_t* __restrict__ binom, int n, int k)
+{
+    if (KM <= 0 || KM > 4) return C(binom, n, k);
+    if (n < 0 || k < 0 || k > n) return 0;
+    const uint64_t m = uint64_t(n);
+    switch (k) {
+    case 0: return 1;
+    case 1: return m;
+    case 2: return m * (m - 1) / 2;
+    case 3: return m * (m - 1) * (m - 2) / 6;
+    default: return m * (m - 1) * (m - 2) * (m - 3) / 24;
+    }
+}
+
 // Smallest r' >= r with t < C(n - r' - 1, m - 1): the next member of the
 // t-th m-subset (lexicographic) of {0..n-1} after value r - 1; t is reduced
 // by the subsets skipped.  Bounded by n - m.
+template <int KM>
 __device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, uint64_t& t, int r, int n, int m)
 {
     if (m == 1) {
@@ -38,7 +56,7 @@ __device__ __forceinline__ int next_member(const uint64_t* __restrict__ binom, u
         return r + int(step);
     }
     while (r < n - m) {
-        const uint64_t cnt = C(binom, n - r - 1, m - 1);
+        const uint64_t cnt = Cs<KM>(binom, n - r - 1, m - 1);
         if (t < cnt) break;
         t -= cnt;
         ++r;
@@ -118,19 +136,19 @@ __global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, 
     const int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (p >= P_eff) return;
     uint64_t idx = uint64_t(p);
-    const uint64_t nprof = ORD ? falling(d, L) : C(binom, d, L);
+    const uint64_t nprof = ORD ? falling(d, L) : Cs<LC>(binom, d, L);
     uint32_t flip = 0;  // bit m: flip the member at position m of the ascending-|y| member list
     if (idx >= nprof) {
         idx -= nprof;
         for (int h = 1; h <= L; ++h) {
-            const uint64_t per = C(binom, L, h);
+            const uint64_t per = Cs<LC>(binom, L, h);
             const uint64_t blk = nprof * per;
             if (idx < blk) {
                 uint64_t fs = idx % per;
                 idx /= per;
                 int r = 0;
                 for (int j = 0; j < h; ++j) {
-                    r = next_member(binom, fs, r, L, h - j);
+                    r = next_member<LC>(binom, fs, r, L, h - j);
                     flip |= 1u << r;
                     ++r;
                 }
@@ -146,7 +164,7 @@ __global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, 
         // profile class delta, then the idx-th delta-subset of the ranks after keep
         int delta = 0;
         for (; delta < L; ++delta) {
-            const uint64_t cnt = delta == 0 ? 1 : C(binom, d - L + delta - 1, delta);
+            const uint64_t cnt = delta == 0 ? 1 : Cs<LC>(binom, d - L + delta - 1, delta);
             if (idx < cnt) break;
             idx -= cnt;
         }
@@ -159,7 +177,7 @@ __global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, 
                 if (j < keep) {
                     rk[j] = j;
                 } else {
-                    r = next_member(binom, idx, r, n, L - j);
+                    r = next_member<LC>(binom, idx, r, n, L - j);
                     rk[j] = keep + 1 + r;
                     ++r;
                 }
@@ -179,9 +197,10 @@ __global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, 
 
 // LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
 // WIDE: 128-bit cone ids looked up in the second-level table (pm).
-// Q counts the rows of qorder/qsign: pm.M per query with clusters.  One
-// thread per (row, position): the position's ranks and flips from the
-// table, mapped through the row's magnitude order.
+// Q counts the rows of qorder/qsign: pm.M per query with clusters.  Block
+// (x, y) serves row x, positions y * 256 + threadIdx.x (one thread per
+// (row, position)): the position's ranks and flips from the table, mapped
+// through the row's magnitude order and signs, staged in shared memory.
 template <int LC, bool WIDE>
 __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
                                                      const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
@@ -192,12 +211,15 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
 {
     constexpr int LM = LC > 0 ? LC : MAX_L;
     if (LC > 0) L = LC;
-    const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (t >= Q * P_eff) return;
-    const int64_t q = t / P_eff;  // row of qorder/qsign
-    const int64_t posn = t - q * P_eff;  // list position
-    const uint8_t* ord = qorder + q * int64_t(d);
-    const uint32_t* sg = qsign + q * (MAX_D / 32);
+    __shared__ uint8_t ord[MAX_D];
+    __shared__ uint32_t sg[MAX_D / 32];
+    const int64_t q = blockIdx.x;  // row of qorder/qsign
+    for (int i = threadIdx.x; i < d; i += blockDim.x) ord[i] = qorder[q * int64_t(d) + i];
+    if (threadIdx.x < MAX_D / 32) sg[threadIdx.x] = qsign[q * (MAX_D / 32) + threadIdx.x];
+    __syncthreads();
+    const int64_t posn = int64_t(blockIdx.y) * blockDim.x + threadIdx.x;  // list position
+    if (posn >= P_eff) return;
+    const int64_t t = q * P_eff + posn;
     uint32_t w[PROBE_TAB_WORDS];
 #pragma unroll
     for (int i = 0; i < PROBE_TAB_WORDS; ++i)
@@ -241,7 +263,7 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
                 code |= bit << (L - 1 - j);
             } else {
                 if (WIDE) rank_w += binom_wide(pm.binom_w, cm[j], pos + 1);
-                else rank += C(binom, cm[j], pos + 1);
+                else rank += Cs<LC>(binom, cm[j], pos + 1);
                 code |= bit << (L - 1 - pos);
             }
         }
@@ -293,7 +315,8 @@ int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d
         const int rc = count_launch();
         if (rc) return rc;
     }
-    const unsigned g = unsigned((n + 255) / 256);
+    if (P_eff > int64_t(65535) * 256 || Q > int64_t(0x7FFFFFFF)) return -2;  // grid limits
+    const dim3 g(unsigned(Q), unsigned((P_eff + 255) / 256));
 #define OSANN_PROBES(LC, W) \
     probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, tab, probes, partial, k, pm)
     if (pm.htab) {

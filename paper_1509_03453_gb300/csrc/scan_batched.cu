@@ -60,21 +60,59 @@ __global__ void wl_fill_kernel(const uint32_t* __restrict__ probes, int64_t n, c
     }
 }
 
+// Shared-memory bitmap of the non-empty cones (N_C <= 12288), one ballot per
+// 32 cones of the offsets; ends with a block barrier.
+__device__ __forceinline__ void load_nonempty_bits(const uint32_t* __restrict__ offsets, int NC,
+                                                   uint32_t* __restrict__ bits)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c0 = 32 * warp; c0 < NC; c0 += 32 * nw) {
+        const int c = c0 + lane;
+        const bool ne = c < NC && __ldg(offsets + c + 1) > __ldg(offsets + c);
+        const uint32_t m = __ballot_sync(0xffffffffu, ne);
+        if (lane == 0) bits[c0 >> 5] = m;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool bit_nonempty(const uint32_t* __restrict__ bits, uint32_t b, uint32_t NC)
+{
+    return b < NC && ((bits[b >> 5] >> (b & 31)) & 1u);
+}
+
+// Calls f(t, cone) for every probe t of [t0, t1), four per thread per step
+// (t0 a multiple of 4; the probe array 16-byte aligned).
+template <typename F>
+__device__ __forceinline__ void for_chunk_probes(const uint32_t* __restrict__ probes, int64_t t0, int64_t t1, F f)
+{
+    const uint4* p4 = reinterpret_cast<const uint4*>(probes);
+    const int64_t v1 = t1 >> 2;
+    for (int64_t v = (t0 >> 2) + threadIdx.x; v < v1; v += blockDim.x) {
+        const uint4 b = p4[v];
+        f(4 * v, b.x);
+        f(4 * v + 1, b.y);
+        f(4 * v + 2, b.z);
+        f(4 * v + 3, b.w);
+    }
+    for (int64_t t = 4 * v1 + threadIdx.x; t < t1; t += blockDim.x) f(t, probes[t]);
+}
+
 // Cone-major per-block histograms: H[c * nb + b] = probes of block b's chunk
 // that hit non-empty cone c.  One exclusive scan of H (plus a trailing zero)
 // then gives every (cone, block) its first slot in the cone-major list.
+// Shared memory: N_C counters and the N_C-bit non-empty bitmap.
 __global__ void __launch_bounds__(512) wl_block_hist_kernel(const uint32_t* __restrict__ probes, int64_t n,
                                                             int64_t chunk, const uint32_t* __restrict__ offsets,
                                                             int NC, uint32_t* __restrict__ H)
 {
     extern __shared__ uint32_t h[];
+    uint32_t* bits = h + NC;
     for (int c = threadIdx.x; c < NC; c += blockDim.x) h[c] = 0;
-    __syncthreads();
+    load_nonempty_bits(offsets, NC, bits);
     const int64_t t0 = int64_t(blockIdx.x) * chunk, t1 = t0 + chunk < n ? t0 + chunk : n;
-    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-        const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, uint32_t(NC))) atomicAdd(&h[b], 1u);
-    }
+    for_chunk_probes(probes, t0, t1, [&](int64_t, uint32_t b) {
+        if (bit_nonempty(bits, b, uint32_t(NC))) atomicAdd(&h[b], 1u);
+    });
     __syncthreads();
     for (int c = threadIdx.x; c < NC; c += blockDim.x) H[int64_t(c) * gridDim.x + blockIdx.x] = h[c];
 }
@@ -92,6 +130,7 @@ __global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __re
                                                             uint4* __restrict__ items)
 {
     extern __shared__ uint32_t cur[];
+    uint32_t* bits = cur + NC;
     for (int c = threadIdx.x; c < NC; c += blockDim.x) cur[c] = Hs[int64_t(c) * gridDim.x + blockIdx.x];
     // this block's share of the item descriptors: one warp per cone
     for (int c = int(blockIdx.x) + int(gridDim.x) * int(threadIdx.x >> 5); c < NC;
@@ -103,12 +142,11 @@ __global__ void __launch_bounds__(512) wl_block_fill_kernel(const uint32_t* __re
             items[o + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
         }
     }
-    __syncthreads();
+    load_nonempty_bits(offsets, NC, bits);  // (its barrier also publishes cur)
     const int64_t t0 = int64_t(blockIdx.x) * chunk, t1 = t0 + chunk < n ? t0 + chunk : n;
-    for (int64_t t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-        const uint32_t b = probes[t];
-        if (cone_nonempty(offsets, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = uint32_t(t);
-    }
+    for_chunk_probes(probes, t0, t1, [&](int64_t t, uint32_t b) {
+        if (bit_nonempty(bits, b, uint32_t(NC))) qlist[atomicAdd(&cur[b], 1u)] = uint32_t(t);
+    });
 }
 
 __global__ void wl_nitems_kernel(const uint32_t* __restrict__ qcount, int64_t NC, int G, uint32_t* __restrict__ nitems)
@@ -143,6 +181,7 @@ __global__ void wl_items_kernel(const uint32_t* __restrict__ nitems, const uint3
 // fill kernel then writes the item descriptors).  item_off[N_C] receives the
 // total.
 constexpr int WL_CONES_THREADS = 1024;
+constexpr int WL_CONES_PER = 12;  // cones per thread: N_C <= 12 * 1024
 
 __global__ void __launch_bounds__(WL_CONES_THREADS) wl_cones_kernel(
     const uint32_t* __restrict__ Hs, int NC, int64_t nb, int G, uint32_t* __restrict__ qcount,
@@ -150,14 +189,24 @@ __global__ void __launch_bounds__(WL_CONES_THREADS) wl_cones_kernel(
 {
     __shared__ uint32_t wsum[WL_CONES_THREADS / 32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int per = (NC + WL_CONES_THREADS - 1) / WL_CONES_THREADS;
+    const int per = (NC + WL_CONES_THREADS - 1) / WL_CONES_THREADS;  // <= WL_CONES_PER
     const int c0 = tid * per < NC ? tid * per : NC, c1 = c0 + per < NC ? c0 + per : NC;
-    uint32_t mine = 0;
-    for (int c = c0; c < c1; ++c) {
-        const uint32_t o = Hs[int64_t(c) * nb], e = Hs[int64_t(c + 1) * nb];  // Hs[N_C * nb] is the total
-        qoff[c] = o;
-        qcount[c] = e - o;
-        mine += (e - o + uint32_t(G) - 1) / uint32_t(G);
+    // this thread's cone boundaries in the scanned histogram (Hs[N_C * nb] is the
+    // total), all loads in flight at once
+    uint32_t e[WL_CONES_PER + 1];
+#pragma unroll
+    for (int i = 0; i <= WL_CONES_PER; ++i) e[i] = c0 + i <= c1 ? Hs[int64_t(c0 + i) * nb] : 0u;
+    uint32_t mine = 0, ni[WL_CONES_PER];
+#pragma unroll
+    for (int i = 0; i < WL_CONES_PER; ++i) {
+        ni[i] = 0;
+        if (c0 + i < c1) {
+            const uint32_t cnt = e[i + 1] - e[i];
+            qoff[c0 + i] = e[i];
+            qcount[c0 + i] = cnt;
+            ni[i] = (cnt + uint32_t(G) - 1) / uint32_t(G);
+            mine += ni[i];
+        }
     }
     // exclusive scan of the per-thread item counts over the CTA
     uint32_t incl = mine;
@@ -179,10 +228,12 @@ __global__ void __launch_bounds__(WL_CONES_THREADS) wl_cones_kernel(
     }
     __syncthreads();
     uint32_t off = wsum[warp] + incl - mine;
-    for (int c = c0; c < c1; ++c) {
-        item_off[c] = off;
-        off += (qcount[c] + uint32_t(G) - 1) / uint32_t(G);
-    }
+#pragma unroll
+    for (int i = 0; i < WL_CONES_PER; ++i)
+        if (c0 + i < c1) {
+            item_off[c0 + i] = off;
+            off += ni[i];
+        }
     if (tid == WL_CONES_THREADS - 1) item_off[NC] = off;
     if (tid == 0) counters[0] = 0;  // work counter of the scan that follows
 }
@@ -218,16 +269,17 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         // per-block cone histograms, one scan, shared-memory cursors: no
         // contended global atomics
         const int nb = wl_blocks_impl(n, num_sms);
-        const int64_t chunk = (n + nb - 1) / nb;
+        const int64_t chunk = ((n + nb - 1) / nb + 3) & ~int64_t(3);  // a multiple of 4 (vector loads)
+        const size_t sm = (size_t(NC) + size_t(NC + 31) / 32) * 4;     // counters + non-empty bitmap
         const int64_t hn = NC * nb + 1;
         cudaMemsetAsync(b.hbuf + NC * nb, 0, 4, st);
-        wl_block_hist_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf);
+        wl_block_hist_kernel<<<unsigned(nb), 512, sm, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf);
         if ((rc = count_launch())) return rc;
         if ((rc = launch_exclusive_scan(b.hbuf, b.hbuf, hn, b.scan_temp, st))) return rc;
         wl_cones_kernel<<<1, WL_CONES_THREADS, 0, st>>>(b.hbuf, int(NC), nb, group, b.qcount, b.qoff, b.item_off,
                                                           b.counters);
         if ((rc = count_launch())) return rc;
-        wl_block_fill_kernel<<<unsigned(nb), 512, size_t(NC) * 4, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf,
+        wl_block_fill_kernel<<<unsigned(nb), 512, sm, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf,
                                                                          b.qlist, b.qcount, b.qoff, b.item_off,
                                                                          group, b.items);
         return count_launch();

@@ -177,3 +177,27 @@ def test_allocation_failures_return_oom_without_leaks(osann):
     assert idx.status() == 0
     assert_knn_match(X, Y, to_np(ids), to_np(d2), oids, od)
     idx.close()
+
+
+def test_misaligned_workspace_is_refused_before_any_launch(osann):
+    """A caller workspace must be 256-byte aligned (the vector loads and
+    16-byte asynchronous copies that read it): a misaligned one is refused
+    with OSANN_ERR_INVALID, nothing runs, and an aligned one works."""
+    import torch
+    from paper_1509_03453_gb300 import OsannError
+    X, Y = _data(N=20_000, Q=100)
+    Xd, Yd = to_dev(X), to_dev(Y)
+    idx = osann.Index(Xd, 2)
+    for path in ("plain", "batched", "fp16"):
+        need = idx.workspace_size(100, 32, 4, path)
+        raw = torch.empty(need + 512, dtype=torch.uint8, device="cuda")
+        base = (-raw.data_ptr()) % 256
+        with pytest.raises(OsannError) as e:
+            idx.search(Yd, 32, 4, path=path, workspace=raw[base + 16:base + 16 + need])
+        assert e.value.code == -1
+        ids, d2 = idx.search(Yd, 32, 4, path=path, workspace=raw[base:base + need])
+        ref = oracle.Index(X, 2)
+        oids, od = ref.search(Y, 32, 4)
+        assert_knn_match(X, Y, to_np(ids), to_np(d2), oids, od)
+    assert idx.status() == 0
+    idx.close()
