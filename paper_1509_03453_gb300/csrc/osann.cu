@@ -414,6 +414,7 @@ constexpr int TC_N_ROWS = 128;  // rows per tensor-core tile (padding of rowstat
 struct WsLayout {
     size_t qorder, qsign, probes, partial, qcount, qoff, fill, nitems, item_off, qlist, items, counters, scan_temp;
     size_t yb, qstat, ubits, scnt, surv, ovf, hbuf, yrot, vcl, ptab;
+    size_t qset;  // query sets of the tensor-core work list, or SIZE_MAX
     size_t total;
     int64_t max_items;
 };
@@ -505,6 +506,7 @@ static int item_group(const osann_index* ix, int mode, int group)
 static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k, int mode, int group = 0, int Mv = 1)
 {
     WsLayout w{};
+    w.qset = SIZE_MAX;
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -534,6 +536,8 @@ static WsLayout ws_layout(const osann_index* ix, int64_t Q, int64_t P_eff, int k
         w.items = take(size_t(mi > 0 ? mi : 1) * 16);
         w.counters = take(256);
         w.hbuf = take(size_t(wl_hist_entries(ix->NC, n, ix->num_sms)) * 4 + 4);
+        const int64_t qw = tc_mode(mode) ? wl_qset_words(ix->NC, Q) : 0;
+        w.qset = qw > 0 ? take(size_t(qw) * 4) : SIZE_MAX;
         w.scan_temp = take(batched_scan_temp_bytes(ix->NC, n, ix->num_sms));
     }
     if (tc_mode(mode)) {
@@ -1323,6 +1327,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         b.qlist = reinterpret_cast<uint32_t*>(w + L.qlist);
         b.items = reinterpret_cast<uint4*>(w + L.items);
         b.hbuf = reinterpret_cast<uint32_t*>(w + L.hbuf);
+        b.qset = L.qset != SIZE_MAX ? reinterpret_cast<uint32_t*>(w + L.qset) : nullptr;
         b.counters = reinterpret_cast<uint32_t*>(w + L.counters);
         b.n_items_dev = b.item_off + ix->NC;
         b.scan_temp = w + L.scan_temp;
@@ -1351,7 +1356,7 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
         if (!rc) {
             StageScope s(OSANN_STAGE_WORKLIST, st);
             rc = launch_worklist(reinterpret_cast<uint32_t*>(w + L.probes), Q, P_eff, ix->offsets, ix->NC, G, b, st,
-                                 ix->num_sms);
+                                 ix->num_sms, tc_mode(mode));
         }
         if (side.st) {
             // join (also after an error, so that the side stream's work stays ordered before the caller's)

@@ -124,14 +124,20 @@ struct BatchedBuffers {
     const uint32_t* n_items_dev;  // device word holding the item count (item_off + NC)
     void* scan_temp;
     int64_t max_items;
+    uint32_t* qset;       // N_C x ceil(Q / 32) query-set words (query-only lists), or null
 };
 size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms);
 int wl_hist_entries(int64_t NC, int64_t n, int num_sms);
+// Words of the query sets of a query-only work list (N_C <= 12288 and at
+// most 256 MB), else 0.
+int64_t wl_qset_words(int64_t NC, int64_t Q);
 // probes: the query-major probe lists (slot q * P_eff + p = flat index);
 // each cone's slots are grouped (ascending per chunk of the list).  Items are
-// in cone order.
+// in cone order.  query_only (the tensor-core screen, which needs only each
+// entry's query): with b.qset, the lists come from query sets, each cone's
+// entries q * P_eff in ascending query order.
 int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC,
-                    int group, BatchedBuffers& b, cudaStream_t st, int num_sms);
+                    int group, BatchedBuffers& b, cudaStream_t st, int num_sms, bool query_only = false);
 int launch_tile_scan(const float* xs, const uint32_t* offsets, const uint32_t* perm, int d_pad, const float* Y,
                      int d, int64_t slots_per_query, int k, const int64_t* query_src, int64_t grid_w, int radius,
                      const BatchedBuffers& b, int group, uint64_t* partial, uint32_t* status, cudaStream_t st,

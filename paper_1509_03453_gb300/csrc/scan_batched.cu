@@ -258,9 +258,228 @@ size_t batched_scan_temp_bytes(int64_t NC, int64_t n, int num_sms)
 }
 
 
-int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC, int group,
-                    BatchedBuffers& b, cudaStream_t st, int num_sms)
+// ---------------------------------------------------------------- query-set work list
+//
+// For the tensor-core screen only the query of a slot matters, so its lists
+// can be built from query sets instead of inverting every (query, position)
+// slot with a scattered store: B[c * W + w] (W = ceil(Q / 32)) holds, in bit
+// j, whether query 32 w + j probes non-empty cone c.  Blocks of 32 queries OR
+// their bits into shared memory; a warp per cone then counts its bits, and
+// after one scan over the cones expands them in ascending query order into
+// contiguous runs of qlist (entry q * S, so entry / S is the query).
+
+constexpr int QSET_THREADS = 256;
+constexpr int QSET_PCHUNK = 4 * QSET_THREADS;  // slots of a query per block: four per thread
+
+// Block (w, part): queries 32 w .. 32 w + 31, slots [part * QSET_PCHUNK, ...)
+// of each (S slots per query; a 16-byte load per query row and thread when
+// S % 4 == 0, eight rows in flight).  B must be zero on entry.
+__global__ void __launch_bounds__(QSET_THREADS) wl_qset_kernel(const uint32_t* __restrict__ probes, int64_t Q,
+                                                               int64_t S, const uint32_t* __restrict__ offsets,
+                                                               int NC, int64_t W, uint32_t* __restrict__ B)
 {
+    extern __shared__ uint32_t qs_words[];
+    uint32_t* bits = qs_words + NC;
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) qs_words[c] = 0;
+    load_nonempty_bits(offsets, NC, bits);
+    const int64_t q0 = int64_t(blockIdx.x) * 32;
+    const int nq = int(Q - q0 < 32 ? Q - q0 : 32);
+    // the block's slot range holds nv groups of four; with nv < blockDim the
+    // threads take several rows at once (row j0, j0 + jstep, ...)
+    const int64_t pb = int64_t(blockIdx.y) * QSET_PCHUNK, pe = pb + QSET_PCHUNK < S ? pb + QSET_PCHUNK : S;
+    const int nv = int((pe - pb + 3) / 4), jstep = int(blockDim.x) / nv;
+    const int j0 = int(threadIdx.x) / nv;
+    const int64_t p = pb + 4 * int64_t(threadIdx.x % nv);  // this thread's slots
+    auto set = [&](uint32_t c, int j) {
+        if (bit_nonempty(bits, c, uint32_t(NC))) atomicOr(&qs_words[c], 1u << j);
+    };
+    if (j0 < jstep) {
+        if ((S & 3) == 0) {
+#pragma unroll 8
+            for (int j = j0; j < nq; j += jstep) {
+                const uint4 c = *reinterpret_cast<const uint4*>(probes + (q0 + j) * S + p);
+                set(c.x, j);
+                set(c.y, j);
+                set(c.z, j);
+                set(c.w, j);
+            }
+        } else {
+            for (int j = j0; j < nq; j += jstep)
+                for (int i = 0; i < 4; ++i)
+                    if (p + i < pe) set(probes[(q0 + j) * S + p + i], j);
+        }
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+        const uint32_t m = qs_words[c];
+        if (m) atomicOr(&B[int64_t(c) * W + blockIdx.x], m);
+    }
+}
+
+// Warp per cone: qcount[c] = bits set in the cone's row.
+__global__ void wl_qset_count_kernel(const uint32_t* __restrict__ B, int NC, int64_t W, uint32_t* __restrict__ qcount)
+{
+    const int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (c >= NC) return;
+    uint32_t n = 0;
+    for (int64_t w = lane; w < W; w += 32) n += __popc(B[c * W + w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) qcount[c] = n;
+}
+
+// Exclusive scan of one value per thread over a CTA of WL_CONES_THREADS
+// threads; *total receives the sum.  wsum: WL_CONES_THREADS / 32 words.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t w = wsum[lane];
+        uint32_t wi = w;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        wsum[lane] = wi - w;
+        if (lane == 31) wsum[32] = wi;
+    }
+    __syncthreads();
+    const uint32_t r = wsum[warp] + incl - v;
+    *total = wsum[32];
+    __syncthreads();  // wsum is reused by the next scan
+    return r;
+}
+
+// One CTA over all cones (N_C <= 12288): first entries (scan of the counts)
+// and item offsets (scan of the item counts); item_off[N_C] = total items;
+// resets the screen's work counter.
+__global__ void __launch_bounds__(WL_CONES_THREADS) wl_qset_cones_kernel(const uint32_t* __restrict__ qcount, int NC,
+                                                                       int G, uint32_t* __restrict__ qoff,
+                                                                       uint32_t* __restrict__ item_off,
+                                                                       uint32_t* __restrict__ counters)
+{
+    __shared__ uint32_t wsum[WL_CONES_THREADS / 32 + 1];
+    const int tid = threadIdx.x;
+    const int per = (NC + WL_CONES_THREADS - 1) / WL_CONES_THREADS;  // <= WL_CONES_PER
+    const int c0 = tid * per < NC ? tid * per : NC, c1 = c0 + per < NC ? c0 + per : NC;
+    uint32_t cnt[WL_CONES_PER], sc = 0, si = 0;
+#pragma unroll
+    for (int i = 0; i < WL_CONES_PER; ++i) {
+        cnt[i] = c0 + i < c1 ? qcount[c0 + i] : 0u;
+        sc += cnt[i];
+        si += (cnt[i] + uint32_t(G) - 1) / uint32_t(G);
+    }
+    uint32_t tot_c, tot_i;
+    uint32_t oc = block_excl_scan(sc, wsum, &tot_c);
+    uint32_t oi = block_excl_scan(si, wsum, &tot_i);
+#pragma unroll
+    for (int i = 0; i < WL_CONES_PER; ++i)
+        if (c0 + i < c1) {
+            qoff[c0 + i] = oc;
+            item_off[c0 + i] = oi;
+            oc += cnt[i];
+            oi += (cnt[i] + uint32_t(G) - 1) / uint32_t(G);
+        }
+    if (tid == 0) {
+        item_off[NC] = tot_i;
+        counters[0] = 0;  // work counter of the scan that follows
+    }
+}
+
+constexpr int QSET_EXPAND_THREADS = 256;
+
+// Warp per cone: its query set in ascending order into qlist[qoff[c] ...]
+// (entry q * S), and its item descriptors.  Per 32 words of the set, each
+// lane writes its word's queries into the warp's shared-memory stage at their
+// ranks, then the warp copies the stage out with consecutive lanes on
+// consecutive entries.
+__global__ void __launch_bounds__(QSET_EXPAND_THREADS) wl_qset_expand_kernel(
+    const uint32_t* __restrict__ B, int NC, int64_t W, int64_t S, const uint32_t* __restrict__ offsets,
+    const uint32_t* __restrict__ qcount, const uint32_t* __restrict__ qoff, const uint32_t* __restrict__ item_off,
+    int G, uint32_t* __restrict__ qlist, uint4* __restrict__ items)
+{
+    __shared__ uint32_t stage_all[QSET_EXPAND_THREADS / 32][32 * 32];
+    const int64_t c = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    uint32_t* stage = stage_all[threadIdx.x >> 5];
+    if (c >= NC) return;
+    const uint32_t cnt = qcount[c];
+    if (cnt == 0) return;
+    uint32_t base = qoff[c];
+    for (int64_t w0 = 0; w0 < W; w0 += 32) {
+        uint32_t m = w0 + lane < W ? B[c * W + w0 + lane] : 0u;
+        const uint32_t n = __popc(m);
+        uint32_t incl = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t pos = incl - n;
+        const uint32_t qb = uint32_t(w0 + lane) * 32u;
+        while (m) {
+            const int j = __ffs(int(m)) - 1;
+            m &= m - 1u;
+            stage[pos++] = (qb + uint32_t(j)) * uint32_t(S);
+        }
+        __syncwarp();
+        for (uint32_t r = lane; r < tot; r += 32) qlist[base + r] = stage[r];
+        __syncwarp();
+        base += tot;
+    }
+    const uint32_t o = item_off[c], ni = (cnt + uint32_t(G) - 1) / uint32_t(G);
+    const uint32_t r0 = offsets[c], r1 = offsets[c + 1], q0 = qoff[c];
+    for (uint32_t g = lane; g < ni; g += 32) {
+        const uint32_t rest = cnt - g * uint32_t(G);
+        items[o + g] = make_uint4(r0, r1, q0 + g * uint32_t(G), rest < uint32_t(G) ? rest : uint32_t(G));
+    }
+}
+
+int64_t wl_qset_words(int64_t NC, int64_t Q)
+{
+    if (NC > 12288) return 0;
+    const int64_t W = (Q + 31) / 32, words = NC * W;
+    return words * 4 <= (int64_t(256) << 20) ? words : 0;  // at most 256 MB of query sets
+}
+
+static int launch_worklist_qset(const uint32_t* probes, int64_t Q, int64_t S, const uint32_t* offsets, int NC, int G,
+                                BatchedBuffers& b, cudaStream_t st, int num_sms)
+{
+    const int64_t W = (Q + 31) / 32;
+    int rc;
+    cudaMemsetAsync(b.qset, 0, size_t(NC) * size_t(W) * 4, st);
+    const int64_t parts = (S + QSET_PCHUNK - 1) / QSET_PCHUNK;
+    if (parts > 65535 || W > int64_t(0x7FFFFFFF)) return -2;  // grid limits
+    const size_t sm = (size_t(NC) + size_t(NC + 31) / 32) * 4;
+    wl_qset_kernel<<<dim3(unsigned(W), unsigned(parts)), QSET_THREADS, sm, st>>>(probes, Q, S, offsets, NC, W, b.qset);
+    if ((rc = count_launch())) return rc;
+    const unsigned wb = unsigned((int64_t(NC) * 32 + 255) / 256);
+    wl_qset_count_kernel<<<wb, 256, 0, st>>>(b.qset, NC, W, b.qcount);
+    if ((rc = count_launch())) return rc;
+    wl_qset_cones_kernel<<<1, WL_CONES_THREADS, 0, st>>>(b.qcount, NC, G, b.qoff, b.item_off, b.counters);
+    if ((rc = count_launch())) return rc;
+    const unsigned eb = unsigned((int64_t(NC) * 32 + QSET_EXPAND_THREADS - 1) / QSET_EXPAND_THREADS);
+    wl_qset_expand_kernel<<<eb, QSET_EXPAND_THREADS, 0, st>>>(b.qset, NC, W, S, offsets, b.qcount, b.qoff,
+                                                               b.item_off, G, b.qlist, b.items);
+    return count_launch();
+}
+
+int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint32_t* offsets, int64_t NC, int group,
+                    BatchedBuffers& b, cudaStream_t st, int num_sms, bool query_only)
+{
+    if (query_only && b.qset && wl_qset_words(NC, Q) > 0)
+        return launch_worklist_qset(probes, Q, P_eff, offsets, int(NC), group, b, st, num_sms);
     const int64_t n = Q * P_eff;
     int rc;
     int64_t cb = (NC + 256) / 256;
