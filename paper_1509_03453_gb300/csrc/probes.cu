@@ -25,20 +25,21 @@ __device__ __forceinline__ uint64_t C(const uint64_t* __restrict__ binom, int n,
     return __ldg(binom + n * (MAX_L + 1) + k);
 }
 
-// C(n, k) for k <= KM: the product formula when KM <= 4 (exact in 64 bits for
-// n <= MAX_D; no table load), the table otherwise.
+// C(n, k) for k <= KM: the product formula when KM <= 4 (no table load; the
+// products stay below 2^32 for n <= MAX_D = 256: 256 * 255 * 254 * 253 <
+// 2^32), the table otherwise.
 template <int KM>
 __device__ __forceinline__ uint64_t Cs(const uint64_t* __restrict__ binom, int n, int k)
 {
     if (KM <= 0 || KM > 4) return C(binom, n, k);
     if (n < 0 || k < 0 || k > n) return 0;
-    const uint64_t m = uint64_t(n);
+    const uint32_t m = uint32_t(n);
     switch (k) {
     case 0: return 1;
     case 1: return m;
-    case 2: return m * (m - 1) / 2;
-    case 3: return m * (m - 1) * (m - 2) / 6;
-    default: return m * (m - 1) * (m - 2) * (m - 3) / 24;
+    case 2: return m * (m - 1) / 2u;
+    case 3: return m * (m - 1) * (m - 2) / 6u;
+    default: return m * (m - 1) * (m - 2) * (m - 3) / 24u;
     }
 }
 
@@ -121,6 +122,7 @@ __device__ __forceinline__ void unrank_ordered(uint64_t idx, int d, int L, int (
 // Words per entry of the position table: the members' magnitude ranks as
 // bytes (MAX_L of them), then the flip mask.
 constexpr int PROBE_TAB_WORDS = MAX_L / 4 + 1;
+constexpr int PROBE_SPAN = 1024;  // list positions per block of the probe kernel
 
 // Which magnitude ranks the profile at list position p takes, and which of
 // its members are sign-flipped, depend only on (d, L, p), not on the query:
@@ -198,9 +200,10 @@ __global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, 
 // LC: L as a compile-time constant (1..4), or 0 for a runtime L <= MAX_L.
 // WIDE: 128-bit cone ids looked up in the second-level table (pm).
 // Q counts the rows of qorder/qsign: pm.M per query with clusters.  Block
-// (x, y) serves row x, positions y * 256 + threadIdx.x (one thread per
-// (row, position)): the position's ranks and flips from the table, mapped
-// through the row's magnitude order and signs, staged in shared memory.
+// (x, y) serves row x, positions y * PROBE_SPAN + threadIdx.x + 256 i (one
+// thread per (row, position), PROBE_SPAN / 256 positions per thread): the
+// position's ranks and flips from the table, mapped through the row's
+// magnitude order and signs, staged in shared memory once per block.
 template <int LC, bool WIDE>
 __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__ qorder,
                                                      const uint32_t* __restrict__ qsign, int64_t Q, int d, int L,
@@ -217,71 +220,72 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
     for (int i = threadIdx.x; i < d; i += blockDim.x) ord[i] = qorder[q * int64_t(d) + i];
     if (threadIdx.x < MAX_D / 32) sg[threadIdx.x] = qsign[q * (MAX_D / 32) + threadIdx.x];
     __syncthreads();
-    const int64_t posn = int64_t(blockIdx.y) * blockDim.x + threadIdx.x;  // list position
-    if (posn >= P_eff) return;
-    const int64_t t = q * P_eff + posn;
-    uint32_t w[PROBE_TAB_WORDS];
+    const int64_t pend = int64_t(blockIdx.y + 1) * PROBE_SPAN < P_eff ? int64_t(blockIdx.y + 1) * PROBE_SPAN : P_eff;
+    for (int64_t posn = int64_t(blockIdx.y) * PROBE_SPAN + threadIdx.x; posn < pend; posn += blockDim.x) {
+        const int64_t t = q * P_eff + posn;
+        uint32_t w[PROBE_TAB_WORDS];
 #pragma unroll
-    for (int i = 0; i < PROBE_TAB_WORDS; ++i)
-        if (i < (LM + 3) / 4 || i == PROBE_TAB_WORDS - 1) w[i] = __ldg(tab + posn * PROBE_TAB_WORDS + i);
-    const uint32_t flip = w[PROBE_TAB_WORDS - 1];
-    int rk[LM];  // member ranks (0-based positions into the query's order)
-    int cm[LM];  // member components
+        for (int i = 0; i < PROBE_TAB_WORDS; ++i)
+            if (i < (LM + 3) / 4 || i == PROBE_TAB_WORDS - 1) w[i] = __ldg(tab + posn * PROBE_TAB_WORDS + i);
+        const uint32_t flip = w[PROBE_TAB_WORDS - 1];
+        int rk[LM];  // member ranks (0-based positions into the query's order)
+        int cm[LM];  // member components
 #pragma unroll
-    for (int j = 0; j < LM; ++j)
-        if (LC > 0 || j < L) {
-            rk[j] = int((w[j >> 2] >> (8 * (j & 3))) & 0xFFu);
-            cm[j] = ord[rk[j]];
-        }
-    // cone id of the profile with the query's signs (and the chosen flips)
-    uint64_t rank = 0;
-    u128 rank_w = 0;
-    uint32_t code = 0;
-#pragma unroll
-    for (int j = 0; j < LM; ++j) {
-        if (LC > 0 || j < L) {
-            int pos = 0, asc = 0;
-#pragma unroll
-            for (int u = 0; u < LM; ++u) {
-                if (LC > 0 || u < L) {
-                    pos += cm[u] < cm[j] ? 1 : 0;  // ascending component index
-                    asc += rk[u] > rk[j] ? 1 : 0;  // ascending magnitude
-                }
+        for (int j = 0; j < LM; ++j)
+            if (LC > 0 || j < L) {
+                rk[j] = int((w[j >> 2] >> (8 * (j & 3))) & 0xFFu);
+                cm[j] = ord[rk[j]];
             }
-            uint32_t bit = (sg[cm[j] >> 5] >> (cm[j] & 31)) & 1u;
-            bit ^= (flip >> asc) & 1u;
-            if (pm.ordered) {
-                // tuple position j: c_j = cm[j] minus the earlier members below it
-                int below = 0;
-                uint64_t after = 1;
+        // cone id of the profile with the query's signs (and the chosen flips)
+        uint64_t rank = 0;
+        u128 rank_w = 0;
+        uint32_t code = 0;
+#pragma unroll
+        for (int j = 0; j < LM; ++j) {
+            if (LC > 0 || j < L) {
+                int pos = 0, asc = 0;
 #pragma unroll
                 for (int u = 0; u < LM; ++u) {
-                    if (u < j && cm[u] < cm[j]) ++below;
-                    if (u > j && (LC > 0 || u < L)) after *= uint64_t(d - u);
+                    if (LC > 0 || u < L) {
+                        pos += cm[u] < cm[j] ? 1 : 0;  // ascending component index
+                        asc += rk[u] > rk[j] ? 1 : 0;  // ascending magnitude
+                    }
                 }
-                rank += uint64_t(cm[j] - below) * after;
-                code |= bit << (L - 1 - j);
-            } else {
-                if (WIDE) rank_w += binom_wide(pm.binom_w, cm[j], pos + 1);
-                else rank += Cs<LC>(binom, cm[j], pos + 1);
-                code |= bit << (L - 1 - pos);
+                uint32_t bit = (sg[cm[j] >> 5] >> (cm[j] & 31)) & 1u;
+                bit ^= (flip >> asc) & 1u;
+                if (pm.ordered) {
+                    // tuple position j: c_j = cm[j] minus the earlier members below it
+                    int below = 0;
+                    uint64_t after = 1;
+#pragma unroll
+                    for (int u = 0; u < LM; ++u) {
+                        if (u < j && cm[u] < cm[j]) ++below;
+                        if (u > j && (LC > 0 || u < L)) after *= uint64_t(d - u);
+                    }
+                    rank += uint64_t(cm[j] - below) * after;
+                    code |= bit << (L - 1 - j);
+                } else {
+                    if (WIDE) rank_w += binom_wide(pm.binom_w, cm[j], pos + 1);
+                    else rank += Cs<LC>(binom, cm[j], pos + 1);
+                    code |= bit << (L - 1 - pos);
+                }
             }
         }
+        const uint32_t cl = pm.vcl ? pm.vcl[q] : 0u;
+        uint32_t cone;
+        if (WIDE) {
+            u128 id = (rank_w << L) | u128(code);
+            if (pm.vcl) id += u128(cl) * ((u128(pm.ncc_hi) << 64) | u128(pm.ncc_lo));
+            cone = cone_lookup(wide_words(id), pm.ukeys, pm.htab, pm.hmask, pm.sentinel);
+        } else {
+            cone = uint32_t((rank << L) | code) + cl * uint32_t(pm.ncc_lo);
+        }
+        // slot of this position in its query's list: query q / M, position
+        // (q % M) * P_eff + p; its flat index is t either way
+        probes[t] = cone;
+        if (partial)
+            for (int j = 0; j < k; ++j) partial[t * k + j] = EMPTY_DI;
     }
-    const uint32_t cl = pm.vcl ? pm.vcl[q] : 0u;
-    uint32_t cone;
-    if (WIDE) {
-        u128 id = (rank_w << L) | u128(code);
-        if (pm.vcl) id += u128(cl) * ((u128(pm.ncc_hi) << 64) | u128(pm.ncc_lo));
-        cone = cone_lookup(wide_words(id), pm.ukeys, pm.htab, pm.hmask, pm.sentinel);
-    } else {
-        cone = uint32_t((rank << L) | code) + cl * uint32_t(pm.ncc_lo);
-    }
-    // slot of this position in its query's list: query q / M, position
-    // (q % M) * P_eff + p; its flat index is t either way
-    probes[t] = cone;
-    if (partial)
-        for (int j = 0; j < k; ++j) partial[t * k + j] = EMPTY_DI;
 }
 
 size_t probe_table_bytes(int64_t P_eff) { return size_t(P_eff > 0 ? P_eff : 1) * PROBE_TAB_WORDS * 4; }
@@ -315,8 +319,8 @@ int launch_probes(const uint8_t* qorder, const uint32_t* qsign, int64_t Q, int d
         const int rc = count_launch();
         if (rc) return rc;
     }
-    if (P_eff > int64_t(65535) * 256 || Q > int64_t(0x7FFFFFFF)) return -2;  // grid limits
-    const dim3 g(unsigned(Q), unsigned((P_eff + 255) / 256));
+    if (P_eff > int64_t(65535) * PROBE_SPAN || Q > int64_t(0x7FFFFFFF)) return -2;  // grid limits
+    const dim3 g(unsigned(Q), unsigned((P_eff + PROBE_SPAN - 1) / PROBE_SPAN));
 #define OSANN_PROBES(LC, W) \
     probes_kernel<LC, W><<<g, 256, 0, st>>>(qorder, qsign, Q, d, L, P_eff, binom, tab, probes, partial, k, pm)
     if (pm.htab) {

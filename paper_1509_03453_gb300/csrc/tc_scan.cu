@@ -236,6 +236,8 @@ int launch_tc_rows(int prec, const float* xs, const float4* rowstat, int64_t N, 
 
 // ---------------------------------------------------------------- rerank
 
+constexpr int RR_U = 4;  // candidate passes with their loads in flight together
+
 // One warp per query: canonical fp32 distance of every survivor (or, after
 // an overflow, of every row of every probed cone), top-k by (distance, id).
 template <int F, int KMAX, bool EXCL>
@@ -273,11 +275,12 @@ __global__ void __launch_bounds__(128) tc_rerank_kernel(const float* __restrict_
     const int64_t src = EXCL ? query_src[q] : -1;
     uint64_t list[KMAX];
     topk_init<KMAX>(list, k);
-    auto consider = [&](uint32_t row, bool valid) {
-        const float4* xr = reinterpret_cast<const float4*>(xs + size_t(valid ? row : 0) * d_pad) + sub * F;
+    // the candidate's canonical distance from its row chunk xv (this lane's F
+    // float4 of the row), then the top-k update
+    auto consider = [&](uint32_t row, bool valid, const float4 (&xv)[F]) {
         float cpart[F];
 #pragma unroll
-        for (int f = 0; f < F; ++f) cpart[f] = sq4(xr[f], qv[f]);
+        for (int f = 0; f < F; ++f) cpart[f] = sq4(xv[f], qv[f]);
         const float dist = lane_tree(pair_tree<F>(cpart), TPR);
         if (valid && sub == 0) {
             const uint32_t id = __ldg(perm + row);
@@ -293,10 +296,26 @@ __global__ void __launch_bounds__(128) tc_rerank_kernel(const float* __restrict_
     };
     const uint32_t n = surv_cnt[q];
     if (n <= uint32_t(cap)) {
-        for (uint32_t b0 = 0; b0 < n; b0 += CPP) {
-            const uint32_t i = b0 + g;
-            const bool valid = i < n;
-            consider(valid ? surv[q * cap + i] : 0u, valid);
+        // RR_U passes at a time: their survivor ids, then their rows, are all
+        // in flight before the first distance
+        for (uint32_t b0 = 0; b0 < n; b0 += RR_U * uint32_t(CPP)) {
+            uint32_t rows[RR_U];
+            bool valid[RR_U];
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u) {
+                const uint32_t i = b0 + uint32_t(u * CPP + g);
+                valid[u] = i < n;
+                rows[u] = valid[u] ? surv[q * cap + i] : 0u;
+            }
+            float4 xv[RR_U][F];
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u) {
+                const float4* xr = reinterpret_cast<const float4*>(xs + size_t(rows[u]) * d_pad) + sub * F;
+#pragma unroll
+                for (int f = 0; f < F; ++f) xv[u][f] = xr[f];
+            }
+#pragma unroll
+            for (int u = 0; u < RR_U; ++u) consider(rows[u], valid[u], xv[u]);
         }
         if (lane == 0) atomicAdd(diag, (unsigned long long)n);
     } else {
