@@ -122,9 +122,8 @@ __device__ __forceinline__ void store_key(int64_t row, const int (&comp)[MAX_L],
 // Vector path (d % 4 == 0, 16-byte aligned rows): one lane per row.  The
 // lane streams its row in pieces of up to KC float4 (the first line fetch
 // brings the piece's cache lines into L1 for the rest of the warp's loads)
-// and keeps the L largest selection keys in a sorted register list: one
-// 32-bit magnitude compare per component, the 64-bit key and an insertion
-// only when the component can enter the list.
+// and keeps the L largest magnitudes in a sorted register list: one 32-bit
+// compare per component, an insertion only when the component can enter.
 template <int LC, bool WIDE, bool ORD>
 __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restrict__ X, int64_t N, int d, int L,
                                                            const uint64_t* __restrict__ binom,
@@ -142,12 +141,20 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
     const int64_t stride = int64_t(gridDim.x) * blockDim.x;
     for (int64_t row = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; row < N; row += stride) {
         const float4* xr = reinterpret_cast<const float4*>(X + row * int64_t(d));
-        uint64_t top[LM];  // descending; 0 = empty (a real selection key is > 0)
+        // the L largest magnitudes so far, descending, with their components and
+        // sign bits (1: x >= 0); -1 = empty.  Components arrive in increasing
+        // index order, so an incoming one never displaces an earlier one of equal
+        // magnitude (the lower component first): a strict 32-bit magnitude
+        // compare places it, and the entries after it shift down.
+        int mag[LM], cix[LM];
+        uint32_t csg[LM];
 #pragma unroll
-        for (int r = 0; r < LM; ++r) top[r] = 0;
-        // magnitude bits of the current L-th key: a component with a smaller
-        // magnitude cannot enter the list (equal ones are decided by the full key)
-        uint32_t lastmag = 0;
+        for (int r = 0; r < LM; ++r) {
+            mag[r] = -1;
+            cix[r] = 0;
+            csg[r] = 0;
+        }
+        int lastmag = -1;  // the L-th entry's magnitude: only a larger one enters
         uint32_t amax = 0;  // largest magnitude bits of the row: >= 0x7F800000 iff non-finite
         float nsq = 0.0f;
         for (int c0 = 0; c0 < n4; c0 += KC) {
@@ -161,33 +168,34 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
 #pragma unroll
                     for (int e = 0; e < 4; ++e) {
                         const float x = x4[e];
-                        const uint32_t a = __float_as_uint(x) & 0x7FFFFFFFu;
-                        amax = a > amax ? a : amax;
+                        const uint32_t au = __float_as_uint(x) & 0x7FFFFFFFu;
+                        amax = au > amax ? au : amax;
                         nsq = fmaf(x, x, nsq);
-                        if (a >= lastmag) {
-                            uint64_t k = sel_key(x, 4 * (c0 + f) + e);
-                            uint64_t last = top[LM - 1];  // the L-th (compile-time index)
+                        if (int(au) > lastmag) {
+                            // insertion: the first entry with a smaller magnitude and
+                            // every one after it move down one place
+                            int m = int(au), ci = 4 * (c0 + f) + e;
+                            uint32_t sg = x >= 0.0f ? 1u : 0u;
+                            bool placed = false;
+#pragma unroll
+                            for (int r = 0; r < LM; ++r) {
+                                if ((LC > 0 || r < L) && (placed || m > mag[r])) {
+                                    placed = true;
+                                    const int tm = mag[r], tc = cix[r];
+                                    const uint32_t ts = csg[r];
+                                    mag[r] = m;
+                                    cix[r] = ci;
+                                    csg[r] = sg;
+                                    m = tm;
+                                    ci = tc;
+                                    sg = ts;
+                                }
+                            }
+                            lastmag = mag[LM - 1];
                             if (LC == 0) {
 #pragma unroll
                                 for (int r = 0; r < LM; ++r)
-                                    if (r == L - 1) last = top[r];
-                            }
-                            if (k > last) {
-#pragma unroll
-                                for (int r = 0; r < LM; ++r) {
-                                    if (LC > 0 || r < L) {
-                                        const uint64_t hi = k > top[r] ? k : top[r];
-                                        k = k > top[r] ? top[r] : k;
-                                        top[r] = hi;
-                                    }
-                                }
-                                last = top[LM - 1];
-                                if (LC == 0) {
-#pragma unroll
-                                    for (int r = 0; r < LM; ++r)
-                                        if (r == L - 1) last = top[r];
-                                }
-                                lastmag = uint32_t(last >> 32);
+                                    if (r == L - 1) lastmag = mag[r];
                             }
                         }
                     }
@@ -205,8 +213,8 @@ __global__ void __launch_bounds__(256) data_keys_row_kernel(const float* __restr
 #pragma unroll
         for (int r = 0; r < LM; ++r)
             if (LC > 0 || r < L) {
-                comp[r] = sel_comp(top[r]);
-                sgn[r] = sel_sign(top[r]);
+                comp[r] = cix[r];
+                sgn[r] = csg[r];
             }
         store_key<LC, WIDE, ORD>(row, comp, sgn, L, d, binom, binom_w, keys, wkeys);
         nmax = fmaxf(nmax, nsq);  // non-finite rows are reported separately

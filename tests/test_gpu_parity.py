@@ -146,3 +146,22 @@ def test_bruteforce_matches_oracle(osann, name):
     gids, gd = idx.bruteforce(to_dev(Ys), k, **kw)
     oids, od = oracle.bruteforce(X, Ys, k, **okw)
     assert_knn_match(X, Ys, to_np(gids), to_np(gd), oids, od)
+
+
+@pytest.mark.parametrize("d,L", [(16, 2), (32, 3), (64, 2), (128, 3), (8, 5)])
+def test_keys_with_ties_bit_exact(osann, d, L):
+    """Vector-path keys (d % 4 == 0) on rows full of equal magnitudes, signed
+    zeros and zero rows: the L largest by magnitude, ties to the lower
+    component (Sec. 2), bit for bit with the oracle, in both key modes."""
+    rng = np.random.default_rng(100 + d + L)
+    X = np.round(rng.standard_normal((20_000, d)) * 1.5).astype(np.float32)
+    X[::9] = 0.0
+    X[1::13] = -0.0
+    X[2::17, : min(d, 6)] = 2.0
+    X[3::19] = np.where(rng.random((len(X[3::19]), d)) < 0.5, -1.0, 1.0).astype(np.float32)
+    assert np.array_equal(to_np(osann.keys(to_dev(X), L)), oracle.keys(X, L).astype(np.int64))
+    if d <= 64:
+        ref = oracle.Index(X, L, key_mode=1)
+        idx = osann.Index(to_dev(X), L, key_mode="ordered")
+        assert np.array_equal(to_np(idx.export()[0]), ref.keys.astype(np.int64))
+        idx.close()
