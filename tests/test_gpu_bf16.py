@@ -114,3 +114,29 @@ def test_fp16_out_of_range_query_takes_the_full_scan(osann):
     assert np.array_equal(to_np(a[0]), to_np(b[0]))
     assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(b[1]).view(np.uint32))
     assert idx.screen_stats()["fallbacks"] >= 1
+
+
+@pytest.mark.parametrize("Q,P", [(1, 1), (1, 7), (31, 3), (32, 64), (33, 5), (65, 130), (97, 1984), (300, 255)])
+def test_query_set_work_list_shapes(osann, Q, P):
+    """The tensor-core work list built from per-cone query sets: query counts
+    around multiples of 32 (the query-set words), slot counts not divisible
+    by 4 (the scalar loads), one query, every cone (P = N_C), and N_C = 1984
+    cones in the shared-memory words: same bits as the batched fp32 path
+    (whose list keeps the slots), parity with the oracle."""
+    rng = np.random.default_rng(7 * Q + P)
+    X = rng.standard_normal((30_011, 32)).astype(np.float32)
+    Y = rng.standard_normal((Q, 32)).astype(np.float32)
+    idx = osann.Index(to_dev(X), 2)
+    assert idx.NC == 1984
+    Yd = to_dev(Y)
+    ref = oracle.Index(X, 2)
+    for k in (1, 3):
+        a = idx.search(Yd, P, k, path="fp16")
+        b = idx.search(Yd, P, k, path="batched")
+        assert np.array_equal(to_np(a[0]), to_np(b[0]))
+        assert np.array_equal(to_np(a[1]).view(np.uint32), to_np(b[1]).view(np.uint32))
+        oids, od = ref.search(Y, P, k)
+        assert_knn_match(X, Y, to_np(a[0]), to_np(a[1]), oids, od)
+    assert idx.screen_stats()["bound_violations"] == 0
+    assert idx.status() == 0
+    idx.close()
