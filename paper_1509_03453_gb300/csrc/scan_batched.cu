@@ -446,6 +446,23 @@ __global__ void __launch_bounds__(QSET_EXPAND_THREADS) wl_qset_expand_kernel(
     }
 }
 
+// The per-cone shared-memory arrays (N_C words and the N_C-bit non-empty
+// bitmap) pass the default 48 KB of dynamic shared memory for N_C > 11904:
+// raise the limit of the kernels that hold them, once per process.
+static void wl_smem_attributes()
+{
+    static bool done[64] = {};  // per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && done[dev]) return;
+    const int lim = int((12288 + 12288 / 32) * 4);
+    cudaFuncSetAttribute(wl_block_hist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(wl_block_fill_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaFuncSetAttribute(wl_qset_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    cudaGetLastError();
+    if (dev >= 0 && dev < 64) done[dev] = true;
+}
+
 int64_t wl_qset_words(int64_t NC, int64_t Q)
 {
     if (NC > 12288) return 0;
@@ -462,6 +479,7 @@ static int launch_worklist_qset(const uint32_t* probes, int64_t Q, int64_t S, co
     const int64_t parts = (S + QSET_PCHUNK - 1) / QSET_PCHUNK;
     if (parts > 65535 || W > int64_t(0x7FFFFFFF)) return -2;  // grid limits
     const size_t sm = (size_t(NC) + size_t(NC + 31) / 32) * 4;
+    wl_smem_attributes();
     wl_qset_kernel<<<dim3(unsigned(W), unsigned(parts)), QSET_THREADS, sm, st>>>(probes, Q, S, offsets, NC, W, b.qset);
     if ((rc = count_launch())) return rc;
     const unsigned wb = unsigned((int64_t(NC) * 32 + 255) / 256);
@@ -490,6 +508,7 @@ int launch_worklist(const uint32_t* probes, int64_t Q, int64_t P_eff, const uint
         const int nb = wl_blocks_impl(n, num_sms);
         const int64_t chunk = ((n + nb - 1) / nb + 3) & ~int64_t(3);  // a multiple of 4 (vector loads)
         const size_t sm = (size_t(NC) + size_t(NC + 31) / 32) * 4;     // counters + non-empty bitmap
+        wl_smem_attributes();
         const int64_t hn = NC * nb + 1;
         cudaMemsetAsync(b.hbuf + NC * nb, 0, 4, st);
         wl_block_hist_kernel<<<unsigned(nb), 512, sm, st>>>(probes, n, chunk, offsets, int(NC), b.hbuf);

@@ -140,3 +140,26 @@ def test_query_set_work_list_shapes(osann, Q, P):
     assert idx.screen_stats()["bound_violations"] == 0
     assert idx.status() == 0
     idx.close()
+
+
+def test_work_lists_at_the_shared_memory_cone_limit(osann):
+    """N_C = C(78, 2) 4 = 12012 cones, near the 12288 that the per-cone
+    shared-memory arrays serve (their size then passes the default 48 KB of
+    dynamic shared memory): both work lists (query sets for the screen,
+    per-block histograms for the fp32 batched path) give the oracle's
+    answer."""
+    rng = np.random.default_rng(78)
+    X = rng.standard_normal((40_000, 78)).astype(np.float32)
+    Y = rng.standard_normal((150, 78)).astype(np.float32)
+    idx = osann.Index(to_dev(X), 2)
+    assert idx.NC == 12012
+    ref = oracle.Index(X, 2)
+    Yd = to_dev(Y)
+    for P in (64, 700):
+        oids, od = ref.search(Y, P, 2)
+        a = idx.search(Yd, P, 2, path="fp16")
+        b = idx.search(Yd, P, 2, path="batched")
+        assert np.array_equal(to_np(a[0]), to_np(b[0]))
+        assert_knn_match(X, Y, to_np(a[0]), to_np(a[1]), oids, od)
+    assert idx.status() == 0
+    idx.close()
