@@ -434,23 +434,23 @@ def serving_roofline(sr, peaks, peak_src):
     w = sr.mix_weights() / SERVE_MAX_BATCH  # max-size batches of each index in the trace
     per, stage_tot = [], {}
     for i, ix in enumerate(sr.idx):
-        path, group = sr.choices[i][-1]
+        path, group, layout = sr.choices[i][-1]
         q = sr.pools[i][:SERVE_MAX_BATCH]
         ws = torch.empty(ix.workspace_size(q.shape[0], sr.P[i], SERVE_K, path, group), dtype=torch.uint8,
                          device=sr.dev)
-        ix.search(q, sr.P[i], SERVE_K, path=path, group=group, workspace=ws)
+        ix.search(q, sr.P[i], SERVE_K, path=path, group=group, layout=layout, workspace=ws)
         torch.cuda.synchronize()
         osann.stats(enable=True, reset=True)
         reps = 5
         for _ in range(reps):
-            ix.search(q, sr.P[i], SERVE_K, path=path, group=group, workspace=ws)
+            ix.search(q, sr.P[i], SERVE_K, path=path, group=group, layout=layout, workspace=ws)
         torch.cuda.synchronize()
         st = osann.stats(enable=False)
         stage_ms = {k: v[0] / reps for k, v in st.items() if v[1]}
         off = ix.export()[1]
         pr = ix.probes(q, sr.P[i])
         pairs = int((off[1:] - off[:-1])[pr.long()].sum().item())
-        per.append({"index": sr.names[i], "path": path, "group": group, "pairs": pairs,
+        per.append({"index": sr.names[i], "path": path, "group": group, "layout": layout, "pairs": pairs,
                     "stage_ms_per_batch": {k: round(v, 4) for k, v in stage_ms.items()}})
         for k, v in stage_ms.items():
             stage_tot[k] = stage_tot.get(k, 0.0) + w[i] * v

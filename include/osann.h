@@ -330,6 +330,27 @@ int osann_search(const osann_index *index, const float *d_queries, int64_t Q, in
 int osann_search_group(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k,
                        int32_t path, int32_t group, void *d_ws, size_t ws_bytes, int64_t *d_ids, float *d_sqdists,
                        void *stream);
+
+/* Layout of the tensor-core screen's query tiles (a tuning knob; the paper
+ * has no counterpart).  OSANN_LAYOUT_SMEM: in shared memory beside the cone
+ * tiles.  OSANN_LAYOUT_TMEM: in tensor memory beside the accumulators, the
+ * MMAs reading only the cone tiles from shared memory (one CTA per SM with
+ * more cone-tile stages); possible for d_pad = 128 (64 < d <= 128) without an
+ * exclusion radius.  OSANN_LAYOUT_DEFAULT: the library's choice (TMEM where
+ * possible). */
+#define OSANN_LAYOUT_DEFAULT 0
+#define OSANN_LAYOUT_SMEM 1
+#define OSANN_LAYOUT_TMEM 2
+
+/* As osann_search_group, with the screen's query-tile layout chosen by the
+ * caller (OSANN_LAYOUT_*): ignored off the tensor-core paths, and
+ * OSANN_LAYOUT_TMEM takes the default where it is not possible.  Results are
+ * those of osann_search, bit for bit, whatever the layout.  The workspace is
+ * osann_search_workspace_size_group(...) bytes.  Errors as osann_search; a
+ * layout outside 0..2 is OSANN_ERR_INVALID. */
+int osann_search_layout(const osann_index *index, const float *d_queries, int64_t Q, int32_t P, int32_t k,
+                        int32_t path, int32_t group, int32_t layout, void *d_ws, size_t ws_bytes, int64_t *d_ids,
+                        float *d_sqdists, void *stream);
 size_t osann_search_workspace_size_group(const osann_index *index, int64_t Q, int32_t P, int32_t k, int32_t path,
                                          int32_t group);
 
@@ -475,17 +496,25 @@ int osann_server_progress(osann_server *server, int32_t wait, uint64_t *done, in
 /* Queries still waiting for a slot, and slots busy. */
 int osann_server_pending(const osann_server *server, int64_t *waiting_queries, int32_t *busy_slots);
 /* Autotuner: for every index and batch bucket, time each candidate (path,
- * work-list group size) -- plain; batched with the default and 32-query
- * groups; fp16 screening with 128- and 64-query groups -- on max_batch rows
- * sampled from the index itself, reps timed runs each, and keep the
- * fastest.  out_choices (nullable) receives (path, group) per (index,
- * bucket).  Call with no request in the server. */
+ * work-list group size, screen layout) -- plain; batched with the default
+ * and 32-query groups; fp16 screening with 128- and 64-query groups, and for
+ * an index with 64 < d <= 128 with 128-query groups in both query-tile
+ * layouts (OSANN_LAYOUT_SMEM, OSANN_LAYOUT_TMEM) -- on max_batch rows sampled
+ * from the index itself, reps timed runs each, and keep the fastest.
+ * out_choices (nullable) receives (path, group) per (index, bucket);
+ * osann_server_choices gives the layouts too.  Call with no request in the
+ * server. */
 int osann_server_tune(osann_server *server, int32_t reps, int32_t *out_choices);
 /* As osann_server_tune, timing each index i on the caller's sample queries
  * d_queries[i] (n_queries[i] rows, device; a NULL entry: rows of the index),
  * which tunes for the query distribution actually served. */
 int osann_server_tune_queries(osann_server *server, const float *const *d_queries, const int64_t *n_queries,
                               int32_t reps, int32_t *out_choices);
+/* The choice of every (index, bucket), index-major, as (path, group,
+ * layout) triples: up to max_out triples into out3 (OSANN_LAYOUT_DEFAULT and
+ * group 0 before tuning).  Returns the number of triples, 0 for a null
+ * server. */
+int osann_server_choices(const osann_server *server, int32_t *out3, int32_t max_out);
 /* Run every slot, index and batch bucket once (capturing the graphs when
  * they are on), so that no capture happens while serving.  Call after
  * osann_server_tune (tuning drops the graphs) with no request in flight. */

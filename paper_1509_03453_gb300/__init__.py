@@ -262,16 +262,19 @@ class Index:
         return int(load().osann_search_workspace_size_group(self._h, Q, P, k, PATHS[path], group))
 
     def search(self, queries, P: int, k: int, path: str = "auto", query_src=None, grid_w: int = 0,
-               radius: int = 0, stream=None, out=None, workspace=None, group: int = 0, clusters: int = 1):
+               radius: int = 0, stream=None, out=None, workspace=None, group: int = 0, clusters: int = 1,
+               layout: str = "default"):
         """Top-k by exact squared distance over the first min(P, N_C)
         probed cones.  Returns (ids int64 [Q,k], sqdists float32 [Q,k]).
         ``group``: queries per work-list item on the batched paths (0 =
-        default); it changes the speed, not the result.  ``clusters``
-        (ROSANNA+ index): nearest clusters visited, P cones in each."""
+        default); ``layout``: the tensor-core screen's query tiles ("smem",
+        "tmem" or "default"); both change the speed, not the result.
+        ``clusters`` (ROSANNA+ index): nearest clusters visited, P cones in
+        each."""
         torch = _torch()
         if clusters != 1:
-            if query_src is not None or group:
-                raise ValueError("clusters > 1 takes no exclusion and no group size")
+            if query_src is not None or group or layout != "default":
+                raise ValueError("clusters > 1 takes no exclusion, group size or layout")
             return self._search_clusters(queries, clusters, P, k, path, stream, out, workspace)
         q = _dev_f32(queries, "queries")
         Q = q.shape[0]
@@ -286,9 +289,11 @@ class Index:
         ws = workspace if workspace is not None else torch.empty(ws_bytes, dtype=torch.uint8, device=q.device)
         L = load()
         if query_src is None:
-            rc = L.osann_search_group(self._h, _ptr(q), Q, P, k, PATHS[path], group, _ptr(ws), ws.numel(),
-                                      _ptr(ids), _ptr(d2), _stream_ptr(stream))
+            rc = L.osann_search_layout(self._h, _ptr(q), Q, P, k, PATHS[path], group, _lib.LAYOUTS[layout],
+                                       _ptr(ws), ws.numel(), _ptr(ids), _ptr(d2), _stream_ptr(stream))
         else:
+            if layout != "default":
+                raise ValueError("the exclusion search takes the default layout")
             src = query_src.contiguous()
             rc = L.osann_search_excl(self._h, _ptr(q), _ptr(src), Q, P, k, grid_w, radius, PATHS[path],
                                      _ptr(ws), ws.numel(), _ptr(ids), _ptr(d2), _stream_ptr(stream))
@@ -480,8 +485,9 @@ class Server:
         return [int(out[i]) for i in range(n)]
 
     def tune(self, reps: int = 3, queries=None):
-        """Autotune (path, group) per (index, bucket); returns the choices.
-        queries: optional list (per index) of sample query tensors."""
+        """Autotune (path, group, layout) per (index, bucket); returns the
+        choices as (path name, group, layout name) triples per index and
+        bucket.  queries: optional list (per index) of sample query tensors."""
         nb = len(self.buckets())
         n = len(self.indexes)
         out = (ctypes.c_int32 * (2 * n * nb))()
@@ -492,9 +498,18 @@ class Server:
             ptrs = (ctypes.c_void_p * n)(*[None if q is None else q.data_ptr() for q in qs])
             cnt = (ctypes.c_int64 * n)(*[0 if q is None else q.shape[0] for q in qs])
             _lib.check(load().osann_server_tune_queries(self._h, ptrs, cnt, reps, out))
-        names = {v: k for k, v in PATHS.items()}
-        return [[(names[out[2 * (i * nb + b)]], int(out[2 * (i * nb + b) + 1])) for b in range(nb)]
-                for i in range(n)]
+        return self.choices()
+
+    def choices(self):
+        """The current (path name, group, layout name) per (index, bucket)."""
+        nb = len(self.buckets())
+        n = len(self.indexes)
+        out = (ctypes.c_int32 * (3 * n * nb))()
+        got = load().osann_server_choices(self._h, out, n * nb)
+        paths = {v: k for k, v in PATHS.items()}
+        layouts = {v: k for k, v in _lib.LAYOUTS.items()}
+        trip = [(paths[out[3 * j]], int(out[3 * j + 1]), layouts[out[3 * j + 2]]) for j in range(got)]
+        return [trip[i * nb:(i + 1) * nb] for i in range(n)]
 
     def warmup(self):
         """Capture every (slot, index, bucket) graph now rather than while serving."""

@@ -23,6 +23,7 @@ ERRORS = {
     -6: "device wait timed out",
 }
 PATHS = {"auto": 0, "plain": 1, "batched": 2, "bf16": 3, "fp16": 4}
+LAYOUTS = {"default": 0, "smem": 1, "tmem": 2}  # query tiles of the tensor-core screen
 CONE_TABLES = {"auto": 0, "dense": 1, "hashed": 2}
 
 
@@ -98,6 +99,9 @@ SIGNATURES = {
                                      c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p, c.c_void_p]),
     "osann_search_workspace_size_group": (c.c_size_t, [c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
                                                        c.c_int32]),
+    "osann_search_layout": (c.c_int, [c.c_void_p, c.c_void_p, c.c_int64, c.c_int32, c.c_int32, c.c_int32,
+                                      c.c_int32, c.c_int32, c.c_void_p, c.c_size_t, c.c_void_p, c.c_void_p,
+                                      c.c_void_p]),
     "osann_server_create": (c.c_int, [c.POINTER(c.c_void_p), c.c_int32, c.POINTER(c.c_int32),
                                       c.POINTER(c.c_int32), c.c_int32, c.c_int64, c.c_size_t, c.c_int32,
                                       c.POINTER(c.c_void_p)]),
@@ -111,6 +115,7 @@ SIGNATURES = {
     "osann_server_tune_queries": (c.c_int, [c.c_void_p, c.POINTER(c.c_void_p), c.POINTER(c.c_int64), c.c_int32,
                                             c.POINTER(c.c_int32)]),
     "osann_server_buckets": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64), c.c_int32]),
+    "osann_server_choices": (c.c_int, [c.c_void_p, c.POINTER(c.c_int32), c.c_int32]),
     "osann_server_warmup": (c.c_int, [c.c_void_p]),
     "osann_server_free": (c.c_int, [c.c_void_p]),
     "osann_server_stats": (c.c_int, [c.c_void_p, c.POINTER(c.c_int64)]),

@@ -1254,9 +1254,10 @@ int osann_probes(const osann_index* ix, const float* d_queries, int64_t Q, int32
 static int search_impl(const osann_index* ix, const float* Y, const int64_t* src, int64_t Q, int32_t P, int32_t k,
                        int64_t grid_w, int32_t radius, int32_t path, void* d_ws, size_t ws_bytes, int64_t* ids,
                        float* dists, void* stream, int32_t group = 0, int32_t M = 1,
-                       cudaEvent_t overlap_from = nullptr)
+                       cudaEvent_t overlap_from = nullptr, int32_t layout = OSANN_LAYOUT_DEFAULT)
 {
     if (!ix || Q < 0 || P < 1 || k < 1 || k > MAX_K || path < 0 || path > OSANN_PATH_FP16 || group < 0 || M < 1 ||
+        layout < OSANN_LAYOUT_DEFAULT || layout > OSANN_LAYOUT_TMEM ||
         (Q > 0 && (!Y || !ids || !dists))) {
         set_error("osann_search: invalid arguments (Q=%lld P=%d k=%d path=%d)", (long long)Q, P, k, path);
         return OSANN_ERR_INVALID;
@@ -1371,7 +1372,8 @@ static int search_impl(const osann_index* ix, const float* Y, const int64_t* src
                                     radius, b, reinterpret_cast<uint32_t*>(w + L.ubits),
                                     reinterpret_cast<uint32_t*>(w + L.scnt), reinterpret_cast<uint32_t*>(w + L.surv),
                                     TC_SURV_CAP, ix->status, ix->diag, ix->xs, Y, P_eff, ix->d, ix->d_pad, k,
-                                    ix->cdot2[prec], ix->Bn, ix->cabs[prec], debug_checks(), st, ix->num_sms);
+                                    ix->cdot2[prec], ix->Bn, ix->cabs[prec], debug_checks(), st, ix->num_sms,
+                                    layout);
             }
             if (!rc) {
                 StageScope s(OSANN_STAGE_TC_RERANK, st);
@@ -1418,6 +1420,14 @@ int osann_search_group(const osann_index* index, const float* d_queries, int64_t
                        void* stream)
 {
     return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, group);
+}
+
+int osann_search_layout(const osann_index* index, const float* d_queries, int64_t Q, int32_t P, int32_t k,
+                        int32_t path, int32_t group, int32_t layout, void* d_ws, size_t ws_bytes, int64_t* d_ids,
+                        float* d_sqdists, void* stream)
+{
+    return search_impl(index, d_queries, nullptr, Q, P, k, 0, 0, path, d_ws, ws_bytes, d_ids, d_sqdists, stream, group,
+                       1, nullptr, layout);
 }
 
 int osann_search_clusters(const osann_index* index, const float* d_queries, int64_t Q, int32_t M, int32_t P,

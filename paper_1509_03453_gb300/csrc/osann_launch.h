@@ -169,7 +169,8 @@ int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float
                    const float4* qstat, const float* tcs, const int64_t* query_src, int64_t grid_w, int radius,
                    const BatchedBuffers& b, uint32_t* Ubits, uint32_t* surv_cnt, uint32_t* surv, int cap,
                    uint32_t* status, unsigned long long* diag, const float* xs, const float* Y, int64_t S, int d,
-                   int d_pad, int k, float cdot2, float Bn, float cabs, int debug, cudaStream_t st, int num_sms);
+                   int d_pad, int k, float cdot2, float Bn, float cabs, int debug, cudaStream_t st, int num_sms,
+                   int layout = 0);
 int launch_tc_rerank(const float* xs, int d_pad, const uint32_t* perm, const uint32_t* offsets, uint32_t NC,
                      const float* Y, int d, int64_t Q, const uint32_t* probes, int64_t P_eff, const uint32_t* surv_cnt,
                      const uint32_t* surv, int cap, int k, const int64_t* query_src, int64_t grid_w, int radius,

@@ -58,6 +58,7 @@ struct Piece {
 struct Choice {
     int path = OSANN_PATH_AUTO;
     int group = 0;
+    int layout = OSANN_LAYOUT_DEFAULT;  // query tiles of the tensor-core screen
 };
 
 struct Graph {
@@ -122,25 +123,31 @@ size_t bucket_of(const osann_server* s, int64_t n)
     return b;
 }
 
-// The candidate (path, group) pairs of the tuner; the workspace of a slot
-// covers all of them.
+// The candidate (path, group, layout) choices of the tuner; the workspace of
+// a slot covers all of them.  The query-tile layout of the screen is a
+// choice only where both exist (d_pad = 128: 64 < d <= 128).
 std::vector<Choice> candidates(const osann_server* s, int i)
 {
-    (void)s;
-    (void)i;
+    int32_t d = 0;
+    osann_info(s->idx[size_t(i)], nullptr, &d, nullptr, nullptr, nullptr);
     std::vector<Choice> c;
-    c.push_back({OSANN_PATH_PLAIN, 0});
-    c.push_back({OSANN_PATH_BATCHED, 0});
-    c.push_back({OSANN_PATH_BATCHED, 32});
-    c.push_back({OSANN_PATH_FP16, 128});
-    c.push_back({OSANN_PATH_FP16, 64});
+    c.push_back({OSANN_PATH_PLAIN, 0, OSANN_LAYOUT_DEFAULT});
+    c.push_back({OSANN_PATH_BATCHED, 0, OSANN_LAYOUT_DEFAULT});
+    c.push_back({OSANN_PATH_BATCHED, 32, OSANN_LAYOUT_DEFAULT});
+    if (d > 64 && d <= 128) {
+        c.push_back({OSANN_PATH_FP16, 128, OSANN_LAYOUT_TMEM});
+        c.push_back({OSANN_PATH_FP16, 128, OSANN_LAYOUT_SMEM});
+    } else {
+        c.push_back({OSANN_PATH_FP16, 128, OSANN_LAYOUT_DEFAULT});
+    }
+    c.push_back({OSANN_PATH_FP16, 64, OSANN_LAYOUT_DEFAULT});
     return c;
 }
 
 int run_search(osann_server* s, Slot& sl, int i, int64_t n, const Choice& c)
 {
-    return osann_search_group(s->idx[i], sl.qbuf, n, s->P[i], s->k[i], c.path, c.group, sl.ws, sl.ws_bytes, sl.ibuf,
-                              sl.dbuf, sl.st);
+    return osann_search_layout(s->idx[i], sl.qbuf, n, s->P[i], s->k[i], c.path, c.group, c.layout, sl.ws, sl.ws_bytes,
+                               sl.ibuf, sl.dbuf, sl.st);
 }
 
 // One batch of `nq` queries of index i, already in the slot's query buffer.
@@ -545,6 +552,18 @@ int osann_server_warmup(osann_server* s)
     if (!rc && e != cudaSuccess) rc = cuda_err(e, "osann_server_warmup");
     cudaSetDevice(cur);
     return rc;
+}
+
+int osann_server_choices(const osann_server* s, int32_t* out3, int32_t max_out)
+{
+    if (!s || (!out3 && max_out > 0)) return 0;
+    const int32_t n = int32_t(s->choice.size());
+    for (int32_t i = 0; i < n && i < max_out; ++i) {
+        out3[3 * i] = s->choice[size_t(i)].path;
+        out3[3 * i + 1] = s->choice[size_t(i)].group;
+        out3[3 * i + 2] = s->choice[size_t(i)].layout;
+    }
+    return n;
 }
 
 int osann_server_buckets(const osann_server* s, int64_t* out, int32_t max_out)

@@ -1,6 +1,7 @@
 // Tensor-core screening path: query preparation (seed bounds, 16-bit query
 // operands), the fp16 scale and row operands, tensor maps, the screening
 // launch (kernel in tc_scan_kernel.cuh) and the exact fp32 rerank.
+#include "osann.h"
 #include "tc_scan_kernel.cuh"
 
 namespace osann {
@@ -417,7 +418,8 @@ int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float
                    const float4* qstat, const float* tcs, const int64_t* query_src, int64_t grid_w, int radius,
                    const BatchedBuffers& b, uint32_t* Ubits, uint32_t* surv_cnt, uint32_t* surv, int cap,
                    uint32_t* status, unsigned long long* diag, const float* xs, const float* Y, int64_t S, int d,
-                   int d_pad, int k, float cdot2, float Bn, float cabs, int debug, cudaStream_t st, int num_sms)
+                   int d_pad, int k, float cdot2, float Bn, float cabs, int debug, cudaStream_t st, int num_sms,
+                   int layout)
 {
     TcArgs a{};
     a.perm = perm;
@@ -454,7 +456,7 @@ int launch_tc_scan(int prec, const void* maps, const uint32_t* perm, const float
     a.Bn = Bn;
     a.cabs = cabs;
     const bool excl = query_src != nullptr;
-    if (d_pad == 128 && !excl) {
+    if (d_pad == 128 && !excl && layout != OSANN_LAYOUT_SMEM) {
         // one CTA per SM with the query tiles in TMEM and five cone-tile stages
         a.stages = tc_stages_at(d_pad);
         return launch_tc_scan_tmem(maps, a, k, prec, debug != 0, st, num_sms);

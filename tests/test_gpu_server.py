@@ -94,8 +94,10 @@ def test_tuned_mix_equals_alone(osann, setup):
     choices = srv.tune(reps=1)
     assert len(choices) == 2 and all(len(c) == len(srv.buckets()) for c in choices)
     for per_index in choices:
-        for path, group in per_index:
+        for path, group, layout in per_index:
             assert path in ("plain", "batched", "fp16")
+            assert layout in ("default", "smem", "tmem")
+    assert srv.choices() == choices
     tickets = [srv.submit(i, pools[i][off:off + q]) for (i, off, q) in reqs]
     srv.drain()
     out = {j: srv.result(t) for j, t in enumerate(tickets)}
