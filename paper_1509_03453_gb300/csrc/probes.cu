@@ -122,7 +122,7 @@ __device__ __forceinline__ void unrank_ordered(uint64_t idx, int d, int L, int (
 // Words per entry of the position table: the members' magnitude ranks as
 // bytes (MAX_L of them), then the flip mask.
 constexpr int PROBE_TAB_WORDS = MAX_L / 4 + 1;
-constexpr int PROBE_SPAN = 1024;  // list positions per block of the probe kernel
+constexpr int PROBE_SPAN = 4096;  // list positions per block of the probe kernel
 
 // Which magnitude ranks the profile at list position p takes, and which of
 // its members are sign-flipped, depend only on (d, L, p), not on the query:
@@ -201,7 +201,7 @@ __global__ void __launch_bounds__(256) probe_ranks_kernel(int64_t P_eff, int d, 
 // WIDE: 128-bit cone ids looked up in the second-level table (pm).
 // Q counts the rows of qorder/qsign: pm.M per query with clusters.  Block
 // (x, y) serves row x, positions y * PROBE_SPAN + threadIdx.x + 256 i (one
-// thread per (row, position), PROBE_SPAN / 256 positions per thread): the
+// thread per (row, position), up to PROBE_SPAN / 256 positions per thread): the
 // position's ranks and flips from the table, mapped through the row's
 // magnitude order and signs, staged in shared memory once per block.
 template <int LC, bool WIDE>
@@ -221,6 +221,7 @@ __global__ void __launch_bounds__(256) probes_kernel(const uint8_t* __restrict__
     if (threadIdx.x < MAX_D / 32) sg[threadIdx.x] = qsign[q * (MAX_D / 32) + threadIdx.x];
     __syncthreads();
     const int64_t pend = int64_t(blockIdx.y + 1) * PROBE_SPAN < P_eff ? int64_t(blockIdx.y + 1) * PROBE_SPAN : P_eff;
+#pragma unroll 4
     for (int64_t posn = int64_t(blockIdx.y) * PROBE_SPAN + threadIdx.x; posn < pend; posn += blockDim.x) {
         const int64_t t = q * P_eff + posn;
         uint32_t w[PROBE_TAB_WORDS];
