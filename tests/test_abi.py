@@ -89,3 +89,18 @@ def test_host_only_argument_checks_of_the_newer_entry_points(L):
     # 128-bit keys: bad sizes are rejected before any device work
     assert L.osann_keys_wide(None, 1, 0, 2, None, None) == -1
     assert L.osann_keys_wide(None, 1, 300, 2, None, None) == -1
+
+
+def test_host_only_checks_of_the_layout_knob(L):
+    c = ctypes
+    # no index, or a layout outside OSANN_LAYOUT_DEFAULT..OSANN_LAYOUT_TMEM: refused on the host
+    assert L.osann_search_layout(None, None, 1, 1, 1, 0, 0, 0, None, 0, None, None, None) == -1
+    assert L.osann_search_layout(None, None, 1, 1, 1, 0, 0, 3, None, 0, None, None, None) == -1
+    # the header's layout constants are the binding's
+    text = open(HEADER).read()
+    for name, v in (("OSANN_LAYOUT_DEFAULT", 0), ("OSANN_LAYOUT_SMEM", 1), ("OSANN_LAYOUT_TMEM", 2)):
+        assert re.search(r"#define\s+%s\s+%d\b" % (name, v), text)
+    assert _lib.LAYOUTS == {"default": 0, "smem": 1, "tmem": 2}
+    # the tuner's choices of no server: none
+    out = (c.c_int32 * 3)()
+    assert L.osann_server_choices(None, out, 1) == 0
