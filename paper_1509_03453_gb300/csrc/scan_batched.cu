@@ -330,7 +330,8 @@ __global__ void wl_qset_count_kernel(const uint32_t* __restrict__ B, int NC, int
 }
 
 // Exclusive scan of one value per thread over a CTA of WL_CONES_THREADS
-// threads; *total receives the sum.  wsum: WL_CONES_THREADS / 32 words.
+// threads; *total receives the sum.  wsum: WL_CONES_THREADS / 32 + 1 words
+// (the warps' offsets, then the total).
 __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t* wsum, uint32_t* total)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
